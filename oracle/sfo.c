@@ -1,0 +1,824 @@
+/*
+ * sfo.c -- FP64 single-threaded CPU oracle of the halfway-domain scene-flow
+ * solve of Thies et al., "Real-time Halfway Domain Reconstruction of Motion
+ * and Geometry" (arXiv 1610.07159).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the parity judge for the CUDA
+ * library: it is called by the tests, by the package's smoke check and by the
+ * benchmark's CPU-baseline leg, and by nothing on the product path. It shares
+ * no code, header, table or constant generator with the CUDA path.
+ *
+ * It is written for a reader who checks it against the paper by eye: plain
+ * loops, one step after another in the paper's order, no blocking, no fusion,
+ * every accumulation in double precision.
+ *
+ * Conventions (the paper's notation, Section 3):
+ *   images   imgs[c] for c = 0: I_0^0 (left, t0), 1: I_1^0 (right, t0),
+ *            2: I_0^1 (left, t1), 3: I_1^1 (right, t1); row-major w*h.
+ *   planes   per level and image: 3 planes (I, dI/dx, dI/dy), layout
+ *            planes[((img*3 + plane)*h + y)*w + x].
+ *   fields   per node 6 unknowns (s_x, s_y, m_x, m_y, d_x, d_y), stored
+ *            component-major: F[comp*G + j*nx + i], G = nx*ny.
+ *   system   block form A[n][q][r][c] (n node, q = 3*(dy+1) + (dx+1) the
+ *            neighbour slot, 6x6 row-major block), b[n*6 + r].
+ *
+ * Readings where the paper is silent or ambiguous are marked [Cn] and match
+ * the list of readings in the design notes.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define SFO_MAX_LEVELS 8
+#define SFO_MAX_GN 16
+#define SFO_STATS_LEN (16 + SFO_MAX_LEVELS * SFO_MAX_GN * 8)
+
+enum { SFO_IRLS = 0, SFO_SQRT_PAPER = 1 };
+enum { SFO_GRAD_BROX = 0, SFO_GRAD_LITERAL = 1 };
+enum { SFO_WFEAT_EIG = 0, SFO_WFEAT_OFF = 1 };
+enum { SFO_TEMPORAL_PROPAGATE = 0, SFO_TEMPORAL_COPY = 1, SFO_TEMPORAL_ZERO = 2 };
+
+typedef struct sfo_params {
+    /* Table 1 (Appendix A) */
+    double w_reg, w_photo, w_grad, w_epi, w_smooth, w_mag;
+    double w_s, w_m, w_d, m_s, m_m, m_d;
+    double eps;   /* pseudo-Huber epsilon, Eq. 12 */
+    double eps_p; /* outlier threshold of W, Section 4.1; <= 0 disables W */
+    double F[9];  /* fundamental matrix, finest-level pixels, row-major */
+    int gn_iters[SFO_MAX_LEVELS];  /* per level, index 0 = finest */
+    int pcg_iters[SFO_MAX_LEVELS];
+    int robust_mode, grad_mode, wfeat_mode;
+    double wfeat_gain, wfeat_tau;
+    int temporal_mode, max_backtracks;
+} sfo_params;
+
+/* Sign of stereo, motion and difference flow in each image's sample position
+ * (Eqs. 1-6): image 0 at x-s-m+d, 1 at x+s-m-d, 2 at x-s+m-d, 3 at x+s+m+d. */
+static const double SIGN[4][3] = {
+    {-1.0, -1.0, +1.0},
+    {+1.0, -1.0, -1.0},
+    {-1.0, +1.0, -1.0},
+    {+1.0, +1.0, +1.0},
+};
+/* The six consistency checks d_k = I_first(p_first) - I_second(p_second),
+ * Eqs. 1-6 in order. */
+static const int CHECK[6][2] = {{1, 0}, {3, 2}, {2, 0}, {3, 1}, {3, 0}, {2, 1}};
+
+/* ------------------------------------------------------------------------ */
+/* Image hierarchy (Section 5.3: mip-map pyramid, factor 2) [C5, C6]         */
+/* ------------------------------------------------------------------------ */
+
+void sfo_level_dims(int w0, int h0, int level, int* w, int* h)
+{
+    int a = w0, b = h0;
+    for (int l = 0; l < level; ++l) {
+        a = (a + 1) / 2;
+        b = (b + 1) / 2;
+    }
+    *w = a;
+    *h = b;
+}
+
+/* One mip-map step: 2x2 box average, ceil(w/2) x ceil(h/2), edge clamped. */
+void sfo_downsample(int w, int h, const double* src, double* dst)
+{
+    int w2 = (w + 1) / 2, h2 = (h + 1) / 2;
+    for (int y = 0; y < h2; ++y)
+        for (int x = 0; x < w2; ++x) {
+            double acc = 0.0;
+            for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a) {
+                    int xx = 2 * x + a, yy = 2 * y + b;
+                    if (xx > w - 1) xx = w - 1;
+                    if (yy > h - 1) yy = h - 1;
+                    acc += src[yy * w + xx];
+                }
+            dst[y * w2 + x] = 0.25 * acc;
+        }
+}
+
+/* Central differences with edge clamping. */
+void sfo_gradients(int w, int h, const double* img, double* gx, double* gy)
+{
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            int xm = x > 0 ? x - 1 : 0, xp = x < w - 1 ? x + 1 : w - 1;
+            int ym = y > 0 ? y - 1 : 0, yp = y < h - 1 ? y + 1 : h - 1;
+            gx[y * w + x] = 0.5 * (img[y * w + xp] - img[y * w + xm]);
+            gy[y * w + x] = 0.5 * (img[yp * w + x] - img[ym * w + x]);
+        }
+}
+
+/* Builds the planes (I, Gx, Gy) of the four images at one level from that
+ * level's four intensity images. */
+void sfo_level_planes(int w, int h, const double* imgs4, double* planes)
+{
+    size_t n = (size_t)w * h;
+    for (int c = 0; c < 4; ++c) {
+        const double* I = imgs4 + c * n;
+        double* P = planes + (size_t)c * 3 * n;
+        memcpy(P, I, n * sizeof(double));
+        sfo_gradients(w, h, I, P + n, P + 2 * n);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Bilinear sampling with derivative [C5, C7]                                */
+/* ------------------------------------------------------------------------ */
+
+/* Bilinear interpolation of plane P (w x h) at (px, py); the position is
+ * clamped to [0, w-1] x [0, h-1]; the cell is min(floor(p), w-2). The
+ * derivative is that of the bilinear interpolant, 0 along a clamped axis. */
+double sfo_sample(int w, int h, const double* P, double px, double py, double* dpx, double* dpy)
+{
+    int clx = 0, cly = 0;
+    double cx = px, cy = py;
+    if (cx < 0.0) { cx = 0.0; clx = 1; }
+    if (cx > w - 1) { cx = w - 1; clx = 1; }
+    if (cy < 0.0) { cy = 0.0; cly = 1; }
+    if (cy > h - 1) { cy = h - 1; cly = 1; }
+    int ix = (int)floor(cx), iy = (int)floor(cy);
+    if (ix > w - 2) ix = w - 2;
+    if (iy > h - 2) iy = h - 2;
+    double fx = cx - ix, fy = cy - iy;
+    double p00 = P[iy * w + ix], p10 = P[iy * w + ix + 1];
+    double p01 = P[(iy + 1) * w + ix], p11 = P[(iy + 1) * w + ix + 1];
+    double v = (1 - fx) * (1 - fy) * p00 + fx * (1 - fy) * p10 + (1 - fx) * fy * p01 + fx * fy * p11;
+    if (dpx) *dpx = clx ? 0.0 : (1 - fy) * (p10 - p00) + fy * (p11 - p01);
+    if (dpy) *dpy = cly ? 0.0 : (1 - fx) * (p01 - p00) + fx * (p11 - p10);
+    return v;
+}
+
+/* Same rule on a node grid (nx x ny): used by prolongation and the temporal
+ * transfer, no derivative. */
+static double grid_sample(int nx, int ny, const double* Fc, double u, double v)
+{
+    return sfo_sample(nx, ny, Fc, u, v, NULL, NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Warp grid (Section 3.3, Eq. 7) [C8]                                       */
+/* ------------------------------------------------------------------------ */
+
+/* The four nodes and bilinear weights of pixel (x, y); node (i, j) sits at
+ * level pixel (i*s, j*s); pixels past the last node clamp to it. */
+void sfo_grid_weights(int x, int y, int s, int nx, int ny, int nodes[4], double wts[4])
+{
+    double u = (double)x / s, v = (double)y / s;
+    if (u > nx - 1) u = nx - 1;
+    if (v > ny - 1) v = ny - 1;
+    int i0 = (int)floor(u), j0 = (int)floor(v);
+    if (i0 > nx - 2) i0 = nx - 2;
+    if (j0 > ny - 2) j0 = ny - 2;
+    double a = u - i0, b = v - j0;
+    nodes[0] = j0 * nx + i0;
+    nodes[1] = j0 * nx + i0 + 1;
+    nodes[2] = (j0 + 1) * nx + i0;
+    nodes[3] = (j0 + 1) * nx + i0 + 1;
+    wts[0] = (1 - a) * (1 - b);
+    wts[1] = a * (1 - b);
+    wts[2] = (1 - a) * b;
+    wts[3] = a * b;
+}
+
+/* Per-pixel fields f[6] = sum_k alpha_k T_k (Eq. 7). */
+static void pixel_fields(int x, int y, int s, int nx, int ny, const double* T, double f[6])
+{
+    int nd[4];
+    double al[4];
+    int G = nx * ny;
+    sfo_grid_weights(x, y, s, nx, ny, nd, al);
+    for (int c = 0; c < 6; ++c) {
+        f[c] = 0.0;
+        for (int k = 0; k < 4; ++k) f[c] += al[k] * T[c * G + nd[k]];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Consistency checks (Section 3.2, Eqs. 1-6) and their analytic Jacobian    */
+/* ------------------------------------------------------------------------ */
+
+/* For pixel (x, y) with fields f = (s, m, d): the six brightness checks e[k],
+ * the six gradient-constancy 2-vectors g[2k], g[2k+1] (difference of the
+ * warped image gradients [C2]) and their Jacobians w.r.t. the six pixel
+ * fields (Je[k][u], Jg[2k+a][u], u = sx, sy, mx, my, dx, dy). */
+void sfo_pixel_terms(int w, int h, const double* planes, double x, double y, const double f[6],
+                     double e[6], double g[12], double Je[36], double Jg[72])
+{
+    size_t n = (size_t)w * h;
+    double val[4][3], dx[4][3], dy[4][3];
+    for (int c = 0; c < 4; ++c) {
+        double px = x + SIGN[c][0] * f[0] + SIGN[c][1] * f[2] + SIGN[c][2] * f[4];
+        double py = y + SIGN[c][0] * f[1] + SIGN[c][1] * f[3] + SIGN[c][2] * f[5];
+        for (int p = 0; p < 3; ++p)
+            val[c][p] = sfo_sample(w, h, planes + (size_t)(c * 3 + p) * n, px, py, &dx[c][p], &dy[c][p]);
+    }
+    for (int k = 0; k < 6; ++k) {
+        int F = CHECK[k][0], S = CHECK[k][1];
+        e[k] = val[F][0] - val[S][0];
+        g[2 * k] = val[F][1] - val[S][1];
+        g[2 * k + 1] = val[F][2] - val[S][2];
+        for (int fld = 0; fld < 3; ++fld) {
+            double sF = SIGN[F][fld], sS = SIGN[S][fld];
+            /* d p_X.x / d field_x = sign, and likewise for y */
+            if (Je) {
+                Je[k * 6 + 2 * fld + 0] = sF * dx[F][0] - sS * dx[S][0];
+                Je[k * 6 + 2 * fld + 1] = sF * dy[F][0] - sS * dy[S][0];
+            }
+            if (Jg) {
+                for (int a = 0; a < 2; ++a) {
+                    Jg[(2 * k + a) * 6 + 2 * fld + 0] = sF * dx[F][1 + a] - sS * dx[S][1 + a];
+                    Jg[(2 * k + a) * 6 + 2 * fld + 1] = sF * dy[F][1 + a] - sS * dy[S][1 + a];
+                }
+            }
+        }
+    }
+}
+
+/* Halfway image: mean of the four warped samples (used by the feature weight). */
+static double halfway_value(int w, int h, const double* planes, int x, int y, const double f[6])
+{
+    size_t n = (size_t)w * h;
+    double acc = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        double px = x + SIGN[c][0] * f[0] + SIGN[c][1] * f[2] + SIGN[c][2] * f[4];
+        double py = y + SIGN[c][0] * f[1] + SIGN[c][1] * f[3] + SIGN[c][2] * f[5];
+        acc += sfo_sample(w, h, planes + (size_t)(c * 3) * n, px, py, NULL, NULL);
+    }
+    return 0.25 * acc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Robust penalties (Eq. 12, Eq. 11, Eq. 13) [C1, C3]                        */
+/* ------------------------------------------------------------------------ */
+
+static double phi(double x, double eps) { return sqrt(x * x + eps * eps); }
+
+/* Gradient-term penalty of |g|^2: Brox convention sqrt(|g|^2 + eps^2) by
+ * default, the literal reading sqrt(|g|^4 + eps^2) on request. */
+static double psi_grad(double q, double eps, int mode)
+{
+    return mode == SFO_GRAD_LITERAL ? sqrt(q * q + eps * eps) : sqrt(q + eps * eps);
+}
+
+/* d psi / d g = coef * g; returns coef. */
+static double psi_grad_coef(double q, double eps, int mode)
+{
+    return mode == SFO_GRAD_LITERAL ? 2.0 * q / sqrt(q * q + eps * eps) : 1.0 / sqrt(q + eps * eps);
+}
+
+/* W (Section 4.1): 1 if the largest brightness check is below eps_p [C11]. */
+static int outlier_weight(const double e[6], double eps_p)
+{
+    if (eps_p <= 0.0) return 1;
+    double mx = 0.0;
+    for (int k = 0; k < 6; ++k)
+        if (fabs(e[k]) > mx) mx = fabs(e[k]);
+    return mx < eps_p ? 1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-level helpers                                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Fundamental matrix in level-l pixels: S F S rescaled to the Frobenius norm
+ * of F, S = diag(2^l, 2^l, 1) [C14]. */
+void sfo_level_F(const double F[9], int level, double Fl[9])
+{
+    double sc[3] = {ldexp(1.0, level), ldexp(1.0, level), 1.0};
+    double n0 = 0.0, n1 = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            Fl[a * 3 + b] = sc[a] * F[a * 3 + b] * sc[b];
+            n0 += F[a * 3 + b] * F[a * 3 + b];
+            n1 += Fl[a * 3 + b] * Fl[a * 3 + b];
+        }
+    if (n1 > 0.0)
+        for (int a = 0; a < 9; ++a) Fl[a] *= sqrt(n0 / n1);
+}
+
+/* Epipolar residuals of node position (X, Y) with totals t[6] (Eqs. 15-17):
+ * r[t] = l_t^T F r_t, and their gradients J[t][6] w.r.t. the node totals. */
+static void epipolar_terms(const double Fl[9], double X, double Y, const double t[6], double r[2], double J[12])
+{
+    /* signs (s, m, d) of l^0, r^0, l^1, r^1: those of images 0, 1, 2, 3 */
+    for (int tt = 0; tt < 2; ++tt) {
+        int il = tt == 0 ? 0 : 2, ir = tt == 0 ? 1 : 3;
+        double l[3], rr[3];
+        l[0] = X + SIGN[il][0] * t[0] + SIGN[il][1] * t[2] + SIGN[il][2] * t[4];
+        l[1] = Y + SIGN[il][0] * t[1] + SIGN[il][1] * t[3] + SIGN[il][2] * t[5];
+        l[2] = 1.0;
+        rr[0] = X + SIGN[ir][0] * t[0] + SIGN[ir][1] * t[2] + SIGN[ir][2] * t[4];
+        rr[1] = Y + SIGN[ir][0] * t[1] + SIGN[ir][1] * t[3] + SIGN[ir][2] * t[5];
+        rr[2] = 1.0;
+        double Fr[3], Ftl[3];
+        for (int a = 0; a < 3; ++a) {
+            Fr[a] = Fl[a * 3 + 0] * rr[0] + Fl[a * 3 + 1] * rr[1] + Fl[a * 3 + 2] * rr[2];
+            Ftl[a] = Fl[0 * 3 + a] * l[0] + Fl[1 * 3 + a] * l[1] + Fl[2 * 3 + a] * l[2];
+        }
+        r[tt] = l[0] * Fr[0] + l[1] * Fr[1] + l[2] * Fr[2];
+        for (int fld = 0; fld < 3; ++fld)
+            for (int a = 0; a < 2; ++a)
+                J[tt * 6 + 2 * fld + a] = SIGN[il][fld] * Fr[a] + SIGN[ir][fld] * Ftl[a];
+    }
+}
+
+/* Feature weight w_i of every node (Section 4.3) [C10]: structure tensor of
+ * the halfway image over the 3x3 pixels at the node, w = 1 + g exp(-lmin/tau). */
+void sfo_feature_weights(int w, int h, int s, int nx, int ny, const double* planes, const double* T,
+                         const sfo_params* p, double* wf)
+{
+    int G = nx * ny;
+    if (p->wfeat_mode == SFO_WFEAT_OFF) {
+        for (int n = 0; n < G; ++n) wf[n] = 1.0;
+        return;
+    }
+    double* H = (double*)malloc(sizeof(double) * w * h);
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            double f[6];
+            pixel_fields(x, y, s, nx, ny, T, f);
+            H[y * w + x] = halfway_value(w, h, planes, x, y, f);
+        }
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            double a = 0.0, b = 0.0, c = 0.0;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int qx = i * s + dx, qy = j * s + dy;
+                    qx = qx < 0 ? 0 : (qx > w - 1 ? w - 1 : qx);
+                    qy = qy < 0 ? 0 : (qy > h - 1 ? h - 1 : qy);
+                    int xm = qx > 0 ? qx - 1 : 0, xp = qx < w - 1 ? qx + 1 : w - 1;
+                    int ym = qy > 0 ? qy - 1 : 0, yp = qy < h - 1 ? qy + 1 : h - 1;
+                    double hx = 0.5 * (H[qy * w + xp] - H[qy * w + xm]);
+                    double hy = 0.5 * (H[yp * w + qx] - H[ym * w + qx]);
+                    a += hx * hx;
+                    b += hx * hy;
+                    c += hy * hy;
+                }
+            double lmin = 0.5 * (a + c) - sqrt(0.25 * (a - c) * (a - c) + b * b);
+            if (lmin < 0.0) lmin = 0.0;
+            wf[j * nx + i] = 1.0 + p->wfeat_gain * exp(-lmin / p->wfeat_tau);
+        }
+    free(H);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Energy (Eqs. 8-18) with W frozen                                           */
+/* ------------------------------------------------------------------------ */
+
+/* terms[0..4] = E_photo, E_grad, E_smooth, E_epi, E_mag (unweighted sums as
+ * in Eqs. 11, 13, 14, 15, 18); returns the weighted total of Eqs. 8-10.
+ * If W is NULL it is computed at this state (and written to Wout if given). */
+double sfo_energy(int w, int h, int s, int nx, int ny, int level, const double* planes,
+                  const double* base, const double* delta, const double* wf, const unsigned char* W,
+                  const sfo_params* p, double terms[5], unsigned char* Wout)
+{
+    int G = nx * ny;
+    double* T = (double*)malloc(sizeof(double) * 6 * G);
+    for (int a = 0; a < 6 * G; ++a) T[a] = base[a] + delta[a];
+    double Ep = 0.0, Eg = 0.0, Es = 0.0, Ee = 0.0, Em = 0.0;
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            double f[6], e[6], g[12];
+            pixel_fields(x, y, s, nx, ny, T, f);
+            sfo_pixel_terms(w, h, planes, x, y, f, e, g, NULL, NULL);
+            int Wi = W ? W[y * w + x] : outlier_weight(e, p->eps_p);
+            if (Wout) Wout[y * w + x] = (unsigned char)Wi;
+            if (!Wi) continue; /* V = 1 [C12] */
+            for (int k = 0; k < 6; ++k) {
+                Ep += phi(e[k], p->eps);
+                Eg += psi_grad(g[2 * k] * g[2 * k] + g[2 * k + 1] * g[2 * k + 1], p->eps, p->grad_mode);
+            }
+        }
+    const double wfl[3] = {p->w_s, p->w_m, p->w_d};
+    const double mfl[3] = {p->m_s, p->m_m, p->m_d};
+    double Fl[9];
+    sfo_level_F(p->F, level, Fl);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int n = j * nx + i;
+            /* Eq. 14: both directed pairs of every 4-neighbour edge [C9] */
+            for (int nb = 0; nb < 2; ++nb) {
+                int i2 = i + (nb == 0), j2 = j + (nb == 1);
+                if (i2 >= nx || j2 >= ny) continue;
+                int m = j2 * nx + i2;
+                for (int fld = 0; fld < 3; ++fld)
+                    for (int a = 0; a < 2; ++a) {
+                        double d = T[(2 * fld + a) * G + n] - T[(2 * fld + a) * G + m];
+                        Es += (wf[n] + wf[m]) * wfl[fld] * d * d;
+                    }
+            }
+            double t6[6], r[2], J[12];
+            for (int c = 0; c < 6; ++c) t6[c] = T[c * G + n];
+            epipolar_terms(Fl, (double)(i * s), (double)(j * s), t6, r, J);
+            Ee += r[0] * r[0] + r[1] * r[1];
+            /* Eq. 18 on the deltas (Section 5.1) [C9] */
+            for (int fld = 0; fld < 3; ++fld)
+                for (int a = 0; a < 2; ++a) {
+                    double d = delta[(2 * fld + a) * G + n];
+                    Em += mfl[fld] * d * d;
+                }
+        }
+    free(T);
+    if (terms) {
+        terms[0] = Ep;
+        terms[1] = Eg;
+        terms[2] = Es;
+        terms[3] = Ee;
+        terms[4] = Em;
+    }
+    return p->w_photo * Ep + p->w_grad * Eg + p->w_reg * (p->w_smooth * Es + p->w_epi * Ee + p->w_mag * Em);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gauss-Newton normal equations (Section 5.1, Eqs. 19-24) [C3]               */
+/* ------------------------------------------------------------------------ */
+
+static int slot_of(int di, int dj) { return 3 * (dj + 1) + (di + 1); }
+
+static void add_block(double* A, int n, int slot, int r, int c, double v) { A[((size_t)n * 9 + slot) * 36 + r * 6 + c] += v; }
+
+/* Assembles A dx = b at the state base + delta, with W taken at this state
+ * (written to Wout) unless W is given. Returns the energy at the state. */
+double sfo_assemble(int w, int h, int s, int nx, int ny, int level, const double* planes,
+                    const double* base, const double* delta, const double* wf, const unsigned char* Win,
+                    const sfo_params* p, double* A, double* b, unsigned char* Wout)
+{
+    int G = nx * ny;
+    memset(A, 0, sizeof(double) * (size_t)G * 9 * 36);
+    memset(b, 0, sizeof(double) * (size_t)G * 6);
+    double* T = (double*)malloc(sizeof(double) * 6 * G);
+    for (int a = 0; a < 6 * G; ++a) T[a] = base[a] + delta[a];
+
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            double f[6], e[6], g[12], Je[36], Jg[72];
+            int nd[4];
+            double al[4];
+            sfo_grid_weights(x, y, s, nx, ny, nd, al);
+            pixel_fields(x, y, s, nx, ny, T, f);
+            sfo_pixel_terms(w, h, planes, x, y, f, e, g, Je, Jg);
+            int Wi = Win ? Win[y * w + x] : outlier_weight(e, p->eps_p);
+            if (Wout) Wout[y * w + x] = (unsigned char)Wi;
+            if (!Wi) continue;
+            /* pixel-level 6x6 H_p and 6-vector b_p */
+            double Hp[36] = {0}, bp[6] = {0};
+            if (p->robust_mode == SFO_IRLS) {
+                /* each robust term c*rho(r) -> weight c*rho'(r)/(2r) on (r + J dx)^2 */
+                for (int k = 0; k < 6; ++k) {
+                    double om = p->w_photo / (2.0 * phi(e[k], p->eps));
+                    for (int r = 0; r < 6; ++r) {
+                        bp[r] -= om * e[k] * Je[k * 6 + r];
+                        for (int c = 0; c < 6; ++c) Hp[r * 6 + c] += om * Je[k * 6 + r] * Je[k * 6 + c];
+                    }
+                    double q = g[2 * k] * g[2 * k] + g[2 * k + 1] * g[2 * k + 1];
+                    double og = 0.5 * p->w_grad * psi_grad_coef(q, p->eps, p->grad_mode);
+                    for (int a = 0; a < 2; ++a)
+                        for (int r = 0; r < 6; ++r) {
+                            bp[r] -= og * g[2 * k + a] * Jg[(2 * k + a) * 6 + r];
+                            for (int c = 0; c < 6; ++c)
+                                Hp[r * 6 + c] += og * Jg[(2 * k + a) * 6 + r] * Jg[(2 * k + a) * 6 + c];
+                        }
+                }
+            } else {
+                /* paper-literal: one residual sqrt(rho) per pixel and term (Eq. 19) */
+                double rho_p = 0.0, rho_g = 0.0, gp[6] = {0}, gg[6] = {0};
+                for (int k = 0; k < 6; ++k) {
+                    double ph = phi(e[k], p->eps);
+                    rho_p += p->w_photo * ph;
+                    for (int r = 0; r < 6; ++r) gp[r] += p->w_photo * e[k] / ph * Je[k * 6 + r];
+                    double q = g[2 * k] * g[2 * k] + g[2 * k + 1] * g[2 * k + 1];
+                    rho_g += p->w_grad * psi_grad(q, p->eps, p->grad_mode);
+                    double cf = p->w_grad * psi_grad_coef(q, p->eps, p->grad_mode);
+                    for (int a = 0; a < 2; ++a)
+                        for (int r = 0; r < 6; ++r) gg[r] += cf * g[2 * k + a] * Jg[(2 * k + a) * 6 + r];
+                }
+                for (int r = 0; r < 6; ++r) {
+                    bp[r] -= 0.5 * (gp[r] + gg[r]);
+                    for (int c = 0; c < 6; ++c) {
+                        if (rho_p > 0) Hp[r * 6 + c] += gp[r] * gp[c] / (4.0 * rho_p);
+                        if (rho_g > 0) Hp[r * 6 + c] += gg[r] * gg[c] / (4.0 * rho_g);
+                    }
+                }
+            }
+            /* chain rule through the bilinear weights to the four nodes (Eq. 7) */
+            for (int k = 0; k < 4; ++k) {
+                int ik = nd[k] % nx, jk = nd[k] / nx;
+                for (int r = 0; r < 6; ++r) b[nd[k] * 6 + r] += al[k] * bp[r];
+                for (int l = 0; l < 4; ++l) {
+                    int il = nd[l] % nx, jl = nd[l] / nx;
+                    int sl = slot_of(il - ik, jl - jk);
+                    for (int r = 0; r < 6; ++r)
+                        for (int c = 0; c < 6; ++c) add_block(A, nd[k], sl, r, c, al[k] * al[l] * Hp[r * 6 + c]);
+                }
+            }
+        }
+
+    /* priors on the nodes: exact Gauss-Newton rows */
+    const double wfl[3] = {p->w_s, p->w_m, p->w_d};
+    const double mfl[3] = {p->m_s, p->m_m, p->m_d};
+    double Fl[9];
+    sfo_level_F(p->F, level, Fl);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int n = j * nx + i;
+            for (int nb = 0; nb < 2; ++nb) {
+                int i2 = i + (nb == 0), j2 = j + (nb == 1);
+                if (i2 >= nx || j2 >= ny) continue;
+                int m = j2 * nx + i2;
+                for (int fld = 0; fld < 3; ++fld) {
+                    double c = p->w_reg * p->w_smooth * (wf[n] + wf[m]) * wfl[fld];
+                    for (int a = 0; a < 2; ++a) {
+                        int u = 2 * fld + a;
+                        double d = T[u * G + n] - T[u * G + m];
+                        add_block(A, n, 4, u, u, c);
+                        add_block(A, m, 4, u, u, c);
+                        add_block(A, n, slot_of(i2 - i, j2 - j), u, u, -c);
+                        add_block(A, m, slot_of(i - i2, j - j2), u, u, -c);
+                        b[n * 6 + u] -= c * d;
+                        b[m * 6 + u] += c * d;
+                    }
+                }
+            }
+            double t6[6], r[2], J[12];
+            for (int c = 0; c < 6; ++c) t6[c] = T[c * G + n];
+            epipolar_terms(Fl, (double)(i * s), (double)(j * s), t6, r, J);
+            double ce = p->w_reg * p->w_epi;
+            for (int tt = 0; tt < 2; ++tt)
+                for (int u = 0; u < 6; ++u) {
+                    b[n * 6 + u] -= ce * r[tt] * J[tt * 6 + u];
+                    for (int v = 0; v < 6; ++v) add_block(A, n, 4, u, v, ce * J[tt * 6 + u] * J[tt * 6 + v]);
+                }
+            for (int fld = 0; fld < 3; ++fld) {
+                double cm = p->w_reg * p->w_mag * mfl[fld];
+                for (int a = 0; a < 2; ++a) {
+                    int u = 2 * fld + a;
+                    add_block(A, n, 4, u, u, cm);
+                    b[n * 6 + u] -= cm * delta[u * G + n];
+                }
+            }
+        }
+    free(T);
+    return sfo_energy(w, h, s, nx, ny, level, planes, base, delta, wf, Win ? Win : Wout, p, NULL, NULL);
+}
+
+/* y = A x for the block system; vectors interleaved per node (n*6 + r). */
+void sfo_apply(int nx, int ny, const double* A, const double* x, double* y)
+{
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int n = j * nx + i;
+            for (int r = 0; r < 6; ++r) y[n * 6 + r] = 0.0;
+            for (int dj = -1; dj <= 1; ++dj)
+                for (int di = -1; di <= 1; ++di) {
+                    int i2 = i + di, j2 = j + dj;
+                    if (i2 < 0 || i2 >= nx || j2 < 0 || j2 >= ny) continue;
+                    int m = j2 * nx + i2;
+                    const double* B = A + ((size_t)n * 9 + slot_of(di, dj)) * 36;
+                    for (int r = 0; r < 6; ++r)
+                        for (int c = 0; c < 6; ++c) y[n * 6 + r] += B[r * 6 + c] * x[m * 6 + c];
+                }
+        }
+}
+
+static double dot(int n, const double* a, const double* b)
+{
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) acc += a[i] * b[i];
+    return acc;
+}
+
+/* Jacobi-preconditioned conjugate gradients on A x = b from x = 0 (Section
+ * 5.1) [C17]; exactly `iters` iterations unless p^T A p or r^T z drops to
+ * 1e-30. model[k] = 0.5 x^T A x - b^T x after iteration k (may be NULL).
+ * Returns the number of iterations run. */
+int sfo_pcg(int nx, int ny, const double* A, const double* b, int iters, double* x, double* model)
+{
+    int N = nx * ny * 6;
+    double* r = (double*)malloc(sizeof(double) * N);
+    double* z = (double*)malloc(sizeof(double) * N);
+    double* pv = (double*)malloc(sizeof(double) * N);
+    double* q = (double*)malloc(sizeof(double) * N);
+    double* Minv = (double*)malloc(sizeof(double) * N);
+    for (int n = 0; n < nx * ny; ++n)
+        for (int u = 0; u < 6; ++u) {
+            double d = A[((size_t)n * 9 + 4) * 36 + u * 6 + u];
+            Minv[n * 6 + u] = d > 0.0 ? 1.0 / d : 1.0;
+        }
+    for (int a = 0; a < N; ++a) {
+        x[a] = 0.0;
+        r[a] = b[a];
+        z[a] = Minv[a] * r[a];
+        pv[a] = z[a];
+    }
+    double rz = dot(N, r, z);
+    int it = 0;
+    for (; it < iters; ++it) {
+        if (rz <= 1e-30) break;
+        sfo_apply(nx, ny, A, pv, q);
+        double pq = dot(N, pv, q);
+        if (pq <= 1e-30) break;
+        double alpha = rz / pq;
+        for (int a = 0; a < N; ++a) {
+            x[a] += alpha * pv[a];
+            r[a] -= alpha * q[a];
+            z[a] = Minv[a] * r[a];
+        }
+        double rz_new = dot(N, r, z);
+        double beta = rz_new / rz;
+        rz = rz_new;
+        for (int a = 0; a < N; ++a) pv[a] = z[a] + beta * pv[a];
+        if (model) {
+            sfo_apply(nx, ny, A, x, q);
+            model[it] = 0.5 * dot(N, x, q) - dot(N, b, x);
+        }
+    }
+    free(r);
+    free(z);
+    free(pv);
+    free(q);
+    free(Minv);
+    return it;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Delta hierarchy (Section 5.3) and temporal transfer [C19]                 */
+/* ------------------------------------------------------------------------ */
+
+/* base = 2 * Up(Tc): fine node (i, j) reads the coarse grid at (i/2, j/2),
+ * bilinear, clamped; displacements double with the pixel size. */
+void sfo_upsample(int nxc, int nyc, const double* Tc, int nx, int ny, double* base)
+{
+    int Gc = nxc * nyc, G = nx * ny;
+    for (int c = 0; c < 6; ++c)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                base[c * G + j * nx + i] = 2.0 * grid_sample(nxc, nyc, Tc + c * Gc, 0.5 * i, 0.5 * j);
+}
+
+/* Constant-velocity transfer of one level's delta to the next frame: the node
+ * at pixel X takes the previous delta at X - 2 m(X), m the previous total
+ * motion at that node (grid coordinates = pixels / s). */
+void sfo_temporal(int s, int nx, int ny, const double* delta_prev, const double* T_prev, int mode, double* delta)
+{
+    int G = nx * ny;
+    if (mode == SFO_TEMPORAL_ZERO) {
+        memset(delta, 0, sizeof(double) * 6 * G);
+        return;
+    }
+    if (mode == SFO_TEMPORAL_COPY) {
+        memcpy(delta, delta_prev, sizeof(double) * 6 * G);
+        return;
+    }
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int n = j * nx + i;
+            double X = (double)(i * s) - 2.0 * T_prev[2 * G + n];
+            double Y = (double)(j * s) - 2.0 * T_prev[3 * G + n];
+            for (int c = 0; c < 6; ++c) delta[c * G + n] = grid_sample(nx, ny, delta_prev + c * G, X / s, Y / s);
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* One frame: Algorithm 1 without the occlusion and illumination maps        */
+/* ------------------------------------------------------------------------ */
+
+/* Packed per-level node arrays: level l starts at 6 * sum_{k<l} G_k. */
+long sfo_packed_size(int w0, int h0, int s, int levels)
+{
+    long tot = 0;
+    for (int l = 0; l < levels; ++l) {
+        int w, h;
+        sfo_level_dims(w0, h0, l, &w, &h);
+        tot += 6L * ((w + s - 1) / s) * ((h + s - 1) / s);
+    }
+    return tot;
+}
+
+/* Solves one frame.
+ *   imgs          4 * w0 * h0 doubles (image order of the file header)
+ *   prev_delta,   packed per-level deltas and totals of the previous frame,
+ *   prev_total    or NULL for the first frame (zero initialisation)
+ *   init_coarsest optional 6 * G_{L-1} initial delta of the coarsest level
+ *                 (overrides the temporal rule there), or NULL
+ *   out_delta,    packed per-level final deltas and totals
+ *   out_total
+ *   stats         SFO_STATS_LEN doubles: [0] final energy, [1..5] its terms,
+ *                 [6] pixels with W = 0 in the last step; at 16 + (l*16+g)*8:
+ *                 E at the linearisation point, E accepted, step t (0 if
+ *                 rejected), pixels with W = 0, PCG iterations run.
+ * Returns 0, or -1 for invalid sizes. */
+int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const double* imgs,
+                    const double* prev_delta, const double* prev_total, const double* init_coarsest,
+                    double* out_delta, double* out_total, double* stats)
+{
+    if (L < 1 || L > SFO_MAX_LEVELS || s < 1) return -1;
+    int W[SFO_MAX_LEVELS], H[SFO_MAX_LEVELS], NX[SFO_MAX_LEVELS], NY[SFO_MAX_LEVELS];
+    long off[SFO_MAX_LEVELS];
+    long acc = 0;
+    for (int l = 0; l < L; ++l) {
+        sfo_level_dims(w0, h0, l, &W[l], &H[l]);
+        NX[l] = (W[l] + s - 1) / s;
+        NY[l] = (H[l] + s - 1) / s;
+        if (W[l] < 2 || H[l] < 2 || NX[l] < 2 || NY[l] < 2) return -1;
+        off[l] = acc;
+        acc += 6L * NX[l] * NY[l];
+    }
+    if (stats) memset(stats, 0, sizeof(double) * SFO_STATS_LEN);
+
+    /* pyramid of intensities, then per-level planes */
+    double* lvl_imgs[SFO_MAX_LEVELS];
+    for (int l = 0; l < L; ++l) lvl_imgs[l] = (double*)malloc(sizeof(double) * 4 * W[l] * H[l]);
+    memcpy(lvl_imgs[0], imgs, sizeof(double) * 4 * W[0] * H[0]);
+    for (int l = 1; l < L; ++l)
+        for (int c = 0; c < 4; ++c)
+            sfo_downsample(W[l - 1], H[l - 1], lvl_imgs[l - 1] + (size_t)c * W[l - 1] * H[l - 1],
+                           lvl_imgs[l] + (size_t)c * W[l] * H[l]);
+
+    for (int l = L - 1; l >= 0; --l) {
+        int w = W[l], h = H[l], nx = NX[l], ny = NY[l], G = nx * ny;
+        double* planes = (double*)malloc(sizeof(double) * 12 * w * h);
+        sfo_level_planes(w, h, lvl_imgs[l], planes);
+        double* base = out_total + off[l]; /* reuse the output as scratch for the base */
+        double* delta = out_delta + off[l];
+        if (l == L - 1) {
+            memset(base, 0, sizeof(double) * 6 * G);
+        } else {
+            sfo_upsample(NX[l + 1], NY[l + 1], out_total + off[l + 1], nx, ny, base);
+        }
+        if (l == L - 1 && init_coarsest) {
+            memcpy(delta, init_coarsest, sizeof(double) * 6 * G);
+        } else if (prev_delta && prev_total) {
+            sfo_temporal(s, nx, ny, prev_delta + off[l], prev_total + off[l], p->temporal_mode, delta);
+        } else {
+            memset(delta, 0, sizeof(double) * 6 * G);
+        }
+        double* T = (double*)malloc(sizeof(double) * 6 * G);
+        for (int a = 0; a < 6 * G; ++a) T[a] = base[a] + delta[a];
+        double* wf = (double*)malloc(sizeof(double) * G);
+        sfo_feature_weights(w, h, s, nx, ny, planes, T, p, wf);
+
+        double* A = (double*)malloc(sizeof(double) * (size_t)G * 9 * 36);
+        double* b = (double*)malloc(sizeof(double) * G * 6);
+        double* x = (double*)malloc(sizeof(double) * G * 6);
+        double* trial = (double*)malloc(sizeof(double) * G * 6);
+        unsigned char* Wm = (unsigned char*)malloc((size_t)w * h);
+        int have_W = 0;
+        for (int g = 0; g < p->gn_iters[l] && g < SFO_MAX_GN; ++g) {
+            double Ecur = sfo_assemble(w, h, s, nx, ny, l, planes, base, delta, wf, NULL, p, A, b, Wm);
+            have_W = 1;
+            int nexcl = 0;
+            for (int a = 0; a < w * h; ++a) nexcl += Wm[a] == 0;
+            int its = sfo_pcg(nx, ny, A, b, p->pcg_iters[l], x, NULL);
+            /* backtracking safeguard [C18]: first t in {1, 1/2, ...} that does
+             * not raise the energy (W frozen at this step's value) */
+            double t = 1.0, Eacc = Ecur, tacc = 0.0;
+            for (int bt = 0; bt <= p->max_backtracks; ++bt, t *= 0.5) {
+                for (int n = 0; n < G; ++n)
+                    for (int c = 0; c < 6; ++c) trial[c * G + n] = delta[c * G + n] + t * x[n * 6 + c];
+                double Et = sfo_energy(w, h, s, nx, ny, l, planes, base, trial, wf, Wm, p, NULL, NULL);
+                if (Et <= Ecur) {
+                    memcpy(delta, trial, sizeof(double) * 6 * G);
+                    Eacc = Et;
+                    tacc = t;
+                    break;
+                }
+            }
+            if (stats) {
+                double* st = stats + 16 + (l * SFO_MAX_GN + g) * 8;
+                st[0] = Ecur;
+                st[1] = Eacc;
+                st[2] = tacc;
+                st[3] = nexcl;
+                st[4] = its;
+            }
+        }
+        if (l == 0 && stats) {
+            /* final energy: with the last step's W, or W at this state */
+            double terms[5];
+            double E = sfo_energy(w, h, s, nx, ny, l, planes, base, delta, wf, have_W ? Wm : NULL, p, terms,
+                                  have_W ? NULL : Wm);
+            stats[0] = E;
+            stats[1] = p->w_photo * terms[0];
+            stats[2] = p->w_grad * terms[1];
+            stats[3] = p->w_reg * p->w_smooth * terms[2];
+            stats[4] = p->w_reg * p->w_epi * terms[3];
+            stats[5] = p->w_reg * p->w_mag * terms[4];
+            int nexcl = 0;
+            for (int a = 0; a < w * h; ++a) nexcl += Wm[a] == 0;
+            stats[6] = nexcl;
+        }
+        for (int a = 0; a < 6 * G; ++a) base[a] += delta[a]; /* the slot now holds the total T_l */
+        free(T);
+        free(wf);
+        free(A);
+        free(b);
+        free(x);
+        free(trial);
+        free(Wm);
+        free(planes);
+    }
+    for (int l = 0; l < L; ++l) free(lvl_imgs[l]);
+    return 0;
+}
