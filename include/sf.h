@@ -1,0 +1,208 @@
+/*
+ * sf.h -- C ABI of the GB300 (sm_103a) halfway-domain scene-flow solver.
+ *
+ * The solver computes, for one stereo quadruple (two rectified, pre-calibrated
+ * monochrome stereo pairs at two time steps, Section 3.1 of Thies et al.,
+ * "Real-time Halfway Domain Reconstruction of Motion and Geometry", arXiv
+ * 1610.07159), the stereo, motion and difference flow fields s, m, d of the
+ * halfway domain (Section 3.1) on a coarse bilinear warp grid (Section 3.3,
+ * Eq. 7). It minimises the energy of Eqs. 8-18 (photometric and gradient
+ * consistency of the six checks of Eqs. 1-6 under the pseudo-Huber penalty of
+ * Eq. 12, smoothness, epipolar and magnitude priors) with robust Gauss-Newton
+ * and preconditioned conjugate gradients (Section 5.1), coarse to fine on a
+ * hierarchy that stores delta flows between levels (Section 5.3, Algorithm 1
+ * without the occlusion and illumination maps).
+ *
+ * Every step runs in CUDA kernels of this library on one GPU; there is no CPU
+ * path. All calls are plain C: pointers, sizes and status codes.
+ *
+ * Conventions
+ *   images      float32, row-major width x height, intensities in [0, 1]
+ *               (monochrome, Section 3.1). Order: L_t = I_0^0, R_t = I_1^0,
+ *               L_t1 = I_0^1, R_t1 = I_1^1 (camera c, time t of I_c^t).
+ *   fields      float32 [6][ny][nx] component-major: s_x, s_y, m_x, m_y, d_x,
+ *               d_y of every warp-grid node, node (i, j) at level pixel
+ *               (i*grid_stride, j*grid_stride); nx = ceil(w / grid_stride),
+ *               ny = ceil(h / grid_stride). Values are in pixels of the level
+ *               (the finest level for sf_solve's output).
+ *   streams     a cudaStream_t passed as void*; NULL is the legacy default
+ *               stream. Calls that take a stream only enqueue work on it.
+ *   ownership   the context owns all of its device memory, allocated in
+ *               sf_create; sf_solve allocates nothing. Caller buffers stay
+ *               the caller's.
+ *   errors      every call returns an sf_status. Errors raised inside
+ *               kernels (a PCG barrier that gave up waiting, a non-finite
+ *               energy) are latched in a device status word and reported by
+ *               sf_get_stats and by the next sf_solve.
+ *   threads     one context per host thread at a time.
+ */
+#ifndef SF_H
+#define SF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SF_API __attribute__((visibility("default")))
+#else
+#define SF_API
+#endif
+
+#define SF_MAX_LEVELS 8
+#define SF_MAX_GN 16
+
+typedef enum sf_status {
+    SF_OK = 0,
+    SF_ERR_ARG = 1,     /* invalid argument or size */
+    SF_ERR_CUDA = 2,    /* a CUDA runtime call failed */
+    SF_ERR_OOM = 3,     /* device or pinned allocation failed */
+    SF_ERR_NUMERIC = 4, /* a non-finite energy was met on the device */
+    SF_ERR_TIMEOUT = 5, /* a device-wide barrier gave up waiting */
+    SF_ERR_STATE = 6    /* call not valid in the context's current state */
+} sf_status;
+
+/* Linearisation of the robust data terms (Section 5, "square root of the
+ * residuals"): SF_IRLS gives each consistency check its own reweighted
+ * residual (same energy, same gradient); SF_SQRT_PAPER uses one residual
+ * sqrt(sum of penalties) per pixel and term, as the paper's residual count
+ * M = 2N + 14G implies. */
+enum { SF_IRLS = 0, SF_SQRT_PAPER = 1 };
+/* Penalty of the gradient term (Eq. 13): SF_GRAD_BROX = sqrt(|g|^2 + eps^2),
+ * SF_GRAD_LITERAL = sqrt(|g|^4 + eps^2) as printed. */
+enum { SF_GRAD_BROX = 0, SF_GRAD_LITERAL = 1 };
+/* Feature weight w_i of the smoothness term (Section 4.3). */
+enum { SF_WFEAT_EIG = 0, SF_WFEAT_OFF = 1 };
+/* Initialisation of frames after the first (Section 5.3). */
+enum { SF_TEMPORAL_PROPAGATE = 0, SF_TEMPORAL_COPY = 1, SF_TEMPORAL_ZERO = 2 };
+/* Storage precision of the image pyramid; residuals and all accumulation
+ * stay in FP32. */
+enum { SF_FP32 = 0, SF_MIXED_BF16 = 1 };
+/* Columns of Table 1 (Appendix A). */
+enum { SF_PRESET_FIG2 = 0, SF_PRESET_FIG568 = 1, SF_PRESET_FIG79 = 2 };
+
+typedef struct sf_params {
+    /* Table 1 (Appendix A); w_smooth = w_mag = 1 in every experiment */
+    float w_reg, w_photo, w_grad, w_epi, w_smooth, w_mag;
+    float w_s, w_m, w_d; /* smoothness weight per flow (Eq. 14) */
+    float m_s, m_m, m_d; /* magnitude weight per flow (Eq. 18) */
+    float eps;           /* pseudo-Huber epsilon, 0.001 (Eq. 12) */
+    float eps_p;         /* outlier threshold of W, 0.2 (Section 4.1); <= 0 disables W */
+    float F[9];          /* fundamental matrix, row-major, finest-level pixels */
+    int gn_iters[SF_MAX_LEVELS];  /* Gauss-Newton steps per level, index 0 = finest */
+    int pcg_iters[SF_MAX_LEVELS]; /* PCG iterations per Gauss-Newton step */
+    int robust_mode;              /* SF_IRLS | SF_SQRT_PAPER */
+    int grad_mode;                /* SF_GRAD_BROX | SF_GRAD_LITERAL */
+    int wfeat_mode;               /* SF_WFEAT_EIG | SF_WFEAT_OFF */
+    float wfeat_gain, wfeat_tau;  /* w_i = 1 + gain * exp(-lambda_min / tau) */
+    int temporal_mode;            /* SF_TEMPORAL_* */
+    int precision;                /* SF_FP32 | SF_MIXED_BF16 */
+    int max_backtracks;           /* step halvings tried before a step is rejected (4) */
+    int use_graph;                /* 1: replay the frame as one captured CUDA graph */
+} sf_params;
+
+typedef struct sf_stats {
+    int status;                   /* latched device status (sf_status) */
+    int frames;                   /* frames solved since sf_create / sf_reset */
+    int levels;
+    int n_excluded;               /* finest-level pixels with W = 0 in the last step */
+    double energy;                /* final energy of the last frame (Eq. 8) */
+    double terms[5];              /* its weighted parts: photo, grad, smooth, epi, mag */
+    /* per level and Gauss-Newton step of the last frame */
+    double step_energy[SF_MAX_LEVELS][SF_MAX_GN];   /* at the linearisation point */
+    double step_accepted[SF_MAX_LEVELS][SF_MAX_GN]; /* after the step */
+    float step_t[SF_MAX_LEVELS][SF_MAX_GN];         /* accepted step length, 0 = rejected */
+    int step_excluded[SF_MAX_LEVELS][SF_MAX_GN];    /* pixels with W = 0 */
+} sf_stats;
+
+typedef struct sf_ctx sf_ctx;
+
+/* Fills *p with a column of Table 1 plus the defaults: eps 0.001, eps_p 0.2,
+ * rectified F = [[0,0,0],[0,0,-1],[0,1,0]], 3 Gauss-Newton steps x 20 PCG
+ * iterations on every level, IRLS, Brox gradient penalty, feature weight
+ * gain 9 and tau 0.001, constant-velocity temporal transfer, FP32, 4
+ * backtracks, graph replay on. Returns SF_ERR_ARG for an unknown preset. */
+SF_API int sf_params_preset(sf_params* p, int preset);
+
+/* Creates a solver for width x height inputs with warp-grid stride
+ * grid_stride (level pixels, same on every level) and `levels` pyramid
+ * levels (mip-map, factor 2, Section 5.3). Every level needs at least 2x2
+ * pixels and 2x2 grid nodes. Allocates all device memory. Returns NULL on
+ * error; sf_last_error() then tells why. */
+SF_API sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_params* p);
+
+/* Enqueues one frame on `stream`: pyramid, coarse-to-fine Gauss-Newton/PCG
+ * solve from the previous frame's state (zero for the first frame after
+ * create/reset), and writes the finest total fields to out_fields
+ * (device, float32 [6][ny][nx]). The four inputs are device pointers. */
+SF_API int sf_solve(sf_ctx* ctx, const float* L_t, const float* R_t, const float* L_t1, const float* R_t1,
+             float* out_fields, void* stream);
+
+/* The same from host memory: copies the four images in (host to device),
+ * solves, copies the fields out (device to host) and waits for the stream.
+ * Host buffers should be pinned for full copy speed. */
+SF_API int sf_solve_host(sf_ctx* ctx, const float* L_t, const float* R_t, const float* L_t1, const float* R_t1,
+                  float* out_fields, void* stream);
+
+/* Level geometry: image size and grid size of `level` (0 = finest). */
+SF_API int sf_grid_dims(const sf_ctx* ctx, int level, int* w, int* h, int* nx, int* ny);
+
+/* Sets the coarsest level's initial delta for the next sf_solve (6 x G device
+ * floats, the fields layout), replacing the temporal rule there once. */
+SF_API int sf_set_init(sf_ctx* ctx, const float* coarsest_delta, void* stream);
+
+/* Forgets the temporal state: the next frame starts from zero. */
+SF_API int sf_reset(sf_ctx* ctx);
+
+/* Waits for the context's work and copies its statistics. */
+SF_API int sf_get_stats(sf_ctx* ctx, sf_stats* out);
+
+/* Copies the final delta and total fields of `level` of the last frame into
+ * device buffers (6 x G floats each; either may be NULL). */
+SF_API int sf_get_state(sf_ctx* ctx, int level, float* delta, float* total, void* stream);
+
+SF_API void sf_destroy(sf_ctx* ctx);
+SF_API const char* sf_status_string(int status);
+SF_API int sf_last_error(void);
+
+/* ---- step-level entry points (parity tests and profiling) --------------
+ * Each runs one stage of the solve on the context's buffers for `level`,
+ * with caller-given state, on `stream`. All pointers are device pointers. */
+
+/* Builds the pyramid from four device images and copies level `level`'s
+ * planes out as float32 [4][3][h][w] (I, dI/dx, dI/dy per image). */
+SF_API int sf_probe_pyramid(sf_ctx* ctx, const float* L_t, const float* R_t, const float* L_t1, const float* R_t1,
+                     int level, float* planes, void* stream);
+
+/* Feature weights w_i (Section 4.3) at totals T (6 x G) on the current
+ * pyramid: writes G floats. */
+SF_API int sf_probe_feature_weights(sf_ctx* ctx, int level, const float* T, float* wfeat, void* stream);
+
+/* Assembles the Gauss-Newton system at base + delta (6 x G each) with
+ * feature weights wfeat (G) on the current pyramid, W taken at that state.
+ * Outputs: blocks (G x 5 x 36: the node's own 6x6 block and those coupling
+ * it to its E, S, SE and SW neighbours, row-major), rhs (G x 6), energy
+ * (1 double: the energy at the state) and W (h*w bytes). */
+SF_API int sf_probe_assemble(sf_ctx* ctx, int level, const float* base, const float* delta, const float* wfeat,
+                      float* blocks, float* rhs, double* energy, unsigned char* W, void* stream);
+
+/* Runs `iters` PCG iterations on the system last assembled for `level`
+ * (by sf_probe_assemble) and writes the solution (G x 6). */
+SF_API int sf_probe_pcg(sf_ctx* ctx, int level, int iters, float* x, void* stream);
+
+/* Copies the outlier mask W (Section 4.1) that Gauss-Newton step `step` of
+ * `level` used in the last frame (h*w bytes, 1 = kept, 0 = pruned). */
+SF_API int sf_probe_wmask(sf_ctx* ctx, int level, int step, unsigned char* W, void* stream);
+
+/* Energy (Eq. 8) at base + delta with W given (h*w bytes, NULL: taken at the
+ * state) and feature weights wfeat; writes 6 doubles: total, then the
+ * weighted photo, grad, smooth, epi and mag parts. */
+SF_API int sf_probe_energy(sf_ctx* ctx, int level, const float* base, const float* delta, const float* wfeat,
+                    const unsigned char* W, double* out6, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SF_H */

@@ -165,7 +165,7 @@ def lib():
         L.sfo_temporal.argtypes = [i, i, i, dp, dp, i, dp]
         L.sfo_packed_size.argtypes = [i, i, i, i]
         L.sfo_packed_size.restype = ctypes.c_long
-        L.sfo_solve_frame.argtypes = [i, i, i, i, pp, dp, dp, dp, dp, dp, dp, dp]
+        L.sfo_solve_frame.argtypes = [i, i, i, i, pp, dp, dp, dp, dp, up, dp, dp, dp]
         L.sfo_solve_frame.restype = i
         _lib = L
     return _lib
@@ -394,18 +394,31 @@ class FrameResult:
 
 
 def solve_frame(imgs4: np.ndarray, s: int, levels: int, p: Params, prev: FrameResult | None = None,
-                init_coarsest: np.ndarray | None = None) -> FrameResult:
-    """Algorithm 1 for one quadruple (without occlusion and illumination maps)."""
+                init_coarsest: np.ndarray | None = None, W_given: list | None = None) -> FrameResult:
+    """Algorithm 1 for one quadruple (without occlusion and illumination maps).
+
+    W_given: optional outlier masks to use instead of taking W in FP64, as
+    W_given[level][step] arrays of the level's image shape."""
     imgs4 = _f64(imgs4)
     _, h, w = imgs4.shape
     n = int(lib().sfo_packed_size(w, h, s, levels))
     delta, total, stats = np.zeros(n), np.zeros(n), np.zeros(STATS_LEN)
     pc = p.to_c()
     ic = None if init_coarsest is None else _f64(init_coarsest).reshape(-1)
+    wg = None
+    if W_given is not None:
+        parts = []
+        for l in range(levels):
+            lw, lh = level_dims(w, h, l)
+            for g in range(p.gn_iters[l]):
+                m = np.ascontiguousarray(W_given[l][g], dtype=np.uint8).reshape(-1)
+                assert m.size == lw * lh
+                parts.append(m)
+        wg = np.ascontiguousarray(np.concatenate(parts) if parts else np.zeros(1, np.uint8))
     rc = lib().sfo_solve_frame(w, h, s, levels, ctypes.byref(pc), _d(imgs4),
                                _d(prev.delta) if prev is not None else None,
                                _d(prev.total) if prev is not None else None,
-                               _d(ic), _d(delta), _d(total), _d(stats))
+                               _d(ic), _u8(wg), _d(delta), _d(total), _d(stats))
     if rc != 0:
         raise ValueError("invalid sizes for the oracle solve")
     return FrameResult(delta, total, stats, packed_offsets(w, h, s, levels))

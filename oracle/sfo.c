@@ -680,6 +680,34 @@ void sfo_temporal(int s, int nx, int ny, const double* delta_prev, const double*
         }
 }
 
+/* Compares a given outlier mask with the one this oracle takes at the state
+ * base + delta: returns the number of pixels that differ and, in *margin, the
+ * largest distance | max_k |e_k| - eps_p | among them (how far from the
+ * threshold the two decisions part). */
+static int w_disagreement(int w, int h, int s, int nx, int ny, const double* planes, const double* base,
+                          const double* delta, const unsigned char* Wg, const sfo_params* p, double* margin)
+{
+    int G = nx * ny, n = 0;
+    double* T = (double*)malloc(sizeof(double) * 6 * G);
+    for (int a = 0; a < 6 * G; ++a) T[a] = base[a] + delta[a];
+    *margin = 0.0;
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            double f[6], e[6], g[12];
+            pixel_fields(x, y, s, nx, ny, T, f);
+            sfo_pixel_terms(w, h, planes, x, y, f, e, g, NULL, NULL);
+            if (outlier_weight(e, p->eps_p) != Wg[y * w + x]) {
+                double mx = 0.0;
+                for (int k = 0; k < 6; ++k)
+                    if (fabs(e[k]) > mx) mx = fabs(e[k]);
+                if (fabs(mx - p->eps_p) > *margin) *margin = fabs(mx - p->eps_p);
+                ++n;
+            }
+        }
+    free(T);
+    return n;
+}
+
 /* ------------------------------------------------------------------------ */
 /* One frame: Algorithm 1 without the occlusion and illumination maps        */
 /* ------------------------------------------------------------------------ */
@@ -704,19 +732,24 @@ long sfo_packed_size(int w0, int h0, int s, int levels)
  *                 (overrides the temporal rule there), or NULL
  *   out_delta,    packed per-level final deltas and totals
  *   out_total
+ *   W_given       optional outlier masks to use instead of taking W here:
+ *                 for l = 0..L-1 and g = 0..gn_iters[l]-1 one w_l*h_l byte
+ *                 mask each, in that order; NULL to take W at each state
  *   stats         SFO_STATS_LEN doubles: [0] final energy, [1..5] its terms,
  *                 [6] pixels with W = 0 in the last step; at 16 + (l*16+g)*8:
  *                 E at the linearisation point, E accepted, step t (0 if
- *                 rejected), pixels with W = 0, PCG iterations run.
+ *                 rejected), pixels with W = 0, PCG iterations run, and with
+ *                 W_given the pixels whose given W differs from the one taken
+ *                 here and the largest | max_k |e_k| - eps_p | among them.
  * Returns 0, or -1 for invalid sizes. */
 int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const double* imgs,
                     const double* prev_delta, const double* prev_total, const double* init_coarsest,
-                    double* out_delta, double* out_total, double* stats)
+                    const unsigned char* W_given, double* out_delta, double* out_total, double* stats)
 {
     if (L < 1 || L > SFO_MAX_LEVELS || s < 1) return -1;
     int W[SFO_MAX_LEVELS], H[SFO_MAX_LEVELS], NX[SFO_MAX_LEVELS], NY[SFO_MAX_LEVELS];
-    long off[SFO_MAX_LEVELS];
-    long acc = 0;
+    long off[SFO_MAX_LEVELS], woff[SFO_MAX_LEVELS];
+    long acc = 0, wacc = 0;
     for (int l = 0; l < L; ++l) {
         sfo_level_dims(w0, h0, l, &W[l], &H[l]);
         NX[l] = (W[l] + s - 1) / s;
@@ -724,6 +757,8 @@ int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const dou
         if (W[l] < 2 || H[l] < 2 || NX[l] < 2 || NY[l] < 2) return -1;
         off[l] = acc;
         acc += 6L * NX[l] * NY[l];
+        woff[l] = wacc;
+        wacc += (long)p->gn_iters[l] * W[l] * H[l];
     }
     if (stats) memset(stats, 0, sizeof(double) * SFO_STATS_LEN);
 
@@ -766,7 +801,11 @@ int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const dou
         unsigned char* Wm = (unsigned char*)malloc((size_t)w * h);
         int have_W = 0;
         for (int g = 0; g < p->gn_iters[l] && g < SFO_MAX_GN; ++g) {
-            double Ecur = sfo_assemble(w, h, s, nx, ny, l, planes, base, delta, wf, NULL, p, A, b, Wm);
+            const unsigned char* Wg = W_given ? W_given + woff[l] + (long)g * w * h : NULL;
+            int ndis = 0;
+            double margin = 0.0;
+            if (Wg) ndis = w_disagreement(w, h, s, nx, ny, planes, base, delta, Wg, p, &margin);
+            double Ecur = sfo_assemble(w, h, s, nx, ny, l, planes, base, delta, wf, Wg, p, A, b, Wm);
             have_W = 1;
             int nexcl = 0;
             for (int a = 0; a < w * h; ++a) nexcl += Wm[a] == 0;
@@ -792,6 +831,8 @@ int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const dou
                 st[2] = tacc;
                 st[3] = nexcl;
                 st[4] = its;
+                st[5] = ndis;
+                st[6] = margin;
             }
         }
         if (l == 0 && stats) {

@@ -1,0 +1,602 @@
+// sf_capi.cu -- the C ABI of include/sf.h: context creation (all device
+// memory up front), argument validation, the per-frame launch sequence of
+// Algorithm 1 (Thies et al., arXiv 1610.07159) without the occlusion and
+// illumination maps, its capture into one CUDA graph, statistics and the
+// step-level probe entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sf_launch.h"
+
+using namespace sfk;
+
+namespace {
+
+thread_local int g_last_error = SF_OK;
+
+struct LevelBuf {
+    float4* tex = nullptr;
+    uint8_t* W = nullptr;
+    float* H = nullptr;
+    float *base = nullptr, *delta = nullptr, *x = nullptr, *wf = nullptr;
+    float *prev_delta = nullptr, *prev_total = nullptr;
+    float *node = nullptr, *rhs = nullptr, *minv = nullptr;
+    float *z = nullptr, *p0 = nullptr, *p1 = nullptr;
+    float* cell = nullptr;
+};
+
+__global__ void k_set_args(DevArgs* a, const float* i0, const float* i1, const float* i2, const float* i3, float* out,
+                           int frame, int use_init)
+{
+    a->in[0] = i0;
+    a->in[1] = i1;
+    a->in[2] = i2;
+    a->in[3] = i3;
+    a->out = out;
+    a->frame = frame;
+    a->use_init = use_init;
+}
+
+} // namespace
+
+struct sf_ctx {
+    int w0 = 0, h0 = 0, s = 0, L = 0;
+    sf_params prm{};
+    LevelGeom geo[SF_MAX_LEVELS]{};
+    LevelBuf lv[SF_MAX_LEVELS];
+    DevParams dp[SF_MAX_LEVELS]{};
+    PcgPlan plan[SF_MAX_LEVELS]{};
+    int asm_blocks[SF_MAX_LEVELS]{};
+    int sm_count = 0;
+    Scratch sc{};
+    double* pcg_part = nullptr;
+    unsigned* bar = nullptr;
+    StepCtrl* ctrl = nullptr; // [SF_MAX_LEVELS * SF_MAX_GN + 1], the last one for probes
+    double* rec = nullptr;    // [8] energy record
+    DevArgs* args = nullptr;
+    float* init_buf = nullptr;
+    int pending_init = 0;
+    float* in_buf[4] = {nullptr, nullptr, nullptr, nullptr};
+    float* out_buf = nullptr;
+    int frames = 0;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_tried = false;
+    cudaStream_t cap = nullptr;
+    cudaStream_t last_stream = nullptr;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+int fail(int code)
+{
+    g_last_error = code;
+    return code;
+}
+
+template <typename T>
+bool dalloc(sf_ctx* c, T** p, size_t count)
+{
+    void* q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T) + 16) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaMemset(q, 0, count * sizeof(T) + 16);
+    c->allocs.push_back(q);
+    *p = (T*)q;
+    return true;
+}
+
+void free_ctx(sf_ctx* c)
+{
+    if (!c) return;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    for (void* p : c->allocs) cudaFree(p);
+    delete c;
+}
+
+DevParams make_dev_params(const sf_params& p, int level)
+{
+    DevParams d{};
+    d.w_reg = p.w_reg;
+    d.w_photo = p.w_photo;
+    d.w_grad = p.w_grad;
+    d.w_epi = p.w_epi;
+    d.w_smooth = p.w_smooth;
+    d.w_mag = p.w_mag;
+    d.wfl[0] = p.w_s;
+    d.wfl[1] = p.w_m;
+    d.wfl[2] = p.w_d;
+    d.mfl[0] = p.m_s;
+    d.mfl[1] = p.m_m;
+    d.mfl[2] = p.m_d;
+    d.eps = p.eps;
+    d.eps_p = p.eps_p;
+    // F in level pixels: S F S rescaled to the Frobenius norm of F, S = diag(2^l, 2^l, 1)
+    double sc[3] = {std::ldexp(1.0, level), std::ldexp(1.0, level), 1.0};
+    double Fl[9], n0 = 0.0, n1 = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            Fl[a * 3 + b] = sc[a] * (double)p.F[a * 3 + b] * sc[b];
+            n0 += (double)p.F[a * 3 + b] * p.F[a * 3 + b];
+            n1 += Fl[a * 3 + b] * Fl[a * 3 + b];
+        }
+    for (int a = 0; a < 9; ++a) d.Fl[a] = (float)(n1 > 0.0 ? Fl[a] * std::sqrt(n0 / n1) : Fl[a]);
+    d.robust_mode = p.robust_mode;
+    d.grad_mode = p.grad_mode;
+    d.wfeat_mode = p.wfeat_mode;
+    d.wfeat_gain = p.wfeat_gain;
+    d.wfeat_tau = p.wfeat_tau;
+    return d;
+}
+
+bool finite_params(const sf_params& p)
+{
+    const float v[] = {p.w_reg, p.w_photo, p.w_grad, p.w_epi, p.w_smooth, p.w_mag, p.w_s, p.w_m, p.w_d,
+                       p.m_s, p.m_m, p.m_d, p.eps, p.eps_p, p.wfeat_gain, p.wfeat_tau};
+    for (float x : v)
+        if (!std::isfinite(x)) return false;
+    for (float x : p.F)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+int check_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return SF_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? SF_ERR_OOM : SF_ERR_CUDA;
+}
+
+// Enqueues one frame of Algorithm 1 on `st` (the inputs come through args).
+int enqueue_frame(sf_ctx* c, cudaStream_t st)
+{
+    const sf_params& P = c->prm;
+    launch_tex0(c->args, nullptr, c->w0, c->h0, c->lv[0].tex, st);
+    for (int l = 1; l < c->L; ++l)
+        launch_texdown(c->lv[l - 1].tex, c->geo[l - 1].w, c->geo[l - 1].h, c->lv[l].tex, c->geo[l].w, c->geo[l].h, st);
+    for (int l = c->L - 1; l >= 0; --l) {
+        const LevelGeom& g = c->geo[l];
+        LevelBuf& b = c->lv[l];
+        const bool has_c = l < c->L - 1;
+        launch_level_init(g, has_c ? &c->geo[l + 1] : nullptr, has_c ? c->lv[l + 1].base : nullptr,
+                          has_c ? c->lv[l + 1].delta : nullptr, b.base, b.delta, b.prev_delta, b.prev_total,
+                          c->init_buf, c->args, P.temporal_mode, st);
+        if (P.wfeat_mode == SF_WFEAT_EIG) {
+            launch_halfway(g, b.tex, b.base, b.delta, b.H, st);
+            launch_wfeat(g, b.H, c->dp[l], b.wf, st);
+        }
+        for (int gi = 0; gi < P.gn_iters[l]; ++gi) {
+            StepCtrl* ctrl = c->ctrl + l * SF_MAX_GN + gi;
+            uint8_t* Wst = b.W + (size_t)gi * g.w * g.h; // this step's outlier mask, kept for inspection
+            launch_assemble(g, b.tex, b.base, b.delta, c->dp[l], Wst, b.cell, c->sc, st);
+            launch_gather(g, b.cell, b.base, b.delta, b.wf, c->dp[l], b.node, b.rhs, b.minv, c->sc, ctrl,
+                          c->asm_blocks[l], st);
+            cudaError_t e = launch_pcg(g, c->plan[l], b.node, b.rhs, b.minv, b.x, b.z, b.p0, b.p1, c->pcg_part, c->bar,
+                                       c->sc.status, P.pcg_iters[l], 0, st);
+            if (e != cudaSuccess) return check_cuda(e);
+            float t = 1.f;
+            for (int j = 0; j <= P.max_backtracks; ++j, t *= 0.5f)
+                launch_energy(g, b.tex, b.base, b.delta, b.x, t, b.wf, c->dp[l], Wst, 0, c->sc, ctrl, 1,
+                              j == P.max_backtracks, nullptr, st);
+            launch_apply_step(g, b.delta, b.x, ctrl, st);
+        }
+        if (l == 0 && P.gn_iters[0] == 0)
+            launch_energy(g, b.tex, b.base, b.delta, nullptr, 0.f, b.wf, c->dp[0], b.W, 1, c->sc, nullptr, 0, 0,
+                          c->rec, st);
+        launch_finish_level(g, b.base, b.delta, b.prev_delta, b.prev_total, c->args, l == 0, st);
+    }
+    return check_cuda(cudaGetLastError());
+}
+
+} // namespace
+
+extern "C" {
+
+int sf_params_preset(sf_params* p, int preset)
+{
+    if (!p) return fail(SF_ERR_ARG);
+    std::memset(p, 0, sizeof(*p));
+    // Table 1 (Appendix A)
+    static const float tab[3][10] = {
+        {1.0f, 1.0f, 2.0f, 0.0f, 5.0f, 5.0f, 0.5f, 5.0f, 100.0f, 1000.0f},
+        {0.5f, 0.5f, 5.0f, 0.5f, 0.75f, 0.5f, 0.01f, 0.5f, 10.0f, 100.0f},
+        {5.0f, 1.0f, 5.0f, 0.5f, 0.5f, 1.0f, 1.0f, 0.1f, 10000.0f, 10000.0f},
+    };
+    if (preset < 0 || preset > 2) return fail(SF_ERR_ARG);
+    const float* t = tab[preset];
+    p->w_reg = t[0];
+    p->w_photo = t[1];
+    p->w_grad = t[2];
+    p->w_epi = t[3];
+    p->w_s = t[4];
+    p->w_m = t[5];
+    p->w_d = t[6];
+    p->m_s = t[7];
+    p->m_m = t[8];
+    p->m_d = t[9];
+    p->w_smooth = 1.0f;
+    p->w_mag = 1.0f;
+    p->eps = 1e-3f;
+    p->eps_p = 0.2f;
+    const float F[9] = {0, 0, 0, 0, 0, -1, 0, 1, 0};
+    std::memcpy(p->F, F, sizeof(F));
+    for (int l = 0; l < SF_MAX_LEVELS; ++l) {
+        p->gn_iters[l] = 3;
+        p->pcg_iters[l] = 20;
+    }
+    p->robust_mode = SF_IRLS;
+    p->grad_mode = SF_GRAD_BROX;
+    p->wfeat_mode = SF_WFEAT_EIG;
+    p->wfeat_gain = 9.0f;
+    p->wfeat_tau = 1e-3f;
+    p->temporal_mode = SF_TEMPORAL_PROPAGATE;
+    p->precision = SF_FP32;
+    p->max_backtracks = 4;
+    p->use_graph = 1;
+    return SF_OK;
+}
+
+sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_params* p)
+{
+    g_last_error = SF_OK;
+    if (!p || width < 2 || height < 2 || grid_stride < 1 || levels < 1 || levels > SF_MAX_LEVELS ||
+        width > (1 << 15) || height > (1 << 15) || grid_stride > 256 || !finite_params(*p) || !(p->eps > 0.f) ||
+        p->max_backtracks < 0 || p->max_backtracks > 8 || p->robust_mode < 0 || p->robust_mode > 1 ||
+        p->grad_mode < 0 || p->grad_mode > 1 || p->wfeat_mode < 0 || p->wfeat_mode > 1 || p->temporal_mode < 0 ||
+        p->temporal_mode > 2 || p->precision != SF_FP32 || !(p->wfeat_tau > 0.f)) {
+        fail(SF_ERR_ARG);
+        return nullptr;
+    }
+    for (int l = 0; l < levels; ++l)
+        if (p->gn_iters[l] < 0 || p->gn_iters[l] > SF_MAX_GN || p->pcg_iters[l] < 0 || p->pcg_iters[l] > 100000) {
+            fail(SF_ERR_ARG);
+            return nullptr;
+        }
+    sf_ctx* c = new (std::nothrow) sf_ctx();
+    if (!c) {
+        fail(SF_ERR_OOM);
+        return nullptr;
+    }
+    c->w0 = width;
+    c->h0 = height;
+    c->s = grid_stride;
+    c->L = levels;
+    c->prm = *p;
+    int w = width, h = height;
+    for (int l = 0; l < levels; ++l) {
+        if (l > 0) {
+            w = (w + 1) / 2;
+            h = (h + 1) / 2;
+        }
+        LevelGeom& g = c->geo[l];
+        g.w = w;
+        g.h = h;
+        g.s = grid_stride;
+        g.nx = (w + grid_stride - 1) / grid_stride;
+        g.ny = (h + grid_stride - 1) / grid_stride;
+        g.G = g.nx * g.ny;
+        g.ncx = g.nx - 1;
+        g.ncy = g.ny - 1;
+        g.level = l;
+        const int en_blocks = std::min((g.w * g.h + 255) / 256, 152 * 8) + (g.G + 255) / 256;
+        if (w < 2 || h < 2 || g.nx < 2 || g.ny < 2 || assemble_blocks(g, nullptr) > MAX_PART || en_blocks > MAX_PART) {
+            delete c;
+            fail(SF_ERR_ARG);
+            return nullptr;
+        }
+        c->dp[l] = make_dev_params(*p, l);
+        c->asm_blocks[l] = assemble_blocks(g, nullptr);
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        fail(SF_ERR_CUDA);
+        return nullptr;
+    }
+    for (int l = 0; l < levels; ++l) {
+        c->plan[l] = pcg_plan(c->geo[l].G, c->sm_count);
+        if (c->plan[l].blocks < 1) {
+            delete c;
+            fail(SF_ERR_ARG);
+            return nullptr;
+        }
+    }
+    bool ok = true;
+    for (int l = 0; l < levels && ok; ++l) {
+        const LevelGeom& g = c->geo[l];
+        LevelBuf& b = c->lv[l];
+        const size_t N = (size_t)g.w * g.h, G6 = (size_t)6 * g.G;
+        ok = dalloc(c, &b.tex, 4 * N) && dalloc(c, &b.W, N * (size_t)std::max(1, p->gn_iters[l])) && dalloc(c, &b.H, N) && dalloc(c, &b.base, G6) &&
+             dalloc(c, &b.delta, G6) && dalloc(c, &b.x, G6) && dalloc(c, &b.wf, (size_t)g.G) &&
+             dalloc(c, &b.prev_delta, G6) && dalloc(c, &b.prev_total, G6) &&
+             dalloc(c, &b.node, (size_t)NODE_VALS * g.G) && dalloc(c, &b.rhs, G6) && dalloc(c, &b.minv, G6) &&
+             dalloc(c, &b.z, G6) && dalloc(c, &b.p0, G6) && dalloc(c, &b.p1, G6) &&
+             dalloc(c, &b.cell, (size_t)CELL_VALS * (g.ncx * g.ncy));
+    }
+    const size_t N0 = (size_t)width * height;
+    ok = ok && dalloc(c, &c->sc.asm_part, 3 * (size_t)MAX_PART) && dalloc(c, &c->sc.gat_part, 3 * (size_t)MAX_PART) &&
+         dalloc(c, &c->sc.en_part, 6 * (size_t)MAX_PART) && dalloc(c, &c->sc.counters, 8) &&
+         dalloc(c, &c->sc.status, 4) && dalloc(c, &c->pcg_part, 2 * (size_t)MAX_PART) && dalloc(c, &c->bar, 4) &&
+         dalloc(c, &c->ctrl, (size_t)SF_MAX_LEVELS * SF_MAX_GN + 1) && dalloc(c, &c->rec, 8) &&
+         dalloc(c, &c->args, 1) && dalloc(c, &c->init_buf, (size_t)6 * c->geo[levels - 1].G) &&
+         dalloc(c, &c->in_buf[0], N0) && dalloc(c, &c->in_buf[1], N0) && dalloc(c, &c->in_buf[2], N0) &&
+         dalloc(c, &c->in_buf[3], N0) && dalloc(c, &c->out_buf, (size_t)6 * c->geo[0].G);
+    if (!ok) {
+        free_ctx(c);
+        fail(SF_ERR_OOM);
+        return nullptr;
+    }
+    if (p->wfeat_mode == SF_WFEAT_OFF)
+        for (int l = 0; l < levels; ++l) launch_fill(c->lv[l].wf, 1.f, (size_t)c->geo[l].G, 0);
+    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(c);
+        fail(SF_ERR_CUDA);
+        return nullptr;
+    }
+    return c;
+}
+
+int sf_solve(sf_ctx* c, const float* L_t, const float* R_t, const float* L_t1, const float* R_t1, float* out_fields,
+             void* stream)
+{
+    if (!c || !L_t || !R_t || !L_t1 || !R_t1 || !out_fields) return fail(SF_ERR_ARG);
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    k_set_args<<<1, 1, 0, st>>>(c->args, L_t, R_t, L_t1, R_t1, out_fields, c->frames, c->pending_init);
+    int rc = check_cuda(cudaGetLastError());
+    if (rc) return fail(rc);
+    if (c->prm.use_graph && !c->graph_tried) {
+        c->graph_tried = true;
+        cudaGraph_t graph = nullptr;
+        bool ok = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        int erc = ok ? enqueue_frame(c, c->cap) : SF_ERR_CUDA;
+        ok = cudaStreamEndCapture(c->cap, &graph) == cudaSuccess && ok && erc == SF_OK;
+        ok = ok && cudaGraphInstantiate(&c->gexec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        if (!ok) {
+            cudaGetLastError();
+            if (c->gexec) cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+            c->prm.use_graph = 0; // launch kernel by kernel instead
+        }
+    }
+    if (c->gexec)
+        rc = check_cuda(cudaGraphLaunch(c->gexec, st));
+    else
+        rc = enqueue_frame(c, st);
+    if (rc) return fail(rc);
+    c->frames += 1;
+    c->pending_init = 0;
+    return SF_OK;
+}
+
+int sf_solve_host(sf_ctx* c, const float* L_t, const float* R_t, const float* L_t1, const float* R_t1,
+                  float* out_fields, void* stream)
+{
+    if (!c || !L_t || !R_t || !L_t1 || !R_t1 || !out_fields) return fail(SF_ERR_ARG);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)c->w0 * c->h0 * sizeof(float);
+    const float* src[4] = {L_t, R_t, L_t1, R_t1};
+    for (int k = 0; k < 4; ++k) {
+        int rc = check_cuda(cudaMemcpyAsync(c->in_buf[k], src[k], bytes, cudaMemcpyHostToDevice, st));
+        if (rc) return fail(rc);
+    }
+    int rc = sf_solve(c, c->in_buf[0], c->in_buf[1], c->in_buf[2], c->in_buf[3], c->out_buf, stream);
+    if (rc) return rc;
+    rc = check_cuda(cudaMemcpyAsync(out_fields, c->out_buf, (size_t)6 * c->geo[0].G * sizeof(float),
+                                    cudaMemcpyDeviceToHost, st));
+    if (rc) return fail(rc);
+    rc = check_cuda(cudaStreamSynchronize(st));
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_grid_dims(const sf_ctx* c, int level, int* w, int* h, int* nx, int* ny)
+{
+    if (!c || level < 0 || level >= c->L) return fail(SF_ERR_ARG);
+    if (w) *w = c->geo[level].w;
+    if (h) *h = c->geo[level].h;
+    if (nx) *nx = c->geo[level].nx;
+    if (ny) *ny = c->geo[level].ny;
+    return SF_OK;
+}
+
+int sf_set_init(sf_ctx* c, const float* coarsest_delta, void* stream)
+{
+    if (!c || !coarsest_delta) return fail(SF_ERR_ARG);
+    const size_t bytes = (size_t)6 * c->geo[c->L - 1].G * sizeof(float);
+    int rc = check_cuda(cudaMemcpyAsync(c->init_buf, coarsest_delta, bytes, cudaMemcpyDeviceToDevice,
+                                        (cudaStream_t)stream));
+    if (rc) return fail(rc);
+    c->pending_init = 1;
+    return SF_OK;
+}
+
+int sf_reset(sf_ctx* c)
+{
+    if (!c) return fail(SF_ERR_ARG);
+    c->frames = 0;
+    c->pending_init = 0;
+    int rc = check_cuda(cudaDeviceSynchronize());
+    if (!rc) rc = check_cuda(cudaMemset(c->sc.status, 0, 4 * sizeof(int)));
+    if (!rc) rc = check_cuda(cudaMemset(c->bar, 0, 4 * sizeof(unsigned)));
+    if (!rc) rc = check_cuda(cudaMemset(c->sc.counters, 0, 8 * sizeof(unsigned)));
+    if (!rc) rc = check_cuda(cudaDeviceSynchronize());
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_get_stats(sf_ctx* c, sf_stats* out)
+{
+    if (!c || !out) return fail(SF_ERR_ARG);
+    int rc = check_cuda(cudaDeviceSynchronize());
+    if (rc) return fail(rc);
+    std::vector<StepCtrl> h((size_t)SF_MAX_LEVELS * SF_MAX_GN + 1);
+    int status = 0;
+    double rec[8];
+    rc = check_cuda(cudaMemcpy(h.data(), c->ctrl, h.size() * sizeof(StepCtrl), cudaMemcpyDeviceToHost));
+    if (!rc) rc = check_cuda(cudaMemcpy(&status, c->sc.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!rc) rc = check_cuda(cudaMemcpy(rec, c->rec, sizeof(rec), cudaMemcpyDeviceToHost));
+    if (rc) return fail(rc);
+    std::memset(out, 0, sizeof(*out));
+    out->status = (status & DEV_TIMEOUT) ? SF_ERR_TIMEOUT : (status & DEV_NUMERIC) ? SF_ERR_NUMERIC : SF_OK;
+    out->frames = c->frames;
+    out->levels = c->L;
+    for (int l = 0; l < c->L; ++l)
+        for (int g = 0; g < c->prm.gn_iters[l] && g < SF_MAX_GN; ++g) {
+            const StepCtrl& s = h[l * SF_MAX_GN + g];
+            out->step_energy[l][g] = s.E_cur;
+            out->step_accepted[l][g] = s.E_acc;
+            out->step_t[l][g] = s.accepted ? s.t : 0.f;
+            out->step_excluded[l][g] = s.n_excluded;
+        }
+    const int g0 = c->prm.gn_iters[0];
+    if (g0 > 0) {
+        const StepCtrl& s = h[g0 - 1];
+        out->energy = s.E_acc;
+        for (int q = 0; q < 5; ++q) out->terms[q] = s.terms_acc[q];
+        out->n_excluded = s.n_excluded;
+    } else {
+        out->energy = rec[0];
+        for (int q = 0; q < 5; ++q) out->terms[q] = rec[1 + q];
+        out->n_excluded = (int)rec[6];
+    }
+    return out->status;
+}
+
+int sf_get_state(sf_ctx* c, int level, float* delta, float* total, void* stream)
+{
+    if (!c || level < 0 || level >= c->L) return fail(SF_ERR_ARG);
+    const size_t bytes = (size_t)6 * c->geo[level].G * sizeof(float);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = SF_OK;
+    if (delta) rc = check_cuda(cudaMemcpyAsync(delta, c->lv[level].prev_delta, bytes, cudaMemcpyDeviceToDevice, st));
+    if (!rc && total)
+        rc = check_cuda(cudaMemcpyAsync(total, c->lv[level].prev_total, bytes, cudaMemcpyDeviceToDevice, st));
+    return rc ? fail(rc) : SF_OK;
+}
+
+void sf_destroy(sf_ctx* c)
+{
+    if (!c) return;
+    cudaDeviceSynchronize();
+    free_ctx(c);
+}
+
+const char* sf_status_string(int s)
+{
+    switch (s) {
+    case SF_OK: return "ok";
+    case SF_ERR_ARG: return "invalid argument";
+    case SF_ERR_CUDA: return "CUDA runtime error";
+    case SF_ERR_OOM: return "out of memory";
+    case SF_ERR_NUMERIC: return "non-finite energy";
+    case SF_ERR_TIMEOUT: return "device barrier timeout";
+    case SF_ERR_STATE: return "invalid state";
+    default: return "unknown status";
+    }
+}
+
+int sf_last_error(void) { return g_last_error; }
+
+// ---- step-level probes ---------------------------------------------------
+
+int sf_probe_pyramid(sf_ctx* c, const float* L_t, const float* R_t, const float* L_t1, const float* R_t1, int level,
+                     float* planes, void* stream)
+{
+    if (!c || !L_t || !R_t || !L_t1 || !R_t1 || !planes || level < 0 || level >= c->L) return fail(SF_ERR_ARG);
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    const float* in[4] = {L_t, R_t, L_t1, R_t1};
+    launch_tex0(nullptr, in, c->w0, c->h0, c->lv[0].tex, st);
+    for (int l = 1; l < c->L; ++l)
+        launch_texdown(c->lv[l - 1].tex, c->geo[l - 1].w, c->geo[l - 1].h, c->lv[l].tex, c->geo[l].w, c->geo[l].h, st);
+    launch_unpack_tex(c->lv[level].tex, c->geo[level].w, c->geo[level].h, planes, st);
+    int rc = check_cuda(cudaGetLastError());
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_probe_feature_weights(sf_ctx* c, int level, const float* T, float* wfeat, void* stream)
+{
+    if (!c || !T || !wfeat || level < 0 || level >= c->L) return fail(SF_ERR_ARG);
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    const LevelGeom& g = c->geo[level];
+    launch_halfway(g, c->lv[level].tex, T, nullptr, c->lv[level].H, st);
+    launch_wfeat(g, c->lv[level].H, c->dp[level], wfeat, st);
+    int rc = check_cuda(cudaGetLastError());
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_probe_assemble(sf_ctx* c, int level, const float* base, const float* delta, const float* wfeat, float* blocks,
+                      float* rhs, double* energy, unsigned char* W, void* stream)
+{
+    if (!c || !base || !delta || !wfeat || level < 0 || level >= c->L) return fail(SF_ERR_ARG);
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    const LevelGeom& g = c->geo[level];
+    LevelBuf& b = c->lv[level];
+    StepCtrl* pc = c->ctrl + SF_MAX_LEVELS * SF_MAX_GN;
+    launch_assemble(g, b.tex, base, delta, c->dp[level], b.W, b.cell, c->sc, st);
+    launch_gather(g, b.cell, base, delta, wfeat, c->dp[level], b.node, b.rhs, b.minv, c->sc, pc, c->asm_blocks[level],
+                  st);
+    if (blocks && rhs) launch_unpack_blocks(g, b.node, b.rhs, blocks, rhs, st);
+    int rc = SF_OK;
+    if (energy) rc = check_cuda(cudaMemcpyAsync(energy, &pc->E_cur, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (!rc && W) rc = check_cuda(cudaMemcpyAsync(W, b.W, (size_t)g.w * g.h, cudaMemcpyDeviceToDevice, st));
+    if (!rc) rc = check_cuda(cudaGetLastError());
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_probe_pcg(sf_ctx* c, int level, int iters, float* x, void* stream)
+{
+    if (!c || !x || level < 0 || level >= c->L || iters < 0) return fail(SF_ERR_ARG);
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    const LevelGeom& g = c->geo[level];
+    LevelBuf& b = c->lv[level];
+    int rc = check_cuda(launch_pcg(g, c->plan[level], b.node, b.rhs, b.minv, x, b.z, b.p0, b.p1, c->pcg_part, c->bar,
+                                   c->sc.status, iters, 1, st));
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_probe_wmask(sf_ctx* c, int level, int step, unsigned char* W, void* stream)
+{
+    if (!c || !W || level < 0 || level >= c->L || step < 0 || step >= std::max(1, c->prm.gn_iters[level]))
+        return fail(SF_ERR_ARG);
+    const size_t N = (size_t)c->geo[level].w * c->geo[level].h;
+    int rc = check_cuda(cudaMemcpyAsync(W, c->lv[level].W + (size_t)step * N, N, cudaMemcpyDeviceToDevice,
+                                        (cudaStream_t)stream));
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_probe_energy(sf_ctx* c, int level, const float* base, const float* delta, const float* wfeat,
+                    const unsigned char* W, double* out6, void* stream)
+{
+    if (!c || !base || !delta || !wfeat || !out6 || level < 0 || level >= c->L) return fail(SF_ERR_ARG);
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    const LevelGeom& g = c->geo[level];
+    LevelBuf& b = c->lv[level];
+    int rc = SF_OK;
+    if (W) rc = check_cuda(cudaMemcpyAsync(b.W, W, (size_t)g.w * g.h, cudaMemcpyDeviceToDevice, st));
+    if (rc) return fail(rc);
+    launch_energy(g, b.tex, base, delta, nullptr, 0.f, wfeat, c->dp[level], b.W, W ? 0 : 1, c->sc, nullptr, 0, 0, c->rec,
+                  st);
+    rc = check_cuda(cudaMemcpyAsync(out6, c->rec, 6 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (!rc) rc = check_cuda(cudaGetLastError());
+    return rc ? fail(rc) : SF_OK;
+}
+
+} // extern "C"

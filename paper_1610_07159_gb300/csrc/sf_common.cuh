@@ -1,0 +1,316 @@
+// sf_common.cuh -- internal layouts and device helpers of the sm_103a
+// halfway-domain scene-flow solver (Thies et al., arXiv 1610.07159).
+//
+// Data layout in device memory (one set per hierarchy level):
+//   tex     float4 [4][h][w]: (I, dI/dx, dI/dy, 0) of the four images, so one
+//           16-byte load fetches a texel with its gradient (Section 5.3 pyramid)
+//   W       uint8  [h][w]: outlier weight of the current Gauss-Newton step
+//   base, delta, x      float [6][G] component-major node fields
+//   cell    float [CELL_VALS][ncell]: per warp-grid cell the ten symmetric 6x6
+//           blocks sum_p alpha_k alpha_l H_p over its pixels and the four
+//           6-vectors sum_p alpha_k b_p (Eq. 7 chain rule of Section 5.1)
+//   node    float [NODE_VALS][G]: per node its own block and those coupling it
+//           to the E, S, SE and SW neighbours (symmetric 6x6, 21 floats each);
+//           the W, N, NW and NE couplings are the neighbours' stored blocks
+//   rhs, minv, r, z, p0, p1   float [6][G] PCG vectors
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sf.h"
+
+namespace sfk {
+
+constexpr int NB = 21;                     // packed symmetric 6x6
+constexpr int NPAIR = 10;                  // corner pairs (k <= l) of a cell
+constexpr int CELL_VALS = NPAIR * NB + 24; // 234
+constexpr int NODE_BLKS = 5;               // self, E, S, SE, SW
+constexpr int NODE_VALS = NODE_BLKS * NB;  // 105
+constexpr int ASM_THREADS = 256;
+constexpr int MAX_PART = 16384;            // partial-sum slots per reduction
+
+// device status bits
+constexpr int DEV_TIMEOUT = 1;
+constexpr int DEV_NUMERIC = 2;
+
+struct LevelGeom {
+    int w, h;     // level image size
+    int nx, ny;   // grid nodes
+    int G;        // nx * ny
+    int ncx, ncy; // cells (nx - 1) x (ny - 1)
+    int s;        // grid stride (level pixels)
+    int level;
+};
+
+// Per-level parameters as the kernels use them.
+struct DevParams {
+    float w_reg, w_photo, w_grad, w_epi, w_smooth, w_mag;
+    float wfl[3];  // w_s, w_m, w_d
+    float mfl[3];  // m_s, m_m, m_d
+    float eps, eps_p;
+    float Fl[9];   // fundamental matrix in this level's pixels
+    int robust_mode, grad_mode, wfeat_mode;
+    float wfeat_gain, wfeat_tau;
+};
+
+// Control record of one Gauss-Newton step (one per level and step).
+struct StepCtrl {
+    double E_cur;        // energy at the linearisation point
+    double E_acc;        // energy after the step (E_cur if rejected)
+    double terms_cur[5]; // weighted photo, grad, smooth, epi, mag at the point
+    double terms_acc[5];
+    float t;             // accepted step length, 0 = rejected
+    int accepted;
+    int n_excluded;
+    int pad;
+};
+
+// Per-frame arguments read by the kernels of a captured graph.
+struct DevArgs {
+    const float* in[4];
+    float* out;
+    int frame;    // frames solved before this one
+    int use_init; // coarsest delta from the warm-start buffer
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+
+__host__ __device__ constexpr int sym_idx(int r, int c)
+{
+    return r <= c ? r * 6 - (r * (r - 1)) / 2 + (c - r) : c * 6 - (c * (c - 1)) / 2 + (r - c);
+}
+
+// Index of the corner pair (k, l) of a cell in the packed cell record.
+__host__ __device__ constexpr int pair_idx(int k, int l)
+{
+    return k <= l ? (k == 0 ? l : (k == 1 ? 3 + l : (k == 2 ? 5 + l : 9))) : pair_idx(l, k);
+}
+
+// Signs of (s, m, d) in each image's sample position (Eqs. 1-6):
+// image 0 at x-s-m+d, 1 at x+s-m-d, 2 at x-s+m-d, 3 at x+s+m+d.
+__host__ __device__ constexpr float sgn(int img, int fld)
+{
+    return (img == 0) ? (fld == 2 ? 1.f : -1.f)
+         : (img == 1) ? (fld == 0 ? 1.f : -1.f)
+         : (img == 2) ? (fld == 1 ? 1.f : -1.f)
+                      : 1.f;
+}
+
+// The six checks d_k = I_first - I_second of Eqs. 1-6.
+__host__ __device__ constexpr int chk_first(int k) { return k == 0 ? 1 : (k == 1 ? 3 : (k == 2 ? 2 : (k == 3 ? 3 : (k == 4 ? 3 : 2)))); }
+__host__ __device__ constexpr int chk_second(int k) { return k == 0 ? 0 : (k == 1 ? 2 : (k == 2 ? 0 : (k == 3 ? 1 : (k == 4 ? 0 : 1)))); }
+
+__device__ __forceinline__ void sym_rank1(float* H, const float* J, float w)
+{
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+        const float wr = w * J[r];
+#pragma unroll
+        for (int c = r; c < 6; ++c) H[sym_idx(r, c)] = fmaf(wr, J[c], H[sym_idx(r, c)]);
+    }
+}
+
+__device__ __forceinline__ void sym_matvec_acc(const float* B, const float* p, float* y)
+{
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+        float a = y[r];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) a = fmaf(B[sym_idx(r, c)], p[c], a);
+        y[r] = a;
+    }
+}
+
+// Cell and fraction along one axis of the sample position x + o (integer
+// pixel x, real offset o). The fraction comes from the offset alone, so it
+// keeps full FP32 precision however large x is. The position is clamped to
+// [0, w-1]; the cell is min(floor(p), w-2); `clamped` marks a clamped axis
+// (its derivative is 0). Offsets are limited to +-1e7 px first, which also
+// keeps the integer arithmetic in range for any input.
+__device__ __forceinline__ void axis_cell(int x, float o, int w, int& ix, float& f, bool& clamped)
+{
+    o = fminf(fmaxf(o, -1.0e7f), 1.0e7f);
+    const float fo = floorf(o);
+    const int pi = x + (int)fo;
+    const float fr = o - fo; // exact, in [0, 1)
+    if (pi < 0) {
+        ix = 0;
+        f = 0.f;
+        clamped = true;
+    } else if (pi > w - 1 || (pi == w - 1 && fr > 0.f)) {
+        ix = w - 2;
+        f = 1.f;
+        clamped = true;
+    } else if (pi == w - 1) {
+        ix = w - 2;
+        f = 1.f;
+        clamped = false;
+    } else {
+        ix = pi;
+        f = fr;
+        clamped = false;
+    }
+}
+
+// Bilinear sample of a texel plane (I, dI/dx, dI/dy) at (x + ox, y + oy)
+// with the derivative of the interpolant.
+struct Tap {
+    float v[3], dx[3], dy[3];
+};
+
+__device__ __forceinline__ void tap4(const float4* __restrict__ T, int w, int h, int x, int y, float ox, float oy,
+                                     Tap& o)
+{
+    int ix, iy;
+    float fx, fy;
+    bool clx, cly;
+    axis_cell(x, ox, w, ix, fx, clx);
+    axis_cell(y, oy, h, iy, fy, cly);
+    const float4* r0 = T + (size_t)iy * w + ix;
+    const float4 a = __ldg(r0), b = __ldg(r0 + 1), c = __ldg(r0 + w), d = __ldg(r0 + w + 1);
+    const float av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z}, cv[3] = {c.x, c.y, c.z}, dv[3] = {d.x, d.y, d.z};
+    const float gx = 1.f - fx, gy = 1.f - fy;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        float top = gx * av[p] + fx * bv[p];
+        float bot = gx * cv[p] + fx * dv[p];
+        o.v[p] = gy * top + fy * bot;
+        o.dx[p] = clx ? 0.f : gy * (bv[p] - av[p]) + fy * (dv[p] - cv[p]);
+        o.dy[p] = cly ? 0.f : bot - top;
+    }
+}
+
+// Intensity only (halfway image).
+__device__ __forceinline__ float tap1(const float4* __restrict__ T, int w, int h, int x, int y, float ox, float oy)
+{
+    int ix, iy;
+    float fx, fy;
+    bool clx, cly;
+    axis_cell(x, ox, w, ix, fx, clx);
+    axis_cell(y, oy, h, iy, fy, cly);
+    const float4* r0 = T + (size_t)iy * w + ix;
+    float a = __ldg(&r0->x), b = __ldg(&(r0 + 1)->x), c = __ldg(&(r0 + w)->x), d = __ldg(&(r0 + w + 1)->x);
+    float top = (1.f - fx) * a + fx * b, bot = (1.f - fx) * c + fx * d;
+    return (1.f - fy) * top + fy * bot;
+}
+
+// Bilinear weights of pixel (x, y) on the warp grid (Eq. 7): cell (i0, j0)
+// and fractions (a, b); pixels past the last node clamp to it.
+__device__ __forceinline__ void grid_cell(int x, int y, int s, int nx, int ny, int& i0, int& j0, float& a, float& b)
+{
+    float u = fminf((float)x / (float)s, (float)(nx - 1));
+    float v = fminf((float)y / (float)s, (float)(ny - 1));
+    i0 = min((int)floorf(u), nx - 2);
+    j0 = min((int)floorf(v), ny - 2);
+    a = u - (float)i0;
+    b = v - (float)j0;
+}
+
+// Fields of a pixel from the four nodes of its cell, F = base + delta (+ t x);
+// delta and x may be null.
+__device__ __forceinline__ void pixel_fields(const float* __restrict__ base, const float* __restrict__ delta,
+                                             const float* __restrict__ x, float t, int G, int n00, int nx, float a,
+                                             float b, float f[6])
+{
+    const int nd[4] = {n00, n00 + 1, n00 + nx, n00 + nx + 1};
+    const float al[4] = {(1.f - a) * (1.f - b), a * (1.f - b), (1.f - a) * b, a * b};
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float T = __ldg(base + c * G + nd[k]);
+            if (delta) T += __ldg(delta + c * G + nd[k]);
+            if (x) T = fmaf(t, __ldg(x + c * G + nd[k]), T);
+            acc = fmaf(al[k], T, acc);
+        }
+        f[c] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < NT / 32; ++i) r += sh[i];
+    return r; // valid in thread 0
+}
+
+// Sum of n partials in a fixed order, the same in every block (warp 0 only).
+__device__ __forceinline__ double fixed_sum(const double* __restrict__ part, int n)
+{
+    const int lane = threadIdx.x & 31;
+    double v = 0.0;
+    for (int i = lane; i < n; i += 32) v += __ldcg(part + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_acquire_s32(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).
+// bar[0] counts arrivals, bar[1] is the generation. A waiter gives up after
+// about one second (clock64 on the SM clock), latches DEV_TIMEOUT and returns
+// false; once the status word holds an error every later barrier returns
+// false at once, so the kernel unwinds instead of hanging.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* status, unsigned nblocks)
+{
+    __shared__ int ok_sh;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = ld_acquire_s32(status) == 0;
+        if (ok) {
+            const unsigned gen = ld_acquire_u32(bar + 1);
+            __threadfence();
+            const unsigned arrived = atomicAdd(bar, 1u);
+            if (arrived == nblocks - 1) {
+                atomicExch(bar, 0u);
+                __threadfence();
+                atomicAdd(bar + 1, 1u);
+            } else {
+                const long long t0 = clock64();
+                while (ld_acquire_u32(bar + 1) == gen) {
+                    if (clock64() - t0 > 2000000000LL) {
+                        atomicOr(status, DEV_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(20);
+                }
+            }
+            __threadfence();
+        }
+        ok_sh = ok;
+    }
+    __syncthreads();
+    return ok_sh != 0;
+}
+
+} // namespace sfk

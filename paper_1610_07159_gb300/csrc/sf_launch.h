@@ -1,0 +1,60 @@
+// sf_launch.h -- host-side launchers of the solver kernels (internal).
+#pragma once
+
+#include "sf_common.cuh"
+
+namespace sfk {
+
+// sf_levels.cu: image pyramid (Section 5.3), level initialisation with the
+// delta hierarchy and temporal transfer, feature weights (Section 4.3).
+void launch_tex0(const DevArgs* args, const float* const* in_direct, int w, int h, float4* tex, cudaStream_t st);
+void launch_texdown(const float4* texp, int wp, int hp, float4* tex, int w, int h, cudaStream_t st);
+void launch_level_init(const LevelGeom& g, const LevelGeom* gc, const float* base_c, const float* delta_c,
+                       float* base, float* delta, const float* prev_delta, const float* prev_total,
+                       const float* init_buf, const DevArgs* args, int temporal_mode, cudaStream_t st);
+void launch_halfway(const LevelGeom& g, const float4* tex, const float* base, const float* delta, float* H,
+                    cudaStream_t st);
+void launch_wfeat(const LevelGeom& g, const float* H, const DevParams& P, float* wf, cudaStream_t st);
+void launch_fill(float* p, float v, size_t n, cudaStream_t st);
+void launch_finish_level(const LevelGeom& g, const float* base, const float* delta, float* prev_delta,
+                         float* prev_total, const DevArgs* args, int write_out, cudaStream_t st);
+void launch_unpack_tex(const float4* tex, int w, int h, float* planes, cudaStream_t st);
+void launch_add(const float* a, const float* b, float* out, size_t n, cudaStream_t st);
+
+// sf_assemble.cu: per-pixel data terms, cell assembly, node gather with the
+// priors, trial energies with the backtracking decision, step update.
+struct Scratch {
+    double* asm_part; // [3][MAX_PART]: photo, grad, excluded
+    double* gat_part; // [3][MAX_PART]: smooth, epi, mag
+    double* en_part;  // [6][MAX_PART]: photo, grad, smooth, epi, mag, excluded
+    unsigned* counters; // [4]
+    int* status;
+};
+int assemble_blocks(const LevelGeom& g, int* cpb_out);
+void launch_assemble(const LevelGeom& g, const float4* tex, const float* base, const float* delta,
+                     const DevParams& P, uint8_t* Wmask, float* cell, const Scratch& sc, cudaStream_t st);
+void launch_gather(const LevelGeom& g, const float* cell, const float* base, const float* delta, const float* wf,
+                   const DevParams& P, float* node, float* rhs, float* minv, const Scratch& sc, StepCtrl* ctrl,
+                   int n_asm_blocks, cudaStream_t st);
+// action: 0 = write the energy record `rec` only; 1 = backtracking trial
+// against ctrl (skips itself once a trial was accepted), `last` marks the
+// final trial. wmode: 0 = use Wmask, 1 = take W at the state and store it.
+void launch_energy(const LevelGeom& g, const float4* tex, const float* base, const float* delta, const float* x,
+                   float t, const float* wf, const DevParams& P, uint8_t* Wmask, int wmode, const Scratch& sc,
+                   StepCtrl* ctrl, int action, int last, double* rec, cudaStream_t st);
+void launch_apply_step(const LevelGeom& g, float* delta, const float* x, const StepCtrl* ctrl, cudaStream_t st);
+void launch_unpack_blocks(const LevelGeom& g, const float* node, const float* rhs, float* blocks, float* rhs_out,
+                          cudaStream_t st);
+
+// sf_pcg.cu: Jacobi-preconditioned CG on the block system, one cooperative
+// launch per solve with a bounded grid barrier between phases.
+struct PcgPlan {
+    int blocks;
+    int npt;
+};
+PcgPlan pcg_plan(int G, int sm_count);
+cudaError_t launch_pcg(const LevelGeom& g, const PcgPlan& plan, const float* node, const float* rhs,
+                       const float* minv, float* x, float* z, float* p0, float* p1, double* part, unsigned* bar,
+                       int* status, int iters, int interleaved_out, cudaStream_t st);
+
+} // namespace sfk

@@ -1,0 +1,275 @@
+"""Thin ctypes binding of the C ABI in include/sf.h (libsf_gb300.so).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels. Tensors passed in must be contiguous CUDA tensors of the stated
+dtype; the binding hands their data pointers and the current CUDA stream to
+the library. There is no CPU path: if the library is missing or fails to
+load, loading raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+MAX_LEVELS = 8
+MAX_GN = 16
+
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_STATE = range(7)
+IRLS, SQRT_PAPER = 0, 1
+GRAD_BROX, GRAD_LITERAL = 0, 1
+WFEAT_EIG, WFEAT_OFF = 0, 1
+TEMPORAL_PROPAGATE, TEMPORAL_COPY, TEMPORAL_ZERO = 0, 1, 2
+FP32, MIXED_BF16 = 0, 1
+PRESET_FIG2, PRESET_FIG568, PRESET_FIG79 = 0, 1, 2
+
+EXPORTED = (
+    "sf_params_preset", "sf_create", "sf_solve", "sf_solve_host", "sf_grid_dims", "sf_set_init", "sf_reset",
+    "sf_get_stats", "sf_get_state", "sf_destroy", "sf_status_string", "sf_last_error", "sf_probe_pyramid",
+    "sf_probe_feature_weights", "sf_probe_assemble", "sf_probe_pcg", "sf_probe_wmask", "sf_probe_energy",
+)
+
+
+class SFError(RuntimeError):
+    pass
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("w_reg", ctypes.c_float), ("w_photo", ctypes.c_float), ("w_grad", ctypes.c_float),
+        ("w_epi", ctypes.c_float), ("w_smooth", ctypes.c_float), ("w_mag", ctypes.c_float),
+        ("w_s", ctypes.c_float), ("w_m", ctypes.c_float), ("w_d", ctypes.c_float),
+        ("m_s", ctypes.c_float), ("m_m", ctypes.c_float), ("m_d", ctypes.c_float),
+        ("eps", ctypes.c_float), ("eps_p", ctypes.c_float), ("F", ctypes.c_float * 9),
+        ("gn_iters", ctypes.c_int * MAX_LEVELS), ("pcg_iters", ctypes.c_int * MAX_LEVELS),
+        ("robust_mode", ctypes.c_int), ("grad_mode", ctypes.c_int), ("wfeat_mode", ctypes.c_int),
+        ("wfeat_gain", ctypes.c_float), ("wfeat_tau", ctypes.c_float),
+        ("temporal_mode", ctypes.c_int), ("precision", ctypes.c_int), ("max_backtracks", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("frames", ctypes.c_int), ("levels", ctypes.c_int), ("n_excluded", ctypes.c_int),
+        ("energy", ctypes.c_double), ("terms", ctypes.c_double * 5),
+        ("step_energy", (ctypes.c_double * MAX_GN) * MAX_LEVELS),
+        ("step_accepted", (ctypes.c_double * MAX_GN) * MAX_LEVELS),
+        ("step_t", (ctypes.c_float * MAX_GN) * MAX_LEVELS),
+        ("step_excluded", (ctypes.c_int * MAX_GN) * MAX_LEVELS),
+    ]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads libsf_gb300.so (building it first if needed); raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    path = _build.LIB_PATH
+    if not os.path.exists(path):
+        raise SFError(f"CUDA library missing: {path}")
+    L = ctypes.CDLL(path)
+    vp, i, fp = ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.sf_params_preset.argtypes = [ctypes.POINTER(Params), i]
+    L.sf_create.argtypes = [i, i, i, i, ctypes.POINTER(Params)]
+    L.sf_create.restype = vp
+    L.sf_solve.argtypes = [vp, fp, fp, fp, fp, fp, vp]
+    L.sf_solve_host.argtypes = [vp, fp, fp, fp, fp, fp, vp]
+    L.sf_grid_dims.argtypes = [vp, i, ip, ip, ip, ip]
+    L.sf_set_init.argtypes = [vp, fp, vp]
+    L.sf_reset.argtypes = [vp]
+    L.sf_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    L.sf_get_state.argtypes = [vp, i, fp, fp, vp]
+    L.sf_destroy.argtypes = [vp]
+    L.sf_destroy.restype = None
+    L.sf_status_string.argtypes = [i]
+    L.sf_status_string.restype = ctypes.c_char_p
+    L.sf_last_error.argtypes = []
+    L.sf_probe_pyramid.argtypes = [vp, fp, fp, fp, fp, i, fp, vp]
+    L.sf_probe_feature_weights.argtypes = [vp, i, fp, fp, vp]
+    L.sf_probe_assemble.argtypes = [vp, i, fp, fp, fp, fp, fp, fp, fp, vp]
+    L.sf_probe_pcg.argtypes = [vp, i, i, fp, vp]
+    L.sf_probe_wmask.argtypes = [vp, i, i, fp, vp]
+    L.sf_probe_energy.argtypes = [vp, i, fp, fp, fp, fp, fp, vp]
+    _lib = L
+    return L
+
+
+def status_string(code: int) -> str:
+    return load().sf_status_string(int(code)).decode()
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != OK:
+        raise SFError(f"{what}: {status_string(rc)} ({rc})")
+
+
+def preset(which: int = PRESET_FIG2, **kw) -> Params:
+    p = Params()
+    _check(load().sf_params_preset(ctypes.byref(p), int(which)), "sf_params_preset")
+    for k, v in kw.items():
+        if k in ("gn_iters", "pcg_iters"):
+            vals = list(v) + [list(v)[-1]] * MAX_LEVELS
+            setattr(p, k, (ctypes.c_int * MAX_LEVELS)(*[int(x) for x in vals[:MAX_LEVELS]]))
+        elif k == "F":
+            p.F = (ctypes.c_float * 9)(*[float(x) for x in v])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _ptr(t: torch.Tensor | None, dtype: torch.dtype | None = None) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise SFError("tensors passed to the library must be contiguous CUDA tensors")
+    if dtype is not None and t.dtype != dtype:
+        raise SFError(f"expected {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Solver:
+    """One solver context (sf_create ... sf_destroy)."""
+
+    def __init__(self, width: int, height: int, grid_stride: int, levels: int, params: Params | None = None):
+        self.L = load()
+        self.params = params if params is not None else preset()
+        torch.cuda.init()
+        self.ctx = self.L.sf_create(int(width), int(height), int(grid_stride), int(levels), ctypes.byref(self.params))
+        if not self.ctx:
+            raise SFError(f"sf_create: {status_string(self.L.sf_last_error())}")
+        self.width, self.height, self.stride, self.levels = int(width), int(height), int(grid_stride), int(levels)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            self.L.sf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dims(self, level: int = 0) -> tuple[int, int, int, int]:
+        w, h, nx, ny = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self.L.sf_grid_dims(self.ctx, int(level), ctypes.byref(w), ctypes.byref(h), ctypes.byref(nx),
+                                   ctypes.byref(ny)), "sf_grid_dims")
+        return w.value, h.value, nx.value, ny.value
+
+    def solve(self, imgs: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """imgs: float32 CUDA [4, H, W] (L_t, R_t, L_t1, R_t1); returns fields [6, ny, nx]."""
+        _, _, nx, ny = self.dims(0)
+        if out is None:
+            out = torch.empty((6, ny, nx), device=imgs.device, dtype=torch.float32)
+        if imgs.shape != (4, self.height, self.width):
+            raise SFError(f"expected images of shape (4, {self.height}, {self.width})")
+        base = _ptr(imgs, torch.float32)
+        n = self.width * self.height * 4
+        _check(self.L.sf_solve(self.ctx, base, base + n, base + 2 * n, base + 3 * n, _ptr(out, torch.float32),
+                               _stream()), "sf_solve")
+        return out
+
+    def solve_ptrs(self, p0: int, p1: int, p2: int, p3: int, out_ptr: int, stream: int) -> None:
+        _check(self.L.sf_solve(self.ctx, p0, p1, p2, p3, out_ptr, stream), "sf_solve")
+
+    def solve_host(self, imgs, out) -> None:
+        """imgs: float32 CPU tensor [4, H, W] (pinned for full speed); out: float32 CPU [6, ny, nx]."""
+        if imgs.is_cuda or out.is_cuda or not imgs.is_contiguous() or not out.is_contiguous():
+            raise SFError("solve_host takes contiguous host tensors")
+        base = imgs.data_ptr()
+        n = self.width * self.height * 4
+        _check(self.L.sf_solve_host(self.ctx, base, base + n, base + 2 * n, base + 3 * n, out.data_ptr(), _stream()),
+               "sf_solve_host")
+
+    def set_init(self, coarsest_delta: torch.Tensor) -> None:
+        _check(self.L.sf_set_init(self.ctx, _ptr(coarsest_delta, torch.float32), _stream()), "sf_set_init")
+
+    def reset(self) -> None:
+        _check(self.L.sf_reset(self.ctx), "sf_reset")
+
+    def stats(self) -> Stats:
+        st = Stats()
+        rc = self.L.sf_get_stats(self.ctx, ctypes.byref(st))
+        if rc not in (OK, ERR_NUMERIC, ERR_TIMEOUT):
+            _check(rc, "sf_get_stats")
+        return st
+
+    def state(self, level: int) -> tuple[torch.Tensor, torch.Tensor]:
+        _, _, nx, ny = self.dims(level)
+        d = torch.empty((6, ny, nx), device="cuda", dtype=torch.float32)
+        t = torch.empty_like(d)
+        _check(self.L.sf_get_state(self.ctx, int(level), _ptr(d), _ptr(t), _stream()), "sf_get_state")
+        return d, t
+
+    # ---- step-level probes ------------------------------------------------
+    def probe_pyramid(self, imgs: torch.Tensor, level: int) -> torch.Tensor:
+        w, h, _, _ = self.dims(level)
+        planes = torch.empty((4, 3, h, w), device="cuda", dtype=torch.float32)
+        base = _ptr(imgs, torch.float32)
+        n = self.width * self.height * 4
+        _check(self.L.sf_probe_pyramid(self.ctx, base, base + n, base + 2 * n, base + 3 * n, int(level), _ptr(planes),
+                                       _stream()), "sf_probe_pyramid")
+        return planes
+
+    def probe_feature_weights(self, level: int, T: torch.Tensor) -> torch.Tensor:
+        _, _, nx, ny = self.dims(level)
+        wf = torch.empty(nx * ny, device="cuda", dtype=torch.float32)
+        _check(self.L.sf_probe_feature_weights(self.ctx, int(level), _ptr(T, torch.float32), _ptr(wf), _stream()),
+               "sf_probe_feature_weights")
+        return wf
+
+    def probe_assemble(self, level: int, base: torch.Tensor, delta: torch.Tensor, wfeat: torch.Tensor):
+        w, h, nx, ny = self.dims(level)
+        G = nx * ny
+        blocks = torch.empty((G, 5, 6, 6), device="cuda", dtype=torch.float32)
+        rhs = torch.empty((G, 6), device="cuda", dtype=torch.float32)
+        energy = torch.empty(1, device="cuda", dtype=torch.float64)
+        W = torch.empty((h, w), device="cuda", dtype=torch.uint8)
+        _check(self.L.sf_probe_assemble(self.ctx, int(level), _ptr(base, torch.float32), _ptr(delta, torch.float32),
+                                        _ptr(wfeat, torch.float32), _ptr(blocks), _ptr(rhs), _ptr(energy), _ptr(W),
+                                        _stream()), "sf_probe_assemble")
+        return blocks, rhs, energy, W
+
+    def probe_pcg(self, level: int, iters: int) -> torch.Tensor:
+        _, _, nx, ny = self.dims(level)
+        x = torch.empty((nx * ny, 6), device="cuda", dtype=torch.float32)
+        _check(self.L.sf_probe_pcg(self.ctx, int(level), int(iters), _ptr(x), _stream()), "sf_probe_pcg")
+        return x
+
+    def probe_wmask(self, level: int, step: int) -> torch.Tensor:
+        w, h, _, _ = self.dims(level)
+        W = torch.empty((h, w), device="cuda", dtype=torch.uint8)
+        _check(self.L.sf_probe_wmask(self.ctx, int(level), int(step), _ptr(W), _stream()), "sf_probe_wmask")
+        return W
+
+    def wmasks(self) -> list:
+        """The outlier masks of every Gauss-Newton step of the last frame, [level][step]."""
+        return [[self.probe_wmask(l, g).cpu().numpy() for g in range(self.params.gn_iters[l])]
+                for l in range(self.levels)]
+
+    def probe_energy(self, level: int, base: torch.Tensor, delta: torch.Tensor, wfeat: torch.Tensor,
+                     W: torch.Tensor | None = None) -> torch.Tensor:
+        out = torch.empty(6, device="cuda", dtype=torch.float64)
+        _check(self.L.sf_probe_energy(self.ctx, int(level), _ptr(base, torch.float32), _ptr(delta, torch.float32),
+                                      _ptr(wfeat, torch.float32), _ptr(W, torch.uint8) if W is not None else None,
+                                      _ptr(out), _stream()), "sf_probe_energy")
+        return out

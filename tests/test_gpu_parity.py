@@ -1,0 +1,262 @@
+"""CUDA path vs the FP64 oracle, through the C ABI, element by element.
+
+Bar (spec tolerance): fields within 1e-3 px max-abs and the final energy
+within 1e-4 relative. Step-level stages use tolerances derived from FP32
+arithmetic on the same inputs (stated per test)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1610_07159_gb300 import scenes, sf
+from tests.gpu_common import LIB_SLOTS, lib_blocks_to_oracle, make_params, rel_max
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-3   # px, max-abs per field
+ENERGY_TOL = 1e-4  # relative
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sf.load()
+    yield
+    torch.cuda.synchronize()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _smooth_state(G, rng, scale=1.0):
+    base = (rng.uniform(-scale, scale, (6, 1)) + 0.2 * rng.standard_normal((6, G)))
+    delta = 0.2 * rng.standard_normal((6, G))
+    return base.astype(np.float32), delta.astype(np.float32)
+
+
+# --------------------------------------------------------------------------- #
+# step level
+# --------------------------------------------------------------------------- #
+
+@pytest.mark.parametrize("w,h,L", [(160, 120, 3), (157, 93, 4)])
+def test_pyramid_parity(w, h, L):
+    q = scenes.random_quadruple(w, h, 3, sigma=0.01)
+    sp, _ = make_params([1], [1])
+    s = sf.Solver(w, h, 2, L, sp)
+    ref = O.pyramid(q.astype(np.float64), L)
+    for l in range(L):
+        planes = s.probe_pyramid(_dev(q), l).cpu().numpy()
+        np.testing.assert_allclose(planes, O.level_planes(ref[l]), atol=2e-6, rtol=0)
+
+
+def _level_setup(w, h, s_, L, level, seed=5, **kw):
+    q = scenes.random_quadruple(w, h, seed, sigma=0.01)
+    sp, op = make_params([1], [1], **kw)
+    solver = sf.Solver(w, h, s_, L, sp)
+    planes = solver.probe_pyramid(_dev(q), level).cpu().numpy().astype(np.float64)
+    # the oracle works on the library's FP32 planes, so the stage is isolated
+    lv = O.Level(planes, s_, level)
+    return solver, lv, op
+
+
+@pytest.mark.parametrize("w,h,s_,level", [(160, 120, 4, 0), (150, 110, 4, 1), (640, 480, 8, 0)])
+def test_feature_weight_parity(w, h, s_, level):
+    solver, lv, op = _level_setup(w, h, s_, 3, level)
+    rng = np.random.default_rng(1)
+    T = (rng.uniform(-1, 1, (6, 1)) + 0.3 * rng.standard_normal((6, lv.G))).astype(np.float32)
+    wf_gpu = solver.probe_feature_weights(level, _dev(T)).cpu().numpy()
+    wf_ref = O.feature_weights(lv, T.astype(np.float64).reshape(-1), op)
+    # exp(-lambda/tau) with tau = 1e-3 amplifies FP32 rounding of lambda; w is in [1, 10]
+    assert np.max(np.abs(wf_gpu - wf_ref)) < 2e-3
+
+
+@pytest.mark.parametrize("w,h,s_,level,kw", [
+    (160, 120, 4, 0, {}),
+    (150, 110, 4, 1, {"w_epi": 0.5, "F": (1e-6, -2e-5, 3e-4, 1e-5, 2e-6, -1.0, -2e-4, 1.0, 5e-3)}),
+    (200, 136, 8, 0, {"robust_mode": O.SQRT_PAPER}),
+    (96, 80, 16, 0, {"grad_mode": O.GRAD_LITERAL, "eps_p": 0.0}),
+])
+def test_assemble_parity(w, h, s_, level, kw):
+    solver, lv, op = _level_setup(w, h, s_, 3, level, **kw)
+    rng = np.random.default_rng(2)
+    base, delta = _smooth_state(lv.G, rng)
+    wf = (1.0 + 3.0 * rng.random(lv.G)).astype(np.float32)
+    blocks, rhs, energy, W = solver.probe_assemble(level, _dev(base), _dev(delta), _dev(wf))
+    blocks, rhs, energy, W = blocks.cpu().numpy(), rhs.cpu().numpy(), energy.item(), W.cpu().numpy()
+    # W decisions: identical except where max|e_k| sits at the threshold in FP32
+    A_ref, b_ref, E_ref, W_ref = O.assemble(lv, base.astype(np.float64).reshape(-1),
+                                            delta.astype(np.float64).reshape(-1), wf.astype(np.float64), op)
+    assert np.mean(W != W_ref) < 1e-4
+    # the rest is compared on the same W
+    A_ref, b_ref, E_ref, _ = O.assemble(lv, base.astype(np.float64).reshape(-1),
+                                        delta.astype(np.float64).reshape(-1), wf.astype(np.float64), op, W=W)
+    # errors relative to the scale of the diagonal blocks (the SE/SW blocks are
+    # sums with small weights alpha_0 alpha_3, so their own maxima are small)
+    scale = np.max(np.abs(A_ref[:, 4]))
+    for k, slot in enumerate(LIB_SLOTS):
+        assert np.max(np.abs(blocks[:, k] - A_ref[:, slot])) < 1e-5 * scale, k
+    assert rel_max(rhs, b_ref) < 2e-5
+    assert abs(energy - E_ref) < 1e-5 * abs(E_ref)
+
+
+@pytest.mark.parametrize("iters", [1, 5, 20])
+def test_pcg_parity_on_the_same_system(iters):
+    solver, lv, op = _level_setup(160, 120, 4, 3, 0)
+    rng = np.random.default_rng(3)
+    base, delta = _smooth_state(lv.G, rng)
+    wf = np.ones(lv.G, dtype=np.float32)
+    blocks, rhs, _, _ = solver.probe_assemble(0, _dev(base), _dev(delta), _dev(wf))
+    x_gpu = solver.probe_pcg(0, iters).cpu().numpy()
+    A = lib_blocks_to_oracle(blocks.cpu().numpy().astype(np.float64), lv.nx, lv.ny)
+    x_ref, _, its = O.pcg(lv.nx, lv.ny, A, rhs.cpu().numpy().astype(np.float64), iters)
+    assert its == iters
+    assert rel_max(x_gpu, x_ref) < 2e-4 * iters
+
+
+def test_energy_parity_with_given_and_computed_W():
+    solver, lv, op = _level_setup(160, 120, 4, 3, 0, w_epi=0.3)
+    rng = np.random.default_rng(4)
+    base, delta = _smooth_state(lv.G, rng)
+    wf = (1.0 + rng.random(lv.G)).astype(np.float32)
+    W = (rng.random((lv.h, lv.w)) < 0.8).astype(np.uint8)
+    out = solver.probe_energy(0, _dev(base), _dev(delta), _dev(wf), torch.from_numpy(W).cuda()).cpu().numpy()
+    E_ref, terms, _ = O.energy(lv, base.astype(np.float64).reshape(-1), delta.astype(np.float64).reshape(-1),
+                               wf.astype(np.float64), op, W)
+    assert abs(out[0] - E_ref) < 1e-6 * E_ref
+    weights = [op.w_photo, op.w_grad, op.w_reg * op.w_smooth, op.w_reg * op.w_epi, op.w_reg * op.w_mag]
+    np.testing.assert_allclose(out[1:], np.array(weights) * terms, rtol=1e-5, atol=1e-9)
+    out2 = solver.probe_energy(0, _dev(base), _dev(delta), _dev(wf), None).cpu().numpy()
+    E2, _, _ = O.energy(lv, base.astype(np.float64).reshape(-1), delta.astype(np.float64).reshape(-1),
+                        wf.astype(np.float64), op)
+    assert abs(out2[0] - E2) < 1e-5 * E2
+
+
+# --------------------------------------------------------------------------- #
+# whole frames
+# --------------------------------------------------------------------------- #
+
+W_MARGIN = 1e-3  # a replayed W decision may part from the FP64 one only this close to eps_p
+
+
+def _solve_both(q, s_, L, gn, pcg, frames=1, **kw):
+    """GPU solve, then the oracle twice: replaying the GPU's outlier masks W
+    (W is an integer decision taken in floating point, so both sides take the
+    kernel's FP32 decision; the replay checks each differing pixel sits at the
+    threshold), and with its own FP64 decisions (energy only)."""
+    sp, op = make_params(gn, pcg, **kw)
+    h, w = q.shape[-2:]
+    solver = sf.Solver(w, h, s_, L, sp)
+    qs = q if q.ndim == 4 else q[None]
+    prev = prev_own = None
+    out = []
+    for f in range(min(frames, len(qs))):
+        fields = solver.solve(_dev(qs[f])).cpu().numpy()
+        st = solver.stats()
+        assert st.status == sf.OK
+        qf = qs[f].astype(np.float64)
+        ref = O.solve_frame(qf, s_, L, op, prev=prev, W_given=solver.wmasks())
+        own = O.solve_frame(qf, s_, L, op, prev=prev_own)
+        prev, prev_own = ref, own
+        out.append((fields, st, ref, own, op, L))
+    return out
+
+
+def _assert_frame_parity(fields, st, ref, own, op, L):
+    for l in range(L):
+        npx = np.prod(O.level_dims(ref.offsets[0][3], ref.offsets[0][4], l))
+        for g in range(op.gn_iters[l]):
+            ndis, margin = ref.step(l, g)[5], ref.step(l, g)[6]
+            assert ndis <= max(2, 1e-3 * npx) and margin <= W_MARGIN, (l, g, ndis, margin)
+    F_ref = ref.fields(0)
+    err = np.max(np.abs(fields - F_ref), axis=(1, 2))
+    assert np.all(err <= FIELD_TOL), err
+    assert abs(st.energy - ref.energy) <= ENERGY_TOL * abs(ref.energy), (st.energy, ref.energy)
+    assert abs(st.energy - own.energy) <= ENERGY_TOL * abs(own.energy), (st.energy, own.energy)
+
+
+def test_config1_frame_parity():
+    q = scenes.plane_quadruple()  # 160x120, disparity 8, motion (2,-1), sigma 0.01
+    for r in _solve_both(q, 4, 3, [5], [10]):
+        _assert_frame_parity(*r)
+        # the step decisions agree too
+        for l in range(3):
+            for g in range(5):
+                assert r[1].step_t[l][g] == r[2].step(l, g)[2]
+
+
+@pytest.mark.parametrize("kw", [{"robust_mode": O.SQRT_PAPER}, {"grad_mode": O.GRAD_LITERAL},
+                                {"wfeat_mode": O.WFEAT_OFF, "eps_p": 0.0}, {"use_graph": 0}])
+def test_config1_frame_parity_modes(kw):
+    q = scenes.plane_quadruple(seed=2)
+    for r in _solve_both(q, 4, 3, [5], [10], **kw):
+        _assert_frame_parity(*r)
+
+
+def test_ragged_scene_parity_with_epipolar_prior():
+    q = scenes.SceneVideo(150, 110, 1, seed=11, disparity=(2, 12), max_motion=4).frames(1)[0]
+    for r in _solve_both(q, 4, 3, [4], [15], preset="fig568"):
+        _assert_frame_parity(*r)
+
+
+def test_config2_video_parity_first_frames():
+    """640x480, stride 8, 4 levels, 3 GN x 20 PCG, temporal transfer over 3 frames."""
+    v = scenes.SceneVideo(640, 480, 3, seed=100)
+    q = v.frames(3)
+    for r in _solve_both(q, 8, 4, [3], [20], frames=3):
+        _assert_frame_parity(*r)
+
+
+def test_repeat_runs_are_bit_identical_and_graph_matches_eager():
+    q = _dev(scenes.plane_quadruple(seed=5))
+    outs = []
+    for g in (1, 1, 0):
+        sp, _ = make_params([3], [10], use_graph=g)
+        s = sf.Solver(160, 120, 4, 3, sp)
+        outs.append(s.solve(q).cpu().numpy())
+        outs.append(s.solve(q).cpu().numpy())  # second frame: temporal path
+    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[3])
+    assert np.array_equal(outs[0], outs[4]) and np.array_equal(outs[1], outs[5])
+
+
+# --------------------------------------------------------------------------- #
+# degenerate cases
+# --------------------------------------------------------------------------- #
+
+def test_stereo_only_and_identical_images():
+    q = scenes.plane_quadruple(disparity=8, motion=(0, 0), seed=3)
+    q[2], q[3] = q[0], q[1]
+    sp, _ = make_params([4], [10])
+    s = sf.Solver(160, 120, 4, 3, sp)
+    F = s.solve(_dev(q)).cpu().numpy()
+    assert np.max(np.abs(F[2:])) < 1e-5 and np.max(np.abs(F[0])) > 1.0
+    q[1:] = q[0]
+    s2 = sf.Solver(160, 120, 4, 3, sp)
+    assert np.max(np.abs(s2.solve(_dev(q)).cpu().numpy())) == 0.0
+
+
+def test_smallest_grid_and_no_steps_on_the_finest_level():
+    q = scenes.random_quadruple(8, 8, 4, sigma=0.01)
+    for r in _solve_both(q, 4, 1, [2], [5]):
+        _assert_frame_parity(*r)
+    q = scenes.plane_quadruple(seed=6)
+    sp, op = make_params([0, 3, 3], [10])
+    s = sf.Solver(160, 120, 4, 3, sp)
+    F = s.solve(_dev(q)).cpu().numpy()
+    st = s.stats()
+    ref = O.solve_frame(q.astype(np.float64), 4, 3, op, W_given=s.wmasks())
+    assert np.max(np.abs(F - ref.fields(0))) <= FIELD_TOL
+    assert abs(st.energy - ref.energy) <= ENERGY_TOL * ref.energy
+
+
+def test_host_entry_point_matches_device_entry_point():
+    q = scenes.plane_quadruple(seed=7)
+    sp, _ = make_params([3], [10])
+    a = sf.Solver(160, 120, 4, 3, sp)
+    b = sf.Solver(160, 120, 4, 3, sp)
+    Fd = a.solve(_dev(q)).cpu().numpy()
+    out = torch.empty((6, 30, 40), dtype=torch.float32).pin_memory()
+    b.solve_host(torch.from_numpy(q).pin_memory(), out)
+    assert np.array_equal(Fd, out.numpy())
