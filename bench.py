@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the halfway-domain scene-flow solve (arXiv 1610.07159).
+
+Workload: a seeded synthetic 640x480 stereo video (30 frames of 3-6
+value-noise textured planes and spheres, disparities 5-40 px, motion up to
+12 px per frame), warp-grid stride 8, 4 pyramid levels, 3 Gauss-Newton x 20
+PCG iterations per level, Figure-2 weights of Table 1. One step = one frame:
+the whole hot path (pyramid, coarse-to-fine Gauss-Newton/PCG with the delta
+hierarchy and temporal transfer) through the C ABI. The video restarts from a
+zero initialisation every 30 frames.
+
+Metric: stereo frames/s (higher is better). Each rank solves its own
+sequence (weak scaling, no collective on the data path); value = frames of
+all ranks / max-over-ranks time.
+
+Timing: W warm-up frames, then K frames, each between CUDA events on the
+launching stream with an L2 flush (a 256 MB write) between frames outside
+the events; inputs of all 30 frames are resident in HBM before timing.
+`e2e` repeats the run through sf_solve_host from pinned host memory (the
+copies in and out inside the timed region). `roofline` is for the kernel
+class with the larger device time, measured live with CUDA events recorded
+inside the frame graph. `cpu_baseline` and `--impl reference` time the FP64
+CPU oracle on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WIDTH, HEIGHT, STRIDE, LEVELS, GN, PCG, NFRAMES = 640, 480, 8, 4, 3, 20, 30
+METRIC = "stereo frames/sec at 640x480 vs plain FP32 at equal energy; % of HBM roofline"
+UNIT = "frames/s"
+WORKLOAD = (f"{WIDTH}x{HEIGHT} synthetic stereo video, {NFRAMES} frames, grid stride {STRIDE}, {LEVELS} levels, "
+            f"{GN} GN x {PCG} PCG per level, Figure-2 weights, FP32")
+FP32_LANES_PER_SM = 128
+
+# Algorithmic work per unit (derivations in the design notes):
+#   PCG: per node  96 B (init) + 516 B per iteration + 24 B (solution)
+#   assembly: 2250 FP32 flops per pixel
+PCG_INIT_B, PCG_ITER_B, PCG_OUT_B = 96, 516, 24
+ASM_FLOPS_PER_PX = 2250
+
+
+def level_sizes():
+    w, h, out = WIDTH, HEIGHT, []
+    for _ in range(LEVELS):
+        out.append((w, h, (w + STRIDE - 1) // STRIDE, (h + STRIDE - 1) // STRIDE))
+        w, h = (w + 1) // 2, (h + 1) // 2
+    return out
+
+
+def pcg_bytes_per_frame():
+    return sum(GN * nx * ny * (PCG_INIT_B + PCG * PCG_ITER_B + PCG_OUT_B) for _, _, nx, ny in level_sizes())
+
+
+def asm_flops_per_frame():
+    return sum(GN * w * h * ASM_FLOPS_PER_PX for w, h, _, _ in level_sizes())
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def source_hash(rel):
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """Per-launch DRAM bytes from the committed ncu summary, if taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)[kernel]
+    except (OSError, ValueError, KeyError):
+        return None
+    if d.get("source_sha256_16") != source_hash(d["source"]):
+        return None
+    return d.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid, self.proc, self.lines = uuid, None, []
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(backend):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None, rank, world, local
+
+
+def max_over_ranks(dist, value, device):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(video, max_seconds=20.0, max_frames=4):
+    import numpy as np
+    import oracle as O
+    p = O.Params.preset("fig2", gn_iters=(GN,) * 8, pcg_iters=(PCG,) * 8)
+    prev, n, t0 = None, 0, time.perf_counter()
+    while n < max_frames and time.perf_counter() - t0 < max_seconds:
+        prev = O.solve_frame(video[n].astype(np.float64), STRIDE, LEVELS, p, prev=prev)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} frames of the same {WIDTH}x{HEIGHT} video (temporal chain), single-threaded "
+                      f"FP64 C oracle, {dt:.1f} s"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1610_07159_gb300 import scenes, sf
+
+    dist, rank, world, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    video = scenes.SceneVideo(WIDTH, HEIGHT, NFRAMES, seed=100 + rank).frames()
+    frames_d = torch.from_numpy(video).to(dev)  # all frames resident in HBM (147 MB)
+    prof = (1 << sf.K_PCG) | (1 << sf.K_ASSEMBLE)
+    params = sf.preset(sf.PRESET_FIG2, gn_iters=[GN], pcg_iters=[PCG], profile_mask=prof)
+    solver = sf.Solver(WIDTH, HEIGHT, STRIDE, LEVELS, params)
+    _, _, nx, ny = solver.dims(0)
+    out = torch.empty((6, ny, nx), device=dev, dtype=torch.float32)
+    flush = torch.empty(64 * 1024 * 1024, device=dev, dtype=torch.float32)  # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step(k, timed, acc):
+        f = k % NFRAMES
+        if f == 0:
+            solver.reset()
+        flush.zero_()
+        if timed:
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+        solver.solve(frames_d[f], out)
+        if timed:
+            e.record(stream)
+            e.synchronize()
+            acc["ms"] += s.elapsed_time(e)
+            for kc in (sf.K_PCG, sf.K_ASSEMBLE):
+                ms, n = solver.kernel_times(kc)
+                acc[kc][0] += ms
+                acc[kc][1] += n
+
+    acc0 = {"ms": 0.0, sf.K_PCG: [0.0, 0], sf.K_ASSEMBLE: [0.0, 0]}
+    for k in range(args.warmup):
+        step(k, False, acc0)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    acc = {"ms": 0.0, sf.K_PCG: [0.0, 0], sf.K_ASSEMBLE: [0.0, 0]}
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        step(k, True, acc)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    st = solver.stats()
+    t_max = max_over_ranks(dist, acc["ms"], dev)
+    value = world * args.steps / (t_max / 1e3)
+
+    # end to end through the host entry point: pinned inputs, copies inside the timed region
+    host_frames = torch.from_numpy(video).pin_memory()
+    host_out = torch.empty((6, ny, nx), dtype=torch.float32).pin_memory()
+    params_e2e = sf.preset(sf.PRESET_FIG2, gn_iters=[GN], pcg_iters=[PCG])
+    solver_e2e = sf.Solver(WIDTH, HEIGHT, STRIDE, LEVELS, params_e2e)
+    for k in range(args.warmup):
+        if k % NFRAMES == 0:
+            solver_e2e.reset()
+        solver_e2e.solve_host(host_frames[k % NFRAMES], host_out)
+    e2e_ms = 0.0
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        f = k % NFRAMES
+        if f == 0:
+            solver_e2e.reset()
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        solver_e2e.solve_host(host_frames[f], host_out)
+        e.record(stream)
+        e.synchronize()
+        e2e_ms += s.elapsed_time(e)
+    e2e_max = max_over_ranks(dist, e2e_ms, dev)
+    e2e_value = world * args.steps / (e2e_max / 1e3)
+
+    # roofline of the dominant kernel class, from the live per-kernel times
+    peaks, peak_src = measured_peaks()
+    pcg_ms, pcg_n = acc[sf.K_PCG]
+    asm_ms, asm_n = acc[sf.K_ASSEMBLE]
+    frames_timed = args.steps
+    pcg_bytes_launch = pcg_bytes_per_frame() * frames_timed / max(pcg_n, 1)
+    asm_flops_launch = asm_flops_per_frame() * frames_timed / max(asm_n, 1)
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    kernels = {
+        "pcg": {"launches": pcg_n, "ms_total": pcg_ms, "us_per_launch": 1e3 * pcg_ms / max(pcg_n, 1),
+                "bytes_per_launch": pcg_bytes_launch,
+                "GBps": pcg_bytes_launch / (pcg_ms / max(pcg_n, 1) / 1e3) / 1e9 if pcg_ms else None},
+        "assemble": {"launches": asm_n, "ms_total": asm_ms, "us_per_launch": 1e3 * asm_ms / max(asm_n, 1),
+                     "flops_per_launch": asm_flops_launch,
+                     "TFLOPs": asm_flops_launch / (asm_ms / max(asm_n, 1) / 1e3) / 1e12 if asm_ms else None},
+    }
+    if pcg_ms >= asm_ms:
+        ach = kernels["pcg"]["GBps"]
+        peak = float(peaks["hbm_gbs"])
+        roof = {"kernel": "k_pcg", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak if ach else None, "traffic": recorded_traffic("k_pcg"),
+                "peak_source": f"{peak_src} copy bandwidth"}
+    else:
+        ach = kernels["assemble"]["TFLOPs"]
+        roof = {"kernel": "k_assemble", "bound": "alu", "achieved": ach, "peak": alu_peak_tflops, "unit": "TFLOP/s",
+                "frac": ach / alu_peak_tflops if ach else None, "traffic": recorded_traffic("k_assemble"),
+                "peak_source": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded ray-cast stereo video; the paper's webcam and Volker data are not available)",
+        "config": {"workload": WORKLOAD, "global_batch": world, "seq_len": NFRAMES,
+                   "parallelism": f"replicas x{world} (independent sequences)",
+                   "l2": "flushed between steps (256 MB write outside the timed events)"},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * WIDTH * HEIGHT * 4,
+                "d2h_bytes_per_step": 6 * nx * ny * 4},
+        "gpu_launches": st.launches * args.steps,
+        "clocks": clk,
+        "energy_last_frame": st.energy,
+        "kernels": kernels,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(video)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as the reference arm: each step solves one 160x240
+    tile (1/8 of a 640x480 frame, same levels, stride and iterations)."""
+    import numpy as np
+
+    import oracle as O
+    from paper_1610_07159_gb300 import scenes
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    video = scenes.SceneVideo(WIDTH, HEIGHT, 2, seed=100).frames(2)
+    tw, th = WIDTH // 4, HEIGHT // 2
+    tiles = [video[f][:, ty * th:(ty + 1) * th, tx * tw:(tx + 1) * tw].astype(np.float64)
+             for f in range(2) for ty in range(2) for tx in range(4)]
+    p = O.Params.preset("fig2", gn_iters=(GN,) * 8, pcg_iters=(PCG,) * 8)
+    for k in range(args.warmup):
+        O.solve_frame(tiles[k % len(tiles)], STRIDE, LEVELS, p)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        O.solve_frame(tiles[k % len(tiles)], STRIDE, LEVELS, p)
+    dt = time.perf_counter() - t0
+    value = args.steps / 8.0 / dt
+    sample = (f"each step solves one {tw}x{th} tile (1/8 of a {WIDTH}x{HEIGHT} frame: {LEVELS} levels, stride "
+              f"{STRIDE}, {GN} GN x {PCG} PCG) with the single-threaded FP64 C oracle; frames/s = steps / 8 / time")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded ray-cast stereo video)",
+        "config": {"workload": WORKLOAD, "global_batch": 1, "seq_len": NFRAMES, "parallelism": "single host core"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=120)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -82,6 +82,20 @@ enum { SF_TEMPORAL_PROPAGATE = 0, SF_TEMPORAL_COPY = 1, SF_TEMPORAL_ZERO = 2 };
 enum { SF_FP32 = 0, SF_MIXED_BF16 = 1 };
 /* Columns of Table 1 (Appendix A). */
 enum { SF_PRESET_FIG2 = 0, SF_PRESET_FIG568 = 1, SF_PRESET_FIG79 = 2 };
+/* Synchronisation of the PCG solve: SF_PCG_AUTO takes one thread-block
+ * cluster when the level fits in one (up to 16 CTAs) and a cooperative launch
+ * over the GPU otherwise; the other two force one of them. */
+enum { SF_PCG_AUTO = 0, SF_PCG_CLUSTER = 1, SF_PCG_GRID = 2 };
+/* Kernel classes, for sf_params.profile_mask and sf_kernel_times. */
+enum {
+    SF_K_PYRAMID = 0,  /* mip-map levels with gradient planes */
+    SF_K_LEVEL = 1,    /* level init, halfway image, feature weights, output */
+    SF_K_ASSEMBLE = 2, /* per-pixel data terms reduced into cell blocks */
+    SF_K_GATHER = 3,   /* node blocks, priors, preconditioner, energy */
+    SF_K_PCG = 4,      /* the conjugate-gradient solve */
+    SF_K_ENERGY = 5,   /* trial energies, backtracking, step update */
+    SF_K_COUNT = 6
+};
 
 typedef struct sf_params {
     /* Table 1 (Appendix A); w_smooth = w_mag = 1 in every experiment */
@@ -101,6 +115,8 @@ typedef struct sf_params {
     int precision;                /* SF_FP32 | SF_MIXED_BF16 */
     int max_backtracks;           /* step halvings tried before a step is rejected (4) */
     int use_graph;                /* 1: replay the frame as one captured CUDA graph */
+    int profile_mask;             /* bit k set: time every launch of kernel class k with CUDA events */
+    int pcg_mode;                 /* SF_PCG_AUTO | SF_PCG_CLUSTER | SF_PCG_GRID */
 } sf_params;
 
 typedef struct sf_stats {
@@ -108,6 +124,8 @@ typedef struct sf_stats {
     int frames;                   /* frames solved since sf_create / sf_reset */
     int levels;
     int n_excluded;               /* finest-level pixels with W = 0 in the last step */
+    int launches;                 /* kernel launches per frame */
+    int pad;
     double energy;                /* final energy of the last frame (Eq. 8) */
     double terms[5];              /* its weighted parts: photo, grad, smooth, epi, mag */
     /* per level and Gauss-Newton step of the last frame */
@@ -162,6 +180,11 @@ SF_API int sf_get_stats(sf_ctx* ctx, sf_stats* out);
 /* Copies the final delta and total fields of `level` of the last frame into
  * device buffers (6 x G floats each; either may be NULL). */
 SF_API int sf_get_state(sf_ctx* ctx, int level, float* delta, float* total, void* stream);
+
+/* Device time of kernel class `klass` in the last frame: the sum over its
+ * launches (ms) and their number. Needs the class in profile_mask; waits for
+ * the context's work. */
+SF_API int sf_kernel_times(sf_ctx* ctx, int klass, double* total_ms, int* launches);
 
 SF_API void sf_destroy(sf_ctx* ctx);
 SF_API const char* sf_status_string(int status);

@@ -142,11 +142,11 @@ template <int MAXOUT>
 __global__ void __launch_bounds__(ETHREADS) k_assemble(LevelGeom g, int cpb, const float4* __restrict__ tex,
                                                        const float* __restrict__ base, const float* __restrict__ delta,
                                                        DevParams P, uint8_t* __restrict__ Wmask,
-                                                       float* __restrict__ cell, double* __restrict__ part)
+                                                       float* __restrict__ cell, float2* __restrict__ part)
 {
     __shared__ float sHB[ETHREADS * HB];
     __shared__ float sA[ETHREADS * 4];
-    __shared__ double sred[ETHREADS / 32];
+    __shared__ ff sred[ETHREADS / 32];
     const int tid = threadIdx.x;
     const int s = g.s;
     const int cj = blockIdx.y, ci0 = blockIdx.x * cpb;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(ETHREADS) k_assemble(LevelGeom g, int cpb, con
     float acc[MAXOUT];
 #pragma unroll
     for (int k = 0; k < MAXOUT; ++k) acc[k] = 0.f;
-    double ep = 0.0, eg = 0.0;
+    float ep = 0.f, eg = 0.f;
     int nex = 0;
 
     for (int c0 = 0; c0 < total; c0 += ETHREADS) {
@@ -236,13 +236,13 @@ __global__ void __launch_bounds__(ETHREADS) k_assemble(LevelGeom g, int cpb, con
         }
     }
     const int blk = blockIdx.y * gridDim.x + blockIdx.x;
-    const double tp = block_sum<ETHREADS>(ep, sred);
-    const double tg = block_sum<ETHREADS>(eg, sred);
-    const double tn = block_sum<ETHREADS>((double)nex, sred);
+    const ff tp = ff_block_sum<ETHREADS>(ff_from(ep), sred);
+    const ff tg = ff_block_sum<ETHREADS>(ff_from(eg), sred);
+    const ff tn = ff_block_sum<ETHREADS>(ff_from((float)nex), sred);
     if (tid == 0) {
-        part[blk] = tp;
-        part[MAX_PART + blk] = tg;
-        part[2 * MAX_PART + blk] = tn;
+        part[blk] = make_float2(tp.hi, tp.lo);
+        part[MAX_PART + blk] = make_float2(tg.hi, tg.lo);
+        part[2 * MAX_PART + blk] = make_float2(tn.hi, tn.lo);
     }
 }
 
@@ -304,8 +304,7 @@ __device__ __forceinline__ void node_total(const float* __restrict__ base, const
 // undirected edge once, weight (w_i + w_j) w_f), epipolar, magnitude.
 __device__ __forceinline__ void node_prior_energy(const LevelGeom& g, const DevParams& P, const float* __restrict__ base,
                                                   const float* __restrict__ delta, const float* __restrict__ x, float t,
-                                                  const float* __restrict__ wf, int n, double& es, double& ee,
-                                                  double& em)
+                                                  const float* __restrict__ wf, int n, float& es, float& ee, float& em)
 {
     const int i = n % g.nx, j = n / g.nx;
     float T[6], d[6];
@@ -327,7 +326,7 @@ __device__ __forceinline__ void node_prior_energy(const LevelGeom& g, const DevP
     es = acc;
     float r[2], J[12];
     epipolar(P.Fl, (float)(i * g.s), (float)(j * g.s), T, r, J);
-    ee = (double)r[0] * r[0] + (double)r[1] * r[1];
+    ee = r[0] * r[0] + r[1] * r[1];
     float m = 0.f;
 #pragma unroll
     for (int u = 0; u < 6; ++u) m += P.mfl[u >> 1] * d[u] * d[u];
@@ -340,14 +339,14 @@ __global__ void __launch_bounds__(ETHREADS) k_gather(LevelGeom g, const float* _
                                                      const float* __restrict__ base, const float* __restrict__ delta,
                                                      const float* __restrict__ wf, DevParams P,
                                                      float* __restrict__ node, float* __restrict__ rhs,
-                                                     float* __restrict__ minv, double* __restrict__ gpart,
-                                                     const double* __restrict__ apart, int n_asm, unsigned* counter,
+                                                     float* __restrict__ minv, float2* __restrict__ gpart,
+                                                     const float2* __restrict__ apart, int n_asm, unsigned* counter,
                                                      StepCtrl* __restrict__ ctrl, int* status)
 {
-    __shared__ double sred[ETHREADS / 32];
+    __shared__ ff sred[ETHREADS / 32];
     __shared__ bool last_sh;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    double es = 0.0, ee = 0.0, em = 0.0;
+    float es = 0.f, ee = 0.f, em = 0.f;
     if (n < g.G) {
         const int i = n % g.nx, j = n / g.nx;
         const int ncx = g.ncx, ncy = g.ncy, G = g.G;
@@ -430,13 +429,13 @@ __global__ void __launch_bounds__(ETHREADS) k_gather(LevelGeom g, const float* _
         node_prior_energy(g, P, base, delta, nullptr, 0.f, wf, n, es, ee, em);
     }
     if (!ctrl) return;
-    const double ts = block_sum<ETHREADS>(es, sred);
-    const double te = block_sum<ETHREADS>(ee, sred);
-    const double tm = block_sum<ETHREADS>(em, sred);
+    const ff ts = ff_block_sum<ETHREADS>(ff_from(es), sred);
+    const ff te = ff_block_sum<ETHREADS>(ff_from(ee), sred);
+    const ff tm = ff_block_sum<ETHREADS>(ff_from(em), sred);
     if (threadIdx.x == 0) {
-        gpart[blockIdx.x] = ts;
-        gpart[MAX_PART + blockIdx.x] = te;
-        gpart[2 * MAX_PART + blockIdx.x] = tm;
+        gpart[blockIdx.x] = make_float2(ts.hi, ts.lo);
+        gpart[MAX_PART + blockIdx.x] = make_float2(te.hi, te.lo);
+        gpart[2 * MAX_PART + blockIdx.x] = make_float2(tm.hi, tm.lo);
         __threadfence();
         const unsigned done = atomicAdd(counter, 1u);
         last_sh = done == gridDim.x - 1;
@@ -445,12 +444,14 @@ __global__ void __launch_bounds__(ETHREADS) k_gather(LevelGeom g, const float* _
     if (!last_sh) return;
     if (threadIdx.x < 32) {
         __threadfence();
-        const double sp = fixed_sum(apart, n_asm);
-        const double sg = fixed_sum(apart + MAX_PART, n_asm);
-        const double sx = fixed_sum(apart + 2 * MAX_PART, n_asm);
-        const double ss = fixed_sum(gpart, gridDim.x);
-        const double se = fixed_sum(gpart + MAX_PART, gridDim.x);
-        const double sm = fixed_sum(gpart + 2 * MAX_PART, gridDim.x);
+        const ff fp = ff_fixed_sum(apart, n_asm);
+        const ff fg = ff_fixed_sum(apart + MAX_PART, n_asm);
+        const ff fx = ff_fixed_sum(apart + 2 * MAX_PART, n_asm);
+        const ff fs = ff_fixed_sum(gpart, gridDim.x);
+        const ff fe = ff_fixed_sum(gpart + MAX_PART, gridDim.x);
+        const ff fm = ff_fixed_sum(gpart + 2 * MAX_PART, gridDim.x);
+        const double sp = (double)fp.hi + fp.lo, sg = (double)fg.hi + fg.lo, sx = (double)fx.hi + fx.lo;
+        const double ss = (double)fs.hi + fs.lo, se = (double)fe.hi + fe.lo, sm = (double)fm.hi + fm.lo;
         if (threadIdx.x == 0) {
             StepCtrl c;
             c.terms_cur[0] = P.w_photo * sp;
@@ -480,14 +481,14 @@ __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, c
                                                      const float* __restrict__ base, const float* __restrict__ delta,
                                                      const float* __restrict__ x, float t, const float* __restrict__ wf,
                                                      DevParams P, uint8_t* __restrict__ Wmask, int wmode,
-                                                     double* __restrict__ part, unsigned* counter,
+                                                     float2* __restrict__ part, unsigned* counter,
                                                      StepCtrl* __restrict__ ctrl, int action, int last,
                                                      double* __restrict__ rec, int* status)
 {
-    __shared__ double sred[ETHREADS / 32];
+    __shared__ ff sred[ETHREADS / 32];
     __shared__ bool last_sh;
     if (action == 1 && ld_acquire_s32(&ctrl->accepted)) return;
-    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if ((int)blockIdx.x < npixblk) {
         const int N = g.w * g.h;
         for (int p = blockIdx.x * ETHREADS + threadIdx.x; p < N; p += npixblk * ETHREADS) {
@@ -503,15 +504,15 @@ __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, c
             if (wmode) Wmask[p] = (uint8_t)Wi;
             v[0] += Ep;
             v[1] += Eg;
-            v[5] += Wi ? 0.0 : 1.0;
+            v[5] += Wi ? 0.f : 1.f;
         }
     } else {
         const int n = (blockIdx.x - npixblk) * ETHREADS + threadIdx.x;
         if (n < g.G) node_prior_energy(g, P, base, delta, x, t, wf, n, v[2], v[3], v[4]);
     }
     for (int q = 0; q < 6; ++q) {
-        const double sq = block_sum<ETHREADS>(v[q], sred);
-        if (threadIdx.x == 0) part[q * MAX_PART + blockIdx.x] = sq;
+        const ff sq = ff_block_sum<ETHREADS>(ff_from(v[q]), sred);
+        if (threadIdx.x == 0) part[q * MAX_PART + blockIdx.x] = make_float2(sq.hi, sq.lo);
     }
     if (threadIdx.x == 0) {
         __threadfence();
@@ -523,7 +524,10 @@ __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, c
     if (threadIdx.x < 32) {
         __threadfence();
         double s[6];
-        for (int q = 0; q < 6; ++q) s[q] = fixed_sum(part + q * MAX_PART, gridDim.x);
+        for (int q = 0; q < 6; ++q) {
+            const ff t = ff_fixed_sum(part + q * MAX_PART, gridDim.x);
+            s[q] = (double)t.hi + t.lo;
+        }
         if (threadIdx.x == 0) {
             double terms[5];
             terms[0] = P.w_photo * s[0];
@@ -576,7 +580,7 @@ __global__ void k_unpack_blocks(int G, const float* __restrict__ node, const flo
 
 template <int MAXOUT>
 void assemble_impl(const LevelGeom& g, int cpb, const float4* tex, const float* base, const float* delta,
-                   const DevParams& P, uint8_t* Wmask, float* cell, double* part, cudaStream_t st)
+                   const DevParams& P, uint8_t* Wmask, float* cell, float2* part, cudaStream_t st)
 {
     dim3 grid((g.ncx + cpb - 1) / cpb, g.ncy);
     k_assemble<MAXOUT><<<grid, ETHREADS, 0, st>>>(g, cpb, tex, base, delta, P, Wmask, cell, part);

@@ -70,6 +70,11 @@ struct sf_ctx {
     cudaStream_t cap = nullptr;
     cudaStream_t last_stream = nullptr;
     std::vector<void*> allocs;
+    // profiling: event pairs around launches of the classes in profile_mask
+    std::vector<cudaEvent_t> ev_begin, ev_end;
+    std::vector<int> ev_class;
+    int nprof = 0;
+    int launches = 0; // kernel launches per frame
 };
 
 namespace {
@@ -99,6 +104,8 @@ void free_ctx(sf_ctx* c)
     if (!c) return;
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap) cudaStreamDestroy(c->cap);
+    for (cudaEvent_t e : c->ev_begin) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_end) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
     delete c;
 }
@@ -156,44 +163,94 @@ int check_cuda(cudaError_t e)
     return e == cudaErrorMemoryAllocation ? SF_ERR_OOM : SF_ERR_CUDA;
 }
 
+// Records a timing event for kernel class k if it is being profiled (inside
+// a stream capture the event becomes an event-record node of the graph).
+void prof_mark(sf_ctx* c, int k, bool begin, cudaStream_t st)
+{
+    if (!(c->prm.profile_mask & (1 << k))) return;
+    if (begin) {
+        if (c->nprof >= (int)c->ev_begin.size()) {
+            cudaEvent_t a, b;
+            if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return;
+            c->ev_begin.push_back(a);
+            c->ev_end.push_back(b);
+            c->ev_class.push_back(k);
+        }
+        c->ev_class[c->nprof] = k;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    cudaEvent_t e = begin ? c->ev_begin[c->nprof] : c->ev_end[c->nprof];
+    if (cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, st);
+    if (!begin) c->nprof += 1;
+}
+
 // Enqueues one frame of Algorithm 1 on `st` (the inputs come through args).
 int enqueue_frame(sf_ctx* c, cudaStream_t st)
 {
     const sf_params& P = c->prm;
+    int nl = 0;
+    c->nprof = 0;
+    prof_mark(c, SF_K_PYRAMID, true, st);
     launch_tex0(c->args, nullptr, c->w0, c->h0, c->lv[0].tex, st);
-    for (int l = 1; l < c->L; ++l)
+    ++nl;
+    for (int l = 1; l < c->L; ++l, ++nl)
         launch_texdown(c->lv[l - 1].tex, c->geo[l - 1].w, c->geo[l - 1].h, c->lv[l].tex, c->geo[l].w, c->geo[l].h, st);
+    prof_mark(c, SF_K_PYRAMID, false, st);
     for (int l = c->L - 1; l >= 0; --l) {
         const LevelGeom& g = c->geo[l];
         LevelBuf& b = c->lv[l];
         const bool has_c = l < c->L - 1;
+        prof_mark(c, SF_K_LEVEL, true, st);
         launch_level_init(g, has_c ? &c->geo[l + 1] : nullptr, has_c ? c->lv[l + 1].base : nullptr,
                           has_c ? c->lv[l + 1].delta : nullptr, b.base, b.delta, b.prev_delta, b.prev_total,
                           c->init_buf, c->args, P.temporal_mode, st);
+        ++nl;
         if (P.wfeat_mode == SF_WFEAT_EIG) {
             launch_halfway(g, b.tex, b.base, b.delta, b.H, st);
             launch_wfeat(g, b.H, c->dp[l], b.wf, st);
+            nl += 2;
         }
+        prof_mark(c, SF_K_LEVEL, false, st);
         for (int gi = 0; gi < P.gn_iters[l]; ++gi) {
             StepCtrl* ctrl = c->ctrl + l * SF_MAX_GN + gi;
             uint8_t* Wst = b.W + (size_t)gi * g.w * g.h; // this step's outlier mask, kept for inspection
+            prof_mark(c, SF_K_ASSEMBLE, true, st);
             launch_assemble(g, b.tex, b.base, b.delta, c->dp[l], Wst, b.cell, c->sc, st);
+            prof_mark(c, SF_K_ASSEMBLE, false, st);
+            prof_mark(c, SF_K_GATHER, true, st);
             launch_gather(g, b.cell, b.base, b.delta, b.wf, c->dp[l], b.node, b.rhs, b.minv, c->sc, ctrl,
                           c->asm_blocks[l], st);
-            cudaError_t e = launch_pcg(g, c->plan[l], b.node, b.rhs, b.minv, b.x, b.z, b.p0, b.p1, c->pcg_part, c->bar,
-                                       c->sc.status, P.pcg_iters[l], 0, st);
+            prof_mark(c, SF_K_GATHER, false, st);
+            prof_mark(c, SF_K_PCG, true, st);
+            cudaError_t e = launch_pcg(g, c->plan[l], b.node, b.rhs, b.minv, b.x, b.z, b.p0, b.p1,
+                                       (float2*)c->pcg_part, c->bar, c->sc.status, P.pcg_iters[l], 0, st);
+            prof_mark(c, SF_K_PCG, false, st);
             if (e != cudaSuccess) return check_cuda(e);
+            nl += 3;
+            prof_mark(c, SF_K_ENERGY, true, st);
             float t = 1.f;
-            for (int j = 0; j <= P.max_backtracks; ++j, t *= 0.5f)
+            for (int j = 0; j <= P.max_backtracks; ++j, t *= 0.5f, ++nl)
                 launch_energy(g, b.tex, b.base, b.delta, b.x, t, b.wf, c->dp[l], Wst, 0, c->sc, ctrl, 1,
                               j == P.max_backtracks, nullptr, st);
             launch_apply_step(g, b.delta, b.x, ctrl, st);
+            ++nl;
+            prof_mark(c, SF_K_ENERGY, false, st);
         }
-        if (l == 0 && P.gn_iters[0] == 0)
+        prof_mark(c, SF_K_LEVEL, true, st);
+        if (l == 0 && P.gn_iters[0] == 0) {
             launch_energy(g, b.tex, b.base, b.delta, nullptr, 0.f, b.wf, c->dp[0], b.W, 1, c->sc, nullptr, 0, 0,
                           c->rec, st);
+            ++nl;
+        }
         launch_finish_level(g, b.base, b.delta, b.prev_delta, b.prev_total, c->args, l == 0, st);
+        ++nl;
+        prof_mark(c, SF_K_LEVEL, false, st);
     }
+    c->launches = nl + 1; // + the argument kernel of sf_solve
     return check_cuda(cudaGetLastError());
 }
 
@@ -252,7 +309,8 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
         width > (1 << 15) || height > (1 << 15) || grid_stride > 256 || !finite_params(*p) || !(p->eps > 0.f) ||
         p->max_backtracks < 0 || p->max_backtracks > 8 || p->robust_mode < 0 || p->robust_mode > 1 ||
         p->grad_mode < 0 || p->grad_mode > 1 || p->wfeat_mode < 0 || p->wfeat_mode > 1 || p->temporal_mode < 0 ||
-        p->temporal_mode > 2 || p->precision != SF_FP32 || !(p->wfeat_tau > 0.f)) {
+        p->temporal_mode > 2 || p->precision != SF_FP32 || !(p->wfeat_tau > 0.f) || p->pcg_mode < 0 ||
+        p->pcg_mode > 2) {
         fail(SF_ERR_ARG);
         return nullptr;
     }
@@ -305,7 +363,7 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
         return nullptr;
     }
     for (int l = 0; l < levels; ++l) {
-        c->plan[l] = pcg_plan(c->geo[l].G, c->sm_count);
+        c->plan[l] = pcg_plan(c->geo[l].G, c->sm_count, p->pcg_mode);
         if (c->plan[l].blocks < 1) {
             delete c;
             fail(SF_ERR_ARG);
@@ -453,6 +511,7 @@ int sf_get_stats(sf_ctx* c, sf_stats* out)
     out->status = (status & DEV_TIMEOUT) ? SF_ERR_TIMEOUT : (status & DEV_NUMERIC) ? SF_ERR_NUMERIC : SF_OK;
     out->frames = c->frames;
     out->levels = c->L;
+    out->launches = c->launches;
     for (int l = 0; l < c->L; ++l)
         for (int g = 0; g < c->prm.gn_iters[l] && g < SF_MAX_GN; ++g) {
             const StepCtrl& s = h[l * SF_MAX_GN + g];
@@ -485,6 +544,27 @@ int sf_get_state(sf_ctx* c, int level, float* delta, float* total, void* stream)
     if (!rc && total)
         rc = check_cuda(cudaMemcpyAsync(total, c->lv[level].prev_total, bytes, cudaMemcpyDeviceToDevice, st));
     return rc ? fail(rc) : SF_OK;
+}
+
+int sf_kernel_times(sf_ctx* c, int klass, double* total_ms, int* launches)
+{
+    if (!c || klass < 0 || klass >= SF_K_COUNT || !total_ms) return fail(SF_ERR_ARG);
+    if (!(c->prm.profile_mask & (1 << klass))) return fail(SF_ERR_STATE);
+    int rc = check_cuda(cudaDeviceSynchronize());
+    if (rc) return fail(rc);
+    double tot = 0.0;
+    int n = 0;
+    for (int i = 0; i < c->nprof; ++i) {
+        if (c->ev_class[i] != klass) continue;
+        float ms = 0.f;
+        rc = check_cuda(cudaEventElapsedTime(&ms, c->ev_begin[i], c->ev_end[i]));
+        if (rc) return fail(rc);
+        tot += ms;
+        ++n;
+    }
+    *total_ms = tot;
+    if (launches) *launches = n;
+    return SF_OK;
 }
 
 void sf_destroy(sf_ctx* c)
@@ -566,8 +646,8 @@ int sf_probe_pcg(sf_ctx* c, int level, int iters, float* x, void* stream)
     c->last_stream = st;
     const LevelGeom& g = c->geo[level];
     LevelBuf& b = c->lv[level];
-    int rc = check_cuda(launch_pcg(g, c->plan[level], b.node, b.rhs, b.minv, x, b.z, b.p0, b.p1, c->pcg_part, c->bar,
-                                   c->sc.status, iters, 1, st));
+    int rc = check_cuda(launch_pcg(g, c->plan[level], b.node, b.rhs, b.minv, x, b.z, b.p0, b.p1,
+                                   (float2*)c->pcg_part, c->bar, c->sc.status, iters, 1, st));
     return rc ? fail(rc) : SF_OK;
 }
 

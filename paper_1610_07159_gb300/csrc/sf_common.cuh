@@ -235,30 +235,70 @@ __device__ __forceinline__ void pixel_fields(const float* __restrict__ base, con
 // reductions
 // ---------------------------------------------------------------------------
 
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* sh)
+// ---------------------------------------------------------------------------
+// float-float (unevaluated sum hi + lo) accumulation: about 44 significant
+// bits from FP32 operations only. GB300's FP64 add has ~64 cycles of latency
+// against ~4.5 for FP32, so reductions on a critical path avoid FP64.
+// two_sum is Knuth's error-free transformation of a + b.
+// ---------------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_add(ff a, ff b)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < NT / 32; ++i) r += sh[i];
-    return r; // valid in thread 0
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    const float h = s + e;
+    return ff{h, e - (h - s)};
 }
 
-// Sum of n partials in a fixed order, the same in every block (warp 0 only).
-__device__ __forceinline__ double fixed_sum(const double* __restrict__ part, int n)
+__device__ __forceinline__ ff ff_from(float v) { return ff{v, 0.f}; }
+
+__device__ __forceinline__ ff ff_shfl_xor(ff v, int m)
+{
+    return ff{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
+}
+
+// Warp butterfly: every lane ends with the same total.
+__device__ __forceinline__ ff ff_warp_sum(ff v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = ff_add(v, ff_shfl_xor(v, o));
+    return v;
+}
+
+// Block sum; the result is valid in every thread. sh needs NT/32 entries.
+template <int NT>
+__device__ __forceinline__ ff ff_block_sum(ff v, ff* sh)
+{
+    v = ff_warp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    ff t = (threadIdx.x & 31) < NT / 32 ? sh[threadIdx.x & 31] : ff{0.f, 0.f};
+    return ff_warp_sum(t);
+}
+
+// Fixed-order sum of n float-float partials written by other blocks (L2
+// loads); every lane of the calling warp gets the same total.
+__device__ __forceinline__ ff ff_fixed_sum(const float2* part, int n)
 {
     const int lane = threadIdx.x & 31;
-    double v = 0.0;
-    for (int i = lane; i < n; i += 32) v += __ldcg(part + i);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    ff v{0.f, 0.f};
+    for (int i = lane; i < n; i += 32) {
+        const float2 t = __ldcg(part + i);
+        v = ff_add(v, ff{t.x, t.y});
+    }
+    return ff_warp_sum(v);
+}
+
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)

@@ -23,10 +23,11 @@ void launch_add(const float* a, const float* b, float* out, size_t n, cudaStream
 
 // sf_assemble.cu: per-pixel data terms, cell assembly, node gather with the
 // priors, trial energies with the backtracking decision, step update.
+// Per-block partial sums are float-float pairs (hi, lo).
 struct Scratch {
-    double* asm_part; // [3][MAX_PART]: photo, grad, excluded
-    double* gat_part; // [3][MAX_PART]: smooth, epi, mag
-    double* en_part;  // [6][MAX_PART]: photo, grad, smooth, epi, mag, excluded
+    float2* asm_part; // [3][MAX_PART]: photo, grad, excluded
+    float2* gat_part; // [3][MAX_PART]: smooth, epi, mag
+    float2* en_part;  // [6][MAX_PART]: photo, grad, smooth, epi, mag, excluded
     unsigned* counters; // [4]
     int* status;
 };
@@ -49,12 +50,13 @@ void launch_unpack_blocks(const LevelGeom& g, const float* node, const float* rh
 // sf_pcg.cu: Jacobi-preconditioned CG on the block system, one cooperative
 // launch per solve with a bounded grid barrier between phases.
 struct PcgPlan {
-    int blocks;
-    int npt;
+    int blocks;  // CTAs of the launch
+    int npt;     // nodes per four-lane group
+    int cluster; // 1: one thread-block cluster, 0: cooperative grid
 };
-PcgPlan pcg_plan(int G, int sm_count);
+PcgPlan pcg_plan(int G, int sm_count, int mode);
 cudaError_t launch_pcg(const LevelGeom& g, const PcgPlan& plan, const float* node, const float* rhs,
-                       const float* minv, float* x, float* z, float* p0, float* p1, double* part, unsigned* bar,
+                       const float* minv, float* x, float* z, float* p0, float* p1, float2* part, unsigned* bar,
                        int* status, int iters, int interleaved_out, cudaStream_t st);
 
 } // namespace sfk

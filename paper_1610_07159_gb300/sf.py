@@ -25,11 +25,13 @@ GRAD_BROX, GRAD_LITERAL = 0, 1
 WFEAT_EIG, WFEAT_OFF = 0, 1
 TEMPORAL_PROPAGATE, TEMPORAL_COPY, TEMPORAL_ZERO = 0, 1, 2
 FP32, MIXED_BF16 = 0, 1
+K_PYRAMID, K_LEVEL, K_ASSEMBLE, K_GATHER, K_PCG, K_ENERGY = range(6)
+PCG_AUTO, PCG_CLUSTER, PCG_GRID = 0, 1, 2
 PRESET_FIG2, PRESET_FIG568, PRESET_FIG79 = 0, 1, 2
 
 EXPORTED = (
     "sf_params_preset", "sf_create", "sf_solve", "sf_solve_host", "sf_grid_dims", "sf_set_init", "sf_reset",
-    "sf_get_stats", "sf_get_state", "sf_destroy", "sf_status_string", "sf_last_error", "sf_probe_pyramid",
+    "sf_get_stats", "sf_get_state", "sf_kernel_times", "sf_destroy", "sf_status_string", "sf_last_error", "sf_probe_pyramid",
     "sf_probe_feature_weights", "sf_probe_assemble", "sf_probe_pcg", "sf_probe_wmask", "sf_probe_energy",
 )
 
@@ -49,13 +51,14 @@ class Params(ctypes.Structure):
         ("robust_mode", ctypes.c_int), ("grad_mode", ctypes.c_int), ("wfeat_mode", ctypes.c_int),
         ("wfeat_gain", ctypes.c_float), ("wfeat_tau", ctypes.c_float),
         ("temporal_mode", ctypes.c_int), ("precision", ctypes.c_int), ("max_backtracks", ctypes.c_int),
-        ("use_graph", ctypes.c_int),
+        ("use_graph", ctypes.c_int), ("profile_mask", ctypes.c_int), ("pcg_mode", ctypes.c_int),
     ]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int), ("frames", ctypes.c_int), ("levels", ctypes.c_int), ("n_excluded", ctypes.c_int),
+        ("launches", ctypes.c_int), ("pad", ctypes.c_int),
         ("energy", ctypes.c_double), ("terms", ctypes.c_double * 5),
         ("step_energy", (ctypes.c_double * MAX_GN) * MAX_LEVELS),
         ("step_accepted", (ctypes.c_double * MAX_GN) * MAX_LEVELS),
@@ -94,6 +97,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sf_reset.argtypes = [vp]
     L.sf_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     L.sf_get_state.argtypes = [vp, i, fp, fp, vp]
+    L.sf_kernel_times.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double), ip]
     L.sf_destroy.argtypes = [vp]
     L.sf_destroy.restype = None
     L.sf_status_string.argtypes = [i]
@@ -212,6 +216,12 @@ class Solver:
         if rc not in (OK, ERR_NUMERIC, ERR_TIMEOUT):
             _check(rc, "sf_get_stats")
         return st
+
+    def kernel_times(self, klass: int) -> tuple[float, int]:
+        """(total ms, launches) of kernel class `klass` in the last frame."""
+        ms, n = ctypes.c_double(), ctypes.c_int()
+        _check(self.L.sf_kernel_times(self.ctx, int(klass), ctypes.byref(ms), ctypes.byref(n)), "sf_kernel_times")
+        return ms.value, n.value
 
     def state(self, level: int) -> tuple[torch.Tensor, torch.Tensor]:
         _, _, nx, ny = self.dims(level)

@@ -47,8 +47,9 @@ def test_struct_layout_matches_header():
 int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(sf_params), offsetof(sf_params, F), offsetof(sf_params, gn_iters),
          offsetof(sf_params, wfeat_gain), offsetof(sf_params, use_graph), sizeof(sf_stats));
-  printf("%zu %zu %zu %zu\n", offsetof(sf_stats, energy), offsetof(sf_stats, step_energy),
-         offsetof(sf_stats, step_t), offsetof(sf_stats, step_excluded));
+  printf("%zu %zu %zu %zu %zu %zu\n", offsetof(sf_stats, energy), offsetof(sf_stats, step_energy),
+         offsetof(sf_stats, step_t), offsetof(sf_stats, step_excluded), offsetof(sf_stats, launches),
+         offsetof(sf_params, profile_mask));
   return 0;
 }
 '''
@@ -62,7 +63,8 @@ int main(void) {
     P, S = sf.Params, sf.Stats
     assert vals[:6] == [ctypes.sizeof(P), P.F.offset, P.gn_iters.offset, P.wfeat_gain.offset, P.use_graph.offset,
                         ctypes.sizeof(S)]
-    assert vals[6:] == [S.energy.offset, S.step_energy.offset, S.step_t.offset, S.step_excluded.offset]
+    assert vals[6:] == [S.energy.offset, S.step_energy.offset, S.step_t.offset, S.step_excluded.offset,
+                        S.launches.offset, P.profile_mask.offset]
 
 
 def test_preset_is_table1(lib):

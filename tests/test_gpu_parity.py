@@ -102,9 +102,9 @@ def test_assemble_parity(w, h, s_, level, kw):
     assert abs(energy - E_ref) < 1e-5 * abs(E_ref)
 
 
-@pytest.mark.parametrize("iters", [1, 5, 20])
-def test_pcg_parity_on_the_same_system(iters):
-    solver, lv, op = _level_setup(160, 120, 4, 3, 0)
+@pytest.mark.parametrize("iters,mode", [(1, 0), (5, 0), (20, 0), (20, sf.PCG_CLUSTER), (20, sf.PCG_GRID)])
+def test_pcg_parity_on_the_same_system(iters, mode):
+    solver, lv, op = _level_setup(160, 120, 4, 3, 0, pcg_mode=mode)
     rng = np.random.default_rng(3)
     base, delta = _smooth_state(lv.G, rng)
     wf = np.ones(lv.G, dtype=np.float32)
@@ -188,7 +188,8 @@ def test_config1_frame_parity():
 
 
 @pytest.mark.parametrize("kw", [{"robust_mode": O.SQRT_PAPER}, {"grad_mode": O.GRAD_LITERAL},
-                                {"wfeat_mode": O.WFEAT_OFF, "eps_p": 0.0}, {"use_graph": 0}])
+                                {"wfeat_mode": O.WFEAT_OFF, "eps_p": 0.0}, {"use_graph": 0},
+                                {"pcg_mode": sf.PCG_GRID}, {"pcg_mode": sf.PCG_CLUSTER}])
 def test_config1_frame_parity_modes(kw):
     q = scenes.plane_quadruple(seed=2)
     for r in _solve_both(q, 4, 3, [5], [10], **kw):
