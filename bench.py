@@ -161,12 +161,18 @@ def dist_setup(backend):
 
 
 def max_over_ranks(dist, value, device):
+    """Largest value over the ranks (each rank's own timed region)."""
     if dist is None:
         return value
     import torch
     t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_rate(world, steps, t_max_ms):
+    """Frames of all ranks per second of the slowest rank (weak scaling)."""
+    return world * steps / (t_max_ms / 1e3)
 
 
 def cpu_baseline(video, max_seconds=20.0, max_frames=4):
@@ -243,7 +249,7 @@ def run_ours(args):
     clk = clocks.stop()
     st = solver.stats()
     t_max = max_over_ranks(dist, acc["ms"], dev)
-    value = world * args.steps / (t_max / 1e3)
+    value = aggregate_rate(world, args.steps, t_max)
 
     # end to end through the host entry point: pinned inputs, copies inside the timed region
     host_frames = torch.from_numpy(video).pin_memory()
@@ -268,7 +274,7 @@ def run_ours(args):
         e.synchronize()
         e2e_ms += s.elapsed_time(e)
     e2e_max = max_over_ranks(dist, e2e_ms, dev)
-    e2e_value = world * args.steps / (e2e_max / 1e3)
+    e2e_value = aggregate_rate(world, args.steps, e2e_max)
 
     # roofline of the dominant kernel class, from the live per-kernel times
     peaks, peak_src = measured_peaks()
