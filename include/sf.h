@@ -225,6 +225,28 @@ SF_API int sf_probe_wmask(sf_ctx* ctx, int level, int step, unsigned char* W, vo
 SF_API int sf_probe_energy(sf_ctx* ctx, int level, const float* base, const float* delta, const float* wfeat,
                     const unsigned char* W, double* out6, void* stream);
 
+/* ---- allocation-free PCG ------------------------------------------------
+ * The paper has no counterpart to this call: it exists for callers that
+ * cannot allocate device memory where they solve (inside a CUDA graph
+ * capture, where cudaMalloc is not allowed; in real-time loops that must not
+ * meet the allocator's implicit device synchronisation; under memory pools
+ * that forbid raw allocations after start-up).
+ *
+ * Runs `iters` Jacobi-preconditioned CG iterations from x = 0 on a block
+ * system in the layout sf_probe_assemble writes: blocks [G][5][6][6] (each
+ * node's own block and those coupling it to its E, S, SE and SW neighbours,
+ * row-major), rhs [G][6]; writes x [G][6]; G = nx * ny, all device memory,
+ * enqueued on `stream`. Allocates nothing: its scratch is one file-scope
+ * device array sized for SF_STATIC_PCG_MAX_NODES nodes (288 KiB), held by
+ * every GPU that loads the library until exit; a larger G returns SF_ERR_ARG
+ * without touching the GPU. The first call on a device looks the array's
+ * device address up (cudaGetSymbolAddress) with that device current, so make
+ * that first call before any stream capture. All calls share the array and
+ * every call writes what it reads before reading it; calls that overlap on
+ * the GPU (other streams, other host threads) race on it. */
+#define SF_STATIC_PCG_MAX_NODES 4096
+SF_API int sf_pcg_static(int nx, int ny, const float* blocks, const float* rhs, int iters, float* x, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

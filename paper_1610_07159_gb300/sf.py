@@ -33,7 +33,9 @@ EXPORTED = (
     "sf_params_preset", "sf_create", "sf_solve", "sf_solve_host", "sf_grid_dims", "sf_set_init", "sf_reset",
     "sf_get_stats", "sf_get_state", "sf_kernel_times", "sf_destroy", "sf_status_string", "sf_last_error", "sf_probe_pyramid",
     "sf_probe_feature_weights", "sf_probe_assemble", "sf_probe_pcg", "sf_probe_wmask", "sf_probe_energy",
+    "sf_pcg_static",
 )
+STATIC_PCG_MAX_NODES = 4096
 
 
 class SFError(RuntimeError):
@@ -109,6 +111,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sf_probe_pcg.argtypes = [vp, i, i, fp, vp]
     L.sf_probe_wmask.argtypes = [vp, i, i, fp, vp]
     L.sf_probe_energy.argtypes = [vp, i, fp, fp, fp, fp, fp, vp]
+    L.sf_pcg_static.argtypes = [i, i, fp, fp, i, fp, vp]
     _lib = L
     return L
 
@@ -148,6 +151,18 @@ def _ptr(t: torch.Tensor | None, dtype: torch.dtype | None = None) -> int | None
 
 def _stream() -> int:
     return torch.cuda.current_stream().cuda_stream
+
+
+def pcg_static(nx: int, ny: int, blocks: torch.Tensor, rhs: torch.Tensor, iters: int,
+               x: torch.Tensor | None = None) -> torch.Tensor:
+    """sf_pcg_static: PCG on a [G,5,6,6] block system with no device allocation
+    inside the call (the caller allocates x, or this wrapper does before it)."""
+    G = int(nx) * int(ny)
+    if x is None:
+        x = torch.empty((G, 6), device=blocks.device, dtype=torch.float32)
+    _check(load().sf_pcg_static(int(nx), int(ny), _ptr(blocks, torch.float32), _ptr(rhs, torch.float32), int(iters),
+                                _ptr(x, torch.float32), _stream()), "sf_pcg_static")
+    return x
 
 
 class Solver:
