@@ -82,10 +82,13 @@ enum { SF_TEMPORAL_PROPAGATE = 0, SF_TEMPORAL_COPY = 1, SF_TEMPORAL_ZERO = 2 };
 enum { SF_FP32 = 0, SF_MIXED_BF16 = 1 };
 /* Columns of Table 1 (Appendix A). */
 enum { SF_PRESET_FIG2 = 0, SF_PRESET_FIG568 = 1, SF_PRESET_FIG79 = 2 };
-/* Synchronisation of the PCG solve: SF_PCG_AUTO takes one thread-block
- * cluster when the level fits in one (up to 16 CTAs) and a cooperative launch
- * over the GPU otherwise; the other two force one of them. */
-enum { SF_PCG_AUTO = 0, SF_PCG_CLUSTER = 1, SF_PCG_GRID = 2 };
+/* Schedule of the PCG solve, per level the first that fits: SF_PCG_DSM (one
+ * thread-block cluster of up to 16 CTAs holding the level's system in
+ * distributed shared memory, one barrier per iteration), then SF_PCG_CLUSTER
+ * (one cluster, vectors in global memory), then SF_PCG_GRID (a cooperative
+ * launch over the GPU). SF_PCG_DSM starts at the first, SF_PCG_AUTO and
+ * SF_PCG_CLUSTER at the second, SF_PCG_GRID takes only the last. */
+enum { SF_PCG_AUTO = 0, SF_PCG_CLUSTER = 1, SF_PCG_GRID = 2, SF_PCG_DSM = 3 };
 /* Kernel classes, for sf_params.profile_mask and sf_kernel_times. */
 enum {
     SF_K_PYRAMID = 0,  /* mip-map levels with gradient planes */
@@ -116,7 +119,8 @@ typedef struct sf_params {
     int max_backtracks;           /* step halvings tried before a step is rejected (4) */
     int use_graph;                /* 1: replay the frame as one captured CUDA graph */
     int profile_mask;             /* bit k set: time every launch of kernel class k with CUDA events */
-    int pcg_mode;                 /* SF_PCG_AUTO | SF_PCG_CLUSTER | SF_PCG_GRID */
+    int pcg_mode;                 /* SF_PCG_AUTO | SF_PCG_CLUSTER | SF_PCG_GRID | SF_PCG_DSM */
+    int video;                    /* 1: allocate the level pipeline of sf_solve_video */
 } sf_params;
 
 typedef struct sf_stats {
@@ -163,6 +167,22 @@ SF_API int sf_solve(sf_ctx* ctx, const float* L_t, const float* R_t, const float
  * Host buffers should be pinned for full copy speed. */
 SF_API int sf_solve_host(sf_ctx* ctx, const float* L_t, const float* R_t, const float* L_t1, const float* R_t1,
                   float* out_fields, void* stream);
+
+/* Solves n consecutive frames of one video, continuing from the context's
+ * temporal state, and writes every frame's finest fields. frames: device
+ * float32 [n][4][h][w] (each frame's L_t, R_t, L_t1, R_t1); outs: device
+ * float32 [n][6][ny][nx]. The hierarchy is pipelined across frames: level l of
+ * frame f needs only level l + 1 of frame f and level l of frame f - 1
+ * (Algorithm 1, Section 5.3), so the levels of consecutive frames run
+ * concurrently on the context's streams. The fields equal those of n
+ * sf_solve calls. Needs params.video = 1 at sf_create (SF_ERR_STATE
+ * otherwise). Enqueued on `stream` (the call returns before the work ends). */
+SF_API int sf_solve_video(sf_ctx* ctx, const float* frames, int n, float* outs, void* stream);
+
+/* The same from host memory (pinned for full copy speed): frames are copied
+ * in and fields out through a ring of device slots, overlapped with the
+ * solve; waits for the stream before returning. */
+SF_API int sf_solve_video_host(sf_ctx* ctx, const float* frames, int n, float* outs, void* stream);
 
 /* Level geometry: image size and grid size of `level` (0 = finest). */
 SF_API int sf_grid_dims(const sf_ctx* ctx, int level, int* w, int* h, int* nx, int* ny);

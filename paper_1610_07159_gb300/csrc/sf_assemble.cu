@@ -236,9 +236,9 @@ __global__ void __launch_bounds__(ETHREADS) k_assemble(LevelGeom g, int cpb, con
         }
     }
     const int blk = blockIdx.y * gridDim.x + blockIdx.x;
-    const ff tp = ff_block_sum<ETHREADS>(ff_from(ep), sred);
-    const ff tg = ff_block_sum<ETHREADS>(ff_from(eg), sred);
-    const ff tn = ff_block_sum<ETHREADS>(ff_from((float)nex), sred);
+    const ff tp = ff_block_sum_fast<ETHREADS>(ep, sred);
+    const ff tg = ff_block_sum_fast<ETHREADS>(eg, sred);
+    const ff tn = ff_block_sum_fast<ETHREADS>((float)nex, sred);
     if (tid == 0) {
         part[blk] = make_float2(tp.hi, tp.lo);
         part[MAX_PART + blk] = make_float2(tg.hi, tg.lo);
@@ -429,9 +429,9 @@ __global__ void __launch_bounds__(ETHREADS) k_gather(LevelGeom g, const float* _
         node_prior_energy(g, P, base, delta, nullptr, 0.f, wf, n, es, ee, em);
     }
     if (!ctrl) return;
-    const ff ts = ff_block_sum<ETHREADS>(ff_from(es), sred);
-    const ff te = ff_block_sum<ETHREADS>(ff_from(ee), sred);
-    const ff tm = ff_block_sum<ETHREADS>(ff_from(em), sred);
+    const ff ts = ff_block_sum_fast<ETHREADS>(es, sred);
+    const ff te = ff_block_sum_fast<ETHREADS>(ee, sred);
+    const ff tm = ff_block_sum_fast<ETHREADS>(em, sred);
     if (threadIdx.x == 0) {
         gpart[blockIdx.x] = make_float2(ts.hi, ts.lo);
         gpart[MAX_PART + blockIdx.x] = make_float2(te.hi, te.lo);
@@ -442,14 +442,14 @@ __global__ void __launch_bounds__(ETHREADS) k_gather(LevelGeom g, const float* _
     }
     __syncthreads();
     if (!last_sh) return;
-    if (threadIdx.x < 32) {
-        __threadfence();
-        const ff fp = ff_fixed_sum(apart, n_asm);
-        const ff fg = ff_fixed_sum(apart + MAX_PART, n_asm);
-        const ff fx = ff_fixed_sum(apart + 2 * MAX_PART, n_asm);
-        const ff fs = ff_fixed_sum(gpart, gridDim.x);
-        const ff fe = ff_fixed_sum(gpart + MAX_PART, gridDim.x);
-        const ff fm = ff_fixed_sum(gpart + 2 * MAX_PART, gridDim.x);
+    __threadfence();
+    {
+        const ff fp = ff_block_fixed_sum<ETHREADS>(apart, n_asm, sred);
+        const ff fg = ff_block_fixed_sum<ETHREADS>(apart + MAX_PART, n_asm, sred);
+        const ff fx = ff_block_fixed_sum<ETHREADS>(apart + 2 * MAX_PART, n_asm, sred);
+        const ff fs = ff_block_fixed_sum<ETHREADS>(gpart, gridDim.x, sred);
+        const ff fe = ff_block_fixed_sum<ETHREADS>(gpart + MAX_PART, gridDim.x, sred);
+        const ff fm = ff_block_fixed_sum<ETHREADS>(gpart + 2 * MAX_PART, gridDim.x, sred);
         const double sp = (double)fp.hi + fp.lo, sg = (double)fg.hi + fg.lo, sx = (double)fx.hi + fx.lo;
         const double ss = (double)fs.hi + fs.lo, se = (double)fe.hi + fe.lo, sm = (double)fm.hi + fm.lo;
         if (threadIdx.x == 0) {
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, c
         if (n < g.G) node_prior_energy(g, P, base, delta, x, t, wf, n, v[2], v[3], v[4]);
     }
     for (int q = 0; q < 6; ++q) {
-        const ff sq = ff_block_sum<ETHREADS>(ff_from(v[q]), sred);
+        const ff sq = ff_block_sum_fast<ETHREADS>(v[q], sred);
         if (threadIdx.x == 0) part[q * MAX_PART + blockIdx.x] = make_float2(sq.hi, sq.lo);
     }
     if (threadIdx.x == 0) {
@@ -521,11 +521,11 @@ __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, c
     }
     __syncthreads();
     if (!last_sh) return;
-    if (threadIdx.x < 32) {
-        __threadfence();
+    __threadfence();
+    {
         double s[6];
         for (int q = 0; q < 6; ++q) {
-            const ff t = ff_fixed_sum(part + q * MAX_PART, gridDim.x);
+            const ff t = ff_block_fixed_sum<ETHREADS>(part + q * MAX_PART, gridDim.x, sred);
             s[q] = (double)t.hi + t.lo;
         }
         if (threadIdx.x == 0) {

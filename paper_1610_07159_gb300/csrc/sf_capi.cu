@@ -54,9 +54,10 @@ struct sf_ctx {
     PcgPlan plan[SF_MAX_LEVELS]{};
     int asm_blocks[SF_MAX_LEVELS]{};
     int sm_count = 0;
-    Scratch sc{};
-    double* pcg_part = nullptr;
-    unsigned* bar = nullptr;
+    Scratch sc[SF_MAX_LEVELS]{};              // per level, so levels can run concurrently
+    float2* pcg_part[SF_MAX_LEVELS]{};
+    int* status = nullptr;                    // device status word shared by all levels
+    unsigned long long* bar = nullptr;        // per level: grid-barrier arrival counter
     StepCtrl* ctrl = nullptr; // [SF_MAX_LEVELS * SF_MAX_GN + 1], the last one for probes
     double* rec = nullptr;    // [8] energy record
     DevArgs* args = nullptr;
@@ -75,6 +76,17 @@ struct sf_ctx {
     std::vector<int> ev_class;
     int nprof = 0;
     int launches = 0; // kernel launches per frame
+    // level pipeline of sf_solve_video (allocated when params.video is set)
+    bool video = false;
+    int ring = 0;                                        // frames in flight
+    float4* ring_tex[SF_MAX_LEVELS][SF_MAX_LEVELS]{};    // [ring slot][level] texels
+    float* vstate_delta[SF_MAX_LEVELS][2]{};             // [level][frame parity]
+    float* vstate_total[SF_MAX_LEVELS][2]{};
+    float* vin[SF_MAX_LEVELS]{};                         // [ring slot] staged host inputs (4 images)
+    float* vout[SF_MAX_LEVELS]{};                        // [ring slot] staged host outputs
+    cudaStream_t vstream[SF_MAX_LEVELS]{};
+    cudaEvent_t vev[SF_MAX_LEVELS]{};
+    cudaEvent_t vfork = nullptr;
 };
 
 namespace {
@@ -104,6 +116,11 @@ void free_ctx(sf_ctx* c)
     if (!c) return;
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap) cudaStreamDestroy(c->cap);
+    for (int l = 0; l < SF_MAX_LEVELS; ++l) {
+        if (c->vstream[l]) cudaStreamDestroy(c->vstream[l]);
+        if (c->vev[l]) cudaEventDestroy(c->vev[l]);
+    }
+    if (c->vfork) cudaEventDestroy(c->vfork);
     for (cudaEvent_t e : c->ev_begin) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_end) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
@@ -188,69 +205,175 @@ void prof_mark(sf_ctx* c, int k, bool begin, cudaStream_t st)
     if (!begin) c->nprof += 1;
 }
 
+// Inputs and outputs of one level's solve.
+struct LevelIO {
+    const float4* tex;                                 // the level's texels
+    const float* coarse_base;                          // coarse totals (base + delta, or the
+    const float* coarse_delta;                         // totals alone when delta is null); null at the top
+    const float* prev_delta, *prev_total;              // temporal state of the previous frame
+    float* out_delta, *out_total;                      // state of this frame
+    float* out_fields;                                 // finest output when args is null
+    const DevArgs* args;                               // frame, warm start and output from the device
+    int frame, use_init;                               // when args is null
+};
+
+void enqueue_pyramid(sf_ctx* c, const DevArgs* args, const float* const* in, float4* const* tex, cudaStream_t st,
+                     int& nl)
+{
+    prof_mark(c, SF_K_PYRAMID, true, st);
+    launch_tex0(args, in, c->w0, c->h0, tex[0], st);
+    ++nl;
+    for (int l = 1; l < c->L; ++l, ++nl)
+        launch_texdown(tex[l - 1], c->geo[l - 1].w, c->geo[l - 1].h, tex[l], c->geo[l].w, c->geo[l].h, st);
+    prof_mark(c, SF_K_PYRAMID, false, st);
+}
+
+// One level of Algorithm 1: initialisation, feature weights, the Gauss-Newton
+// steps (assembly, gather, PCG, backtracking trials, update) and the hand-off.
+int enqueue_level(sf_ctx* c, int l, const LevelIO& io, cudaStream_t st, int& nl)
+{
+    const sf_params& P = c->prm;
+    const LevelGeom& g = c->geo[l];
+    LevelBuf& b = c->lv[l];
+    const Scratch& sc = c->sc[l];
+    const bool has_c = l < c->L - 1;
+    prof_mark(c, SF_K_LEVEL, true, st);
+    launch_level_init(g, has_c ? &c->geo[l + 1] : nullptr, io.coarse_base, io.coarse_delta, b.base, b.delta,
+                      io.prev_delta, io.prev_total, c->init_buf, io.args, P.temporal_mode, io.frame, io.use_init, st);
+    ++nl;
+    if (P.wfeat_mode == SF_WFEAT_EIG) {
+        launch_halfway(g, io.tex, b.base, b.delta, b.H, st);
+        launch_wfeat(g, b.H, c->dp[l], b.wf, st);
+        nl += 2;
+    }
+    prof_mark(c, SF_K_LEVEL, false, st);
+    for (int gi = 0; gi < P.gn_iters[l]; ++gi) {
+        StepCtrl* ctrl = c->ctrl + l * SF_MAX_GN + gi;
+        uint8_t* Wst = b.W + (size_t)gi * g.w * g.h; // this step's outlier mask, kept for inspection
+        prof_mark(c, SF_K_ASSEMBLE, true, st);
+        launch_assemble(g, io.tex, b.base, b.delta, c->dp[l], Wst, b.cell, sc, st);
+        prof_mark(c, SF_K_ASSEMBLE, false, st);
+        prof_mark(c, SF_K_GATHER, true, st);
+        launch_gather(g, b.cell, b.base, b.delta, b.wf, c->dp[l], b.node, b.rhs, b.minv, sc, ctrl, c->asm_blocks[l],
+                      st);
+        prof_mark(c, SF_K_GATHER, false, st);
+        prof_mark(c, SF_K_PCG, true, st);
+        cudaError_t e = launch_pcg(g, c->plan[l], b.node, b.rhs, b.minv, b.x, b.z, b.p0, b.p1, c->pcg_part[l],
+                                   c->bar + l, c->status, P.pcg_iters[l], 0, st);
+        prof_mark(c, SF_K_PCG, false, st);
+        if (e != cudaSuccess) return check_cuda(e);
+        nl += 3;
+        prof_mark(c, SF_K_ENERGY, true, st);
+        float t = 1.f;
+        for (int j = 0; j <= P.max_backtracks; ++j, t *= 0.5f, ++nl)
+            launch_energy(g, io.tex, b.base, b.delta, b.x, t, b.wf, c->dp[l], Wst, 0, sc, ctrl, 1,
+                          j == P.max_backtracks, nullptr, st);
+        launch_apply_step(g, b.delta, b.x, ctrl, st);
+        ++nl;
+        prof_mark(c, SF_K_ENERGY, false, st);
+    }
+    prof_mark(c, SF_K_LEVEL, true, st);
+    if (l == 0 && P.gn_iters[0] == 0) {
+        launch_energy(g, io.tex, b.base, b.delta, nullptr, 0.f, b.wf, c->dp[0], b.W, 1, sc, nullptr, 0, 0, c->rec,
+                      st);
+        ++nl;
+    }
+    launch_finish_level(g, b.base, b.delta, io.out_delta, io.out_total, io.args, l == 0, io.out_fields, st);
+    ++nl;
+    prof_mark(c, SF_K_LEVEL, false, st);
+    return check_cuda(cudaGetLastError());
+}
+
 // Enqueues one frame of Algorithm 1 on `st` (the inputs come through args).
 int enqueue_frame(sf_ctx* c, cudaStream_t st)
 {
-    const sf_params& P = c->prm;
     int nl = 0;
     c->nprof = 0;
-    prof_mark(c, SF_K_PYRAMID, true, st);
-    launch_tex0(c->args, nullptr, c->w0, c->h0, c->lv[0].tex, st);
-    ++nl;
-    for (int l = 1; l < c->L; ++l, ++nl)
-        launch_texdown(c->lv[l - 1].tex, c->geo[l - 1].w, c->geo[l - 1].h, c->lv[l].tex, c->geo[l].w, c->geo[l].h, st);
-    prof_mark(c, SF_K_PYRAMID, false, st);
+    float4* tex[SF_MAX_LEVELS];
+    for (int l = 0; l < c->L; ++l) tex[l] = c->lv[l].tex;
+    enqueue_pyramid(c, c->args, nullptr, tex, st, nl);
     for (int l = c->L - 1; l >= 0; --l) {
-        const LevelGeom& g = c->geo[l];
-        LevelBuf& b = c->lv[l];
         const bool has_c = l < c->L - 1;
-        prof_mark(c, SF_K_LEVEL, true, st);
-        launch_level_init(g, has_c ? &c->geo[l + 1] : nullptr, has_c ? c->lv[l + 1].base : nullptr,
-                          has_c ? c->lv[l + 1].delta : nullptr, b.base, b.delta, b.prev_delta, b.prev_total,
-                          c->init_buf, c->args, P.temporal_mode, st);
-        ++nl;
-        if (P.wfeat_mode == SF_WFEAT_EIG) {
-            launch_halfway(g, b.tex, b.base, b.delta, b.H, st);
-            launch_wfeat(g, b.H, c->dp[l], b.wf, st);
-            nl += 2;
-        }
-        prof_mark(c, SF_K_LEVEL, false, st);
-        for (int gi = 0; gi < P.gn_iters[l]; ++gi) {
-            StepCtrl* ctrl = c->ctrl + l * SF_MAX_GN + gi;
-            uint8_t* Wst = b.W + (size_t)gi * g.w * g.h; // this step's outlier mask, kept for inspection
-            prof_mark(c, SF_K_ASSEMBLE, true, st);
-            launch_assemble(g, b.tex, b.base, b.delta, c->dp[l], Wst, b.cell, c->sc, st);
-            prof_mark(c, SF_K_ASSEMBLE, false, st);
-            prof_mark(c, SF_K_GATHER, true, st);
-            launch_gather(g, b.cell, b.base, b.delta, b.wf, c->dp[l], b.node, b.rhs, b.minv, c->sc, ctrl,
-                          c->asm_blocks[l], st);
-            prof_mark(c, SF_K_GATHER, false, st);
-            prof_mark(c, SF_K_PCG, true, st);
-            cudaError_t e = launch_pcg(g, c->plan[l], b.node, b.rhs, b.minv, b.x, b.z, b.p0, b.p1,
-                                       (float2*)c->pcg_part, c->bar, c->sc.status, P.pcg_iters[l], 0, st);
-            prof_mark(c, SF_K_PCG, false, st);
-            if (e != cudaSuccess) return check_cuda(e);
-            nl += 3;
-            prof_mark(c, SF_K_ENERGY, true, st);
-            float t = 1.f;
-            for (int j = 0; j <= P.max_backtracks; ++j, t *= 0.5f, ++nl)
-                launch_energy(g, b.tex, b.base, b.delta, b.x, t, b.wf, c->dp[l], Wst, 0, c->sc, ctrl, 1,
-                              j == P.max_backtracks, nullptr, st);
-            launch_apply_step(g, b.delta, b.x, ctrl, st);
-            ++nl;
-            prof_mark(c, SF_K_ENERGY, false, st);
-        }
-        prof_mark(c, SF_K_LEVEL, true, st);
-        if (l == 0 && P.gn_iters[0] == 0) {
-            launch_energy(g, b.tex, b.base, b.delta, nullptr, 0.f, b.wf, c->dp[0], b.W, 1, c->sc, nullptr, 0, 0,
-                          c->rec, st);
-            ++nl;
-        }
-        launch_finish_level(g, b.base, b.delta, b.prev_delta, b.prev_total, c->args, l == 0, st);
-        ++nl;
-        prof_mark(c, SF_K_LEVEL, false, st);
+        LevelBuf& b = c->lv[l];
+        LevelIO io{b.tex, has_c ? c->lv[l + 1].base : nullptr, has_c ? c->lv[l + 1].delta : nullptr,
+                   b.prev_delta, b.prev_total, b.prev_delta, b.prev_total, nullptr, c->args, 0, 0};
+        int rc = enqueue_level(c, l, io, st, nl);
+        if (rc) return rc;
     }
     c->launches = nl + 1; // + the argument kernel of sf_solve
+    return SF_OK;
+}
+
+// The level pipeline over n frames: step s runs level l on frame
+// s - (L - 1 - l), levels on their own streams, with a join between steps.
+// Level l of frame f needs level l + 1 of frame f (previous step) and level l
+// of frame f - 1 (previous step), so the result equals the sequential order.
+// host_in / host_out: stage frames from and to host memory through the ring.
+int enqueue_video(sf_ctx* c, const float* frames, const float* host_in, int n, float* outs, float* host_out,
+                  cudaStream_t st)
+{
+    const int L = c->L, R = c->ring;
+    const size_t N0 = (size_t)c->w0 * c->h0, G6 = (size_t)6 * c->geo[0].G;
+    const int f0 = c->frames;
+    int nl = 0;
+    c->nprof = 0;
+    if (cudaEventRecord(c->vfork, st) != cudaSuccess) return check_cuda(cudaGetLastError());
+    for (int l = 0; l < L; ++l) cudaStreamWaitEvent(c->vstream[l], c->vfork, 0);
+    if (f0 > 0)
+        for (int l = 0; l < L; ++l) {
+            const size_t bytes = (size_t)6 * c->geo[l].G * sizeof(float);
+            cudaMemcpyAsync(c->vstate_delta[l][(f0 - 1) & 1], c->lv[l].prev_delta, bytes, cudaMemcpyDeviceToDevice,
+                            c->vstream[l]);
+            cudaMemcpyAsync(c->vstate_total[l][(f0 - 1) & 1], c->lv[l].prev_total, bytes, cudaMemcpyDeviceToDevice,
+                            c->vstream[l]);
+        }
+    for (int s = 0; s < n + L - 1; ++s) {
+        if (s > 0) {
+            for (int l = 0; l < L; ++l) cudaEventRecord(c->vev[l], c->vstream[l]);
+            for (int l = 0; l < L; ++l)
+                for (int m = 0; m < L; ++m)
+                    if (m != l) cudaStreamWaitEvent(c->vstream[l], c->vev[m], 0);
+        }
+        for (int l = L - 1; l >= 0; --l) {
+            const int fl = s - (L - 1 - l);
+            if (fl < 0 || fl >= n) continue;
+            const int fg = f0 + fl, slot = fg % R;
+            cudaStream_t bs = c->vstream[l];
+            if (l == L - 1) {
+                const float* src = frames + (size_t)fl * 4 * N0;
+                if (host_in) {
+                    cudaMemcpyAsync(c->vin[slot], host_in + (size_t)fl * 4 * N0, 4 * N0 * sizeof(float),
+                                    cudaMemcpyHostToDevice, bs);
+                    src = c->vin[slot];
+                }
+                const float* in[4] = {src, src + N0, src + 2 * N0, src + 3 * N0};
+                enqueue_pyramid(c, nullptr, in, c->ring_tex[slot], bs, nl);
+            }
+            const bool has_c = l < L - 1;
+            float* out = nullptr;
+            if (l == 0) out = host_out ? c->vout[slot] : outs + (size_t)fl * G6;
+            LevelIO io{c->ring_tex[slot][l], has_c ? c->vstate_total[l + 1][fg & 1] : nullptr, nullptr,
+                       c->vstate_delta[l][(fg + 1) & 1], c->vstate_total[l][(fg + 1) & 1],
+                       c->vstate_delta[l][fg & 1], c->vstate_total[l][fg & 1], out, nullptr, fg,
+                       (l == L - 1 && fl == 0) ? c->pending_init : 0};
+            int rc = enqueue_level(c, l, io, bs, nl);
+            if (rc) return rc;
+            if (l == 0 && host_out)
+                cudaMemcpyAsync(host_out + (size_t)fl * G6, out, G6 * sizeof(float), cudaMemcpyDeviceToHost, bs);
+        }
+    }
+    for (int l = 0; l < L; ++l) {
+        cudaEventRecord(c->vev[l], c->vstream[l]);
+        cudaStreamWaitEvent(st, c->vev[l], 0);
+    }
+    // hand the last frame's state back to the single-frame path
+    const int fz = f0 + n - 1;
+    for (int l = 0; l < L; ++l) {
+        const size_t bytes = (size_t)6 * c->geo[l].G * sizeof(float);
+        cudaMemcpyAsync(c->lv[l].prev_delta, c->vstate_delta[l][fz & 1], bytes, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(c->lv[l].prev_total, c->vstate_total[l][fz & 1], bytes, cudaMemcpyDeviceToDevice, st);
+    }
+    c->launches = n > 0 ? nl / n : 0;
     return check_cuda(cudaGetLastError());
 }
 
@@ -310,7 +433,7 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
         p->max_backtracks < 0 || p->max_backtracks > 8 || p->robust_mode < 0 || p->robust_mode > 1 ||
         p->grad_mode < 0 || p->grad_mode > 1 || p->wfeat_mode < 0 || p->wfeat_mode > 1 || p->temporal_mode < 0 ||
         p->temporal_mode > 2 || p->precision != SF_FP32 || !(p->wfeat_tau > 0.f) || p->pcg_mode < 0 ||
-        p->pcg_mode > 2) {
+        p->pcg_mode > 3) {
         fail(SF_ERR_ARG);
         return nullptr;
     }
@@ -383,9 +506,28 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
              dalloc(c, &b.cell, (size_t)CELL_VALS * (g.ncx * g.ncy));
     }
     const size_t N0 = (size_t)width * height;
-    ok = ok && dalloc(c, &c->sc.asm_part, 3 * (size_t)MAX_PART) && dalloc(c, &c->sc.gat_part, 3 * (size_t)MAX_PART) &&
-         dalloc(c, &c->sc.en_part, 6 * (size_t)MAX_PART) && dalloc(c, &c->sc.counters, 8) &&
-         dalloc(c, &c->sc.status, 4) && dalloc(c, &c->pcg_part, 2 * (size_t)MAX_PART) && dalloc(c, &c->bar, 4) &&
+    ok = ok && dalloc(c, &c->status, 4);
+    for (int l = 0; l < levels && ok; ++l) {
+        Scratch& sc = c->sc[l];
+        ok = dalloc(c, &sc.asm_part, 3 * (size_t)MAX_PART) && dalloc(c, &sc.gat_part, 3 * (size_t)MAX_PART) &&
+             dalloc(c, &sc.en_part, 6 * (size_t)MAX_PART) && dalloc(c, &sc.counters, 8) &&
+             dalloc(c, &c->pcg_part[l], 2 * (size_t)MAX_PART);
+        sc.status = c->status;
+    }
+    if (ok && p->video) {
+        c->video = true;
+        c->ring = levels;
+        for (int r = 0; r < c->ring && ok; ++r) {
+            for (int l = 0; l < levels && ok; ++l)
+                ok = dalloc(c, &c->ring_tex[r][l], 4 * (size_t)c->geo[l].w * c->geo[l].h);
+            ok = ok && dalloc(c, &c->vin[r], 4 * N0) && dalloc(c, &c->vout[r], (size_t)6 * c->geo[0].G);
+        }
+        for (int l = 0; l < levels && ok; ++l)
+            for (int q = 0; q < 2 && ok; ++q)
+                ok = dalloc(c, &c->vstate_delta[l][q], (size_t)6 * c->geo[l].G) &&
+                     dalloc(c, &c->vstate_total[l][q], (size_t)6 * c->geo[l].G);
+    }
+    ok = ok && dalloc(c, &c->bar, (size_t)SF_MAX_LEVELS) &&
          dalloc(c, &c->ctrl, (size_t)SF_MAX_LEVELS * SF_MAX_GN + 1) && dalloc(c, &c->rec, 8) &&
          dalloc(c, &c->args, 1) && dalloc(c, &c->init_buf, (size_t)6 * c->geo[levels - 1].G) &&
          dalloc(c, &c->in_buf[0], N0) && dalloc(c, &c->in_buf[1], N0) && dalloc(c, &c->in_buf[2], N0) &&
@@ -397,8 +539,14 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
     }
     if (p->wfeat_mode == SF_WFEAT_OFF)
         for (int l = 0; l < levels; ++l) launch_fill(c->lv[l].wf, 1.f, (size_t)c->geo[l].G, 0);
-    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaDeviceSynchronize() != cudaSuccess) {
+    bool sok = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess;
+    if (sok && c->video) {
+        sok = cudaEventCreateWithFlags(&c->vfork, cudaEventDisableTiming) == cudaSuccess;
+        for (int l = 0; l < levels && sok; ++l)
+            sok = cudaStreamCreateWithFlags(&c->vstream[l], cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&c->vev[l], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!sok || cudaDeviceSynchronize() != cudaSuccess) {
         cudaGetLastError();
         free_ctx(c);
         fail(SF_ERR_CUDA);
@@ -461,6 +609,33 @@ int sf_solve_host(sf_ctx* c, const float* L_t, const float* R_t, const float* L_
     return rc ? fail(rc) : SF_OK;
 }
 
+int sf_solve_video(sf_ctx* c, const float* frames, int n, float* outs, void* stream)
+{
+    if (!c || !frames || !outs || n < 1) return fail(SF_ERR_ARG);
+    if (!c->video) return fail(SF_ERR_STATE);
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    int rc = enqueue_video(c, frames, nullptr, n, outs, nullptr, st);
+    if (rc) return fail(rc);
+    c->frames += n;
+    c->pending_init = 0;
+    return SF_OK;
+}
+
+int sf_solve_video_host(sf_ctx* c, const float* frames, int n, float* outs, void* stream)
+{
+    if (!c || !frames || !outs || n < 1) return fail(SF_ERR_ARG);
+    if (!c->video) return fail(SF_ERR_STATE);
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    int rc = enqueue_video(c, nullptr, frames, n, nullptr, outs, st);
+    if (rc) return fail(rc);
+    c->frames += n;
+    c->pending_init = 0;
+    rc = check_cuda(cudaStreamSynchronize(st));
+    return rc ? fail(rc) : SF_OK;
+}
+
 int sf_grid_dims(const sf_ctx* c, int level, int* w, int* h, int* nx, int* ny)
 {
     if (!c || level < 0 || level >= c->L) return fail(SF_ERR_ARG);
@@ -488,9 +663,9 @@ int sf_reset(sf_ctx* c)
     c->frames = 0;
     c->pending_init = 0;
     int rc = check_cuda(cudaDeviceSynchronize());
-    if (!rc) rc = check_cuda(cudaMemset(c->sc.status, 0, 4 * sizeof(int)));
-    if (!rc) rc = check_cuda(cudaMemset(c->bar, 0, 4 * sizeof(unsigned)));
-    if (!rc) rc = check_cuda(cudaMemset(c->sc.counters, 0, 8 * sizeof(unsigned)));
+    if (!rc) rc = check_cuda(cudaMemset(c->status, 0, 4 * sizeof(int)));
+    if (!rc) rc = check_cuda(cudaMemset(c->bar, 0, SF_MAX_LEVELS * sizeof(unsigned long long)));
+    for (int l = 0; l < c->L && !rc; ++l) rc = check_cuda(cudaMemset(c->sc[l].counters, 0, 8 * sizeof(unsigned)));
     if (!rc) rc = check_cuda(cudaDeviceSynchronize());
     return rc ? fail(rc) : SF_OK;
 }
@@ -504,7 +679,7 @@ int sf_get_stats(sf_ctx* c, sf_stats* out)
     int status = 0;
     double rec[8];
     rc = check_cuda(cudaMemcpy(h.data(), c->ctrl, h.size() * sizeof(StepCtrl), cudaMemcpyDeviceToHost));
-    if (!rc) rc = check_cuda(cudaMemcpy(&status, c->sc.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!rc) rc = check_cuda(cudaMemcpy(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (!rc) rc = check_cuda(cudaMemcpy(rec, c->rec, sizeof(rec), cudaMemcpyDeviceToHost));
     if (rc) return fail(rc);
     std::memset(out, 0, sizeof(*out));
@@ -628,8 +803,8 @@ int sf_probe_assemble(sf_ctx* c, int level, const float* base, const float* delt
     const LevelGeom& g = c->geo[level];
     LevelBuf& b = c->lv[level];
     StepCtrl* pc = c->ctrl + SF_MAX_LEVELS * SF_MAX_GN;
-    launch_assemble(g, b.tex, base, delta, c->dp[level], b.W, b.cell, c->sc, st);
-    launch_gather(g, b.cell, base, delta, wfeat, c->dp[level], b.node, b.rhs, b.minv, c->sc, pc, c->asm_blocks[level],
+    launch_assemble(g, b.tex, base, delta, c->dp[level], b.W, b.cell, c->sc[level], st);
+    launch_gather(g, b.cell, base, delta, wfeat, c->dp[level], b.node, b.rhs, b.minv, c->sc[level], pc, c->asm_blocks[level],
                   st);
     if (blocks && rhs) launch_unpack_blocks(g, b.node, b.rhs, blocks, rhs, st);
     int rc = SF_OK;
@@ -647,7 +822,7 @@ int sf_probe_pcg(sf_ctx* c, int level, int iters, float* x, void* stream)
     const LevelGeom& g = c->geo[level];
     LevelBuf& b = c->lv[level];
     int rc = check_cuda(launch_pcg(g, c->plan[level], b.node, b.rhs, b.minv, x, b.z, b.p0, b.p1,
-                                   (float2*)c->pcg_part, c->bar, c->sc.status, iters, 1, st));
+                                   c->pcg_part[level], c->bar + level, c->status, iters, 1, st));
     return rc ? fail(rc) : SF_OK;
 }
 
@@ -672,7 +847,7 @@ int sf_probe_energy(sf_ctx* c, int level, const float* base, const float* delta,
     int rc = SF_OK;
     if (W) rc = check_cuda(cudaMemcpyAsync(b.W, W, (size_t)g.w * g.h, cudaMemcpyDeviceToDevice, st));
     if (rc) return fail(rc);
-    launch_energy(g, b.tex, base, delta, nullptr, 0.f, wfeat, c->dp[level], b.W, W ? 0 : 1, c->sc, nullptr, 0, 0, c->rec,
+    launch_energy(g, b.tex, base, delta, nullptr, 0.f, wfeat, c->dp[level], b.W, W ? 0 : 1, c->sc[level], nullptr, 0, 0, c->rec,
                   st);
     rc = check_cuda(cudaMemcpyAsync(out6, c->rec, 6 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if (!rc) rc = check_cuda(cudaGetLastError());

@@ -270,6 +270,27 @@ __device__ __forceinline__ ff ff_warp_sum(ff v)
     return v;
 }
 
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block sum; the result is valid in every thread. sh needs NT/32 entries.
+// Within a warp the 32 values are summed in FP32 (a fixed tree), across warps
+// and blocks in float-float.
+template <int NT>
+__device__ __forceinline__ ff ff_block_sum_fast(float x, ff* sh)
+{
+    const float w = warp_sum(x);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = ff_from(w);
+    __syncthreads();
+    ff t = (threadIdx.x & 31) < NT / 32 ? sh[threadIdx.x & 31] : ff{0.f, 0.f};
+    return ff_warp_sum(t);
+}
+
 // Block sum; the result is valid in every thread. sh needs NT/32 entries.
 template <int NT>
 __device__ __forceinline__ ff ff_block_sum(ff v, ff* sh)
@@ -295,6 +316,20 @@ __device__ __forceinline__ ff ff_fixed_sum(const float2* part, int n)
     return ff_warp_sum(v);
 }
 
+// Fixed-order sum of n float-float partials by a whole block: thread t folds
+// indices t, t + NT, ... in order, then a fixed block reduction. Every thread
+// of the block gets the same total.
+template <int NT>
+__device__ __forceinline__ ff ff_block_fixed_sum(const float2* part, int n, ff* sh)
+{
+    ff v{0.f, 0.f};
+    for (int i = threadIdx.x; i < n; i += NT) {
+        const float2 t = __ldcg(part + i);
+        v = ff_add(v, ff{t.x, t.y});
+    }
+    return ff_block_sum<NT>(v, sh);
+}
+
 __device__ __forceinline__ void cluster_sync_all()
 {
     asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
@@ -315,37 +350,55 @@ __device__ __forceinline__ int ld_acquire_s32(const int* p)
     return v;
 }
 
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).
-// bar[0] counts arrivals, bar[1] is the generation. A waiter gives up after
-// about one second (clock64 on the SM clock), latches DEV_TIMEOUT and returns
-// false; once the status word holds an error every later barrier returns
-// false at once, so the kernel unwinds instead of hanging.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* status, unsigned nblocks)
+// Grid-wide barrier for a cooperative launch (all blocks co-resident), on a
+// 64-bit arrival counter that only grows. Every launch of one kernel on one
+// counter has the same number of blocks N and passes the same number of
+// barriers in every block, so the counter is a multiple of N when a launch
+// starts; a block reads it once (grid_barrier_base) before its first arrival,
+// when at most N-1 arrivals of the first barrier can be in. Barrier k of the
+// launch waits for base + k*N arrivals. Arrivals are fire-and-forget
+// reductions (red.release.gpu), so N blocks do not queue behind returning
+// atomics. A waiter gives up after about one second (clock64 on the SM clock),
+// latches DEV_TIMEOUT and returns false; once the status word holds an error
+// every later barrier returns false at once, so the kernel unwinds instead of
+// hanging. After a timeout the counter is no longer a multiple of N: the
+// context resets it together with the status word.
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long grid_barrier_base(unsigned long long* ctr, unsigned nblocks)
+{
+    __shared__ unsigned long long base_sh;
+    if (threadIdx.x == 0) base_sh = (ld_acquire_u64(ctr) / nblocks) * nblocks;
+    __syncthreads();
+    return base_sh;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, int* status, unsigned long long target)
 {
     __shared__ int ok_sh;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = ld_acquire_s32(status) == 0;
         if (ok) {
-            const unsigned gen = ld_acquire_u32(bar + 1);
-            __threadfence();
-            const unsigned arrived = atomicAdd(bar, 1u);
-            if (arrived == nblocks - 1) {
-                atomicExch(bar, 0u);
-                __threadfence();
-                atomicAdd(bar + 1, 1u);
-            } else {
-                const long long t0 = clock64();
-                while (ld_acquire_u32(bar + 1) == gen) {
-                    if (clock64() - t0 > 2000000000LL) {
-                        atomicOr(status, DEV_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(20);
+            red_release_add_u64(ctr, 1ull);
+            const long long t0 = clock64();
+            while (ld_acquire_u64(ctr) < target) {
+                if (clock64() - t0 > 2000000000LL) {
+                    atomicOr(status, DEV_TIMEOUT);
+                    ok = 0;
+                    break;
                 }
             }
-            __threadfence();
         }
         ok_sh = ok;
     }

@@ -9,15 +9,18 @@ namespace sfk {
 // delta hierarchy and temporal transfer, feature weights (Section 4.3).
 void launch_tex0(const DevArgs* args, const float* const* in_direct, int w, int h, float4* tex, cudaStream_t st);
 void launch_texdown(const float4* texp, int wp, int hp, float4* tex, int w, int h, cudaStream_t st);
+// args == nullptr: frame and use_init are taken as given (eager launches);
+// delta_c == nullptr: base_c holds the coarse totals.
 void launch_level_init(const LevelGeom& g, const LevelGeom* gc, const float* base_c, const float* delta_c,
                        float* base, float* delta, const float* prev_delta, const float* prev_total,
-                       const float* init_buf, const DevArgs* args, int temporal_mode, cudaStream_t st);
+                       const float* init_buf, const DevArgs* args, int temporal_mode, int frame, int use_init,
+                       cudaStream_t st);
 void launch_halfway(const LevelGeom& g, const float4* tex, const float* base, const float* delta, float* H,
                     cudaStream_t st);
 void launch_wfeat(const LevelGeom& g, const float* H, const DevParams& P, float* wf, cudaStream_t st);
 void launch_fill(float* p, float v, size_t n, cudaStream_t st);
 void launch_finish_level(const LevelGeom& g, const float* base, const float* delta, float* prev_delta,
-                         float* prev_total, const DevArgs* args, int write_out, cudaStream_t st);
+                         float* prev_total, const DevArgs* args, int write_out, float* out, cudaStream_t st);
 void launch_unpack_tex(const float4* tex, int w, int h, float* planes, cudaStream_t st);
 void launch_add(const float* a, const float* b, float* out, size_t n, cudaStream_t st);
 
@@ -52,11 +55,13 @@ void launch_unpack_blocks(const LevelGeom& g, const float* node, const float* rh
 struct PcgPlan {
     int blocks;  // CTAs of the launch
     int npt;     // nodes per four-lane group
-    int cluster; // 1: one thread-block cluster, 0: cooperative grid
+    int cluster; // 2: one cluster, state in distributed shared memory;
+                 // 1: one cluster, vectors in global memory; 0: cooperative grid
+    int npc;     // nodes per CTA (cluster == 2)
 };
 PcgPlan pcg_plan(int G, int sm_count, int mode);
 cudaError_t launch_pcg(const LevelGeom& g, const PcgPlan& plan, const float* node, const float* rhs,
-                       const float* minv, float* x, float* z, float* p0, float* p1, float2* part, unsigned* bar,
-                       int* status, int iters, int interleaved_out, cudaStream_t st);
+                       const float* minv, float* x, float* z, float* p0, float* p1, float2* part,
+                       unsigned long long* bar, int* status, int iters, int interleaved_out, cudaStream_t st);
 
 } // namespace sfk

@@ -73,14 +73,15 @@ __global__ void k_texdown(const float4* __restrict__ texp, int wp, int hp, float
 __global__ void k_level_init(LevelGeom g, int have_coarse, int nxc, int nyc, const float* __restrict__ base_c,
                              const float* __restrict__ delta_c, float* __restrict__ base, float* __restrict__ delta,
                              const float* __restrict__ prev_delta, const float* __restrict__ prev_total,
-                             const float* __restrict__ init_buf, const DevArgs* __restrict__ args, int temporal_mode)
+                             const float* __restrict__ init_buf, const DevArgs* __restrict__ args, int temporal_mode,
+                             int frame_direct, int use_init_direct)
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.G) return;
     const int i = n % g.nx, j = n / g.nx;
     const int Gc = nxc * nyc;
-    const int frame = args ? args->frame : 0;
-    const int use_init = args ? args->use_init : 0;
+    const int frame = args ? args->frame : frame_direct;
+    const int use_init = args ? args->use_init : use_init_direct;
     for (int c = 0; c < 6; ++c) {
         float b = 0.f;
         if (have_coarse) {
@@ -90,10 +91,11 @@ __global__ void k_level_init(LevelGeom g, int have_coarse, int nxc, int nyc, con
             const int i0 = min((int)floorf(u), nxc - 2), j0 = min((int)floorf(v), nyc - 2);
             const float a = u - (float)i0, bb = v - (float)j0;
             const int m = j0 * nxc + i0;
-            const float t00 = base_c[c * Gc + m] + delta_c[c * Gc + m];
-            const float t10 = base_c[c * Gc + m + 1] + delta_c[c * Gc + m + 1];
-            const float t01 = base_c[c * Gc + m + nxc] + delta_c[c * Gc + m + nxc];
-            const float t11 = base_c[c * Gc + m + nxc + 1] + delta_c[c * Gc + m + nxc + 1];
+            // delta_c == nullptr: base_c already holds the coarse totals
+            const float t00 = base_c[c * Gc + m] + (delta_c ? delta_c[c * Gc + m] : 0.f);
+            const float t10 = base_c[c * Gc + m + 1] + (delta_c ? delta_c[c * Gc + m + 1] : 0.f);
+            const float t01 = base_c[c * Gc + m + nxc] + (delta_c ? delta_c[c * Gc + m + nxc] : 0.f);
+            const float t11 = base_c[c * Gc + m + nxc + 1] + (delta_c ? delta_c[c * Gc + m + nxc + 1] : 0.f);
             const float top = (1.f - a) * t00 + a * t10, bot = (1.f - a) * t01 + a * t11;
             b = 2.f * ((1.f - bb) * top + bb * bot);
         }
@@ -178,7 +180,7 @@ __global__ void k_add(const float* a, const float* b, float* out, size_t n)
 // writes the output fields.
 __global__ void k_finish_level(int n6, const float* __restrict__ base, const float* __restrict__ delta,
                                float* __restrict__ prev_delta, float* __restrict__ prev_total,
-                               const DevArgs* __restrict__ args, int write_out)
+                               const DevArgs* __restrict__ args, int write_out, float* __restrict__ out_direct)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n6) return;
@@ -186,7 +188,7 @@ __global__ void k_finish_level(int n6, const float* __restrict__ base, const flo
     const float T = base[k] + d;
     prev_delta[k] = d;
     prev_total[k] = T;
-    if (write_out) args->out[k] = T;
+    if (write_out) (args ? args->out : out_direct)[k] = T;
 }
 
 __global__ void k_unpack_tex(const float4* __restrict__ tex, int n, float* __restrict__ planes)
@@ -226,11 +228,12 @@ void launch_texdown(const float4* texp, int wp, int hp, float4* tex, int w, int 
 
 void launch_level_init(const LevelGeom& g, const LevelGeom* gc, const float* base_c, const float* delta_c,
                        float* base, float* delta, const float* prev_delta, const float* prev_total,
-                       const float* init_buf, const DevArgs* args, int temporal_mode, cudaStream_t st)
+                       const float* init_buf, const DevArgs* args, int temporal_mode, int frame, int use_init,
+                       cudaStream_t st)
 {
     k_level_init<<<(g.G + T1D - 1) / T1D, T1D, 0, st>>>(g, gc != nullptr, gc ? gc->nx : 0, gc ? gc->ny : 0, base_c,
                                                         delta_c, base, delta, prev_delta, prev_total, init_buf,
-                                                        args, temporal_mode);
+                                                        args, temporal_mode, frame, use_init);
 }
 
 void launch_halfway(const LevelGeom& g, const float4* tex, const float* base, const float* delta, float* H,
@@ -252,10 +255,11 @@ void launch_add(const float* a, const float* b, float* out, size_t n, cudaStream
 }
 
 void launch_finish_level(const LevelGeom& g, const float* base, const float* delta, float* prev_delta,
-                         float* prev_total, const DevArgs* args, int write_out, cudaStream_t st)
+                         float* prev_total, const DevArgs* args, int write_out, float* out, cudaStream_t st)
 {
     const int n6 = 6 * g.G;
-    k_finish_level<<<(n6 + T1D - 1) / T1D, T1D, 0, st>>>(n6, base, delta, prev_delta, prev_total, args, write_out);
+    k_finish_level<<<(n6 + T1D - 1) / T1D, T1D, 0, st>>>(n6, base, delta, prev_delta, prev_total, args, write_out,
+                                                         out);
 }
 
 void launch_unpack_tex(const float4* tex, int w, int h, float* planes, cudaStream_t st)

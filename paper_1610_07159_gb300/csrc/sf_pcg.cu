@@ -19,7 +19,13 @@
 // CTAs) the launch is a single cluster and the phases meet at the hardware
 // cluster barrier; larger levels use a cooperative launch over the whole GPU
 // and a bounded global-memory barrier.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "sf_launch.h"
+
+namespace cg = cooperative_groups;
 
 namespace sfk {
 
@@ -29,7 +35,8 @@ constexpr int PT = 256; // threads per block
 constexpr int NPB = PT / 4; // nodes per block and pass
 
 struct ClusterSync {
-    __device__ __forceinline__ bool sync(unsigned*, int*) const
+    __device__ __forceinline__ void start(unsigned long long*) {}
+    __device__ __forceinline__ bool sync(unsigned long long*, int*)
     {
         cluster_sync_all();
         return true;
@@ -37,7 +44,13 @@ struct ClusterSync {
 };
 
 struct GridSync {
-    __device__ __forceinline__ bool sync(unsigned* bar, int* status) const { return grid_barrier(bar, status, gridDim.x); }
+    unsigned long long target;
+    __device__ __forceinline__ void start(unsigned long long* ctr) { target = grid_barrier_base(ctr, gridDim.x); }
+    __device__ __forceinline__ bool sync(unsigned long long* ctr, int* status)
+    {
+        target += gridDim.x;
+        return grid_barrier(ctr, status, target);
+    }
 };
 
 // Stencil slot s of node (i, j): the block (owner node, block index) and the
@@ -81,10 +94,11 @@ __device__ __forceinline__ float sel6(const float* v, int c)
 }
 
 template <class Sync>
-__device__ __forceinline__ ff allreduce(ff v, ff* sh, float2* part, const Sync& sy, unsigned* bar, int* status, bool& ok)
+__device__ __forceinline__ ff allreduce(float v, ff* sh, float2* part, Sync& sy, unsigned long long* bar, int* status,
+                                        bool& ok)
 {
     __shared__ ff bc;
-    const ff b = ff_block_sum<PT>(v, sh);
+    const ff b = ff_block_sum_fast<PT>(v, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = make_float2(b.hi, b.lo);
     ok = sy.sync(bar, status) && ok;
     if (threadIdx.x < 32) {
@@ -98,10 +112,11 @@ __device__ __forceinline__ ff allreduce(ff v, ff* sh, float2* part, const Sync& 
 template <int NPT, class Sync>
 __global__ void __launch_bounds__(PT) k_pcg(LevelGeom g, const float* __restrict__ node, const float* __restrict__ rhs,
                                             const float* __restrict__ minv, float* __restrict__ xout, float* z,
-                                            float* p0, float* p1, float2* part, unsigned* bar, int* status, int iters,
-                                            int interleaved, Sync sy)
+                                            float* p0, float* p1, float2* part, unsigned long long* bar, int* status,
+                                            int iters, int interleaved, Sync sy)
 {
     __shared__ ff sred[PT / 32];
+    sy.start(bar);
     const int G = g.G, nx = g.nx, ny = g.ny;
     const int q4 = threadIdx.x & 3;
     const int c0 = q4, c1 = q4 + 4;
@@ -109,10 +124,13 @@ __global__ void __launch_bounds__(PT) k_pcg(LevelGeom g, const float* __restrict
     const int stride = gridDim.x * NPB;
     const int slot0 = blockIdx.x * NPB + (threadIdx.x >> 2);
     float xr[NPT][2], rr[NPT][2], zr[NPT][2], pr[NPT][2], mr[NPT][2], qr[NPT][2];
+    int ni[NPT], nj[NPT]; // node coordinates, computed once
     float acc = 0.f;
 #pragma unroll
     for (int k = 0; k < NPT; ++k) {
         const int n = slot0 + k * stride;
+        nj[k] = n / nx;
+        ni[k] = n - nj[k] * nx;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int c = h ? c1 : c0;
@@ -133,7 +151,7 @@ __global__ void __launch_bounds__(PT) k_pcg(LevelGeom g, const float* __restrict
     bool ok = true;
     float2* part_pq = part;
     float2* part_rz = part + MAX_PART;
-    ff rz = allreduce(ff_from(acc), sred, part_rz, sy, bar, status, ok);
+    ff rz = allreduce(acc, sred, part_rz, sy, bar, status, ok);
     float beta = 0.f;
     for (int it = 0; it < iters && ok; ++it) {
         if (!(rz.hi > 1e-30f)) break;
@@ -154,7 +172,7 @@ __global__ void __launch_bounds__(PT) k_pcg(LevelGeom g, const float* __restrict
             }
             float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (live) {
-                const int i = n % nx, j = n / nx;
+                const int i = ni[k], j = nj[k];
 #pragma unroll
                 for (int ss = 0; ss < 3; ++ss) {
                     const int s = ss == 2 ? 8 : q4 + 4 * ss;
@@ -186,7 +204,7 @@ __global__ void __launch_bounds__(PT) k_pcg(LevelGeom g, const float* __restrict
                 acc = fmaf(pr[k][1], qr[k][1], acc);
             }
         }
-        const ff pq = allreduce(ff_from(acc), sred, part_pq, sy, bar, status, ok);
+        const ff pq = allreduce(acc, sred, part_pq, sy, bar, status, ok);
         if (!ok || !(pq.hi > 1e-30f)) break;
         const float alpha = rz.hi / pq.hi;
         acc = 0.f;
@@ -204,7 +222,7 @@ __global__ void __launch_bounds__(PT) k_pcg(LevelGeom g, const float* __restrict
                 acc = fmaf(rr[k][h], zr[k][h], acc);
             }
         }
-        const ff rz_new = allreduce(ff_from(acc), sred, part_rz, sy, bar, status, ok);
+        const ff rz_new = allreduce(acc, sred, part_rz, sy, bar, status, ok);
         beta = rz_new.hi / rz.hi;
         rz = rz_new;
     }
@@ -224,10 +242,310 @@ __global__ void __launch_bounds__(PT) k_pcg(LevelGeom g, const float* __restrict
     }
 }
 
+// ---------------------------------------------------------------------------
+// Single-cluster PCG with everything in distributed shared memory.
+//
+// Each CTA of one cluster owns a contiguous range of npc nodes and keeps, per
+// owned node, its five coupling blocks (21 floats padded to 24 for 16-byte
+// loads), its preconditioner and two published sets (r, w, s) in shared
+// memory; neighbours read them through distributed shared memory. The loop
+// is the Chronopoulos-Gear form of PCG (algebraically the same iterates as
+// the textbook loop): with u = M r and w = A u, the two dot products
+// gamma = r.u and delta = w.u come from one fused reduction, and a neighbour's
+// u_{i+1} = M (r_i - alpha (w_i + beta s_{i-1})) is formed on the fly from
+// its published r_i, w_i and s_{i-1}. So an iteration has one matrix-vector
+// product, one reduction and one cluster barrier.
+// ---------------------------------------------------------------------------
+constexpr int CT = 512;          // threads per CTA
+constexpr int CT_NPB = CT / 4;   // node slots per pass
+constexpr int NF_BLK = 120, NF_MINV = 8, NF_PUB = 24;
+constexpr int NODE_F = NF_BLK + NF_MINV + 2 * NF_PUB; // 176 floats per owned node
+constexpr int PUB_R = 0, PUB_W = 8, PUB_S = 16;
+
+__device__ __forceinline__ void ld6(const float* p, float v[6])
+{
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    const float2 b = *reinterpret_cast<const float2*>(p + 4);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
+    v[4] = b.x;
+    v[5] = b.y;
+}
+
+__device__ __forceinline__ void ld21(const float* p, float B[NB])
+{
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const float4 a = reinterpret_cast<const float4*>(p)[q];
+        B[4 * q] = a.x;
+        B[4 * q + 1] = a.y;
+        B[4 * q + 2] = a.z;
+        B[4 * q + 3] = a.w;
+    }
+    B[20] = p[20];
+}
+
+// Block sums of two values (FP32 within a warp, float-float across warps);
+// valid in every thread.
+__device__ __forceinline__ void ff_block_sum2(float x, float y, ff& a, ff& b, ff* sh)
+{
+    x = warp_sum(x);
+    y = warp_sum(y);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        sh[2 * (threadIdx.x >> 5)] = ff_from(x);
+        sh[2 * (threadIdx.x >> 5) + 1] = ff_from(y);
+    }
+    __syncthreads();
+    const int l = threadIdx.x & 31;
+    a = l < CT / 32 ? sh[2 * l] : ff{0.f, 0.f};
+    b = l < CT / 32 ? sh[2 * l + 1] : ff{0.f, 0.f};
+    a = ff_warp_sum(a);
+    b = ff_warp_sum(b);
+}
+
+// Owning CTA and local index of node m near this CTA's range [n_lo, n_lo + npc):
+// stencil neighbours are at most one grid row away, so a few steps suffice.
+__device__ __forceinline__ void dsm_owner(int m, int rank, int n_lo, int npc, int& r, int& l)
+{
+    r = rank;
+    l = m - n_lo;
+    while (l < 0) {
+        l += npc;
+        --r;
+    }
+    while (l >= npc) {
+        l -= npc;
+        ++r;
+    }
+}
+
+template <int NPT>
+__global__ void __launch_bounds__(CT, 1) k_pcg_dsm(LevelGeom g, int npc, const float* __restrict__ node,
+                                                const float* __restrict__ rhs, const float* __restrict__ minv_g,
+                                                float* __restrict__ xout, int iters, int interleaved)
+{
+    extern __shared__ float4 dsm4[];
+    float* sm = reinterpret_cast<float*>(dsm4);
+    __shared__ ff sred[2 * (CT / 32)];
+    __shared__ float2 cpart[2][2]; // [parity][gamma, delta] of this CTA as float-float pairs
+    cg::cluster_group cl = cg::this_cluster();
+    const int G = g.G, nx = g.nx, ny = g.ny;
+    const int rank = (int)cl.block_rank();
+    const int C = (int)cl.num_blocks();
+    const int n_lo = rank * npc;
+    const int n_own = min(npc, G - n_lo);
+    const int q4 = threadIdx.x & 3;
+    const int c0 = q4, c1 = q4 + 4;
+    const bool has1 = c1 < 6;
+    const int ls = threadIdx.x >> 2;
+
+    // stage the owned nodes' blocks and preconditioner; publish r_0 = b, s_{-1} = 0
+    for (int t = threadIdx.x; t < n_own * NODE_VALS; t += CT) {
+        const int e = t / n_own, ln = t - e * n_own;
+        const int blk = e / NB, ee = e - blk * NB;
+        sm[ln * NODE_F + blk * 24 + ee] = __ldg(node + (size_t)e * G + n_lo + ln);
+    }
+    for (int t = threadIdx.x; t < n_own * 6; t += CT) {
+        const int c = t / n_own, ln = t - c * n_own;
+        float* nd = sm + ln * NODE_F;
+        nd[NF_BLK + c] = __ldg(minv_g + c * G + n_lo + ln);
+        nd[NF_BLK + NF_MINV + PUB_R + c] = __ldg(rhs + c * G + n_lo + ln);
+        nd[NF_BLK + NF_MINV + PUB_S + c] = 0.f;
+    }
+    float xr[NPT][2], rr[NPT][2], ur[NPT][2], wr[NPT][2], sr[NPT][2], pr[NPT][2], mr[NPT][2];
+    int ni[NPT], nj[NPT]; // node coordinates, computed once
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int ln = ls + k * CT_NPB;
+        nj[k] = (n_lo + ln) / nx;
+        ni[k] = n_lo + ln - nj[k] * nx;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = h ? c1 : c0;
+            const bool live = ln < n_own && (h == 0 || has1);
+            const float r0 = live ? __ldg(rhs + c * G + n_lo + ln) : 0.f;
+            mr[k][h] = live ? __ldg(minv_g + c * G + n_lo + ln) : 0.f;
+            rr[k][h] = r0;
+            ur[k][h] = mr[k][h] * r0;
+            xr[k][h] = wr[k][h] = sr[k][h] = pr[k][h] = 0.f;
+        }
+    }
+    cl.sync();
+
+    float alpha = 0.f, beta = 0.f;
+    ff gam{0.f, 0.f};
+    for (int i = -1; i < iters; ++i) {
+        // i = -1 is the set-up pass: w_0 = A u_0 and the first reduction
+        const int par = i < 0 ? 0 : (i & 1);
+        const int npar = i < 0 ? 0 : (par ^ 1);
+        if (i >= 0) {
+            // own updates: p_i, s_i, x_{i+1}, r_{i+1}, u_{i+1}
+#pragma unroll
+            for (int k = 0; k < NPT; ++k)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    pr[k][h] = fmaf(beta, pr[k][h], ur[k][h]);
+                    sr[k][h] = fmaf(beta, sr[k][h], wr[k][h]);
+                    xr[k][h] = fmaf(alpha, pr[k][h], xr[k][h]);
+                    rr[k][h] = fmaf(-alpha, sr[k][h], rr[k][h]);
+                    ur[k][h] = mr[k][h] * rr[k][h];
+                }
+            if (i == iters - 1) break;
+            // publish r_{i+1} and s_i for the next pass
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int ln = ls + k * CT_NPB;
+                if (ln >= n_own) continue;
+                float* pub = sm + ln * NODE_F + NF_BLK + NF_MINV + npar * NF_PUB;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (!(h == 0 || has1)) continue;
+                    const int c = h ? c1 : c0;
+                    pub[PUB_R + c] = rr[k][h];
+                    pub[PUB_S + c] = sr[k][h];
+                }
+            }
+        }
+        // w_{i+1} = A u_{i+1}, neighbours' u formed on the fly from buffer `par`
+        float gp = 0.f, dp = 0.f;
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            const int ln = ls + k * CT_NPB;
+            const bool live = ln < n_own;
+            const int n = n_lo + ln;
+            float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (live) {
+                const int ii = ni[k], jj = nj[k];
+#pragma unroll
+                for (int ss = 0; ss < 3; ++ss) {
+                    const int s = ss == 2 ? 8 : q4 + 4 * ss;
+                    if (ss == 2 && q4 != 0) continue;
+                    int owner, blk, pn;
+                    if (!stencil_slot(s, ii, jj, nx, ny, n, owner, blk, pn)) continue;
+                    int ro, lo, rp, lp;
+                    dsm_owner(owner, rank, n_lo, npc, ro, lo);
+                    dsm_owner(pn, rank, n_lo, npc, rp, lp);
+                    const float* ob = cl.map_shared_rank(sm, ro) + lo * NODE_F + blk * 24;
+                    const float* pb = cl.map_shared_rank(sm, rp) + lp * NODE_F;
+                    float B[NB], mm[6], rv[6], wv[6], sv[6], u[6];
+                    ld21(ob, B);
+                    ld6(pb + NF_BLK, mm);
+                    ld6(pb + NF_BLK + NF_MINV + par * NF_PUB + PUB_R, rv);
+                    if (i >= 0) {
+                        ld6(pb + NF_BLK + NF_MINV + par * NF_PUB + PUB_W, wv);
+                        ld6(pb + NF_BLK + NF_MINV + par * NF_PUB + PUB_S, sv);
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) u[c] = mm[c] * fmaf(-alpha, fmaf(beta, sv[c], wv[c]), rv[c]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) u[c] = mm[c] * rv[c];
+                    }
+                    sym_matvec_acc(B, u, q);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                q[c] += __shfl_xor_sync(0xffffffffu, q[c], 1);
+                q[c] += __shfl_xor_sync(0xffffffffu, q[c], 2);
+            }
+            if (live) {
+                wr[k][0] = sel6(q, c0);
+                wr[k][1] = has1 ? sel6(q, c1) : 0.f;
+                float* pub = sm + ln * NODE_F + NF_BLK + NF_MINV + npar * NF_PUB;
+                pub[PUB_W + c0] = wr[k][0];
+                if (has1) pub[PUB_W + c1] = wr[k][1];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    gp = fmaf(rr[k][h], ur[k][h], gp);
+                    dp = fmaf(wr[k][h], ur[k][h], dp);
+                }
+            }
+        }
+        ff ga, de;
+        ff_block_sum2(gp, dp, ga, de, sred);
+        const int slot = i < 0 ? 0 : npar;
+        if (threadIdx.x == 0) {
+            cpart[slot][0] = make_float2(ga.hi, ga.lo);
+            cpart[slot][1] = make_float2(de.hi, de.lo);
+        }
+        cl.sync();
+        // every CTA sums the CTAs' partials in rank order
+        ff G2{0.f, 0.f}, D2{0.f, 0.f};
+        for (int rk = 0; rk < C; ++rk) {
+            const float2* rp = &cl.map_shared_rank(&cpart[0][0], rk)[slot * 2];
+            const float2 a = rp[0], b = rp[1];
+            G2 = ff_add(G2, ff{a.x, a.y});
+            D2 = ff_add(D2, ff{b.x, b.y});
+        }
+        if (i < 0) {
+            if (!(G2.hi > 1e-30f) || !(D2.hi > 1e-30f)) {
+                alpha = 0.f; // x stays 0
+                iters = 0;
+                break;
+            }
+            alpha = G2.hi / D2.hi;
+            beta = 0.f;
+        } else {
+            const float bnew = G2.hi / gam.hi;
+            const float pap = D2.hi - bnew * G2.hi / alpha;
+            if (!(G2.hi > 1e-30f) || !(pap > 1e-30f)) break;
+            beta = bnew;
+            alpha = G2.hi / pap;
+        }
+        gam = G2;
+    }
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int ln = ls + k * CT_NPB;
+        if (ln >= n_own) continue;
+        const int n = n_lo + ln;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!(h == 0 || has1)) continue;
+            const int c = h ? c1 : c0;
+            if (interleaved)
+                xout[n * 6 + c] = xr[k][h];
+            else
+                xout[c * G + n] = xr[k][h];
+        }
+    }
+    cl.sync(); // no CTA leaves while others may still read its shared memory
+}
+
+template <int NPT>
+cudaError_t launch_dsm(int ctas, int npc, const LevelGeom& g, const float* node, const float* rhs, const float* minv,
+                       float* x, int iters, int interleaved, cudaStream_t st)
+{
+    auto kern = k_pcg_dsm<NPT>;
+    const size_t smem = (size_t)npc * NODE_F * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (ctas > 8) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(CT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ctas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, g, npc, node, rhs, minv, x, iters, interleaved);
+}
+
 template <int NPT>
 cudaError_t launch_cluster(int blocks, const LevelGeom& g, const float* node, const float* rhs, const float* minv,
-                           float* x, float* z, float* p0, float* p1, float2* part, unsigned* bar, int* status, int iters,
-                           int interleaved, cudaStream_t st)
+                           float* x, float* z, float* p0, float* p1, float2* part, unsigned long long* bar, int* status,
+                           int iters, int interleaved, cudaStream_t st)
 {
     auto kern = k_pcg<NPT, ClusterSync>;
     if (blocks > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -249,11 +567,11 @@ cudaError_t launch_cluster(int blocks, const LevelGeom& g, const float* node, co
 
 template <int NPT>
 cudaError_t launch_grid(int blocks, const LevelGeom& g, const float* node, const float* rhs, const float* minv, float* x,
-                        float* z, float* p0, float* p1, float2* part, unsigned* bar, int* status, int iters,
+                        float* z, float* p0, float* p1, float2* part, unsigned long long* bar, int* status, int iters,
                         int interleaved, cudaStream_t st)
 {
     LevelGeom gg = g;
-    GridSync sy;
+    GridSync sy{0ull};
     void* args[] = {(void*)&gg, (void*)&node, (void*)&rhs, (void*)&minv, (void*)&x, (void*)&z, (void*)&p0,
                     (void*)&p1, (void*)&part, (void*)&bar, (void*)&status, (void*)&iters, (void*)&interleaved,
                     (void*)&sy};
@@ -295,12 +613,41 @@ int max_cluster_blocks()
     return cached;
 }
 
+int dsm_max_npc()
+{
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        optin = 227 * 1024;
+    }
+    // static shared memory of the kernel is small (< 1 KB); keep 2 KB spare
+    return (optin - 2048) / (int)(NODE_F * sizeof(float));
+}
+
 } // namespace
 
 PcgPlan pcg_plan(int G, int sm_count, int mode)
 {
-    PcgPlan p{1, 1, 0};
+    // preference: DSM (DSM only) -> cluster with global vectors (AUTO, DSM,
+    // CLUSTER) -> cooperative grid (all)
+    PcgPlan p{1, 1, 0, 0};
     const int maxc = max_cluster_blocks();
+    if (mode == SF_PCG_DSM) {
+        const int cap = dsm_max_npc();
+        for (int npt = 1; npt <= 3; ++npt) {
+            const int npc = std::min(CT_NPB * npt, cap);
+            const int ctas0 = (G + npc - 1) / npc;
+            if (ctas0 <= maxc) {
+                const int even = (G + ctas0 - 1) / ctas0; // spread the nodes evenly
+                p.blocks = (G + even - 1) / even;
+                p.npt = npt;
+                p.cluster = 2;
+                p.npc = even;
+                return p;
+            }
+        }
+    }
     if (mode != SF_PCG_GRID) {
         for (int npt : {1, 2, 4}) {
             const int need = (G + NPB * npt - 1) / (NPB * npt);
@@ -310,10 +657,6 @@ PcgPlan pcg_plan(int G, int sm_count, int mode)
                 p.cluster = 1;
                 return p;
             }
-        }
-        if (mode == SF_PCG_CLUSTER) {
-            p.blocks = -1;
-            return p;
         }
     }
     int cap = max_coop_blocks(sm_count);
@@ -332,10 +675,17 @@ PcgPlan pcg_plan(int G, int sm_count, int mode)
 }
 
 cudaError_t launch_pcg(const LevelGeom& g, const PcgPlan& plan, const float* node, const float* rhs, const float* minv,
-                       float* x, float* z, float* p0, float* p1, float2* part, unsigned* bar, int* status, int iters,
-                       int interleaved_out, cudaStream_t st)
+                       float* x, float* z, float* p0, float* p1, float2* part, unsigned long long* bar, int* status,
+                       int iters, int interleaved_out, cudaStream_t st)
 {
-    if (plan.cluster) {
+    if (plan.cluster == 2) {
+        switch (plan.npt) {
+        case 1: return launch_dsm<1>(plan.blocks, plan.npc, g, node, rhs, minv, x, iters, interleaved_out, st);
+        case 2: return launch_dsm<2>(plan.blocks, plan.npc, g, node, rhs, minv, x, iters, interleaved_out, st);
+        default: return launch_dsm<3>(plan.blocks, plan.npc, g, node, rhs, minv, x, iters, interleaved_out, st);
+        }
+    }
+    if (plan.cluster == 1) {
         switch (plan.npt) {
         case 1: return launch_cluster<1>(plan.blocks, g, node, rhs, minv, x, z, p0, p1, part, bar, status, iters, interleaved_out, st);
         case 2: return launch_cluster<2>(plan.blocks, g, node, rhs, minv, x, z, p0, p1, part, bar, status, iters, interleaved_out, st);

@@ -26,11 +26,12 @@ WFEAT_EIG, WFEAT_OFF = 0, 1
 TEMPORAL_PROPAGATE, TEMPORAL_COPY, TEMPORAL_ZERO = 0, 1, 2
 FP32, MIXED_BF16 = 0, 1
 K_PYRAMID, K_LEVEL, K_ASSEMBLE, K_GATHER, K_PCG, K_ENERGY = range(6)
-PCG_AUTO, PCG_CLUSTER, PCG_GRID = 0, 1, 2
+PCG_AUTO, PCG_CLUSTER, PCG_GRID, PCG_DSM = 0, 1, 2, 3
 PRESET_FIG2, PRESET_FIG568, PRESET_FIG79 = 0, 1, 2
 
 EXPORTED = (
-    "sf_params_preset", "sf_create", "sf_solve", "sf_solve_host", "sf_grid_dims", "sf_set_init", "sf_reset",
+    "sf_params_preset", "sf_create", "sf_solve", "sf_solve_host", "sf_solve_video", "sf_solve_video_host",
+    "sf_grid_dims", "sf_set_init", "sf_reset",
     "sf_get_stats", "sf_get_state", "sf_kernel_times", "sf_destroy", "sf_status_string", "sf_last_error", "sf_probe_pyramid",
     "sf_probe_feature_weights", "sf_probe_assemble", "sf_probe_pcg", "sf_probe_wmask", "sf_probe_energy",
     "sf_pcg_static",
@@ -54,6 +55,7 @@ class Params(ctypes.Structure):
         ("wfeat_gain", ctypes.c_float), ("wfeat_tau", ctypes.c_float),
         ("temporal_mode", ctypes.c_int), ("precision", ctypes.c_int), ("max_backtracks", ctypes.c_int),
         ("use_graph", ctypes.c_int), ("profile_mask", ctypes.c_int), ("pcg_mode", ctypes.c_int),
+        ("video", ctypes.c_int),
     ]
 
 
@@ -94,6 +96,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sf_create.restype = vp
     L.sf_solve.argtypes = [vp, fp, fp, fp, fp, fp, vp]
     L.sf_solve_host.argtypes = [vp, fp, fp, fp, fp, fp, vp]
+    L.sf_solve_video.argtypes = [vp, fp, i, fp, vp]
+    L.sf_solve_video_host.argtypes = [vp, fp, i, fp, vp]
     L.sf_grid_dims.argtypes = [vp, i, ip, ip, ip, ip]
     L.sf_set_init.argtypes = [vp, fp, vp]
     L.sf_reset.argtypes = [vp]
@@ -218,6 +222,25 @@ class Solver:
         n = self.width * self.height * 4
         _check(self.L.sf_solve_host(self.ctx, base, base + n, base + 2 * n, base + 3 * n, out.data_ptr(), _stream()),
                "sf_solve_host")
+
+    def solve_video(self, frames: torch.Tensor, outs: torch.Tensor | None = None) -> torch.Tensor:
+        """frames: float32 CUDA [n, 4, H, W]; returns fields [n, 6, ny, nx] (level pipeline)."""
+        n = frames.shape[0]
+        _, _, nx, ny = self.dims(0)
+        if outs is None:
+            outs = torch.empty((n, 6, ny, nx), device=frames.device, dtype=torch.float32)
+        if tuple(frames.shape[1:]) != (4, self.height, self.width) or tuple(outs.shape) != (n, 6, ny, nx):
+            raise SFError("solve_video: shape mismatch")
+        _check(self.L.sf_solve_video(self.ctx, _ptr(frames, torch.float32), int(n), _ptr(outs, torch.float32),
+                                     _stream()), "sf_solve_video")
+        return outs
+
+    def solve_video_host(self, frames, outs) -> None:
+        """frames: float32 CPU [n, 4, H, W] (pinned for speed); outs: float32 CPU [n, 6, ny, nx]."""
+        if frames.is_cuda or outs.is_cuda or not frames.is_contiguous() or not outs.is_contiguous():
+            raise SFError("solve_video_host takes contiguous host tensors")
+        _check(self.L.sf_solve_video_host(self.ctx, frames.data_ptr(), int(frames.shape[0]), outs.data_ptr(),
+                                          _stream()), "sf_solve_video_host")
 
     def set_init(self, coarsest_delta: torch.Tensor) -> None:
         _check(self.L.sf_set_init(self.ctx, _ptr(coarsest_delta, torch.float32), _stream()), "sf_set_init")

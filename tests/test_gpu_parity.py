@@ -102,7 +102,8 @@ def test_assemble_parity(w, h, s_, level, kw):
     assert abs(energy - E_ref) < 1e-5 * abs(E_ref)
 
 
-@pytest.mark.parametrize("iters,mode", [(1, 0), (5, 0), (20, 0), (20, sf.PCG_CLUSTER), (20, sf.PCG_GRID)])
+@pytest.mark.parametrize("iters,mode", [(1, 0), (5, 0), (20, 0), (20, sf.PCG_CLUSTER), (20, sf.PCG_GRID),
+                                        (1, sf.PCG_DSM), (20, sf.PCG_DSM)])
 def test_pcg_parity_on_the_same_system(iters, mode):
     solver, lv, op = _level_setup(160, 120, 4, 3, 0, pcg_mode=mode)
     rng = np.random.default_rng(3)
@@ -189,7 +190,7 @@ def test_config1_frame_parity():
 
 @pytest.mark.parametrize("kw", [{"robust_mode": O.SQRT_PAPER}, {"grad_mode": O.GRAD_LITERAL},
                                 {"wfeat_mode": O.WFEAT_OFF, "eps_p": 0.0}, {"use_graph": 0},
-                                {"pcg_mode": sf.PCG_GRID}, {"pcg_mode": sf.PCG_CLUSTER}])
+                                {"pcg_mode": sf.PCG_GRID}, {"pcg_mode": sf.PCG_CLUSTER}, {"pcg_mode": sf.PCG_DSM}])
 def test_config1_frame_parity_modes(kw):
     q = scenes.plane_quadruple(seed=2)
     for r in _solve_both(q, 4, 3, [5], [10], **kw):
@@ -208,6 +209,29 @@ def test_config2_video_parity_first_frames():
     q = v.frames(3)
     for r in _solve_both(q, 8, 4, [3], [20], frames=3):
         _assert_frame_parity(*r)
+
+
+def test_video_pipeline_equals_frame_by_frame():
+    """sf_solve_video overlaps the levels of consecutive frames; every frame's
+    fields must equal those of sequential sf_solve calls bit for bit."""
+    n = 6
+    v = scenes.SceneVideo(320, 240, n, seed=101, disparity=(3, 20), max_motion=6).frames(n)
+    sp, _ = make_params([3], [10])
+    seq = sf.Solver(320, 240, 8, 3, sp)
+    ref = np.stack([seq.solve(_dev(v[f])).cpu().numpy() for f in range(n)])
+    sp_v, _ = make_params([3], [10], video=1)
+    vid = sf.Solver(320, 240, 8, 3, sp_v)
+    out = np.concatenate([vid.solve_video(_dev(v[:4])).cpu().numpy(), vid.solve_video(_dev(v[4:])).cpu().numpy()])
+    assert np.array_equal(out, ref)
+    d_seq, t_seq = seq.state(1)
+    d_vid, t_vid = vid.state(1)
+    assert torch.equal(d_seq, d_vid) and torch.equal(t_seq, t_vid)
+    vid2 = sf.Solver(320, 240, 8, 3, sp_v)
+    host_out = torch.empty((n, 6, 30, 40), dtype=torch.float32).pin_memory()
+    vid2.solve_video_host(torch.from_numpy(v).pin_memory(), host_out)
+    assert np.array_equal(host_out.numpy(), ref)
+    plain = sf.Solver(320, 240, 8, 3, sp)
+    assert plain.L.sf_solve_video(plain.ctx, 1, 1, 1, None) == sf.ERR_STATE
 
 
 def test_repeat_runs_are_bit_identical_and_graph_matches_eager():
