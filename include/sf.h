@@ -77,9 +77,11 @@ enum { SF_GRAD_BROX = 0, SF_GRAD_LITERAL = 1 };
 enum { SF_WFEAT_EIG = 0, SF_WFEAT_OFF = 1 };
 /* Initialisation of frames after the first (Section 5.3). */
 enum { SF_TEMPORAL_PROPAGATE = 0, SF_TEMPORAL_COPY = 1, SF_TEMPORAL_ZERO = 2 };
-/* Storage precision of the image pyramid; residuals and all accumulation
- * stay in FP32. */
-enum { SF_FP32 = 0, SF_MIXED_BF16 = 1 };
+/* Storage precision of the image pyramid (intensity and gradient texels,
+ * from which the Jacobian is formed on the fly): FP32, or 16-bit BF16 / FP16
+ * (half the texel bytes). Residuals, Jacobians, normal equations, PCG and all
+ * accumulation stay in FP32. */
+enum { SF_FP32 = 0, SF_MIXED_BF16 = 1, SF_MIXED_FP16 = 2 };
 /* Columns of Table 1 (Appendix A). */
 enum { SF_PRESET_FIG2 = 0, SF_PRESET_FIG568 = 1, SF_PRESET_FIG79 = 2 };
 /* Schedule of the PCG solve, per level the first that fits: SF_PCG_DSM (one
@@ -115,7 +117,7 @@ typedef struct sf_params {
     int wfeat_mode;               /* SF_WFEAT_EIG | SF_WFEAT_OFF */
     float wfeat_gain, wfeat_tau;  /* w_i = 1 + gain * exp(-lambda_min / tau) */
     int temporal_mode;            /* SF_TEMPORAL_* */
-    int precision;                /* SF_FP32 | SF_MIXED_BF16 */
+    int precision;                /* SF_FP32 | SF_MIXED_BF16 | SF_MIXED_FP16 */
     int max_backtracks;           /* step halvings tried before a step is rejected (4) */
     int use_graph;                /* 1: replay the frame as one captured CUDA graph */
     int profile_mask;             /* bit k set: time every launch of kernel class k with CUDA events */

@@ -27,8 +27,8 @@ __constant__ int c_pair_l[NPAIR] = {0, 1, 2, 3, 1, 2, 3, 2, 3, 3};
 // Data terms of one pixel at fields f (Eqs. 1-6, 11-13). Returns the
 // unweighted photometric and gradient penalties; with ASSEMBLE also the
 // pixel's 6x6 normal-equation block H (packed) and right-hand side b.
-template <bool ASSEMBLE>
-__device__ __forceinline__ void pixel_data(const float4* __restrict__ tex, int w, int h, int x, int y, const float f[6],
+template <bool ASSEMBLE, class TT>
+__device__ __forceinline__ void pixel_data(const typename TT::T* __restrict__ tex, int w, int h, int x, int y, const float f[6],
                                            const DevParams& P, int Wgiven, int& Wout, float& Ep, float& Eg, float* H,
                                            float* b)
 {
@@ -38,7 +38,7 @@ __device__ __forceinline__ void pixel_data(const float4* __restrict__ tex, int w
     for (int c = 0; c < 4; ++c) {
         const float ox = sgn(c, 0) * f[0] + sgn(c, 1) * f[2] + sgn(c, 2) * f[4];
         const float oy = sgn(c, 0) * f[1] + sgn(c, 1) * f[3] + sgn(c, 2) * f[5];
-        tap4(tex + c * plane, w, h, x, y, ox, oy, tp[c]);
+        tap4<TT>(tex + c * plane, w, h, x, y, ox, oy, tp[c]);
     }
     float e[6];
 #pragma unroll
@@ -134,12 +134,39 @@ __device__ __forceinline__ void pixel_data(const float4* __restrict__ tex, int w
     }
 }
 
+// Adds term(lo) .. term(hi-1) to the compensated sum (a, e): runs of SUMRUN
+// terms are summed plainly and each run's sum enters with one Kahan step. A
+// cell's right-hand side nearly cancels near convergence, and its blocks sum
+// hundreds of pixels at the finest levels; the compensation keeps both
+// accurate at a quarter of the cost of compensating every term.
+constexpr int SUMRUN = 4;
+template <class Term>
+__device__ __forceinline__ void comp_sum(float& a, float& e, int lo, int hi, Term term)
+{
+    int q = lo;
+    for (; q + SUMRUN <= hi; q += SUMRUN) {
+        float run = term(q);
+#pragma unroll
+        for (int r = 1; r < SUMRUN; ++r) run += term(q + r);
+        const float y = run - e;
+        const float t = a + y;
+        e = (t - a) - y;
+        a = t;
+    }
+    for (; q < hi; ++q) {
+        const float y = term(q) - e;
+        const float t = a + y;
+        e = (t - a) - y;
+        a = t;
+    }
+}
+
 // One CTA assembles `cpb` consecutive cells of one cell row. Pixels are
 // enumerated cell-major (regular cells s x ch, the row's last cell may be
 // wider), processed in chunks of ETHREADS; each thread owns up to MAXOUT of
 // the cpb * CELL_VALS outputs and sums its cell's pixels of every chunk.
-template <int MAXOUT>
-__global__ void __launch_bounds__(ETHREADS) k_assemble(LevelGeom g, int cpb, const float4* __restrict__ tex,
+template <int MAXOUT, class TT>
+__global__ void __launch_bounds__(ETHREADS) k_assemble(LevelGeom g, int cpb, const typename TT::T* __restrict__ tex,
                                                        const float* __restrict__ base, const float* __restrict__ delta,
                                                        DevParams P, uint8_t* __restrict__ Wmask,
                                                        float* __restrict__ cell, float2* __restrict__ part)
@@ -159,9 +186,9 @@ __global__ void __launch_bounds__(ETHREADS) k_assemble(LevelGeom g, int cpb, con
     const int total = (ncell - 1) * per_reg + cw_last * ch;
     const int nout = ncell * CELL_VALS;
 
-    float acc[MAXOUT];
+    float acc[MAXOUT], cmp[MAXOUT]; // cmp: Kahan compensation of the cell sums
 #pragma unroll
-    for (int k = 0; k < MAXOUT; ++k) acc[k] = 0.f;
+    for (int k = 0; k < MAXOUT; ++k) acc[k] = cmp[k] = 0.f;
     float ep = 0.f, eg = 0.f;
     int nex = 0;
 
@@ -186,7 +213,7 @@ __global__ void __launch_bounds__(ETHREADS) k_assemble(LevelGeom g, int cpb, con
             pixel_fields(base, delta, nullptr, 0.f, g.G, j0 * g.nx + i0, g.nx, a, bb, f);
             int Wi;
             float Ep, Eg;
-            pixel_data<true>(tex, g.w, g.h, x, y, f, P, -1, Wi, Ep, Eg, H, bv);
+            pixel_data<true, TT>(tex, g.w, g.h, x, y, f, P, -1, Wi, Ep, Eg, H, bv);
             Wmask[y * g.w + x] = (uint8_t)Wi;
             ep += Ep;
             eg += Eg;
@@ -211,16 +238,17 @@ __global__ void __launch_bounds__(ETHREADS) k_assemble(LevelGeom g, int cpb, con
                 int lo = c * per_reg, hi = (c == ncell - 1) ? total : (c + 1) * per_reg;
                 lo = max(lo, c0) - c0;
                 hi = min(hi, c0 + ETHREADS) - c0;
-                float a = acc[k];
+                float a = acc[k], e = cmp[k];
                 if (r < NPAIR * NB) {
-                    const int pr = r / NB, e = r - pr * NB;
+                    const int pr = r / NB, ee = r - pr * NB;
                     const int kk = c_pair_k[pr], ll = c_pair_l[pr];
-                    for (int q = lo; q < hi; ++q) a = fmaf(sA[q * 4 + kk] * sA[q * 4 + ll], sHB[q * HB + e], a);
+                    comp_sum(a, e, lo, hi, [&](int q) { return sA[q * 4 + kk] * sA[q * 4 + ll] * sHB[q * HB + ee]; });
                 } else {
                     const int rr = r - NPAIR * NB;
                     const int kk = rr / 6, comp = rr - kk * 6;
-                    for (int q = lo; q < hi; ++q) a = fmaf(sA[q * 4 + kk], sHB[q * HB + NB + comp], a);
+                    comp_sum(a, e, lo, hi, [&](int q) { return sA[q * 4 + kk] * sHB[q * HB + NB + comp]; });
                 }
+                cmp[k] = e;
                 acc[k] = a;
             }
         }
@@ -232,7 +260,7 @@ __global__ void __launch_bounds__(ETHREADS) k_assemble(LevelGeom g, int cpb, con
         const int o = tid + k * ETHREADS;
         if (o < nout) {
             const int c = o / CELL_VALS, r = o - c * CELL_VALS;
-            cell[(size_t)r * ncell_tot + cj * g.ncx + ci0 + c] = acc[k];
+            cell[(size_t)r * ncell_tot + cj * g.ncx + ci0 + c] = acc[k] - cmp[k];
         }
     }
     const int blk = blockIdx.y * gridDim.x + blockIdx.x;
@@ -319,7 +347,7 @@ __device__ __forceinline__ void node_prior_energy(const LevelGeom& g, const DevP
         const float ww = wf[n] + wf[m];
 #pragma unroll
         for (int u = 0; u < 6; ++u) {
-            const float df = T[u] - Tm[u];
+            const float df = (base[u * g.G + n] - base[u * g.G + m]) + (d[u] - dm[u]);
             acc += ww * P.wfl[u >> 1] * df * df;
         }
     }
@@ -387,8 +415,10 @@ __global__ void __launch_bounds__(ETHREADS) k_gather(LevelGeom g, const float* _
 #pragma unroll
             for (int u = 0; u < 6; ++u) {
                 const float c = ww * P.wfl[u >> 1];
+                // T_n - T_m as (base difference) + (delta difference): no cancellation of the large totals
+                const float df = (base[u * g.G + n] - base[u * g.G + m]) + (d[u] - dm[u]);
                 Bs[sym_idx(u, u)] += c;
-                bb[u] -= c * (T[u] - Tm[u]);
+                bb[u] -= c * df;
                 if (q == 0) Be[sym_idx(u, u)] -= c;
                 if (q == 1) Bso[sym_idx(u, u)] -= c;
             }
@@ -477,7 +507,8 @@ __global__ void __launch_bounds__(ETHREADS) k_gather(LevelGeom g, const float* _
 // Energy at base + delta (+ t x): pixel blocks first, then node blocks;
 // the last block to finish sums the partials in a fixed order and either
 // writes the record or takes the backtracking decision.
-__global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, const float4* __restrict__ tex,
+template <class TT>
+__global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, const typename TT::T* __restrict__ tex,
                                                      const float* __restrict__ base, const float* __restrict__ delta,
                                                      const float* __restrict__ x, float t, const float* __restrict__ wf,
                                                      DevParams P, uint8_t* __restrict__ Wmask, int wmode,
@@ -500,7 +531,7 @@ __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, c
             pixel_fields(base, delta, x, t, g.G, j0 * g.nx + i0, g.nx, a, bb, f);
             int Wi;
             float Ep, Eg;
-            pixel_data<false>(tex, g.w, g.h, xx, y, f, P, wmode ? -1 : (int)Wmask[p], Wi, Ep, Eg, nullptr, nullptr);
+            pixel_data<false, TT>(tex, g.w, g.h, xx, y, f, P, wmode ? -1 : (int)Wmask[p], Wi, Ep, Eg, nullptr, nullptr);
             if (wmode) Wmask[p] = (uint8_t)Wi;
             v[0] += Ep;
             v[1] += Eg;
@@ -579,11 +610,12 @@ __global__ void k_unpack_blocks(int G, const float* __restrict__ node, const flo
 }
 
 template <int MAXOUT>
-void assemble_impl(const LevelGeom& g, int cpb, const float4* tex, const float* base, const float* delta,
+void assemble_impl(const LevelGeom& g, int cpb, const void* tex, int prec, const float* base, const float* delta,
                    const DevParams& P, uint8_t* Wmask, float* cell, float2* part, cudaStream_t st)
 {
     dim3 grid((g.ncx + cpb - 1) / cpb, g.ncy);
-    k_assemble<MAXOUT><<<grid, ETHREADS, 0, st>>>(g, cpb, tex, base, delta, P, Wmask, cell, part);
+    SF_TEX_DISPATCH(prec, TT, k_assemble<MAXOUT, TT><<<grid, ETHREADS, 0, st>>>(
+                                  g, cpb, static_cast<const typename TT::T*>(tex), base, delta, P, Wmask, cell, part));
 }
 
 } // namespace
@@ -597,22 +629,22 @@ int assemble_blocks(const LevelGeom& g, int* cpb_out)
     return ((g.ncx + cpb - 1) / cpb) * g.ncy;
 }
 
-void launch_assemble(const LevelGeom& g, const float4* tex, const float* base, const float* delta, const DevParams& P,
-                     uint8_t* Wmask, float* cell, const Scratch& sc, cudaStream_t st)
+void launch_assemble(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta,
+                     const DevParams& P, uint8_t* Wmask, float* cell, const Scratch& sc, cudaStream_t st)
 {
     int cpb;
     assemble_blocks(g, &cpb);
     const int need = (cpb * CELL_VALS + ETHREADS - 1) / ETHREADS;
     if (need <= 1)
-        assemble_impl<1>(g, cpb, tex, base, delta, P, Wmask, cell, sc.asm_part, st);
+        assemble_impl<1>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, st);
     else if (need <= 2)
-        assemble_impl<2>(g, cpb, tex, base, delta, P, Wmask, cell, sc.asm_part, st);
+        assemble_impl<2>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, st);
     else if (need <= 4)
-        assemble_impl<4>(g, cpb, tex, base, delta, P, Wmask, cell, sc.asm_part, st);
+        assemble_impl<4>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, st);
     else if (need <= 8)
-        assemble_impl<8>(g, cpb, tex, base, delta, P, Wmask, cell, sc.asm_part, st);
+        assemble_impl<8>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, st);
     else
-        assemble_impl<16>(g, cpb, tex, base, delta, P, Wmask, cell, sc.asm_part, st);
+        assemble_impl<16>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, st);
 }
 
 void launch_gather(const LevelGeom& g, const float* cell, const float* base, const float* delta, const float* wf,
@@ -624,15 +656,16 @@ void launch_gather(const LevelGeom& g, const float* cell, const float* base, con
                                           n_asm_blocks, sc.counters + 0, ctrl, sc.status);
 }
 
-void launch_energy(const LevelGeom& g, const float4* tex, const float* base, const float* delta, const float* x, float t,
-                   const float* wf, const DevParams& P, uint8_t* Wmask, int wmode, const Scratch& sc, StepCtrl* ctrl,
-                   int action, int last, double* rec, cudaStream_t st)
+void launch_energy(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta, const float* x,
+                   float t, const float* wf, const DevParams& P, uint8_t* Wmask, int wmode, const Scratch& sc,
+                   StepCtrl* ctrl, int action, int last, double* rec, cudaStream_t st)
 {
     int npix = (g.w * g.h + ETHREADS - 1) / ETHREADS;
     if (npix > 152 * 8) npix = 152 * 8;
     const int nnode = (g.G + ETHREADS - 1) / ETHREADS;
-    k_energy<<<npix + nnode, ETHREADS, 0, st>>>(g, npix, tex, base, delta, x, t, wf, P, Wmask, wmode, sc.en_part,
-                                                sc.counters + 1, ctrl, action, last, rec, sc.status);
+    SF_TEX_DISPATCH(prec, TT, k_energy<TT><<<npix + nnode, ETHREADS, 0, st>>>(
+                                  g, npix, static_cast<const typename TT::T*>(tex), base, delta, x, t, wf, P, Wmask,
+                                  wmode, sc.en_part, sc.counters + 1, ctrl, action, last, rec, sc.status));
 }
 
 void launch_apply_step(const LevelGeom& g, float* delta, const float* x, const StepCtrl* ctrl, cudaStream_t st)

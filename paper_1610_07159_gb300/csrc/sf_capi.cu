@@ -21,7 +21,7 @@ namespace {
 thread_local int g_last_error = SF_OK;
 
 struct LevelBuf {
-    float4* tex = nullptr;
+    void* tex = nullptr; // texels, typed by the precision mode
     uint8_t* W = nullptr;
     float* H = nullptr;
     float *base = nullptr, *delta = nullptr, *x = nullptr, *wf = nullptr;
@@ -79,7 +79,7 @@ struct sf_ctx {
     // level pipeline of sf_solve_video (allocated when params.video is set)
     bool video = false;
     int ring = 0;                                        // frames in flight
-    float4* ring_tex[SF_MAX_LEVELS][SF_MAX_LEVELS]{};    // [ring slot][level] texels
+    void* ring_tex[SF_MAX_LEVELS][SF_MAX_LEVELS]{};      // [ring slot][level] texels
     float* vstate_delta[SF_MAX_LEVELS][2]{};             // [level][frame parity]
     float* vstate_total[SF_MAX_LEVELS][2]{};
     float* vin[SF_MAX_LEVELS]{};                         // [ring slot] staged host inputs (4 images)
@@ -207,7 +207,7 @@ void prof_mark(sf_ctx* c, int k, bool begin, cudaStream_t st)
 
 // Inputs and outputs of one level's solve.
 struct LevelIO {
-    const float4* tex;                                 // the level's texels
+    const void* tex;                                   // the level's texels
     const float* coarse_base;                          // coarse totals (base + delta, or the
     const float* coarse_delta;                         // totals alone when delta is null); null at the top
     const float* prev_delta, *prev_total;              // temporal state of the previous frame
@@ -217,14 +217,15 @@ struct LevelIO {
     int frame, use_init;                               // when args is null
 };
 
-void enqueue_pyramid(sf_ctx* c, const DevArgs* args, const float* const* in, float4* const* tex, cudaStream_t st,
+void enqueue_pyramid(sf_ctx* c, const DevArgs* args, const float* const* in, void* const* tex, cudaStream_t st,
                      int& nl)
 {
+    const int prec = c->prm.precision;
     prof_mark(c, SF_K_PYRAMID, true, st);
-    launch_tex0(args, in, c->w0, c->h0, tex[0], st);
+    launch_tex0(args, in, c->w0, c->h0, tex[0], prec, st);
     ++nl;
     for (int l = 1; l < c->L; ++l, ++nl)
-        launch_texdown(tex[l - 1], c->geo[l - 1].w, c->geo[l - 1].h, tex[l], c->geo[l].w, c->geo[l].h, st);
+        launch_texdown(tex[l - 1], c->geo[l - 1].w, c->geo[l - 1].h, tex[l], c->geo[l].w, c->geo[l].h, prec, st);
     prof_mark(c, SF_K_PYRAMID, false, st);
 }
 
@@ -242,7 +243,7 @@ int enqueue_level(sf_ctx* c, int l, const LevelIO& io, cudaStream_t st, int& nl)
                       io.prev_delta, io.prev_total, c->init_buf, io.args, P.temporal_mode, io.frame, io.use_init, st);
     ++nl;
     if (P.wfeat_mode == SF_WFEAT_EIG) {
-        launch_halfway(g, io.tex, b.base, b.delta, b.H, st);
+        launch_halfway(g, io.tex, P.precision, b.base, b.delta, b.H, st);
         launch_wfeat(g, b.H, c->dp[l], b.wf, st);
         nl += 2;
     }
@@ -251,7 +252,7 @@ int enqueue_level(sf_ctx* c, int l, const LevelIO& io, cudaStream_t st, int& nl)
         StepCtrl* ctrl = c->ctrl + l * SF_MAX_GN + gi;
         uint8_t* Wst = b.W + (size_t)gi * g.w * g.h; // this step's outlier mask, kept for inspection
         prof_mark(c, SF_K_ASSEMBLE, true, st);
-        launch_assemble(g, io.tex, b.base, b.delta, c->dp[l], Wst, b.cell, sc, st);
+        launch_assemble(g, io.tex, P.precision, b.base, b.delta, c->dp[l], Wst, b.cell, sc, st);
         prof_mark(c, SF_K_ASSEMBLE, false, st);
         prof_mark(c, SF_K_GATHER, true, st);
         launch_gather(g, b.cell, b.base, b.delta, b.wf, c->dp[l], b.node, b.rhs, b.minv, sc, ctrl, c->asm_blocks[l],
@@ -266,7 +267,7 @@ int enqueue_level(sf_ctx* c, int l, const LevelIO& io, cudaStream_t st, int& nl)
         prof_mark(c, SF_K_ENERGY, true, st);
         float t = 1.f;
         for (int j = 0; j <= P.max_backtracks; ++j, t *= 0.5f, ++nl)
-            launch_energy(g, io.tex, b.base, b.delta, b.x, t, b.wf, c->dp[l], Wst, 0, sc, ctrl, 1,
+            launch_energy(g, io.tex, P.precision, b.base, b.delta, b.x, t, b.wf, c->dp[l], Wst, 0, sc, ctrl, 1,
                           j == P.max_backtracks, nullptr, st);
         launch_apply_step(g, b.delta, b.x, ctrl, st);
         ++nl;
@@ -274,7 +275,8 @@ int enqueue_level(sf_ctx* c, int l, const LevelIO& io, cudaStream_t st, int& nl)
     }
     prof_mark(c, SF_K_LEVEL, true, st);
     if (l == 0 && P.gn_iters[0] == 0) {
-        launch_energy(g, io.tex, b.base, b.delta, nullptr, 0.f, b.wf, c->dp[0], b.W, 1, sc, nullptr, 0, 0, c->rec,
+        launch_energy(g, io.tex, P.precision, b.base, b.delta, nullptr, 0.f, b.wf, c->dp[0], b.W, 1, sc, nullptr, 0, 0,
+                      c->rec,
                       st);
         ++nl;
     }
@@ -289,7 +291,7 @@ int enqueue_frame(sf_ctx* c, cudaStream_t st)
 {
     int nl = 0;
     c->nprof = 0;
-    float4* tex[SF_MAX_LEVELS];
+    void* tex[SF_MAX_LEVELS];
     for (int l = 0; l < c->L; ++l) tex[l] = c->lv[l].tex;
     enqueue_pyramid(c, c->args, nullptr, tex, st, nl);
     for (int l = c->L - 1; l >= 0; --l) {
@@ -432,7 +434,8 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
         width > (1 << 15) || height > (1 << 15) || grid_stride > 256 || !finite_params(*p) || !(p->eps > 0.f) ||
         p->max_backtracks < 0 || p->max_backtracks > 8 || p->robust_mode < 0 || p->robust_mode > 1 ||
         p->grad_mode < 0 || p->grad_mode > 1 || p->wfeat_mode < 0 || p->wfeat_mode > 1 || p->temporal_mode < 0 ||
-        p->temporal_mode > 2 || p->precision != SF_FP32 || !(p->wfeat_tau > 0.f) || p->pcg_mode < 0 ||
+        p->temporal_mode > 2 || p->precision < SF_FP32 || p->precision > SF_MIXED_FP16 || !(p->wfeat_tau > 0.f) ||
+        p->pcg_mode < 0 ||
         p->pcg_mode > 3) {
         fail(SF_ERR_ARG);
         return nullptr;
@@ -498,7 +501,7 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
         const LevelGeom& g = c->geo[l];
         LevelBuf& b = c->lv[l];
         const size_t N = (size_t)g.w * g.h, G6 = (size_t)6 * g.G;
-        ok = dalloc(c, &b.tex, 4 * N) && dalloc(c, &b.W, N * (size_t)std::max(1, p->gn_iters[l])) && dalloc(c, &b.H, N) && dalloc(c, &b.base, G6) &&
+        ok = dalloc(c, reinterpret_cast<char**>(&b.tex), 4 * N * texel_bytes(p->precision)) && dalloc(c, &b.W, N * (size_t)std::max(1, p->gn_iters[l])) && dalloc(c, &b.H, N) && dalloc(c, &b.base, G6) &&
              dalloc(c, &b.delta, G6) && dalloc(c, &b.x, G6) && dalloc(c, &b.wf, (size_t)g.G) &&
              dalloc(c, &b.prev_delta, G6) && dalloc(c, &b.prev_total, G6) &&
              dalloc(c, &b.node, (size_t)NODE_VALS * g.G) && dalloc(c, &b.rhs, G6) && dalloc(c, &b.minv, G6) &&
@@ -519,7 +522,8 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
         c->ring = levels;
         for (int r = 0; r < c->ring && ok; ++r) {
             for (int l = 0; l < levels && ok; ++l)
-                ok = dalloc(c, &c->ring_tex[r][l], 4 * (size_t)c->geo[l].w * c->geo[l].h);
+                ok = dalloc(c, reinterpret_cast<char**>(&c->ring_tex[r][l]),
+                            4 * (size_t)c->geo[l].w * c->geo[l].h * texel_bytes(p->precision));
             ok = ok && dalloc(c, &c->vin[r], 4 * N0) && dalloc(c, &c->vout[r], (size_t)6 * c->geo[0].G);
         }
         for (int l = 0; l < levels && ok; ++l)
@@ -774,10 +778,12 @@ int sf_probe_pyramid(sf_ctx* c, const float* L_t, const float* R_t, const float*
     cudaStream_t st = (cudaStream_t)stream;
     c->last_stream = st;
     const float* in[4] = {L_t, R_t, L_t1, R_t1};
-    launch_tex0(nullptr, in, c->w0, c->h0, c->lv[0].tex, st);
+    const int prec = c->prm.precision;
+    launch_tex0(nullptr, in, c->w0, c->h0, c->lv[0].tex, prec, st);
     for (int l = 1; l < c->L; ++l)
-        launch_texdown(c->lv[l - 1].tex, c->geo[l - 1].w, c->geo[l - 1].h, c->lv[l].tex, c->geo[l].w, c->geo[l].h, st);
-    launch_unpack_tex(c->lv[level].tex, c->geo[level].w, c->geo[level].h, planes, st);
+        launch_texdown(c->lv[l - 1].tex, c->geo[l - 1].w, c->geo[l - 1].h, c->lv[l].tex, c->geo[l].w, c->geo[l].h, prec,
+                       st);
+    launch_unpack_tex(c->lv[level].tex, prec, c->geo[level].w, c->geo[level].h, planes, st);
     int rc = check_cuda(cudaGetLastError());
     return rc ? fail(rc) : SF_OK;
 }
@@ -788,7 +794,7 @@ int sf_probe_feature_weights(sf_ctx* c, int level, const float* T, float* wfeat,
     cudaStream_t st = (cudaStream_t)stream;
     c->last_stream = st;
     const LevelGeom& g = c->geo[level];
-    launch_halfway(g, c->lv[level].tex, T, nullptr, c->lv[level].H, st);
+    launch_halfway(g, c->lv[level].tex, c->prm.precision, T, nullptr, c->lv[level].H, st);
     launch_wfeat(g, c->lv[level].H, c->dp[level], wfeat, st);
     int rc = check_cuda(cudaGetLastError());
     return rc ? fail(rc) : SF_OK;
@@ -803,7 +809,7 @@ int sf_probe_assemble(sf_ctx* c, int level, const float* base, const float* delt
     const LevelGeom& g = c->geo[level];
     LevelBuf& b = c->lv[level];
     StepCtrl* pc = c->ctrl + SF_MAX_LEVELS * SF_MAX_GN;
-    launch_assemble(g, b.tex, base, delta, c->dp[level], b.W, b.cell, c->sc[level], st);
+    launch_assemble(g, b.tex, c->prm.precision, base, delta, c->dp[level], b.W, b.cell, c->sc[level], st);
     launch_gather(g, b.cell, base, delta, wfeat, c->dp[level], b.node, b.rhs, b.minv, c->sc[level], pc, c->asm_blocks[level],
                   st);
     if (blocks && rhs) launch_unpack_blocks(g, b.node, b.rhs, blocks, rhs, st);
@@ -847,7 +853,8 @@ int sf_probe_energy(sf_ctx* c, int level, const float* base, const float* delta,
     int rc = SF_OK;
     if (W) rc = check_cuda(cudaMemcpyAsync(b.W, W, (size_t)g.w * g.h, cudaMemcpyDeviceToDevice, st));
     if (rc) return fail(rc);
-    launch_energy(g, b.tex, base, delta, nullptr, 0.f, wfeat, c->dp[level], b.W, W ? 0 : 1, c->sc[level], nullptr, 0, 0, c->rec,
+    launch_energy(g, b.tex, c->prm.precision, base, delta, nullptr, 0.f, wfeat, c->dp[level], b.W, W ? 0 : 1,
+                  c->sc[level], nullptr, 0, 0, c->rec,
                   st);
     rc = check_cuda(cudaMemcpyAsync(out6, c->rec, 6 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if (!rc) rc = check_cuda(cudaGetLastError());

@@ -2,8 +2,10 @@
 // halfway-domain scene-flow solver (Thies et al., arXiv 1610.07159).
 //
 // Data layout in device memory (one set per hierarchy level):
-//   tex     float4 [4][h][w]: (I, dI/dx, dI/dy, 0) of the four images, so one
-//           16-byte load fetches a texel with its gradient (Section 5.3 pyramid)
+//   tex     [4][h][w] texels (I, dI/dx, dI/dy, 0) of the four images, so one
+//           load fetches a texel with its gradient (Section 5.3 pyramid):
+//           float4 (16 bytes) in FP32 mode, four FP16 or BF16 values (8 bytes)
+//           in the mixed-precision modes
 //   W       uint8  [h][w]: outlier weight of the current Gauss-Newton step
 //   base, delta, x      float [6][G] component-major node fields
 //   cell    float [CELL_VALS][ncell]: per warp-grid cell the ten symmetric 6x6
@@ -15,6 +17,8 @@
 //   rhs, minv, r, z, p0, p1   float [6][G] PCG vectors
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -155,22 +159,81 @@ __device__ __forceinline__ void axis_cell(int x, float o, int w, int& ix, float&
     }
 }
 
+// Texel storage: FP32 (float4) or 16-bit (four halves or bfloat16s in 8
+// bytes). Loads convert to FP32; all arithmetic after the load is FP32.
+struct TexF32 {
+    using T = float4;
+    __device__ __forceinline__ static float4 ld(const T* p) { return __ldg(p); }
+    __device__ __forceinline__ static T pack(float a, float b, float c) { return make_float4(a, b, c, 0.f); }
+};
+
+struct TexF16 {
+    using T = uint2;
+    __device__ __forceinline__ static float4 ld(const T* p)
+    {
+        const uint2 v = __ldg(p);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    __device__ __forceinline__ static T pack(float a, float b, float c)
+    {
+        const __half2 h0 = __floats2half2_rn(a, b), h1 = __floats2half2_rn(c, 0.f);
+        return make_uint2(*reinterpret_cast<const unsigned*>(&h0), *reinterpret_cast<const unsigned*>(&h1));
+    }
+};
+
+struct TexBF16 {
+    using T = uint2;
+    __device__ __forceinline__ static float4 ld(const T* p)
+    {
+        const uint2 v = __ldg(p);
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    __device__ __forceinline__ static T pack(float a, float b, float c)
+    {
+        const __nv_bfloat162 h0 = __floats2bfloat162_rn(a, b), h1 = __floats2bfloat162_rn(c, 0.f);
+        return make_uint2(*reinterpret_cast<const unsigned*>(&h0), *reinterpret_cast<const unsigned*>(&h1));
+    }
+};
+
+// Bytes per texel of a precision mode.
+__host__ __device__ constexpr int texel_bytes(int prec) { return prec == SF_FP32 ? 16 : 8; }
+
+// Host-side dispatch of a texel-typed launch on the precision mode.
+#define SF_TEX_DISPATCH(prec, TT, ...)                                                                       \
+    do {                                                                                                   \
+        if ((prec) == SF_MIXED_FP16) {                                                                     \
+            using TT = TexF16;                                                                             \
+            __VA_ARGS__;                                                                                   \
+        } else if ((prec) == SF_MIXED_BF16) {                                                              \
+            using TT = TexBF16;                                                                            \
+            __VA_ARGS__;                                                                                   \
+        } else {                                                                                           \
+            using TT = TexF32;                                                                             \
+            __VA_ARGS__;                                                                                   \
+        }                                                                                                  \
+    } while (0)
+
 // Bilinear sample of a texel plane (I, dI/dx, dI/dy) at (x + ox, y + oy)
 // with the derivative of the interpolant.
 struct Tap {
     float v[3], dx[3], dy[3];
 };
 
-__device__ __forceinline__ void tap4(const float4* __restrict__ T, int w, int h, int x, int y, float ox, float oy,
-                                     Tap& o)
+template <class TT>
+__device__ __forceinline__ void tap4(const typename TT::T* __restrict__ T, int w, int h, int x, int y, float ox,
+                                     float oy, Tap& o)
 {
     int ix, iy;
     float fx, fy;
     bool clx, cly;
     axis_cell(x, ox, w, ix, fx, clx);
     axis_cell(y, oy, h, iy, fy, cly);
-    const float4* r0 = T + (size_t)iy * w + ix;
-    const float4 a = __ldg(r0), b = __ldg(r0 + 1), c = __ldg(r0 + w), d = __ldg(r0 + w + 1);
+    const typename TT::T* r0 = T + (size_t)iy * w + ix;
+    const float4 a = TT::ld(r0), b = TT::ld(r0 + 1), c = TT::ld(r0 + w), d = TT::ld(r0 + w + 1);
     const float av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z}, cv[3] = {c.x, c.y, c.z}, dv[3] = {d.x, d.y, d.z};
     const float gx = 1.f - fx, gy = 1.f - fy;
 #pragma unroll
@@ -184,15 +247,17 @@ __device__ __forceinline__ void tap4(const float4* __restrict__ T, int w, int h,
 }
 
 // Intensity only (halfway image).
-__device__ __forceinline__ float tap1(const float4* __restrict__ T, int w, int h, int x, int y, float ox, float oy)
+template <class TT>
+__device__ __forceinline__ float tap1(const typename TT::T* __restrict__ T, int w, int h, int x, int y, float ox,
+                                      float oy)
 {
     int ix, iy;
     float fx, fy;
     bool clx, cly;
     axis_cell(x, ox, w, ix, fx, clx);
     axis_cell(y, oy, h, iy, fy, cly);
-    const float4* r0 = T + (size_t)iy * w + ix;
-    float a = __ldg(&r0->x), b = __ldg(&(r0 + 1)->x), c = __ldg(&(r0 + w)->x), d = __ldg(&(r0 + w + 1)->x);
+    const typename TT::T* r0 = T + (size_t)iy * w + ix;
+    float a = TT::ld(r0).x, b = TT::ld(r0 + 1).x, c = TT::ld(r0 + w).x, d = TT::ld(r0 + w + 1).x;
     float top = (1.f - fx) * a + fx * b, bot = (1.f - fx) * c + fx * d;
     return (1.f - fy) * top + fy * bot;
 }

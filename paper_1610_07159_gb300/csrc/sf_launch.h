@@ -7,21 +7,23 @@ namespace sfk {
 
 // sf_levels.cu: image pyramid (Section 5.3), level initialisation with the
 // delta hierarchy and temporal transfer, feature weights (Section 4.3).
-void launch_tex0(const DevArgs* args, const float* const* in_direct, int w, int h, float4* tex, cudaStream_t st);
-void launch_texdown(const float4* texp, int wp, int hp, float4* tex, int w, int h, cudaStream_t st);
+// Texel buffers are typed by the precision mode (sf_params.precision): FP32
+// float4 or 16-bit packed in 8 bytes (texel_bytes).
+void launch_tex0(const DevArgs* args, const float* const* in_direct, int w, int h, void* tex, int prec, cudaStream_t st);
+void launch_texdown(const void* texp, int wp, int hp, void* tex, int w, int h, int prec, cudaStream_t st);
 // args == nullptr: frame and use_init are taken as given (eager launches);
 // delta_c == nullptr: base_c holds the coarse totals.
 void launch_level_init(const LevelGeom& g, const LevelGeom* gc, const float* base_c, const float* delta_c,
                        float* base, float* delta, const float* prev_delta, const float* prev_total,
                        const float* init_buf, const DevArgs* args, int temporal_mode, int frame, int use_init,
                        cudaStream_t st);
-void launch_halfway(const LevelGeom& g, const float4* tex, const float* base, const float* delta, float* H,
+void launch_halfway(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta, float* H,
                     cudaStream_t st);
 void launch_wfeat(const LevelGeom& g, const float* H, const DevParams& P, float* wf, cudaStream_t st);
 void launch_fill(float* p, float v, size_t n, cudaStream_t st);
 void launch_finish_level(const LevelGeom& g, const float* base, const float* delta, float* prev_delta,
                          float* prev_total, const DevArgs* args, int write_out, float* out, cudaStream_t st);
-void launch_unpack_tex(const float4* tex, int w, int h, float* planes, cudaStream_t st);
+void launch_unpack_tex(const void* tex, int prec, int w, int h, float* planes, cudaStream_t st);
 void launch_add(const float* a, const float* b, float* out, size_t n, cudaStream_t st);
 
 // sf_assemble.cu: per-pixel data terms, cell assembly, node gather with the
@@ -35,7 +37,7 @@ struct Scratch {
     int* status;
 };
 int assemble_blocks(const LevelGeom& g, int* cpb_out);
-void launch_assemble(const LevelGeom& g, const float4* tex, const float* base, const float* delta,
+void launch_assemble(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta,
                      const DevParams& P, uint8_t* Wmask, float* cell, const Scratch& sc, cudaStream_t st);
 void launch_gather(const LevelGeom& g, const float* cell, const float* base, const float* delta, const float* wf,
                    const DevParams& P, float* node, float* rhs, float* minv, const Scratch& sc, StepCtrl* ctrl,
@@ -43,7 +45,7 @@ void launch_gather(const LevelGeom& g, const float* cell, const float* base, con
 // action: 0 = write the energy record `rec` only; 1 = backtracking trial
 // against ctrl (skips itself once a trial was accepted), `last` marks the
 // final trial. wmode: 0 = use Wmask, 1 = take W at the state and store it.
-void launch_energy(const LevelGeom& g, const float4* tex, const float* base, const float* delta, const float* x,
+void launch_energy(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta, const float* x,
                    float t, const float* wf, const DevParams& P, uint8_t* Wmask, int wmode, const Scratch& sc,
                    StepCtrl* ctrl, int action, int last, double* rec, cudaStream_t st);
 void launch_apply_step(const LevelGeom& g, float* delta, const float* x, const StepCtrl* ctrl, cudaStream_t st);

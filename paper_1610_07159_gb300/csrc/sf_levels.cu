@@ -24,8 +24,9 @@ __device__ __forceinline__ float grid_bilerp(const float* __restrict__ F, int nx
 }
 
 // Level 0 texels: intensity and central-difference gradients, edge clamped.
+template <class TT>
 __global__ void k_tex0(const DevArgs* __restrict__ args, const float* in0, const float* in1, const float* in2,
-                       const float* in3, int w, int h, float4* __restrict__ tex)
+                       const float* in3, int w, int h, typename TT::T* __restrict__ tex)
 {
     const int c = blockIdx.y;
     const float* I = args ? args->in[c] : (c == 0 ? in0 : c == 1 ? in1 : c == 2 ? in2 : in3);
@@ -36,35 +37,38 @@ __global__ void k_tex0(const DevArgs* __restrict__ args, const float* in0, const
         const float v = __ldg(I + p);
         const float gx = 0.5f * (__ldg(I + y * w + xp) - __ldg(I + y * w + xm));
         const float gy = 0.5f * (__ldg(I + yp * w + x) - __ldg(I + ym * w + x));
-        tex[(size_t)c * n + p] = make_float4(v, gx, gy, 0.f);
+        tex[(size_t)c * n + p] = TT::pack(v, gx, gy);
     }
 }
 
-__device__ __forceinline__ float box2(const float4* __restrict__ P, int wp, int hp, int x, int y)
+template <class TT>
+__device__ __forceinline__ float box2(const typename TT::T* __restrict__ P, int wp, int hp, int x, int y)
 {
     const int x0 = min(2 * x, wp - 1), x1 = min(2 * x + 1, wp - 1);
     const int y0 = min(2 * y, hp - 1), y1 = min(2 * y + 1, hp - 1);
-    float acc = __ldg(&P[y0 * wp + x0].x);
-    acc += __ldg(&P[y0 * wp + x1].x);
-    acc += __ldg(&P[y1 * wp + x0].x);
-    acc += __ldg(&P[y1 * wp + x1].x);
+    float acc = TT::ld(&P[y0 * wp + x0]).x;
+    acc += TT::ld(&P[y0 * wp + x1]).x;
+    acc += TT::ld(&P[y1 * wp + x0]).x;
+    acc += TT::ld(&P[y1 * wp + x1]).x;
     return 0.25f * acc;
 }
 
 // Next mip level: 2x2 box of the finer intensity (edge clamped), gradients
 // from the box values of the four neighbours.
-__global__ void k_texdown(const float4* __restrict__ texp, int wp, int hp, float4* __restrict__ tex, int w, int h)
+template <class TT>
+__global__ void k_texdown(const typename TT::T* __restrict__ texp, int wp, int hp, typename TT::T* __restrict__ tex,
+                          int w, int h)
 {
     const int c = blockIdx.y;
-    const float4* P = texp + (size_t)c * wp * hp;
+    const typename TT::T* P = texp + (size_t)c * wp * hp;
     const int n = w * h;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         const int y = p / w, x = p - y * w;
         const int xm = max(x - 1, 0), xp = min(x + 1, w - 1), ym = max(y - 1, 0), yp = min(y + 1, h - 1);
-        const float v = box2(P, wp, hp, x, y);
-        const float gx = 0.5f * (box2(P, wp, hp, xp, y) - box2(P, wp, hp, xm, y));
-        const float gy = 0.5f * (box2(P, wp, hp, x, yp) - box2(P, wp, hp, x, ym));
-        tex[(size_t)c * n + p] = make_float4(v, gx, gy, 0.f);
+        const float v = box2<TT>(P, wp, hp, x, y);
+        const float gx = 0.5f * (box2<TT>(P, wp, hp, xp, y) - box2<TT>(P, wp, hp, xm, y));
+        const float gy = 0.5f * (box2<TT>(P, wp, hp, x, yp) - box2<TT>(P, wp, hp, x, ym));
+        tex[(size_t)c * n + p] = TT::pack(v, gx, gy);
     }
 }
 
@@ -119,7 +123,8 @@ __global__ void k_level_init(LevelGeom g, int have_coarse, int nxc, int nyc, con
 }
 
 // Halfway image H(x) = mean of the four warped intensities.
-__global__ void k_halfway(LevelGeom g, const float4* __restrict__ tex, const float* __restrict__ base,
+template <class TT>
+__global__ void k_halfway(LevelGeom g, const typename TT::T* __restrict__ tex, const float* __restrict__ base,
                           const float* __restrict__ delta, float* __restrict__ H)
 {
     const int n = g.w * g.h;
@@ -136,7 +141,7 @@ __global__ void k_halfway(LevelGeom g, const float4* __restrict__ tex, const flo
         for (int c = 0; c < 4; ++c) {
             const float ox = sgn(c, 0) * f[0] + sgn(c, 1) * f[2] + sgn(c, 2) * f[4];
             const float oy = sgn(c, 0) * f[1] + sgn(c, 1) * f[3] + sgn(c, 2) * f[5];
-            acc += tap1(tex + c * plane, g.w, g.h, x, y, ox, oy);
+            acc += tap1<TT>(tex + c * plane, g.w, g.h, x, y, ox, oy);
         }
         H[p] = 0.25f * acc;
     }
@@ -191,11 +196,12 @@ __global__ void k_finish_level(int n6, const float* __restrict__ base, const flo
     if (write_out) (args ? args->out : out_direct)[k] = T;
 }
 
-__global__ void k_unpack_tex(const float4* __restrict__ tex, int n, float* __restrict__ planes)
+template <class TT>
+__global__ void k_unpack_tex(const typename TT::T* __restrict__ tex, int n, float* __restrict__ planes)
 {
     const int c = blockIdx.y;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const float4 t = tex[(size_t)c * n + p];
+        const float4 t = TT::ld(tex + (size_t)c * n + p);
         planes[((size_t)c * 3 + 0) * n + p] = t.x;
         planes[((size_t)c * 3 + 1) * n + p] = t.y;
         planes[((size_t)c * 3 + 2) * n + p] = t.z;
@@ -211,19 +217,23 @@ inline int grid1d(size_t n, int cap = 152 * 16)
 
 } // namespace
 
-void launch_tex0(const DevArgs* args, const float* const* in_direct, int w, int h, float4* tex, cudaStream_t st)
+void launch_tex0(const DevArgs* args, const float* const* in_direct, int w, int h, void* tex, int prec, cudaStream_t st)
 {
     dim3 grid(grid1d((size_t)w * h), 4);
-    if (args)
-        k_tex0<<<grid, T1D, 0, st>>>(args, nullptr, nullptr, nullptr, nullptr, w, h, tex);
-    else
-        k_tex0<<<grid, T1D, 0, st>>>(nullptr, in_direct[0], in_direct[1], in_direct[2], in_direct[3], w, h, tex);
+    SF_TEX_DISPATCH(prec, TT, {
+        auto* t = static_cast<typename TT::T*>(tex);
+        if (args)
+            k_tex0<TT><<<grid, T1D, 0, st>>>(args, nullptr, nullptr, nullptr, nullptr, w, h, t);
+        else
+            k_tex0<TT><<<grid, T1D, 0, st>>>(nullptr, in_direct[0], in_direct[1], in_direct[2], in_direct[3], w, h, t);
+    });
 }
 
-void launch_texdown(const float4* texp, int wp, int hp, float4* tex, int w, int h, cudaStream_t st)
+void launch_texdown(const void* texp, int wp, int hp, void* tex, int w, int h, int prec, cudaStream_t st)
 {
     dim3 grid(grid1d((size_t)w * h), 4);
-    k_texdown<<<grid, T1D, 0, st>>>(texp, wp, hp, tex, w, h);
+    SF_TEX_DISPATCH(prec, TT, k_texdown<TT><<<grid, T1D, 0, st>>>(static_cast<const typename TT::T*>(texp), wp, hp,
+                                                                   static_cast<typename TT::T*>(tex), w, h));
 }
 
 void launch_level_init(const LevelGeom& g, const LevelGeom* gc, const float* base_c, const float* delta_c,
@@ -236,10 +246,11 @@ void launch_level_init(const LevelGeom& g, const LevelGeom* gc, const float* bas
                                                         args, temporal_mode, frame, use_init);
 }
 
-void launch_halfway(const LevelGeom& g, const float4* tex, const float* base, const float* delta, float* H,
+void launch_halfway(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta, float* H,
                     cudaStream_t st)
 {
-    k_halfway<<<grid1d((size_t)g.w * g.h), T1D, 0, st>>>(g, tex, base, delta, H);
+    SF_TEX_DISPATCH(prec, TT, k_halfway<TT><<<grid1d((size_t)g.w * g.h), T1D, 0, st>>>(
+                                  g, static_cast<const typename TT::T*>(tex), base, delta, H));
 }
 
 void launch_wfeat(const LevelGeom& g, const float* H, const DevParams& P, float* wf, cudaStream_t st)
@@ -262,10 +273,11 @@ void launch_finish_level(const LevelGeom& g, const float* base, const float* del
                                                          out);
 }
 
-void launch_unpack_tex(const float4* tex, int w, int h, float* planes, cudaStream_t st)
+void launch_unpack_tex(const void* tex, int prec, int w, int h, float* planes, cudaStream_t st)
 {
     dim3 grid(grid1d((size_t)w * h), 4);
-    k_unpack_tex<<<grid, T1D, 0, st>>>(tex, w * h, planes);
+    SF_TEX_DISPATCH(prec, TT, k_unpack_tex<TT><<<grid, T1D, 0, st>>>(static_cast<const typename TT::T*>(tex), w * h,
+                                                                      planes));
 }
 
 } // namespace sfk
