@@ -247,6 +247,62 @@ SF_API int sf_probe_wmask(sf_ctx* ctx, int level, int step, unsigned char* W, vo
 SF_API int sf_probe_energy(sf_ctx* ctx, int level, const float* base, const float* delta, const float* wfeat,
                     const unsigned char* W, double* out6, void* stream);
 
+/* ---- batched solve of many sequences ----------------------------------
+ * The paper solves one stereo sequence at a time (Algorithm 1). These calls
+ * solve n independent sequences of any sizes together: each frame step runs
+ * Algorithm 1 once for every sequence in ONE kernel launch, one thread-block
+ * cluster per sequence (its stages meet at the hardware cluster barrier), the
+ * launch captured once into a CUDA graph and replayed. All sequences share
+ * the parameters and the grid stride; each has its own size and level count
+ * and its own temporal state. FP32 texels only (params.precision must be
+ * SF_FP32), and params.gn_iters[0] >= 1.
+ *
+ * Inputs and outputs are packed device buffers: sequence i's four images
+ * (L_t, R_t, L_t1, R_t1, each w_i * h_i floats) start at float offset
+ * in_offsets[i] of `in`, its finest fields (float32 [6][ny][nx]) at
+ * out_offsets[i] of `out`; sf_batch_layout gives the offsets and totals
+ * (sequences in the order given, each packed after the previous one). */
+typedef struct sf_batch sf_batch;
+
+/* Creates a batch of n sequences (widths[i] x heights[i], levels[i] levels,
+ * each as sf_create would accept) and allocates all device memory. Writes
+ * the batch to *out; returns SF_OK or an error code. */
+SF_API int sf_batch_create(int n, const int* widths, const int* heights, const int* levels, int grid_stride,
+                           const sf_params* p, sf_batch** out);
+
+/* Offsets (floats) of each sequence in the packed input and output buffers
+ * (arrays of n entries, either may be NULL) and the buffer sizes. */
+SF_API int sf_batch_layout(const sf_batch* b, size_t* in_offsets, size_t* out_offsets, size_t* in_total,
+                           size_t* out_total);
+
+/* Enqueues one frame step of every sequence on `stream` (returns before the
+ * work ends). `in` and `out` are device buffers in the packed layout. */
+SF_API int sf_batch_solve(sf_batch* b, const float* in, float* out, void* stream);
+
+/* Schedule of the launch: CTAs per sequence (`cluster`, a power of two up to
+ * 16) and the divisor of the cells each CTA assembles at a time (cpb_div,
+ * 1..4; 1 = as many cells as one pass of 256 threads covers). SF_ERR_ARG if
+ * the GPU cannot hold one such cluster. */
+SF_API int sf_batch_set_schedule(sf_batch* b, int cluster, int cpb_div);
+SF_API int sf_batch_get_schedule(const sf_batch* b, int* cluster, int* cpb_div);
+
+/* Autotuner: times `steps` frame steps on in/out (after one warm-up) for
+ * every schedule the GPU can hold (clusters of 2..16 CTAs, cpb_div 1 and 2),
+ * keeps the fastest and writes its time per step (ms) to best_ms (may be
+ * NULL). Results are cached per process, keyed by the batch's shape (sizes,
+ * levels, stride, iteration counts): a later batch of the same shape takes
+ * the cached schedule without timing. Runs only before the first frame
+ * (SF_ERR_STATE otherwise) and leaves every sequence at frame 0. */
+SF_API int sf_batch_tune(sf_batch* b, const float* in, float* out, int steps, void* stream, float* best_ms);
+
+/* The context of sequence i, owned by the batch (do not destroy it): for
+ * sf_get_stats, sf_get_state, sf_probe_wmask and sf_grid_dims. */
+SF_API sf_ctx* sf_batch_sequence(sf_batch* b, int i);
+
+/* Forgets every sequence's temporal state and status. */
+SF_API int sf_batch_reset(sf_batch* b);
+SF_API void sf_batch_destroy(sf_batch* b);
+
 /* ---- allocation-free PCG ------------------------------------------------
  * The paper has no counterpart to this call: it exists for callers that
  * cannot allocate device memory where they solve (inside a CUDA graph

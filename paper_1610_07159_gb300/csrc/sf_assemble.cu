@@ -13,158 +13,13 @@
 //     preconditioner and the energy at the linearisation point;
 //   * energies of trial steps with the backtracking decision and the update.
 #include "sf_launch.h"
+#include "sf_stages.cuh"
 
 namespace sfk {
 
 namespace {
 
-constexpr int ETHREADS = 256;
-constexpr int HB = NB + 6; // H_p and b_p of a pixel in shared memory (odd stride)
-
-__constant__ int c_pair_k[NPAIR] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 3};
-__constant__ int c_pair_l[NPAIR] = {0, 1, 2, 3, 1, 2, 3, 2, 3, 3};
-
-// Data terms of one pixel at fields f (Eqs. 1-6, 11-13). Returns the
-// unweighted photometric and gradient penalties; with ASSEMBLE also the
-// pixel's 6x6 normal-equation block H (packed) and right-hand side b.
-template <bool ASSEMBLE, class TT>
-__device__ __forceinline__ void pixel_data(const typename TT::T* __restrict__ tex, int w, int h, int x, int y, const float f[6],
-                                           const DevParams& P, int Wgiven, int& Wout, float& Ep, float& Eg, float* H,
-                                           float* b)
-{
-    const size_t plane = (size_t)w * h;
-    Tap tp[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const float ox = sgn(c, 0) * f[0] + sgn(c, 1) * f[2] + sgn(c, 2) * f[4];
-        const float oy = sgn(c, 0) * f[1] + sgn(c, 1) * f[3] + sgn(c, 2) * f[5];
-        tap4<TT>(tex + c * plane, w, h, x, y, ox, oy, tp[c]);
-    }
-    float e[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) e[k] = tp[chk_first(k)].v[0] - tp[chk_second(k)].v[0];
-    int Wi = Wgiven;
-    if (Wi < 0) {
-        if (P.eps_p <= 0.f) {
-            Wi = 1;
-        } else {
-            float mx = 0.f;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) mx = fmaxf(mx, fabsf(e[k]));
-            Wi = mx < P.eps_p ? 1 : 0;
-        }
-    }
-    Wout = Wi;
-    Ep = 0.f;
-    Eg = 0.f;
-    if (ASSEMBLE) {
-#pragma unroll
-        for (int q = 0; q < NB; ++q) H[q] = 0.f;
-#pragma unroll
-        for (int q = 0; q < 6; ++q) b[q] = 0.f;
-    }
-    if (!Wi) return;
-    const float eps2 = P.eps * P.eps;
-    const bool literal = P.grad_mode == SF_GRAD_LITERAL;
-    const bool irls = P.robust_mode == SF_IRLS;
-    float gp[6], gg[6];
-    float rho_p = 0.f, rho_g = 0.f;
-    if (ASSEMBLE && !irls) {
-#pragma unroll
-        for (int q = 0; q < 6; ++q) gp[q] = gg[q] = 0.f;
-    }
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        const int F = chk_first(k), S = chk_second(k);
-        const float ph = sqrtf(fmaf(e[k], e[k], eps2));
-        Ep += ph;
-        const float gxk = tp[F].v[1] - tp[S].v[1], gyk = tp[F].v[2] - tp[S].v[2];
-        const float q = fmaf(gxk, gxk, gyk * gyk);
-        const float psi = literal ? sqrtf(fmaf(q, q, eps2)) : sqrtf(q + eps2);
-        Eg += psi;
-        if (ASSEMBLE) {
-            float J[6];
-#pragma unroll
-            for (int fl = 0; fl < 3; ++fl) {
-                J[2 * fl] = sgn(F, fl) * tp[F].dx[0] - sgn(S, fl) * tp[S].dx[0];
-                J[2 * fl + 1] = sgn(F, fl) * tp[F].dy[0] - sgn(S, fl) * tp[S].dy[0];
-            }
-            // d psi / d g = coefg * g
-            const float coefg = literal ? 2.f * q / psi : 1.f / psi;
-            if (irls) {
-                const float om = P.w_photo / (2.f * ph);
-                sym_rank1(H, J, om);
-#pragma unroll
-                for (int r = 0; r < 6; ++r) b[r] -= om * e[k] * J[r];
-            } else {
-                rho_p += P.w_photo * ph;
-                const float cf = P.w_photo * e[k] / ph;
-#pragma unroll
-                for (int r = 0; r < 6; ++r) gp[r] = fmaf(cf, J[r], gp[r]);
-                rho_g += P.w_grad * psi;
-            }
-            const float og = 0.5f * P.w_grad * coefg;
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                float Jg[6];
-#pragma unroll
-                for (int fl = 0; fl < 3; ++fl) {
-                    Jg[2 * fl] = sgn(F, fl) * tp[F].dx[1 + a] - sgn(S, fl) * tp[S].dx[1 + a];
-                    Jg[2 * fl + 1] = sgn(F, fl) * tp[F].dy[1 + a] - sgn(S, fl) * tp[S].dy[1 + a];
-                }
-                const float ga = a == 0 ? gxk : gyk;
-                if (irls) {
-                    sym_rank1(H, Jg, og);
-#pragma unroll
-                    for (int r = 0; r < 6; ++r) b[r] -= og * ga * Jg[r];
-                } else {
-                    const float cf = P.w_grad * coefg * ga;
-#pragma unroll
-                    for (int r = 0; r < 6; ++r) gg[r] = fmaf(cf, Jg[r], gg[r]);
-                }
-            }
-        }
-    }
-    if (ASSEMBLE && !irls) {
-        // one residual sqrt(rho) per pixel and term: J = grad rho / (2 sqrt rho)
-#pragma unroll
-        for (int r = 0; r < 6; ++r) b[r] -= 0.5f * (gp[r] + gg[r]);
-        if (rho_p > 0.f) sym_rank1(H, gp, 0.25f / rho_p);
-        if (rho_g > 0.f) sym_rank1(H, gg, 0.25f / rho_g);
-    }
-}
-
-// Adds term(lo) .. term(hi-1) to the compensated sum (a, e): runs of SUMRUN
-// terms are summed plainly and each run's sum enters with one Kahan step. A
-// cell's right-hand side nearly cancels near convergence, and its blocks sum
-// hundreds of pixels at the finest levels; the compensation keeps both
-// accurate at a quarter of the cost of compensating every term.
-constexpr int SUMRUN = 4;
-template <class Term>
-__device__ __forceinline__ void comp_sum(float& a, float& e, int lo, int hi, Term term)
-{
-    int q = lo;
-    for (; q + SUMRUN <= hi; q += SUMRUN) {
-        float run = term(q);
-#pragma unroll
-        for (int r = 1; r < SUMRUN; ++r) run += term(q + r);
-        const float y = run - e;
-        const float t = a + y;
-        e = (t - a) - y;
-        a = t;
-    }
-    for (; q < hi; ++q) {
-        const float y = term(q) - e;
-        const float t = a + y;
-        e = (t - a) - y;
-        a = t;
-    }
-}
-
-// One CTA assembles `cpb` consecutive cells of one cell row. Pixels are
-// enumerated cell-major (regular cells s x ch, the row's last cell may be
-// wider), processed in chunks of ETHREADS; each thread owns up to MAXOUT of
-// the cpb * CELL_VALS outputs and sums its cell's pixels of every chunk.
+// One CTA per cell group (assemble_group), then the block's energy partials.
 template <int MAXOUT, class TT>
 __global__ void __launch_bounds__(ETHREADS) k_assemble(LevelGeom g, int cpb, const typename TT::T* __restrict__ tex,
                                                        const float* __restrict__ base, const float* __restrict__ delta,
@@ -175,94 +30,9 @@ __global__ void __launch_bounds__(ETHREADS) k_assemble(LevelGeom g, int cpb, con
     __shared__ float sA[ETHREADS * 4];
     __shared__ ff sred[ETHREADS / 32];
     const int tid = threadIdx.x;
-    const int s = g.s;
-    const int cj = blockIdx.y, ci0 = blockIdx.x * cpb;
-    const int ncell = min(cpb, g.ncx - ci0);
-    const int y0 = cj * s;
-    const int ch = (cj == g.ncy - 1 ? g.h : (cj + 1) * s) - y0;
-    const int lastc = ci0 + ncell - 1;
-    const int cw_last = (lastc == g.ncx - 1 ? g.w : (lastc + 1) * s) - lastc * s;
-    const int per_reg = s * ch;
-    const int total = (ncell - 1) * per_reg + cw_last * ch;
-    const int nout = ncell * CELL_VALS;
-
-    float acc[MAXOUT], cmp[MAXOUT]; // cmp: Kahan compensation of the cell sums
-#pragma unroll
-    for (int k = 0; k < MAXOUT; ++k) acc[k] = cmp[k] = 0.f;
     float ep = 0.f, eg = 0.f;
     int nex = 0;
-
-    for (int c0 = 0; c0 < total; c0 += ETHREADS) {
-        const int p = c0 + tid;
-        float H[NB], bv[6];
-        float al[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int q = 0; q < NB; ++q) H[q] = 0.f;
-#pragma unroll
-        for (int q = 0; q < 6; ++q) bv[q] = 0.f;
-        if (p < total) {
-            const int c = min(p / per_reg, ncell - 1);
-            const int q = p - c * per_reg;
-            const int cw = (c == ncell - 1) ? cw_last : s;
-            const int ly = q / cw, lx = q - ly * cw;
-            const int x = (ci0 + c) * s + lx, y = y0 + ly;
-            int i0, j0;
-            float a, bb;
-            grid_cell(x, y, s, g.nx, g.ny, i0, j0, a, bb);
-            float f[6];
-            pixel_fields(base, delta, nullptr, 0.f, g.G, j0 * g.nx + i0, g.nx, a, bb, f);
-            int Wi;
-            float Ep, Eg;
-            pixel_data<true, TT>(tex, g.w, g.h, x, y, f, P, -1, Wi, Ep, Eg, H, bv);
-            Wmask[y * g.w + x] = (uint8_t)Wi;
-            ep += Ep;
-            eg += Eg;
-            nex += Wi ? 0 : 1;
-            al[0] = (1.f - a) * (1.f - bb);
-            al[1] = a * (1.f - bb);
-            al[2] = (1.f - a) * bb;
-            al[3] = a * bb;
-        }
-#pragma unroll
-        for (int q = 0; q < NB; ++q) sHB[tid * HB + q] = H[q];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) sHB[tid * HB + NB + q] = bv[q];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) sA[tid * 4 + q] = al[q];
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < MAXOUT; ++k) {
-            const int o = tid + k * ETHREADS;
-            if (o < nout) {
-                const int c = o / CELL_VALS, r = o - c * CELL_VALS;
-                int lo = c * per_reg, hi = (c == ncell - 1) ? total : (c + 1) * per_reg;
-                lo = max(lo, c0) - c0;
-                hi = min(hi, c0 + ETHREADS) - c0;
-                float a = acc[k], e = cmp[k];
-                if (r < NPAIR * NB) {
-                    const int pr = r / NB, ee = r - pr * NB;
-                    const int kk = c_pair_k[pr], ll = c_pair_l[pr];
-                    comp_sum(a, e, lo, hi, [&](int q) { return sA[q * 4 + kk] * sA[q * 4 + ll] * sHB[q * HB + ee]; });
-                } else {
-                    const int rr = r - NPAIR * NB;
-                    const int kk = rr / 6, comp = rr - kk * 6;
-                    comp_sum(a, e, lo, hi, [&](int q) { return sA[q * 4 + kk] * sHB[q * HB + NB + comp]; });
-                }
-                cmp[k] = e;
-                acc[k] = a;
-            }
-        }
-        __syncthreads();
-    }
-    const int ncell_tot = g.ncx * g.ncy;
-#pragma unroll
-    for (int k = 0; k < MAXOUT; ++k) {
-        const int o = tid + k * ETHREADS;
-        if (o < nout) {
-            const int c = o / CELL_VALS, r = o - c * CELL_VALS;
-            cell[(size_t)r * ncell_tot + cj * g.ncx + ci0 + c] = acc[k] - cmp[k];
-        }
-    }
+    assemble_group<MAXOUT, TT>(g, cpb, blockIdx.x, blockIdx.y, tex, base, delta, P, Wmask, cell, sHB, sA, ep, eg, nex);
     const int blk = blockIdx.y * gridDim.x + blockIdx.x;
     const ff tp = ff_block_sum_fast<ETHREADS>(ep, sred);
     const ff tg = ff_block_sum_fast<ETHREADS>(eg, sred);
@@ -272,93 +42,6 @@ __global__ void __launch_bounds__(ETHREADS) k_assemble(LevelGeom g, int cpb, con
         part[MAX_PART + blk] = make_float2(tg.hi, tg.lo);
         part[2 * MAX_PART + blk] = make_float2(tn.hi, tn.lo);
     }
-}
-
-__device__ __forceinline__ void add_cell_pair(float* dst, const float* __restrict__ cell, int ncx, int ncy, int ci,
-                                              int cj, int pr)
-{
-    if (ci < 0 || cj < 0 || ci >= ncx || cj >= ncy) return;
-    const int nc = ncx * ncy, c = cj * ncx + ci;
-#pragma unroll
-    for (int e = 0; e < NB; ++e) dst[e] += __ldg(cell + (size_t)(pr * NB + e) * nc + c);
-}
-
-__device__ __forceinline__ void add_cell_rhs(float* dst, const float* __restrict__ cell, int ncx, int ncy, int ci,
-                                             int cj, int corner)
-{
-    if (ci < 0 || cj < 0 || ci >= ncx || cj >= ncy) return;
-    const int nc = ncx * ncy, c = cj * ncx + ci;
-#pragma unroll
-    for (int r = 0; r < 6; ++r) dst[r] += __ldg(cell + (size_t)(NPAIR * NB + corner * 6 + r) * nc + c);
-}
-
-// Epipolar residuals of one node (Eqs. 15-17) and their gradients.
-__device__ __forceinline__ void epipolar(const float* Fl, float X, float Y, const float t[6], float r[2], float J[12])
-{
-#pragma unroll
-    for (int tt = 0; tt < 2; ++tt) {
-        const int il = tt == 0 ? 0 : 2, ir = tt == 0 ? 1 : 3;
-        const float l0 = X + sgn(il, 0) * t[0] + sgn(il, 1) * t[2] + sgn(il, 2) * t[4];
-        const float l1 = Y + sgn(il, 0) * t[1] + sgn(il, 1) * t[3] + sgn(il, 2) * t[5];
-        const float r0 = X + sgn(ir, 0) * t[0] + sgn(ir, 1) * t[2] + sgn(ir, 2) * t[4];
-        const float r1 = Y + sgn(ir, 0) * t[1] + sgn(ir, 1) * t[3] + sgn(ir, 2) * t[5];
-        float Fr[3], Ftl[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            Fr[a] = Fl[a * 3 + 0] * r0 + Fl[a * 3 + 1] * r1 + Fl[a * 3 + 2];
-            Ftl[a] = Fl[0 * 3 + a] * l0 + Fl[1 * 3 + a] * l1 + Fl[2 * 3 + a];
-        }
-        r[tt] = l0 * Fr[0] + l1 * Fr[1] + Fr[2];
-#pragma unroll
-        for (int fl = 0; fl < 3; ++fl)
-#pragma unroll
-            for (int a = 0; a < 2; ++a) J[tt * 6 + 2 * fl + a] = sgn(il, fl) * Fr[a] + sgn(ir, fl) * Ftl[a];
-    }
-}
-
-__device__ __forceinline__ void node_total(const float* __restrict__ base, const float* __restrict__ delta,
-                                           const float* __restrict__ x, float t, int G, int n, float T[6], float d[6])
-{
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        float dd = delta[c * G + n];
-        if (x) dd = fmaf(t, x[c * G + n], dd);
-        d[c] = dd;
-        T[c] = base[c * G + n] + dd;
-    }
-}
-
-// Prior energies of one node: smoothness over its E and S edges (each
-// undirected edge once, weight (w_i + w_j) w_f), epipolar, magnitude.
-__device__ __forceinline__ void node_prior_energy(const LevelGeom& g, const DevParams& P, const float* __restrict__ base,
-                                                  const float* __restrict__ delta, const float* __restrict__ x, float t,
-                                                  const float* __restrict__ wf, int n, float& es, float& ee, float& em)
-{
-    const int i = n % g.nx, j = n / g.nx;
-    float T[6], d[6];
-    node_total(base, delta, x, t, g.G, n, T, d);
-    float acc = 0.f;
-    for (int nb = 0; nb < 2; ++nb) {
-        const int i2 = i + (nb == 0), j2 = j + (nb == 1);
-        if (i2 >= g.nx || j2 >= g.ny) continue;
-        const int m = j2 * g.nx + i2;
-        float Tm[6], dm[6];
-        node_total(base, delta, x, t, g.G, m, Tm, dm);
-        const float ww = wf[n] + wf[m];
-#pragma unroll
-        for (int u = 0; u < 6; ++u) {
-            const float df = (base[u * g.G + n] - base[u * g.G + m]) + (d[u] - dm[u]);
-            acc += ww * P.wfl[u >> 1] * df * df;
-        }
-    }
-    es = acc;
-    float r[2], J[12];
-    epipolar(P.Fl, (float)(i * g.s), (float)(j * g.s), T, r, J);
-    ee = r[0] * r[0] + r[1] * r[1];
-    float m = 0.f;
-#pragma unroll
-    for (int u = 0; u < 6; ++u) m += P.mfl[u >> 1] * d[u] * d[u];
-    em = m;
 }
 
 // Gather of the node system from the cell blocks plus the prior rows, the
@@ -375,89 +58,7 @@ __global__ void __launch_bounds__(ETHREADS) k_gather(LevelGeom g, const float* _
     __shared__ bool last_sh;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     float es = 0.f, ee = 0.f, em = 0.f;
-    if (n < g.G) {
-        const int i = n % g.nx, j = n / g.nx;
-        const int ncx = g.ncx, ncy = g.ncy, G = g.G;
-        float Bs[NB], Be[NB], Bso[NB], Bse[NB], Bsw[NB], bb[6];
-#pragma unroll
-        for (int e = 0; e < NB; ++e) Bs[e] = Be[e] = Bso[e] = Bse[e] = Bsw[e] = 0.f;
-#pragma unroll
-        for (int r = 0; r < 6; ++r) bb[r] = 0.f;
-        // corners: 0 (ci,cj), 1 (ci+1,cj), 2 (ci,cj+1), 3 (ci+1,cj+1)
-        add_cell_pair(Bs, cell, ncx, ncy, i - 1, j - 1, pair_idx(3, 3));
-        add_cell_pair(Bs, cell, ncx, ncy, i, j - 1, pair_idx(2, 2));
-        add_cell_pair(Bs, cell, ncx, ncy, i - 1, j, pair_idx(1, 1));
-        add_cell_pair(Bs, cell, ncx, ncy, i, j, pair_idx(0, 0));
-        add_cell_pair(Be, cell, ncx, ncy, i, j - 1, pair_idx(2, 3));
-        add_cell_pair(Be, cell, ncx, ncy, i, j, pair_idx(0, 1));
-        add_cell_pair(Bso, cell, ncx, ncy, i - 1, j, pair_idx(1, 3));
-        add_cell_pair(Bso, cell, ncx, ncy, i, j, pair_idx(0, 2));
-        add_cell_pair(Bse, cell, ncx, ncy, i, j, pair_idx(0, 3));
-        add_cell_pair(Bsw, cell, ncx, ncy, i - 1, j, pair_idx(1, 2));
-        add_cell_rhs(bb, cell, ncx, ncy, i - 1, j - 1, 3);
-        add_cell_rhs(bb, cell, ncx, ncy, i, j - 1, 2);
-        add_cell_rhs(bb, cell, ncx, ncy, i - 1, j, 1);
-        add_cell_rhs(bb, cell, ncx, ncy, i, j, 0);
-
-        float T[6], d[6];
-        node_total(base, delta, nullptr, 0.f, G, n, T, d);
-        const float wn = wf[n];
-        // smoothness (Eq. 14): every 4-neighbour edge, both directed pairs
-        const int nbi[4] = {i + 1, i, i - 1, i};
-        const int nbj[4] = {j, j + 1, j, j - 1};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (nbi[q] < 0 || nbj[q] < 0 || nbi[q] >= g.nx || nbj[q] >= g.ny) continue;
-            const int m = nbj[q] * g.nx + nbi[q];
-            const float ww = P.w_reg * P.w_smooth * (wn + wf[m]);
-            float Tm[6], dm[6];
-            node_total(base, delta, nullptr, 0.f, G, m, Tm, dm);
-#pragma unroll
-            for (int u = 0; u < 6; ++u) {
-                const float c = ww * P.wfl[u >> 1];
-                // T_n - T_m as (base difference) + (delta difference): no cancellation of the large totals
-                const float df = (base[u * g.G + n] - base[u * g.G + m]) + (d[u] - dm[u]);
-                Bs[sym_idx(u, u)] += c;
-                bb[u] -= c * df;
-                if (q == 0) Be[sym_idx(u, u)] -= c;
-                if (q == 1) Bso[sym_idx(u, u)] -= c;
-            }
-        }
-        // epipolar (Eqs. 15-17)
-        {
-            float r[2], J[12];
-            epipolar(P.Fl, (float)(i * g.s), (float)(j * g.s), T, r, J);
-            const float ce = P.w_reg * P.w_epi;
-            if (ce != 0.f) {
-                sym_rank1(Bs, J, ce);
-                sym_rank1(Bs, J + 6, ce);
-#pragma unroll
-                for (int u = 0; u < 6; ++u) bb[u] -= ce * (r[0] * J[u] + r[1] * J[6 + u]);
-            }
-        }
-        // magnitude (Eq. 18) on the delta
-#pragma unroll
-        for (int u = 0; u < 6; ++u) {
-            const float cm = P.w_reg * P.w_mag * P.mfl[u >> 1];
-            Bs[sym_idx(u, u)] += cm;
-            bb[u] -= cm * d[u];
-        }
-#pragma unroll
-        for (int e = 0; e < NB; ++e) {
-            node[(size_t)(0 * NB + e) * G + n] = Bs[e];
-            node[(size_t)(1 * NB + e) * G + n] = Be[e];
-            node[(size_t)(2 * NB + e) * G + n] = Bso[e];
-            node[(size_t)(3 * NB + e) * G + n] = Bse[e];
-            node[(size_t)(4 * NB + e) * G + n] = Bsw[e];
-        }
-#pragma unroll
-        for (int u = 0; u < 6; ++u) {
-            rhs[u * G + n] = bb[u];
-            const float dg = Bs[sym_idx(u, u)];
-            minv[u * G + n] = dg > 0.f ? 1.f / dg : 1.f;
-        }
-        node_prior_energy(g, P, base, delta, nullptr, 0.f, wf, n, es, ee, em);
-    }
+    if (n < g.G) gather_node(g, n, cell, base, delta, wf, P, node, rhs, minv, es, ee, em);
     if (!ctrl) return;
     const ff ts = ff_block_sum_fast<ETHREADS>(es, sred);
     const ff te = ff_block_sum_fast<ETHREADS>(ee, sred);

@@ -9,7 +9,10 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "sf_launch.h"
@@ -381,6 +384,126 @@ int enqueue_video(sf_ctx* c, const float* frames, const float* host_in, int n, f
 
 } // namespace
 
+// ---------------------------------------------------------------------------
+// batched solve: one cluster per sequence, one launch per frame step
+// ---------------------------------------------------------------------------
+
+struct sf_batch {
+    int n = 0, s = 0, maxout = 4;
+    std::vector<sf_ctx*> seq;
+    std::vector<BSeq> hseq;
+    BSeq* dseq = nullptr;
+    int* dorder = nullptr;
+    int* dframes = nullptr;
+    float2* dpart = nullptr;
+    std::vector<size_t> in_off, out_off;
+    size_t in_total = 0, out_total = 0;
+    int cluster = 8, cpb_div = 1;
+    const float* last_in = nullptr;
+    float* last_out = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool use_graph = true;
+    cudaStream_t cap = nullptr;
+    std::string key;
+};
+
+namespace {
+
+struct BatchSchedule {
+    int cluster, cpb_div;
+    float ms;
+};
+
+std::mutex g_tune_mu;
+std::map<std::string, BatchSchedule> g_tune_cache; // per process: shape key -> chosen schedule
+
+void batch_free(sf_batch* b)
+{
+    if (!b) return;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (sf_ctx* c : b->seq) free_ctx(c);
+    if (b->dseq) cudaFree(b->dseq);
+    if (b->dorder) cudaFree(b->dorder);
+    if (b->dframes) cudaFree(b->dframes);
+    if (b->dpart) cudaFree(b->dpart);
+    delete b;
+}
+
+// Descriptor of every level for the current schedule (cells per group).
+int batch_fill(sf_batch* b)
+{
+    // the upload replaces the device descriptors, input and output pointers
+    // included: the next step sets those again
+    b->last_in = nullptr;
+    b->last_out = nullptr;
+    for (int i = 0; i < b->n; ++i) {
+        sf_ctx* c = b->seq[i];
+        BSeq& S = b->hseq[i];
+        for (int l = 0; l < c->L; ++l) {
+            BLevel& B = S.lv[l];
+            const LevelGeom& g = c->geo[l];
+            B.cpb = batch_cells_per_group(b->s, b->cpb_div);
+            B.gx = (g.ncx + B.cpb - 1) / B.cpb;
+            B.n_groups = B.gx * g.ncy;
+        }
+    }
+    return check_cuda(cudaMemcpy(b->dseq, b->hseq.data(), sizeof(BSeq) * b->n, cudaMemcpyHostToDevice));
+}
+
+void batch_drop_graph(sf_batch* b)
+{
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+}
+
+int batch_enqueue(sf_batch* b, cudaStream_t st)
+{
+    return check_cuda(launch_batch_frame(b->dseq, b->dorder, b->n, b->cluster, b->maxout, st));
+}
+
+int batch_step(sf_batch* b, const float* in, float* out, cudaStream_t st)
+{
+    if (in != b->last_in || out != b->last_out) {
+        launch_batch_args(b->dseq, b->n, in, out, st);
+        int rc = check_cuda(cudaGetLastError());
+        if (rc) return rc;
+        b->last_in = in;
+        b->last_out = out;
+    }
+    if (b->use_graph && !b->gexec) {
+        cudaGraph_t graph = nullptr;
+        bool ok = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        int erc = ok ? batch_enqueue(b, b->cap) : SF_ERR_CUDA;
+        ok = cudaStreamEndCapture(b->cap, &graph) == cudaSuccess && ok && erc == SF_OK;
+        ok = ok && cudaGraphInstantiate(&b->gexec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        if (!ok) {
+            cudaGetLastError();
+            batch_drop_graph(b);
+            b->use_graph = false;
+        }
+    }
+    int rc = b->gexec ? check_cuda(cudaGraphLaunch(b->gexec, st)) : batch_enqueue(b, st);
+    if (rc) return rc;
+    for (sf_ctx* c : b->seq) {
+        c->frames += 1;
+        c->launches = 1;
+    }
+    return SF_OK;
+}
+
+int batch_zero_frames(sf_batch* b)
+{
+    int rc = check_cuda(cudaDeviceSynchronize());
+    if (!rc) rc = check_cuda(cudaMemset(b->dframes, 0, sizeof(int) * b->n));
+    if (!rc) rc = check_cuda(cudaDeviceSynchronize());
+    for (sf_ctx* c : b->seq) c->frames = 0;
+    return rc;
+}
+
+} // namespace
+
 extern "C" {
 
 int sf_params_preset(sf_params* p, int preset)
@@ -687,7 +810,10 @@ int sf_get_stats(sf_ctx* c, sf_stats* out)
     if (!rc) rc = check_cuda(cudaMemcpy(rec, c->rec, sizeof(rec), cudaMemcpyDeviceToHost));
     if (rc) return fail(rc);
     std::memset(out, 0, sizeof(*out));
-    out->status = (status & DEV_TIMEOUT) ? SF_ERR_TIMEOUT : (status & DEV_NUMERIC) ? SF_ERR_NUMERIC : SF_OK;
+    out->status = (status & DEV_TIMEOUT)   ? SF_ERR_TIMEOUT
+                  : (status & DEV_NUMERIC) ? SF_ERR_NUMERIC
+                  : (status & DEV_NOARGS)  ? SF_ERR_STATE
+                                           : SF_OK;
     out->frames = c->frames;
     out->levels = c->L;
     out->launches = c->launches;
@@ -859,6 +985,235 @@ int sf_probe_energy(sf_ctx* c, int level, const float* base, const float* delta,
     rc = check_cuda(cudaMemcpyAsync(out6, c->rec, 6 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if (!rc) rc = check_cuda(cudaGetLastError());
     return rc ? fail(rc) : SF_OK;
+}
+
+int sf_batch_create(int n, const int* widths, const int* heights, const int* levels, int grid_stride,
+                    const sf_params* p, sf_batch** out)
+{
+    g_last_error = SF_OK;
+    if (!out) return fail(SF_ERR_ARG);
+    *out = nullptr;
+    if (n < 1 || n > (1 << 16) || !widths || !heights || !levels || !p || p->precision != SF_FP32 ||
+        p->gn_iters[0] < 1)
+        return fail(SF_ERR_ARG);
+    sf_batch* b = new (std::nothrow) sf_batch();
+    if (!b) return fail(SF_ERR_OOM);
+    b->n = n;
+    b->s = grid_stride;
+    b->maxout = batch_maxout(grid_stride > 0 ? grid_stride : 1);
+    sf_params q = *p;
+    q.use_graph = 0;
+    q.video = 0;
+    q.profile_mask = 0;
+    std::string key = std::to_string(n) + "|" + std::to_string(grid_stride);
+    for (int i = 0; i < n; ++i) {
+        sf_ctx* c = sf_create(widths[i], heights[i], grid_stride, levels[i], &q);
+        if (!c) {
+            const int e = g_last_error;
+            batch_free(b);
+            return fail(e ? e : SF_ERR_ARG);
+        }
+        b->seq.push_back(c);
+        key += "|" + std::to_string(widths[i]) + "x" + std::to_string(heights[i]) + "x" + std::to_string(levels[i]);
+    }
+    for (int l = 0; l < SF_MAX_LEVELS; ++l)
+        key += "|" + std::to_string(p->gn_iters[l]) + ":" + std::to_string(p->pcg_iters[l]);
+    key += "|" + std::to_string(p->max_backtracks) + "|" + std::to_string(p->wfeat_mode);
+    b->key = key;
+    bool ok = cudaMalloc(&b->dseq, sizeof(BSeq) * n) == cudaSuccess &&
+              cudaMalloc(&b->dorder, sizeof(int) * n) == cudaSuccess &&
+              cudaMalloc(&b->dframes, sizeof(int) * n) == cudaSuccess &&
+              cudaMalloc(&b->dpart, sizeof(float2) * 2 * 8 * BATCH_MAX_CLUSTER * (size_t)n) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) ok = cudaMemset(b->dframes, 0, sizeof(int) * n) == cudaSuccess;
+    b->hseq.resize(n);
+    b->in_off.resize(n);
+    b->out_off.resize(n);
+    for (int i = 0; i < n && ok; ++i) {
+        sf_ctx* c = b->seq[i];
+        BSeq& S = b->hseq[i];
+        std::memset(&S, 0, sizeof(S));
+        S.L = c->L;
+        S.w0 = c->w0;
+        S.h0 = c->h0;
+        S.temporal_mode = c->prm.temporal_mode;
+        S.wfeat_mode = c->prm.wfeat_mode;
+        S.max_backtracks = c->prm.max_backtracks;
+        S.use_init = 0;
+        S.frames = b->dframes + i;
+        S.init_buf = c->init_buf;
+        S.status = c->status;
+        S.part = b->dpart + (size_t)i * 2 * 8 * BATCH_MAX_CLUSTER;
+        S.in_off = b->in_total;
+        S.out_off = b->out_total;
+        b->in_off[i] = b->in_total;
+        b->out_off[i] = b->out_total;
+        b->in_total += (size_t)4 * c->w0 * c->h0;
+        b->out_total += (size_t)6 * c->geo[0].G;
+        for (int l = 0; l < c->L && ok; ++l) {
+            BLevel& B = S.lv[l];
+            LevelBuf& lb = c->lv[l];
+            B.g = c->geo[l];
+            B.P = c->dp[l];
+            B.tex = lb.tex;
+            B.W = lb.W;
+            B.H = lb.H;
+            B.base = lb.base;
+            B.delta = lb.delta;
+            B.x = lb.x;
+            B.wf = lb.wf;
+            B.prev_delta = lb.prev_delta;
+            B.prev_total = lb.prev_total;
+            B.node = lb.node;
+            B.rhs = lb.rhs;
+            B.minv = lb.minv;
+            B.z = lb.z;
+            B.p0 = lb.p0;
+            B.p1 = lb.p1;
+            B.cell = lb.cell;
+            B.ctrl = c->ctrl + l * SF_MAX_GN;
+            B.gn = c->prm.gn_iters[l];
+            B.pcg = c->prm.pcg_iters[l];
+            const size_t G6 = (size_t)6 * c->geo[l].G;
+            ok = dalloc(c, &B.r, G6) && dalloc(c, &B.q, G6);
+        }
+    }
+    // longest sequences first, so the last clusters to start are short ones
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return (long long)b->seq[a]->w0 * b->seq[a]->h0 > (long long)b->seq[c]->w0 * b->seq[c]->h0;
+    });
+    ok = ok && cudaMemcpy(b->dorder, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok) {
+        batch_prepare(BATCH_MAX_CLUSTER, b->maxout);
+        // default schedule: the largest portable cluster the GPU can hold
+        b->cluster = 8;
+        while (b->cluster > 1 && batch_active_clusters(b->cluster, b->maxout) < 1) b->cluster /= 2;
+        ok = batch_fill(b) == SF_OK && cudaDeviceSynchronize() == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        batch_free(b);
+        return fail(SF_ERR_CUDA);
+    }
+    *out = b;
+    return SF_OK;
+}
+
+int sf_batch_layout(const sf_batch* b, size_t* in_offsets, size_t* out_offsets, size_t* in_total, size_t* out_total)
+{
+    if (!b) return fail(SF_ERR_ARG);
+    for (int i = 0; i < b->n; ++i) {
+        if (in_offsets) in_offsets[i] = b->in_off[i];
+        if (out_offsets) out_offsets[i] = b->out_off[i];
+    }
+    if (in_total) *in_total = b->in_total;
+    if (out_total) *out_total = b->out_total;
+    return SF_OK;
+}
+
+int sf_batch_solve(sf_batch* b, const float* in, float* out, void* stream)
+{
+    if (!b || !in || !out) return fail(SF_ERR_ARG);
+    int rc = batch_step(b, in, out, (cudaStream_t)stream);
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_batch_set_schedule(sf_batch* b, int cluster, int cpb_div)
+{
+    if (!b || cluster < 1 || cluster > BATCH_MAX_CLUSTER || (cluster & (cluster - 1)) || cpb_div < 1 || cpb_div > 4)
+        return fail(SF_ERR_ARG);
+    if (batch_active_clusters(cluster, b->maxout) < 1) return fail(SF_ERR_ARG);
+    int rc = check_cuda(cudaDeviceSynchronize());
+    if (rc) return fail(rc);
+    b->cluster = cluster;
+    b->cpb_div = cpb_div;
+    batch_drop_graph(b);
+    rc = batch_fill(b);
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_batch_get_schedule(const sf_batch* b, int* cluster, int* cpb_div)
+{
+    if (!b) return fail(SF_ERR_ARG);
+    if (cluster) *cluster = b->cluster;
+    if (cpb_div) *cpb_div = b->cpb_div;
+    return SF_OK;
+}
+
+int sf_batch_tune(sf_batch* b, const float* in, float* out, int steps, void* stream, float* best_ms)
+{
+    if (!b || !in || !out || steps < 1) return fail(SF_ERR_ARG);
+    for (sf_ctx* c : b->seq)
+        if (c->frames != 0) return fail(SF_ERR_STATE);
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(b->key);
+        if (it != g_tune_cache.end()) {
+            if (best_ms) *best_ms = it->second.ms;
+            return sf_batch_set_schedule(b, it->second.cluster, it->second.cpb_div);
+        }
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(check_cuda(cudaErrorUnknown));
+    BatchSchedule best{b->cluster, b->cpb_div, -1.f};
+    int rc = SF_OK;
+    for (int cl = 2; cl <= BATCH_MAX_CLUSTER && !rc; cl *= 2) {
+        if (batch_active_clusters(cl, b->maxout) < 1) continue;
+        for (int div = 1; div <= 2 && !rc; ++div) {
+            rc = sf_batch_set_schedule(b, cl, div);
+            if (!rc) rc = batch_zero_frames(b);
+            if (!rc) rc = batch_step(b, in, out, st); // warm-up
+            if (!rc) rc = check_cuda(cudaEventRecord(e0, st));
+            for (int k = 0; k < steps && !rc; ++k) rc = batch_step(b, in, out, st);
+            if (!rc) rc = check_cuda(cudaEventRecord(e1, st));
+            if (!rc) rc = check_cuda(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            if (!rc) rc = check_cuda(cudaEventElapsedTime(&ms, e0, e1));
+            ms /= steps;
+            if (!rc && (best.ms < 0.f || ms < best.ms)) best = BatchSchedule{cl, div, ms};
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return fail(rc);
+    rc = sf_batch_set_schedule(b, best.cluster, best.cpb_div);
+    if (!rc) rc = batch_zero_frames(b);
+    if (rc) return fail(rc);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[b->key] = best;
+    }
+    if (best_ms) *best_ms = best.ms;
+    return SF_OK;
+}
+
+sf_ctx* sf_batch_sequence(sf_batch* b, int i)
+{
+    if (!b || i < 0 || i >= b->n) {
+        fail(SF_ERR_ARG);
+        return nullptr;
+    }
+    return b->seq[i];
+}
+
+int sf_batch_reset(sf_batch* b)
+{
+    if (!b) return fail(SF_ERR_ARG);
+    int rc = batch_zero_frames(b);
+    for (sf_ctx* c : b->seq)
+        if (!rc) rc = check_cuda(cudaMemset(c->status, 0, 4 * sizeof(int)));
+    if (!rc) rc = check_cuda(cudaDeviceSynchronize());
+    return rc ? fail(rc) : SF_OK;
+}
+
+void sf_batch_destroy(sf_batch* b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    batch_free(b);
 }
 
 } // extern "C"

@@ -37,6 +37,7 @@ constexpr int MAX_PART = 16384;            // partial-sum slots per reduction
 // device status bits
 constexpr int DEV_TIMEOUT = 1;
 constexpr int DEV_NUMERIC = 2;
+constexpr int DEV_NOARGS = 4;  // a launch found no input or output buffer
 
 struct LevelGeom {
     int w, h;     // level image size
@@ -276,8 +277,7 @@ __device__ __forceinline__ void grid_cell(int x, int y, int s, int nx, int ny, i
 
 // Fields of a pixel from the four nodes of its cell, F = base + delta (+ t x);
 // delta and x may be null.
-__device__ __forceinline__ void pixel_fields(const float* __restrict__ base, const float* __restrict__ delta,
-                                             const float* __restrict__ x, float t, int G, int n00, int nx, float a,
+__device__ __forceinline__ void pixel_fields(const float* base, const float* delta, const float* x, float t, int G, int n00, int nx, float a,
                                              float b, float f[6])
 {
     const int nd[4] = {n00, n00 + 1, n00 + nx, n00 + nx + 1};
@@ -287,9 +287,9 @@ __device__ __forceinline__ void pixel_fields(const float* __restrict__ base, con
         float acc = 0.f;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            float T = __ldg(base + c * G + nd[k]);
-            if (delta) T += __ldg(delta + c * G + nd[k]);
-            if (x) T = fmaf(t, __ldg(x + c * G + nd[k]), T);
+            float T = base[c * G + nd[k]];
+            if (delta) T += delta[c * G + nd[k]];
+            if (x) T = fmaf(t, x[c * G + nd[k]], T);
             acc = fmaf(al[k], T, acc);
         }
         f[c] = acc;

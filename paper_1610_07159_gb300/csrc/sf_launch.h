@@ -66,4 +66,47 @@ cudaError_t launch_pcg(const LevelGeom& g, const PcgPlan& plan, const float* nod
                        const float* minv, float* x, float* z, float* p0, float* p1, float2* part,
                        unsigned long long* bar, int* status, int iters, int interleaved_out, cudaStream_t st);
 
+// sf_batch.cu: the frame solve of many independent sequences in one launch,
+// one thread-block cluster per sequence. Descriptors live in device memory
+// and are read-only during a launch (the per-frame input and output pointers
+// are set by launch_batch_args before it).
+struct BLevel {
+    LevelGeom g;
+    DevParams P;
+    const void* tex;   // FP32 texels [4][h][w]
+    uint8_t* W;        // [gn][h][w] outlier masks
+    float* H;          // halfway image [h][w]
+    float *base, *delta, *x, *wf, *prev_delta, *prev_total; // [6][G] (wf: [G])
+    float *node, *rhs, *minv;                               // [105][G], [6][G], [6][G]
+    float *r, *z, *p0, *p1, *q;                             // PCG vectors [6][G]
+    float* cell;       // [234][ncells]
+    StepCtrl* ctrl;    // [SF_MAX_GN]
+    int gn, pcg;       // Gauss-Newton steps and PCG iterations of the level
+    int cpb, gx;       // cells per assembly group; groups per cell row
+    int n_groups;      // gx * (ny - 1)
+    int pad;
+};
+
+struct BSeq {
+    int L, w0, h0;
+    int temporal_mode, wfeat_mode, max_backtracks, use_init;
+    int pad;
+    const float* in;   // 4 planes of w0 * h0 (set per frame)
+    float* out;        // 6 x G0 (set per frame)
+    int* frames;       // frames solved so far; the launch increments it
+    const float* init_buf;
+    int* status;       // the sequence's status word
+    float2* part;      // [2][8][16] cluster partial sums
+    size_t in_off, out_off; // offsets of this sequence in the packed buffers
+    BLevel lv[SF_MAX_LEVELS];
+};
+
+constexpr int BATCH_MAX_CLUSTER = 16;
+int batch_maxout(int s);
+void batch_prepare(int cluster, int maxout);
+int batch_active_clusters(int cluster, int maxout);
+cudaError_t launch_batch_frame(const BSeq* seqs, const int* order, int nseq, int cluster, int maxout, cudaStream_t st);
+void launch_batch_args(BSeq* seqs, int nseq, const float* in, float* out, cudaStream_t st);
+int batch_cells_per_group(int s, int div);
+
 } // namespace sfk

@@ -4,24 +4,13 @@
 // (Section 5.3), the halfway image and the feature weight w_i of the
 // smoothness term (Section 4.3), and the per-level output.
 #include "sf_launch.h"
+#include "sf_stages.cuh"
 
 namespace sfk {
 
 namespace {
 
 constexpr int T1D = 256;
-
-__device__ __forceinline__ float grid_bilerp(const float* __restrict__ F, int nx, int ny, float u, float v)
-{
-    u = fminf(fmaxf(u, 0.f), (float)(nx - 1));
-    v = fminf(fmaxf(v, 0.f), (float)(ny - 1));
-    int i0 = min((int)floorf(u), nx - 2), j0 = min((int)floorf(v), ny - 2);
-    float a = u - (float)i0, b = v - (float)j0;
-    const float* r = F + j0 * nx + i0;
-    float top = (1.f - a) * r[0] + a * r[1];
-    float bot = (1.f - a) * r[nx] + a * r[nx + 1];
-    return (1.f - b) * top + b * bot;
-}
 
 // Level 0 texels: intensity and central-difference gradients, edge clamped.
 template <class TT>
@@ -31,26 +20,8 @@ __global__ void k_tex0(const DevArgs* __restrict__ args, const float* in0, const
     const int c = blockIdx.y;
     const float* I = args ? args->in[c] : (c == 0 ? in0 : c == 1 ? in1 : c == 2 ? in2 : in3);
     const int n = w * h;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const int y = p / w, x = p - y * w;
-        const int xm = max(x - 1, 0), xp = min(x + 1, w - 1), ym = max(y - 1, 0), yp = min(y + 1, h - 1);
-        const float v = __ldg(I + p);
-        const float gx = 0.5f * (__ldg(I + y * w + xp) - __ldg(I + y * w + xm));
-        const float gy = 0.5f * (__ldg(I + yp * w + x) - __ldg(I + ym * w + x));
-        tex[(size_t)c * n + p] = TT::pack(v, gx, gy);
-    }
-}
-
-template <class TT>
-__device__ __forceinline__ float box2(const typename TT::T* __restrict__ P, int wp, int hp, int x, int y)
-{
-    const int x0 = min(2 * x, wp - 1), x1 = min(2 * x + 1, wp - 1);
-    const int y0 = min(2 * y, hp - 1), y1 = min(2 * y + 1, hp - 1);
-    float acc = TT::ld(&P[y0 * wp + x0]).x;
-    acc += TT::ld(&P[y0 * wp + x1]).x;
-    acc += TT::ld(&P[y1 * wp + x0]).x;
-    acc += TT::ld(&P[y1 * wp + x1]).x;
-    return 0.25f * acc;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+        tex[(size_t)c * n + p] = tex0_texel<TT>(I, w, h, p);
 }
 
 // Next mip level: 2x2 box of the finer intensity (edge clamped), gradients
@@ -62,14 +33,8 @@ __global__ void k_texdown(const typename TT::T* __restrict__ texp, int wp, int h
     const int c = blockIdx.y;
     const typename TT::T* P = texp + (size_t)c * wp * hp;
     const int n = w * h;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const int y = p / w, x = p - y * w;
-        const int xm = max(x - 1, 0), xp = min(x + 1, w - 1), ym = max(y - 1, 0), yp = min(y + 1, h - 1);
-        const float v = box2<TT>(P, wp, hp, x, y);
-        const float gx = 0.5f * (box2<TT>(P, wp, hp, xp, y) - box2<TT>(P, wp, hp, xm, y));
-        const float gy = 0.5f * (box2<TT>(P, wp, hp, x, yp) - box2<TT>(P, wp, hp, x, ym));
-        tex[(size_t)c * n + p] = TT::pack(v, gx, gy);
-    }
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+        tex[(size_t)c * n + p] = texdown_texel<TT>(P, wp, hp, w, h, p);
 }
 
 // base = 2 Up(T_coarse) (node (i, j) reads coarse grid coordinates (i/2, j/2)),
@@ -82,44 +47,10 @@ __global__ void k_level_init(LevelGeom g, int have_coarse, int nxc, int nyc, con
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.G) return;
-    const int i = n % g.nx, j = n / g.nx;
-    const int Gc = nxc * nyc;
     const int frame = args ? args->frame : frame_direct;
     const int use_init = args ? args->use_init : use_init_direct;
-    for (int c = 0; c < 6; ++c) {
-        float b = 0.f;
-        if (have_coarse) {
-            // T_coarse = base_c + delta_c, interpolated on the fly
-            const float u = fminf(fmaxf(0.5f * i, 0.f), (float)(nxc - 1));
-            const float v = fminf(fmaxf(0.5f * j, 0.f), (float)(nyc - 1));
-            const int i0 = min((int)floorf(u), nxc - 2), j0 = min((int)floorf(v), nyc - 2);
-            const float a = u - (float)i0, bb = v - (float)j0;
-            const int m = j0 * nxc + i0;
-            // delta_c == nullptr: base_c already holds the coarse totals
-            const float t00 = base_c[c * Gc + m] + (delta_c ? delta_c[c * Gc + m] : 0.f);
-            const float t10 = base_c[c * Gc + m + 1] + (delta_c ? delta_c[c * Gc + m + 1] : 0.f);
-            const float t01 = base_c[c * Gc + m + nxc] + (delta_c ? delta_c[c * Gc + m + nxc] : 0.f);
-            const float t11 = base_c[c * Gc + m + nxc + 1] + (delta_c ? delta_c[c * Gc + m + nxc + 1] : 0.f);
-            const float top = (1.f - a) * t00 + a * t10, bot = (1.f - a) * t01 + a * t11;
-            b = 2.f * ((1.f - bb) * top + bb * bot);
-        }
-        base[c * g.G + n] = b;
-    }
-    for (int c = 0; c < 6; ++c) {
-        float d = 0.f;
-        if (!have_coarse && use_init) {
-            d = init_buf[c * g.G + n];
-        } else if (frame > 0) {
-            if (temporal_mode == SF_TEMPORAL_COPY) {
-                d = prev_delta[c * g.G + n];
-            } else if (temporal_mode == SF_TEMPORAL_PROPAGATE) {
-                const float X = (float)(i * g.s) - 2.f * prev_total[2 * g.G + n];
-                const float Y = (float)(j * g.s) - 2.f * prev_total[3 * g.G + n];
-                d = grid_bilerp(prev_delta + c * g.G, g.nx, g.ny, X / (float)g.s, Y / (float)g.s);
-            }
-        }
-        delta[c * g.G + n] = d;
-    }
+    level_init_node(g, have_coarse, nxc, nyc, base_c, delta_c, base, delta, prev_delta, prev_total, init_buf,
+                    temporal_mode, frame, use_init, n);
 }
 
 // Halfway image H(x) = mean of the four warped intensities.
@@ -128,22 +59,8 @@ __global__ void k_halfway(LevelGeom g, const typename TT::T* __restrict__ tex, c
                           const float* __restrict__ delta, float* __restrict__ H)
 {
     const int n = g.w * g.h;
-    const size_t plane = (size_t)n;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const int y = p / g.w, x = p - y * g.w;
-        int i0, j0;
-        float a, b;
-        grid_cell(x, y, g.s, g.nx, g.ny, i0, j0, a, b);
-        float f[6];
-        pixel_fields(base, delta, nullptr, 0.f, g.G, j0 * g.nx + i0, g.nx, a, b, f);
-        float acc = 0.f;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float ox = sgn(c, 0) * f[0] + sgn(c, 1) * f[2] + sgn(c, 2) * f[4];
-            const float oy = sgn(c, 0) * f[1] + sgn(c, 1) * f[3] + sgn(c, 2) * f[5];
-            acc += tap1<TT>(tex + c * plane, g.w, g.h, x, y, ox, oy);
-        }
-        H[p] = 0.25f * acc;
+        H[p] = halfway_pixel<TT>(g, tex, base, delta, p);
     }
 }
 
@@ -153,21 +70,7 @@ __global__ void k_wfeat(LevelGeom g, const float* __restrict__ H, DevParams P, f
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.G) return;
-    const int i = n % g.nx, j = n / g.nx;
-    float a = 0.f, b = 0.f, c = 0.f;
-    for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-            const int qx = min(max(i * g.s + dx, 0), g.w - 1), qy = min(max(j * g.s + dy, 0), g.h - 1);
-            const int xm = max(qx - 1, 0), xp = min(qx + 1, g.w - 1), ym = max(qy - 1, 0), yp = min(qy + 1, g.h - 1);
-            const float hx = 0.5f * (H[qy * g.w + xp] - H[qy * g.w + xm]);
-            const float hy = 0.5f * (H[yp * g.w + qx] - H[ym * g.w + qx]);
-            a = fmaf(hx, hx, a);
-            b = fmaf(hx, hy, b);
-            c = fmaf(hy, hy, c);
-        }
-    float lmin = 0.5f * (a + c) - sqrtf(0.25f * (a - c) * (a - c) + b * b);
-    lmin = fmaxf(lmin, 0.f);
-    wf[n] = 1.f + P.wfeat_gain * expf(-lmin / P.wfeat_tau);
+    wf[n] = wfeat_node(g, H, P, n);
 }
 
 __global__ void k_fill(float* p, float v, size_t n)

@@ -24,6 +24,7 @@
 #include <algorithm>
 
 #include "sf_launch.h"
+#include "sf_stages.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -52,46 +53,6 @@ struct GridSync {
         return grid_barrier(ctr, status, target);
     }
 };
-
-// Stencil slot s of node (i, j): the block (owner node, block index) and the
-// node whose p it multiplies. Slots: 0 self, 1 E, 2 S, 3 SE, 4 SW (stored at
-// the node), 5 W, 6 N, 7 NW, 8 NE (stored at the neighbour, which is also the
-// p node). Returns false where the neighbour is off the grid.
-__device__ __forceinline__ bool stencil_slot(int s, int i, int j, int nx, int ny, int n, int& owner, int& blk, int& pn)
-{
-    // packed per slot: di+1, dj+1 of the p node (2 bits each), block index (3 bits), stored-at-neighbour flag
-    constexpr unsigned long long T = 0ull | (0x05ull << 0)   // 0: di 0 dj 0 blk 0 own   -> (1,1)
-                                    | ((0x06ull | (1ull << 4)) << 8)  // 1: di 1 dj 0 blk 1
-                                    | ((0x09ull | (2ull << 4)) << 16) // 2: di 0 dj 1 blk 2
-                                    | ((0x0Aull | (3ull << 4)) << 24) // 3: di 1 dj 1 blk 3
-                                    | ((0x08ull | (4ull << 4)) << 32) // 4: di -1 dj 1 blk 4
-                                    | ((0x04ull | (1ull << 4) | 0x80ull) << 40) // 5: di -1 dj 0 blk 1 nb
-                                    | ((0x01ull | (2ull << 4) | 0x80ull) << 48) // 6: di 0 dj -1 blk 2 nb
-                                    | ((0x00ull | (3ull << 4) | 0x80ull) << 56); // 7: di -1 dj -1 blk 3 nb
-    unsigned e;
-    if (s < 8)
-        e = (unsigned)(T >> (8 * s)) & 0xffu;
-    else
-        e = 0x02u | (4u << 4) | 0x80u; // 8: di 1 dj -1 blk 4 nb
-    const int di = (int)(e & 3u) - 1, dj = (int)((e >> 2) & 3u) - 1;
-    blk = (int)((e >> 4) & 7u);
-    const int i2 = i + di, j2 = j + dj;
-    if (i2 < 0 || i2 >= nx || j2 < 0 || j2 >= ny) return false;
-    pn = n + dj * nx + di;
-    owner = (e & 0x80u) ? pn : n;
-    return true;
-}
-
-__device__ __forceinline__ float sel6(const float* v, int c)
-{
-    float r = v[0];
-    r = c == 1 ? v[1] : r;
-    r = c == 2 ? v[2] : r;
-    r = c == 3 ? v[3] : r;
-    r = c == 4 ? v[4] : r;
-    r = c == 5 ? v[5] : r;
-    return r;
-}
 
 template <class Sync>
 __device__ __forceinline__ ff allreduce(float v, ff* sh, float2* part, Sync& sy, unsigned long long* bar, int* status,

@@ -34,7 +34,8 @@ EXPORTED = (
     "sf_grid_dims", "sf_set_init", "sf_reset",
     "sf_get_stats", "sf_get_state", "sf_kernel_times", "sf_destroy", "sf_status_string", "sf_last_error", "sf_probe_pyramid",
     "sf_probe_feature_weights", "sf_probe_assemble", "sf_probe_pcg", "sf_probe_wmask", "sf_probe_energy",
-    "sf_pcg_static",
+    "sf_pcg_static", "sf_batch_create", "sf_batch_layout", "sf_batch_solve", "sf_batch_set_schedule",
+    "sf_batch_get_schedule", "sf_batch_tune", "sf_batch_sequence", "sf_batch_reset", "sf_batch_destroy",
 )
 STATIC_PCG_MAX_NODES = 4096
 
@@ -116,6 +117,18 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sf_probe_wmask.argtypes = [vp, i, i, fp, vp]
     L.sf_probe_energy.argtypes = [vp, i, fp, fp, fp, fp, fp, vp]
     L.sf_pcg_static.argtypes = [i, i, fp, fp, i, fp, vp]
+    sz = ctypes.POINTER(ctypes.c_size_t)
+    L.sf_batch_create.argtypes = [i, ip, ip, ip, i, ctypes.POINTER(Params), ctypes.POINTER(vp)]
+    L.sf_batch_layout.argtypes = [vp, sz, sz, sz, sz]
+    L.sf_batch_solve.argtypes = [vp, fp, fp, vp]
+    L.sf_batch_set_schedule.argtypes = [vp, i, i]
+    L.sf_batch_get_schedule.argtypes = [vp, ip, ip]
+    L.sf_batch_tune.argtypes = [vp, fp, fp, i, vp, ctypes.POINTER(ctypes.c_float)]
+    L.sf_batch_sequence.argtypes = [vp, i]
+    L.sf_batch_sequence.restype = vp
+    L.sf_batch_reset.argtypes = [vp]
+    L.sf_batch_destroy.argtypes = [vp]
+    L.sf_batch_destroy.restype = None
     _lib = L
     return L
 
@@ -172,18 +185,25 @@ def pcg_static(nx: int, ny: int, blocks: torch.Tensor, rhs: torch.Tensor, iters:
 class Solver:
     """One solver context (sf_create ... sf_destroy)."""
 
-    def __init__(self, width: int, height: int, grid_stride: int, levels: int, params: Params | None = None):
+    def __init__(self, width: int, height: int, grid_stride: int, levels: int, params: Params | None = None,
+                 _view_of: int | None = None):
         self.L = load()
         self.params = params if params is not None else preset()
         torch.cuda.init()
-        self.ctx = self.L.sf_create(int(width), int(height), int(grid_stride), int(levels), ctypes.byref(self.params))
+        self.owned = _view_of is None
+        if self.owned:
+            self.ctx = self.L.sf_create(int(width), int(height), int(grid_stride), int(levels),
+                                        ctypes.byref(self.params))
+        else:
+            self.ctx = _view_of
         if not self.ctx:
             raise SFError(f"sf_create: {status_string(self.L.sf_last_error())}")
         self.width, self.height, self.stride, self.levels = int(width), int(height), int(grid_stride), int(levels)
 
     def close(self) -> None:
         if getattr(self, "ctx", None):
-            self.L.sf_destroy(self.ctx)
+            if self.owned:
+                self.L.sf_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):
@@ -321,3 +341,94 @@ class Solver:
                                       _ptr(wfeat, torch.float32), _ptr(W, torch.uint8) if W is not None else None,
                                       _ptr(out), _stream()), "sf_probe_energy")
         return out
+
+
+class Batch:
+    """n independent sequences solved together (sf_batch_create ... sf_batch_destroy):
+    one launch per frame step, one thread-block cluster per sequence."""
+
+    def __init__(self, sizes, levels, grid_stride: int, params: Params | None = None):
+        self.L = load()
+        self.params = params if params is not None else preset()
+        torch.cuda.init()
+        self.sizes = [(int(w), int(h)) for w, h in sizes]
+        self.levels = [int(l) for l in levels]
+        self.n = len(self.sizes)
+        self.stride = int(grid_stride)
+        W = (ctypes.c_int * self.n)(*[w for w, _ in self.sizes])
+        H = (ctypes.c_int * self.n)(*[h for _, h in self.sizes])
+        Lv = (ctypes.c_int * self.n)(*self.levels)
+        out = ctypes.c_void_p()
+        _check(self.L.sf_batch_create(self.n, W, H, Lv, self.stride, ctypes.byref(self.params), ctypes.byref(out)),
+               "sf_batch_create")
+        self.b = out.value
+        ino = (ctypes.c_size_t * self.n)()
+        outo = (ctypes.c_size_t * self.n)()
+        it, ot = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(self.L.sf_batch_layout(self.b, ino, outo, ctypes.byref(it), ctypes.byref(ot)), "sf_batch_layout")
+        self.in_offsets, self.out_offsets = list(ino), list(outo)
+        self.in_total, self.out_total = it.value, ot.value
+        self._views = {}
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            self._views.clear()
+            self.L.sf_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pack(self, quads) -> torch.Tensor:
+        """Packed device input from n arrays/tensors of shape [4, h_i, w_i]."""
+        buf = torch.empty(self.in_total, device="cuda", dtype=torch.float32)
+        for i, q in enumerate(quads):
+            t = torch.as_tensor(q, dtype=torch.float32).reshape(-1)
+            buf[self.in_offsets[i]:self.in_offsets[i] + t.numel()].copy_(t, non_blocking=True)
+        return buf
+
+    def unpack(self, out: torch.Tensor) -> list:
+        """Per-sequence views [6, ny_i, nx_i] of a packed output."""
+        res = []
+        for i, (w, h) in enumerate(self.sizes):
+            nx, ny = -(-w // self.stride), -(-h // self.stride)
+            o = self.out_offsets[i]
+            res.append(out[o:o + 6 * nx * ny].view(6, ny, nx))
+        return res
+
+    def solve(self, packed_in: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.out_total, device="cuda", dtype=torch.float32)
+        _check(self.L.sf_batch_solve(self.b, _ptr(packed_in, torch.float32), _ptr(out, torch.float32), _stream()),
+               "sf_batch_solve")
+        return out
+
+    def set_schedule(self, cluster: int, cpb_div: int = 1) -> None:
+        _check(self.L.sf_batch_set_schedule(self.b, int(cluster), int(cpb_div)), "sf_batch_set_schedule")
+
+    def schedule(self) -> tuple[int, int]:
+        c, d = ctypes.c_int(), ctypes.c_int()
+        _check(self.L.sf_batch_get_schedule(self.b, ctypes.byref(c), ctypes.byref(d)), "sf_batch_get_schedule")
+        return c.value, d.value
+
+    def tune(self, packed_in: torch.Tensor, out: torch.Tensor, steps: int = 2) -> float:
+        ms = ctypes.c_float()
+        _check(self.L.sf_batch_tune(self.b, _ptr(packed_in, torch.float32), _ptr(out, torch.float32), int(steps),
+                                    _stream(), ctypes.byref(ms)), "sf_batch_tune")
+        return ms.value
+
+    def reset(self) -> None:
+        _check(self.L.sf_batch_reset(self.b), "sf_batch_reset")
+
+    def sequence(self, i: int) -> Solver:
+        """A non-owning Solver view of sequence i (stats, state, wmasks)."""
+        if i not in self._views:
+            ctx = self.L.sf_batch_sequence(self.b, int(i))
+            if not ctx:
+                raise SFError("sf_batch_sequence: bad index")
+            w, h = self.sizes[i]
+            self._views[i] = Solver(w, h, self.stride, self.levels[i], self.params, _view_of=ctx)
+        return self._views[i]
