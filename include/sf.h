@@ -247,6 +247,16 @@ SF_API int sf_probe_wmask(sf_ctx* ctx, int level, int step, unsigned char* W, vo
 SF_API int sf_probe_energy(sf_ctx* ctx, int level, const float* base, const float* delta, const float* wfeat,
                     const unsigned char* W, double* out6, void* stream);
 
+/* C[s][M][N] = A[M, K] * B[N, K]^T over split s of K (K split into `splits`
+ * contiguous ranges of 64-wide chunks; the splits' partial products are
+ * written separately), on the tensor cores: A and B device BF16, row-major
+ * with K contiguous, K a multiple of 64, N a multiple of 16, BN the N tile
+ * (16..256, a multiple of 16), C device FP32. The primitive of the
+ * warm-start network's convolutions; waits for the stream. SF_ERR_TIMEOUT
+ * if a tensor-core wait timed out. */
+SF_API int sf_probe_gemm_bf16(const void* A, const void* B, int M, int N, int K, int BN, int splits, float* C,
+                              void* stream);
+
 /* ---- batched solve of many sequences ----------------------------------
  * The paper solves one stereo sequence at a time (Algorithm 1). These calls
  * solve n independent sequences of any sizes together: each frame step runs

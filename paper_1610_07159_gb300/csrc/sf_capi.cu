@@ -1216,4 +1216,36 @@ void sf_batch_destroy(sf_batch* b)
     batch_free(b);
 }
 
+int sf_probe_gemm_bf16(const void* A, const void* B, int M, int N, int K, int BN, int splits, float* C, void* stream)
+{
+    if (!C || splits < 1 || BN < 16) return fail(SF_ERR_ARG);
+    GemmArgs a{};
+    a.A = static_cast<const __nv_bfloat16*>(A);
+    a.B = static_cast<const __nv_bfloat16*>(B);
+    a.lda = K;
+    a.ldb = K;
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.BN = BN;
+    const int nkc = K / 64;
+    a.kc_per_split = (nkc + splits - 1) / splits;
+    a.n_store = N;
+    a.ldc = N;
+    a.split_stride = (long long)M * N;
+    a.C = C;
+    int* err = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return fail(check_cuda(cudaErrorMemoryAllocation));
+    cudaMemset(err, 0, sizeof(int));
+    a.err = err;
+    int rc = gemm_check(a);
+    if (!rc) rc = check_cuda(launch_gemm(a, GEMM_F32, splits, (cudaStream_t)stream));
+    int h = 0;
+    if (!rc) rc = check_cuda(cudaStreamSynchronize((cudaStream_t)stream));
+    if (!rc) rc = check_cuda(cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost));
+    cudaFree(err);
+    if (!rc && h) rc = SF_ERR_TIMEOUT;
+    return rc ? fail(rc) : SF_OK;
+}
+
 } // extern "C"

@@ -1,0 +1,189 @@
+// sf_gemm.cu -- BF16 x BF16 -> FP32 matrix product on the fifth-generation
+// tensor cores (tcgen05), the one contraction of the warm-start network
+// (every convolution of its forward and backward pass is lowered to it).
+//
+//   C[M, N] = A[M, K] * B[N, K]^T      (both operands K-major, K % 64 == 0)
+//
+// One CTA of four warps computes a 128 x BN tile (BN <= 256, a multiple of
+// 16) over a range of K: per 64-wide K chunk the warps stage the A and B
+// tiles in shared memory in the tensor core's K-major layout without
+// swizzling (8-row x 16-byte core matrices, contiguous along K), one thread
+// issues four 128 x BN x 16 MMAs into a tensor-memory accumulator and commits
+// them to an mbarrier, and the next chunk is staged once the barrier reports
+// the MMAs done. The epilogue reads the accumulator lane by lane
+// (tcgen05.ld, warp w owns rows 32w .. 32w + 31) and applies one of the
+// epilogues below. Split-K (grid.y) writes FP32 partial products that a
+// fixed-order reduction sums, so results do not depend on scheduling.
+//
+// Every mbarrier wait gives up after about one second; the CTA then waits
+// once more for its MMAs in flight, frees its tensor memory, raises the
+// error word and returns.
+#include <cuda_bf16.h>
+
+#include "sf_launch.h"
+#include "sf_tc.cuh"
+
+namespace sfk {
+
+namespace {
+
+constexpr int GT = 128;  // threads per CTA
+constexpr int BM = 128;  // rows per tile
+constexpr int BK = 64;   // K per chunk (128 bytes of BF16)
+constexpr uint32_t LBO = 128;            // next core matrix along K
+constexpr uint32_t SBO = 8 * LBO;        // next 8-row group
+
+// byte offset of (row r, 16-byte vector v) of a tile in the K-major layout
+__device__ __forceinline__ uint32_t tile_off(int r, int v) { return (uint32_t)((r >> 3) * SBO + v * LBO + (r & 7) * 16); }
+
+// Stages rows [r0, r0 + rows) x K chunk kc of a row-major BF16 matrix; rows
+// at or past nrows are zero.
+__device__ __forceinline__ void stage(uint8_t* tile, const __nv_bfloat16* src, int ld, int r0, int rows, int nrows,
+                                      int kc)
+{
+    for (int i = threadIdx.x; i < rows * 8; i += GT) {
+        const int r = i >> 3, v = i & 7;
+        uint4 val = make_uint4(0u, 0u, 0u, 0u);
+        if (r0 + r < nrows) val = *reinterpret_cast<const uint4*>(src + (size_t)(r0 + r) * ld + kc * BK + v * 8);
+        *reinterpret_cast<uint4*>(tile + tile_off(r, v)) = val;
+    }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(GT, 1) k_gemm(GemmArgs a)
+{
+    extern __shared__ uint8_t dsm[];
+    // A tile (16 KiB) then B tile (up to 32 KiB), 128-byte aligned
+    uint8_t* sA = dsm + ((128u - (tc::smem_u32(dsm) & 127u)) & 127u);
+    uint8_t* sB = sA + BM * BK * 2;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.z * a.BN, split = blockIdx.y;
+    const int bn = min(a.BN, a.N - n0); // a multiple of 16
+    const uint32_t ncols = bn <= 32 ? 32u : bn <= 64 ? 64u : bn <= 128 ? 128u : 256u;
+    const uint32_t mbar_s = tc::smem_u32(&mbar);
+    if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_sh), ncols);
+    if (tid == 0) tc::mbar_init(mbar_s, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = tmem_sh;
+    const uint32_t idesc = tc::idesc_bf16_f32(BM, bn);
+    const int nkc = a.K / BK;
+    const int kc0 = split * a.kc_per_split, kc1 = min(nkc, kc0 + a.kc_per_split);
+    const uint32_t sa = tc::smem_u32(sA), sb = tc::smem_u32(sB);
+
+    uint32_t parity = 0;
+    bool pending = false, failed = false, issued = false;
+    auto wait_pending = [&]() -> bool {
+        const bool w = tc::mbar_wait(mbar_s, parity);
+        const bool any_fail = __syncthreads_or(!w) != 0;
+        if (!any_fail) {
+            parity ^= 1u;
+            pending = false;
+        }
+        return !any_fail;
+    };
+    for (int kc = kc0; kc < kc1; ++kc) {
+        if (pending && !wait_pending()) {
+            failed = true;
+            break;
+        }
+        tc::fence_after_sync();
+        stage(sA, a.A, a.lda, m0, BM, a.M, kc);
+        stage(sB, a.B, a.ldb, n0, bn, a.N, kc);
+        tc::fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+#pragma unroll
+            for (int j = 0; j < BK / 16; ++j)
+                tc::mma_bf16(tbase, tc::smem_desc(sa + 256u * j, LBO, SBO), tc::smem_desc(sb + 256u * j, LBO, SBO),
+                             idesc, (kc > kc0 || j > 0) ? 1u : 0u);
+            tc::mma_commit(mbar_s);
+        }
+        pending = true;
+        issued = true;
+    }
+    if (!failed && pending && !wait_pending()) failed = true;
+    if (failed && pending) wait_pending(); // the MMAs still in flight, once more
+    tc::fence_after_sync();
+
+    if (!failed) {
+        const int m = m0 + warp * 32 + lane;
+        const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
+        for (int c = 0; c < bn; c += 8) {
+            float v[8];
+            if (issued) {
+                tc::tmem_ld8(trow + (uint32_t)c, v);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) v[i] = 0.f;
+            }
+            if (m >= a.M) continue;
+            const int n = n0 + c;
+            if (EPI == GEMM_F32) {
+                float* dst = a.C + (size_t)split * a.split_stride + (size_t)m * a.ldc + n;
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (n + i < a.n_store) dst[i] = v[i];
+            } else if (EPI == GEMM_BIAS_RELU_BF16) {
+                __nv_bfloat16* dst = a.Cb + (size_t)m * a.ldc + n;
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (n + i < a.n_store) dst[i] = __float2bfloat16_rn(fmaxf(v[i] + a.bias[n + i], 0.f));
+            } else { // GEMM_BIAS_NCHW_F32: image-major output [m / hw][n][m % hw]
+                const int img = m / a.out_hw, px = m - img * a.out_hw;
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (n + i < a.n_store)
+                        a.C[((size_t)img * a.n_store + n + i) * a.out_hw + px] = v[i] + a.bias[n + i];
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(a.err, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, ncols);
+}
+
+} // namespace
+
+int gemm_check(const GemmArgs& a)
+{
+    if (!a.A || !a.B || !a.err || a.M < 1 || a.N < 16 || a.N % 16 || a.K < BK || a.K % BK || a.lda < a.K ||
+        a.ldb < a.K || a.lda % 8 || a.ldb % 8 || a.BN < 16 || a.BN > 256 || a.BN % 16 || a.kc_per_split < 1 ||
+        a.n_store < 1)
+        return SF_ERR_ARG;
+    if (((uintptr_t)a.A | (uintptr_t)a.B) & 15) return SF_ERR_ARG;
+    return SF_OK;
+}
+
+constexpr int GEMM_SMEM = BM * BK * 2 + 256 * BK * 2 + 128;
+
+template <int EPI>
+void launch_epi(const GemmArgs& a, dim3 grid, cudaStream_t st)
+{
+    static bool attr = false; // set once per process (idempotent)
+    if (!attr) {
+        cudaFuncSetAttribute(k_gemm<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+        attr = true;
+    }
+    k_gemm<EPI><<<grid, GT, GEMM_SMEM, st>>>(a);
+}
+
+cudaError_t launch_gemm(const GemmArgs& a, int epi, int splits, cudaStream_t st)
+{
+    dim3 grid((a.M + BM - 1) / BM, splits, (a.N + a.BN - 1) / a.BN);
+    if (epi == GEMM_F32)
+        launch_epi<GEMM_F32>(a, grid, st);
+    else if (epi == GEMM_BIAS_RELU_BF16)
+        launch_epi<GEMM_BIAS_RELU_BF16>(a, grid, st);
+    else
+        launch_epi<GEMM_BIAS_NCHW_F32>(a, grid, st);
+    return cudaGetLastError();
+}
+
+} // namespace sfk

@@ -1,6 +1,8 @@
 // sf_launch.h -- host-side launchers of the solver kernels (internal).
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "sf_common.cuh"
 
 namespace sfk {
@@ -108,5 +110,28 @@ int batch_active_clusters(int cluster, int maxout);
 cudaError_t launch_batch_frame(const BSeq* seqs, const int* order, int nseq, int cluster, int maxout, cudaStream_t st);
 void launch_batch_args(BSeq* seqs, int nseq, const float* in, float* out, cudaStream_t st);
 int batch_cells_per_group(int s, int div);
+
+// sf_gemm.cu: C = A * B^T on the tensor cores (tcgen05), BF16 operands
+// (row-major, K contiguous, K % 64 == 0, 16-byte aligned rows), FP32
+// accumulation; grid (M tiles of 128, K splits, N tiles of BN).
+enum { GEMM_F32 = 0, GEMM_BIAS_RELU_BF16 = 1, GEMM_BIAS_NCHW_F32 = 2 };
+struct GemmArgs {
+    const __nv_bfloat16* A;
+    const __nv_bfloat16* B;
+    int lda, ldb;        // row strides (elements)
+    int M, N, K;         // N % 16 == 0
+    int BN;              // N tile (16 .. 256, % 16)
+    int kc_per_split;    // 64-wide K chunks per split
+    int n_store;         // columns written (<= N)
+    int ldc;             // row stride of C / Cb
+    int out_hw;          // GEMM_BIAS_NCHW_F32: pixels per image
+    long long split_stride; // GEMM_F32: elements between split partials
+    float* C;            // GEMM_F32, GEMM_BIAS_NCHW_F32
+    __nv_bfloat16* Cb;   // GEMM_BIAS_RELU_BF16
+    const float* bias;
+    int* err;            // set to 1 if an mbarrier wait timed out
+};
+int gemm_check(const GemmArgs& a);
+cudaError_t launch_gemm(const GemmArgs& a, int epi, int splits, cudaStream_t st);
 
 } // namespace sfk

@@ -36,6 +36,7 @@ EXPORTED = (
     "sf_probe_feature_weights", "sf_probe_assemble", "sf_probe_pcg", "sf_probe_wmask", "sf_probe_energy",
     "sf_pcg_static", "sf_batch_create", "sf_batch_layout", "sf_batch_solve", "sf_batch_set_schedule",
     "sf_batch_get_schedule", "sf_batch_tune", "sf_batch_sequence", "sf_batch_reset", "sf_batch_destroy",
+    "sf_probe_gemm_bf16",
 )
 STATIC_PCG_MAX_NODES = 4096
 
@@ -129,6 +130,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sf_batch_reset.argtypes = [vp]
     L.sf_batch_destroy.argtypes = [vp]
     L.sf_batch_destroy.restype = None
+    L.sf_probe_gemm_bf16.argtypes = [vp, vp, i, i, i, i, i, fp, vp]
     _lib = L
     return L
 
@@ -168,6 +170,19 @@ def _ptr(t: torch.Tensor | None, dtype: torch.dtype | None = None) -> int | None
 
 def _stream() -> int:
     return torch.cuda.current_stream().cuda_stream
+
+
+def gemm_bf16(A: torch.Tensor, B: torch.Tensor, BN: int = 256, splits: int = 1) -> torch.Tensor:
+    """[splits, M, N] FP32 partial products of A[M, K] @ B[N, K]^T (BF16 CUDA
+    tensors, K % 64 == 0, N % 16 == 0) on the tensor cores."""
+    L = load()
+    assert A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16 and A.is_contiguous() and B.is_contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((splits, M, N), device="cuda", dtype=torch.float32)
+    _check(L.sf_probe_gemm_bf16(A.data_ptr(), B.data_ptr(), M, N, K, int(BN), int(splits), _ptr(C), _stream()),
+           "sf_probe_gemm_bf16")
+    return C
 
 
 def pcg_static(nx: int, ny: int, blocks: torch.Tensor, rhs: torch.Tensor, iters: int,
