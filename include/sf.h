@@ -257,6 +257,53 @@ SF_API int sf_probe_energy(sf_ctx* ctx, int level, const float* base, const floa
 SF_API int sf_probe_gemm_bf16(const void* A, const void* B, int M, int N, int K, int BN, int splits, float* C,
                               void* stream);
 
+/* ---- learned warm start --------------------------------------------------
+ * The paper starts the first frame from zero flows and names a smarter
+ * first-frame initialisation as future work (Section 7). The warm start is a
+ * six-layer convolutional network (3x3 kernels, zero padding 1, ReLU after
+ * all but the last layer: 4->32 stride 2, 32->64 stride 2, 64->64 stride 2,
+ * 64->64, 64->32, 32->6) that maps the four coarsest-level images of a
+ * quadruple (60 x 80, the coarsest level of 640 x 480 with four levels), less
+ * 1/2, to the coarsest level's six delta fields on its 8 x 10 warp grid; the
+ * prediction replaces the zero start of the coarsest level. Training and
+ * inference run on the GPU: every convolution is a BF16 tensor-core GEMM
+ * with FP32 accumulation; biases, master weights, gradients and the Adam
+ * moments are FP32.
+ *
+ * Parameters travel as one FP32 vector in the standard layout: for each layer
+ * in order its weights [out][in][3][3], then its biases [out]
+ * (sf_net_param_count() floats). Images: device FP32 [B][4][60][80];
+ * outputs and targets: device FP32 [B][6][8][10]. */
+typedef struct sf_net sf_net;
+SF_API int sf_net_param_count(void);
+/* Allocates a network for batches of up to max_batch quadruples. */
+SF_API int sf_net_create(int max_batch, sf_net** out);
+/* Loads parameters (device FP32, standard layout) and clears the Adam state. */
+SF_API int sf_net_set_params(sf_net* n, const float* params, void* stream);
+SF_API int sf_net_get_params(sf_net* n, float* params, void* stream);
+SF_API int sf_net_forward(sf_net* n, const float* imgs, int batch, float* out, void* stream);
+/* Forward and backward pass of the mean squared error against target:
+ * writes the gradient (device, standard layout; may be NULL) and the loss
+ * (device float; may be NULL). */
+SF_API int sf_net_gradients(sf_net* n, const float* imgs, const float* target, int batch, float* grads, float* loss,
+                            void* stream);
+/* One training step: forward, backward and an Adam update (beta1 0.9, beta2
+ * 0.999, epsilon 1e-8, bias-corrected) with learning rate lr. */
+SF_API int sf_net_train_step(sf_net* n, const float* imgs, const float* target, int batch, float lr, float* loss,
+                             void* stream);
+/* Waits for the device; SF_ERR_TIMEOUT if a tensor-core wait timed out. */
+SF_API int sf_net_status(sf_net* n);
+SF_API void sf_net_destroy(sf_net* n);
+/* The coarsest-level intensities of a quadruple (device FP32 [4][h][w] of
+ * the context's coarsest level), through the context's pyramid kernels. */
+SF_API int sf_coarsest_images(sf_ctx* ctx, const float* L_t, const float* R_t, const float* L_t1, const float* R_t1,
+                              float* out, void* stream);
+/* Predicts the coarsest level's initial delta of the next sf_solve on ctx
+ * from the quadruple (the context's coarsest level must be 80 x 60 with an
+ * 8 x 10 grid; SF_ERR_ARG otherwise), as sf_set_init would set it. */
+SF_API int sf_warm_start(sf_net* n, sf_ctx* ctx, const float* L_t, const float* R_t, const float* L_t1,
+                         const float* R_t1, void* stream);
+
 /* ---- batched solve of many sequences ----------------------------------
  * The paper solves one stereo sequence at a time (Algorithm 1). These calls
  * solve n independent sequences of any sizes together: each frame step runs

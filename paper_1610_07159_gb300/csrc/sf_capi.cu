@@ -504,6 +504,10 @@ int batch_zero_frames(sf_batch* b)
 
 } // namespace
 
+struct sf_net {
+    NetImpl* p = nullptr;
+};
+
 extern "C" {
 
 int sf_params_preset(sf_params* p, int preset)
@@ -1246,6 +1250,120 @@ int sf_probe_gemm_bf16(const void* A, const void* B, int M, int N, int K, int BN
     cudaFree(err);
     if (!rc && h) rc = SF_ERR_TIMEOUT;
     return rc ? fail(rc) : SF_OK;
+}
+
+int sf_net_param_count(void) { return (int)net_param_count(); }
+
+int sf_net_create(int max_batch, sf_net** out)
+{
+    if (!out) return fail(SF_ERR_ARG);
+    *out = nullptr;
+    int rc = SF_OK;
+    NetImpl* p = net_create(max_batch, &rc);
+    if (!p) return fail(rc);
+    sf_net* n = new (std::nothrow) sf_net();
+    if (!n) {
+        net_free(p);
+        return fail(SF_ERR_OOM);
+    }
+    n->p = p;
+    *out = n;
+    return SF_OK;
+}
+
+int sf_net_set_params(sf_net* n, const float* params, void* stream)
+{
+    if (!n || !params) return fail(SF_ERR_ARG);
+    int rc = net_set_params(n->p, params, (cudaStream_t)stream);
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_net_get_params(sf_net* n, float* params, void* stream)
+{
+    if (!n || !params) return fail(SF_ERR_ARG);
+    int rc = net_get_params(n->p, params, (cudaStream_t)stream);
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_net_forward(sf_net* n, const float* imgs, int batch, float* out, void* stream)
+{
+    if (!n || !imgs || !out) return fail(SF_ERR_ARG);
+    int rc = net_forward(n->p, imgs, (long long)4 * NET_IN_H * NET_IN_W, (long long)NET_IN_H * NET_IN_W, batch, out,
+                         (cudaStream_t)stream);
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_net_gradients(sf_net* n, const float* imgs, const float* target, int batch, float* grads, float* loss,
+                     void* stream)
+{
+    if (!n || !imgs || !target) return fail(SF_ERR_ARG);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = net_backward(n->p, imgs, target, batch, st);
+    if (!rc && grads) rc = net_grads_std(n->p, grads, st);
+    if (!rc && loss) rc = check_cuda(cudaMemcpyAsync(loss, net_loss_ptr(n->p), sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_net_train_step(sf_net* n, const float* imgs, const float* target, int batch, float lr, float* loss,
+                      void* stream)
+{
+    if (!n || !imgs || !target || !(lr > 0.f)) return fail(SF_ERR_ARG);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = net_backward(n->p, imgs, target, batch, st);
+    if (!rc) rc = net_adam(n->p, lr, st);
+    if (!rc && loss) rc = check_cuda(cudaMemcpyAsync(loss, net_loss_ptr(n->p), sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_net_status(sf_net* n)
+{
+    if (!n) return fail(SF_ERR_ARG);
+    int rc = check_cuda(cudaDeviceSynchronize());
+    if (!rc) rc = net_error(n->p);
+    return rc ? fail(rc) : SF_OK;
+}
+
+void sf_net_destroy(sf_net* n)
+{
+    if (!n) return;
+    cudaDeviceSynchronize();
+    net_free(n->p);
+    delete n;
+}
+
+int sf_coarsest_images(sf_ctx* c, const float* L_t, const float* R_t, const float* L_t1, const float* R_t1, float* out,
+                       void* stream)
+{
+    if (!c || !L_t || !R_t || !L_t1 || !R_t1 || !out) return fail(SF_ERR_ARG);
+    cudaStream_t st = (cudaStream_t)stream;
+    void* tex[SF_MAX_LEVELS];
+    for (int l = 0; l < c->L; ++l) tex[l] = c->lv[l].tex;
+    const float* in[4] = {L_t, R_t, L_t1, R_t1};
+    int nl = 0;
+    const int mask = c->prm.profile_mask;
+    c->prm.profile_mask = 0;
+    enqueue_pyramid(c, nullptr, in, tex, st, nl);
+    c->prm.profile_mask = mask;
+    const LevelGeom& g = c->geo[c->L - 1];
+    launch_tex_intensity(c->lv[c->L - 1].tex, c->prm.precision, g.w, g.h, out, st);
+    int rc = check_cuda(cudaGetLastError());
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_warm_start(sf_net* n, sf_ctx* c, const float* L_t, const float* R_t, const float* L_t1, const float* R_t1,
+                  void* stream)
+{
+    if (!n || !c) return fail(SF_ERR_ARG);
+    const LevelGeom& g = c->geo[c->L - 1];
+    if (g.w != NET_IN_W || g.h != NET_IN_H || g.nx != NET_OUT_W || g.ny != NET_OUT_H) return fail(SF_ERR_ARG);
+    cudaStream_t st = (cudaStream_t)stream;
+    float* in = net_in_ptr(n->p);
+    int rc = sf_coarsest_images(c, L_t, R_t, L_t1, R_t1, in, stream);
+    if (rc) return rc;
+    rc = net_forward(n->p, in, (long long)4 * NET_IN_H * NET_IN_W, (long long)NET_IN_H * NET_IN_W, 1, c->init_buf, st);
+    if (rc) return fail(rc);
+    c->pending_init = 1;
+    return SF_OK;
 }
 
 } // extern "C"

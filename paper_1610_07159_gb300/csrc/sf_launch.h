@@ -134,4 +134,23 @@ struct GemmArgs {
 int gemm_check(const GemmArgs& a);
 cudaError_t launch_gemm(const GemmArgs& a, int epi, int splits, cudaStream_t st);
 
+// sf_net.cu: the warm-start network (training and inference).
+constexpr int NET_IN_H = 60, NET_IN_W = 80, NET_OUT_C = 6, NET_OUT_H = 8, NET_OUT_W = 10;
+struct NetImpl;
+NetImpl* net_create(int max_batch, int* rc);
+void net_free(NetImpl* n);
+size_t net_param_count();
+int net_set_params(NetImpl* n, const float* p, cudaStream_t st);
+int net_get_params(NetImpl* n, float* p, cudaStream_t st);
+int net_forward(NetImpl* n, const float* img, long long img_stride, long long ch_stride, int batch, float* out,
+                cudaStream_t st);
+int net_backward(NetImpl* n, const float* img, const float* target, int batch, cudaStream_t st);
+int net_grads_std(NetImpl* n, float* g, cudaStream_t st);
+int net_adam(NetImpl* n, float lr, cudaStream_t st);
+int net_error(NetImpl* n);
+float* net_loss_ptr(NetImpl* n);
+float* net_out_ptr(NetImpl* n);
+float* net_in_ptr(NetImpl* n);
+void launch_tex_intensity(const void* tex, int prec, int w, int h, float* out, cudaStream_t st);
+
 } // namespace sfk

@@ -111,6 +111,14 @@ __global__ void k_unpack_tex(const typename TT::T* __restrict__ tex, int n, floa
     }
 }
 
+template <class TT>
+__global__ void k_tex_intensity(const typename TT::T* __restrict__ tex, int n, float* __restrict__ out)
+{
+    const int c = blockIdx.y;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+        out[(size_t)c * n + p] = TT::ld(tex + (size_t)c * n + p).x;
+}
+
 inline int grid1d(size_t n, int cap = 152 * 16)
 {
     size_t b = (n + T1D - 1) / T1D;
@@ -174,6 +182,13 @@ void launch_finish_level(const LevelGeom& g, const float* base, const float* del
     const int n6 = 6 * g.G;
     k_finish_level<<<(n6 + T1D - 1) / T1D, T1D, 0, st>>>(n6, base, delta, prev_delta, prev_total, args, write_out,
                                                          out);
+}
+
+void launch_tex_intensity(const void* tex, int prec, int w, int h, float* out, cudaStream_t st)
+{
+    dim3 grid(grid1d((size_t)w * h), 4);
+    SF_TEX_DISPATCH(prec, TT, k_tex_intensity<TT><<<grid, T1D, 0, st>>>(static_cast<const typename TT::T*>(tex),
+                                                                         w * h, out));
 }
 
 void launch_unpack_tex(const void* tex, int prec, int w, int h, float* planes, cudaStream_t st)

@@ -36,7 +36,9 @@ EXPORTED = (
     "sf_probe_feature_weights", "sf_probe_assemble", "sf_probe_pcg", "sf_probe_wmask", "sf_probe_energy",
     "sf_pcg_static", "sf_batch_create", "sf_batch_layout", "sf_batch_solve", "sf_batch_set_schedule",
     "sf_batch_get_schedule", "sf_batch_tune", "sf_batch_sequence", "sf_batch_reset", "sf_batch_destroy",
-    "sf_probe_gemm_bf16",
+    "sf_probe_gemm_bf16", "sf_net_param_count", "sf_net_create", "sf_net_set_params", "sf_net_get_params",
+    "sf_net_forward", "sf_net_gradients", "sf_net_train_step", "sf_net_status", "sf_net_destroy",
+    "sf_coarsest_images", "sf_warm_start",
 )
 STATIC_PCG_MAX_NODES = 4096
 
@@ -131,6 +133,18 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sf_batch_destroy.argtypes = [vp]
     L.sf_batch_destroy.restype = None
     L.sf_probe_gemm_bf16.argtypes = [vp, vp, i, i, i, i, i, fp, vp]
+    L.sf_net_param_count.argtypes = []
+    L.sf_net_create.argtypes = [i, ctypes.POINTER(vp)]
+    L.sf_net_set_params.argtypes = [vp, fp, vp]
+    L.sf_net_get_params.argtypes = [vp, fp, vp]
+    L.sf_net_forward.argtypes = [vp, fp, i, fp, vp]
+    L.sf_net_gradients.argtypes = [vp, fp, fp, i, fp, fp, vp]
+    L.sf_net_train_step.argtypes = [vp, fp, fp, i, ctypes.c_float, fp, vp]
+    L.sf_net_status.argtypes = [vp]
+    L.sf_net_destroy.argtypes = [vp]
+    L.sf_net_destroy.restype = None
+    L.sf_coarsest_images.argtypes = [vp, fp, fp, fp, fp, fp, vp]
+    L.sf_warm_start.argtypes = [vp, vp, fp, fp, fp, fp, vp]
     _lib = L
     return L
 
@@ -447,3 +461,85 @@ class Batch:
             w, h = self.sizes[i]
             self._views[i] = Solver(w, h, self.stride, self.levels[i], self.params, _view_of=ctx)
         return self._views[i]
+
+
+NET_IN = (4, 60, 80)
+NET_OUT = (6, 8, 10)
+
+
+class Net:
+    """The warm-start network (sf_net_create ... sf_net_destroy)."""
+
+    def __init__(self, max_batch: int = 256):
+        self.L = load()
+        torch.cuda.init()
+        out = ctypes.c_void_p()
+        _check(self.L.sf_net_create(int(max_batch), ctypes.byref(out)), "sf_net_create")
+        self.n = out.value
+        self.max_batch = int(max_batch)
+        self.n_params = int(self.L.sf_net_param_count())
+
+    def close(self) -> None:
+        if getattr(self, "n", None):
+            self.L.sf_net_destroy(self.n)
+            self.n = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat: torch.Tensor) -> None:
+        assert flat.numel() == self.n_params
+        _check(self.L.sf_net_set_params(self.n, _ptr(flat, torch.float32), _stream()), "sf_net_set_params")
+
+    def get_params(self) -> torch.Tensor:
+        p = torch.empty(self.n_params, device="cuda", dtype=torch.float32)
+        _check(self.L.sf_net_get_params(self.n, _ptr(p), _stream()), "sf_net_get_params")
+        return p
+
+    def forward(self, imgs: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        B = imgs.shape[0]
+        if out is None:
+            out = torch.empty((B,) + NET_OUT, device="cuda", dtype=torch.float32)
+        _check(self.L.sf_net_forward(self.n, _ptr(imgs, torch.float32), B, _ptr(out, torch.float32), _stream()),
+               "sf_net_forward")
+        return out
+
+    def gradients(self, imgs: torch.Tensor, target: torch.Tensor):
+        g = torch.empty(self.n_params, device="cuda", dtype=torch.float32)
+        loss = torch.empty(1, device="cuda", dtype=torch.float32)
+        _check(self.L.sf_net_gradients(self.n, _ptr(imgs, torch.float32), _ptr(target, torch.float32),
+                                       imgs.shape[0], _ptr(g), _ptr(loss), _stream()), "sf_net_gradients")
+        return g, loss
+
+    def train_step(self, imgs: torch.Tensor, target: torch.Tensor, lr: float, loss: torch.Tensor | None = None):
+        if loss is None:
+            loss = torch.empty(1, device="cuda", dtype=torch.float32)
+        _check(self.L.sf_net_train_step(self.n, _ptr(imgs, torch.float32), _ptr(target, torch.float32),
+                                        imgs.shape[0], ctypes.c_float(lr), _ptr(loss), _stream()),
+               "sf_net_train_step")
+        return loss
+
+    def status(self) -> None:
+        _check(self.L.sf_net_status(self.n), "sf_net_status")
+
+    def warm_start(self, solver: "Solver", imgs: torch.Tensor) -> None:
+        """Sets solver's coarsest initial delta for its next solve from the quadruple imgs [4, h, w]."""
+        base = _ptr(imgs, torch.float32)
+        n = solver.width * solver.height * 4
+        _check(self.L.sf_warm_start(self.n, solver.ctx, base, base + n, base + 2 * n, base + 3 * n, _stream()),
+               "sf_warm_start")
+
+
+def coarsest_images(solver: "Solver", imgs: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """The four coarsest-level intensities [4, h, w] of a quadruple imgs [4, H, W]."""
+    w, h, _, _ = solver.dims(solver.levels - 1)
+    if out is None:
+        out = torch.empty((4, h, w), device="cuda", dtype=torch.float32)
+    base = _ptr(imgs, torch.float32)
+    n = solver.width * solver.height * 4
+    _check(load().sf_coarsest_images(solver.ctx, base, base + n, base + 2 * n, base + 3 * n, _ptr(out, torch.float32),
+                                     _stream()), "sf_coarsest_images")
+    return out
