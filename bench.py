@@ -191,6 +191,128 @@ def cpu_baseline(video, max_seconds=20.0, max_frames=4):
                       f"FP64 C oracle, {dt:.1f} s"}
 
 
+def variant_batched(dev, steps=3):
+    """64 independent sequences of uneven sizes solved together: one launch per
+    frame step (one thread-block cluster per sequence) under a captured graph,
+    with the autotuned schedule."""
+    import torch
+
+    from paper_1610_07159_gb300 import scenes, scenes_device, sf
+
+    sizes = scenes.batch_sizes(64, seed=4000)
+    levels = [4 if w * h <= 640 * 480 else 5 for w, h in sizes]
+    b = sf.Batch(sizes, levels, STRIDE, sf.preset(sf.PRESET_FIG2, gn_iters=[GN], pcg_iters=[PCG]))
+    vids = [scenes_device.frames(scenes.SceneVideo(w, h, steps + 1, seed=5000 + i), steps + 1, dev,
+                                 dtype=torch.float32) for i, (w, h) in enumerate(sizes)]
+    packed = [b.pack([v[f] for v in vids]) for f in range(steps + 1)]
+    del vids
+    out = torch.empty(b.out_total, device=dev, dtype=torch.float32)
+    t0 = time.time()
+    b.tune(packed[0], out, steps=2)
+    tune_s = time.time() - t0
+    b.solve(packed[0], out)  # warm-up frame
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for f in range(1, steps + 1):
+        b.solve(packed[f], out)
+    e.record()
+    e.synchronize()
+    ms = s.elapsed_time(e) / steps
+    px = sum(w * h for w, h in sizes)
+    flops = sum(GN * ASM_FLOPS_PER_PX * w * h * sum(4.0 ** -l for l in range(L)) for (w, h), L in zip(sizes, levels))
+    nodes = 0
+    for (w, h), L in zip(sizes, levels):
+        for l in range(L):
+            wl, hl = -(-w // 2 ** l), -(-h // 2 ** l)
+            nodes += (-(-wl // STRIDE)) * (-(-hl // STRIDE))
+    pcg_bytes = GN * nodes * (PCG_INIT_B + PCG * PCG_ITER_B + PCG_OUT_B)
+    energies = [b.sequence(i).stats().energy for i in range(len(sizes))]
+    res = {"sequences": len(sizes), "sizes": "seeded uniform draw from {320x240, 640x480, 960x540, 1280x720}",
+           "levels": "4 up to 640x480, 5 above", "ms_per_frame_step": ms, "frames_per_s": len(sizes) * 1e3 / ms,
+           "Mpx_per_s": px / ms / 1e3, "schedule": {"cluster_ctas": b.schedule()[0], "cpb_div": b.schedule()[1]},
+           "tune_s": tune_s, "launches_per_frame_step": 1,
+           "assembly_TFLOPs": flops / (ms / 1e3) / 1e12, "pcg_GBps": pcg_bytes / (ms / 1e3) / 1e9,
+           "note": "rates over the whole launch (all stages share it)",
+           "all_finite": bool(all(e == e for e in energies))}
+    b.close()
+    return res
+
+
+def variant_mixed(dev, frames_d):
+    """The headline video in the 16-bit texel modes, with the final energy of
+    the last frame against FP32."""
+    import torch
+
+    from paper_1610_07159_gb300 import sf
+
+    out = {}
+    for name, prec in (("fp32", sf.FP32), ("fp16", sf.MIXED_FP16), ("bf16", sf.MIXED_BF16)):
+        s = sf.Solver(WIDTH, HEIGHT, STRIDE, LEVELS,
+                      sf.preset(sf.PRESET_FIG2, gn_iters=[GN], pcg_iters=[PCG], video=1, precision=prec))
+        outs = torch.empty((NFRAMES, 6, HEIGHT // STRIDE, WIDTH // STRIDE), device=dev, dtype=torch.float32)
+        s.solve_video(frames_d, outs)
+        s.reset()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        s.solve_video(frames_d, outs)
+        b.record()
+        b.synchronize()
+        out[name] = {"fps": NFRAMES * 1e3 / a.elapsed_time(b), "energy_last_frame": s.stats().energy}
+        s.close()
+    for name in ("fp16", "bf16"):
+        out[name]["energy_rel_vs_fp32"] = (out[name]["energy_last_frame"] - out["fp32"]["energy_last_frame"]) / \
+            out["fp32"]["energy_last_frame"]
+    return out
+
+
+def variant_warm_start(dev, n_videos=8):
+    """First frames at 640x480: the zero start with the full schedule against
+    the learned warm start with the cheapest schedule whose mean final energy
+    is within 1% of it (the 1e-4 acceptance is reported per schedule)."""
+    import numpy as np
+    import torch
+
+    from paper_1610_07159_gb300 import scenes, scenes_device, sf, warmstart as ws
+
+    d = np.load(os.path.join(ROOT, "paper_1610_07159_gb300", "data", "warmstart_640x480.npz"))
+    net = sf.Net(1)
+    net.set_params(torch.from_numpy(d["params"]).to(dev))
+    ev = ws.evaluate(net, n_videos, seed0=980000, schedules=ws.SCHEDULES)
+    ok = [r for r in ev["schedules"] if r["warm_mean_rel"] <= 0.01]
+    pick = min(ok, key=lambda r: r["cost"]) if ok else None
+    quads = [scenes_device.frames(scenes.SceneVideo(WIDTH, HEIGHT, 1, seed=980000 + v), 1, dev)[0]
+             for v in range(n_videos)]
+
+    def fps(gn, warm):
+        """First-frame rate: every frame from a reset state, each timed alone
+        (the warm start's pyramid and network pass inside the timed region)."""
+        s = sf.Solver(WIDTH, HEIGHT, STRIDE, LEVELS, ws.solver_params(gn))
+        tot = 0.0
+        for rep in range(2):
+            for q in quads:
+                s.reset()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                if warm:
+                    net.warm_start(s, q)
+                s.solve(q)
+                b.record()
+                b.synchronize()
+                if rep:
+                    tot += a.elapsed_time(b)
+        s.close()
+        return len(quads) * 1e3 / tot
+
+    res = {"frames": n_videos, "cold_schedule": list(ws.FULL), "cold_first_frame_fps": fps(ws.FULL, False),
+           "accepted_at_1e-4": ev["cheapest_warm"],
+           "per_schedule": [{k: r[k] for k in ("gn", "cost", "warm_mean_rel", "warm_max_rel", "cold_mean_rel",
+                                                "cold_max_rel", "warm_accepted")} for r in ev["schedules"]]}
+    if pick:
+        res.update({"warm_schedule": pick["gn"], "warm_first_frame_fps": fps(pick["gn"], True),
+                    "warm_mean_rel_energy": pick["warm_mean_rel"], "warm_max_rel_energy": pick["warm_max_rel"]})
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -358,6 +480,10 @@ def run_ours(args):
         "energy_last_frame": st.energy,
         "kernels": kernels,
     }
+    if rank == 0 and not args.no_variants:
+        line["variants"]["batched_64_uneven"] = variant_batched(dev)
+        line["variants"]["mixed_precision"] = variant_mixed(dev, frames_d)
+        line["variants"]["learned_warm_start"] = variant_warm_start(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(video)
     if rank == 0:
@@ -410,6 +536,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the batched, mixed and warm-start variants")
     ap.add_argument("--arm", choices=("all", "video", "frames"), default="all",
                     help="for profiling runs: only the pipelined video arm, or only the frame-by-frame arm")
     args = ap.parse_args()

@@ -20,19 +20,19 @@ namespace sfk {
 namespace {
 
 // One CTA per cell group (assemble_group), then the block's energy partials.
-template <int MAXOUT, class TT>
-__global__ void __launch_bounds__(ETHREADS) k_assemble(LevelGeom g, int cpb, const typename TT::T* __restrict__ tex,
+template <int MAXT, class TT>
+__global__ void __launch_bounds__(ETHREADS, 2) k_assemble(LevelGeom g, int cpb, const typename TT::T* __restrict__ tex,
                                                        const float* __restrict__ base, const float* __restrict__ delta,
                                                        DevParams P, uint8_t* __restrict__ Wmask,
                                                        float* __restrict__ cell, float2* __restrict__ part)
 {
     __shared__ float sHB[ETHREADS * HB];
-    __shared__ float sA[ETHREADS * 4];
+    __shared__ __align__(16) float sW[ETHREADS * WROW];
     __shared__ ff sred[ETHREADS / 32];
     const int tid = threadIdx.x;
     float ep = 0.f, eg = 0.f;
     int nex = 0;
-    assemble_group<MAXOUT, TT>(g, cpb, blockIdx.x, blockIdx.y, tex, base, delta, P, Wmask, cell, sHB, sA, ep, eg, nex);
+    assemble_group<MAXT, TT>(g, cpb, blockIdx.x, blockIdx.y, tex, base, delta, P, Wmask, cell, sHB, sW, ep, eg, nex);
     const int blk = blockIdx.y * gridDim.x + blockIdx.x;
     const ff tp = ff_block_sum_fast<ETHREADS>(ep, sred);
     const ff tg = ff_block_sum_fast<ETHREADS>(eg, sred);
@@ -210,12 +210,12 @@ __global__ void k_unpack_blocks(int G, const float* __restrict__ node, const flo
     for (int r = 0; r < 6; ++r) rhs_out[n * 6 + r] = rhs[r * G + n];
 }
 
-template <int MAXOUT>
+template <int MAXT>
 void assemble_impl(const LevelGeom& g, int cpb, const void* tex, int prec, const float* base, const float* delta,
                    const DevParams& P, uint8_t* Wmask, float* cell, float2* part, cudaStream_t st)
 {
     dim3 grid((g.ncx + cpb - 1) / cpb, g.ncy);
-    SF_TEX_DISPATCH(prec, TT, k_assemble<MAXOUT, TT><<<grid, ETHREADS, 0, st>>>(
+    SF_TEX_DISPATCH(prec, TT, k_assemble<MAXT, TT><<<grid, ETHREADS, 0, st>>>(
                                   g, cpb, static_cast<const typename TT::T*>(tex), base, delta, P, Wmask, cell, part));
 }
 
@@ -225,7 +225,7 @@ int assemble_blocks(const LevelGeom& g, int* cpb_out)
 {
     int cpb = ETHREADS / (g.s * g.s);
     if (cpb < 1) cpb = 1;
-    while (cpb * CELL_VALS > 16 * ETHREADS) --cpb;
+    while (assemble_tasks_per_thread(cpb) > 4) --cpb;
     if (cpb_out) *cpb_out = cpb;
     return ((g.ncx + cpb - 1) / cpb) * g.ncy;
 }
@@ -235,17 +235,13 @@ void launch_assemble(const LevelGeom& g, const void* tex, int prec, const float*
 {
     int cpb;
     assemble_blocks(g, &cpb);
-    const int need = (cpb * CELL_VALS + ETHREADS - 1) / ETHREADS;
+    const int need = assemble_tasks_per_thread(cpb);
     if (need <= 1)
         assemble_impl<1>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, st);
     else if (need <= 2)
         assemble_impl<2>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, st);
-    else if (need <= 4)
-        assemble_impl<4>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, st);
-    else if (need <= 8)
-        assemble_impl<8>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, st);
     else
-        assemble_impl<16>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, st);
+        assemble_impl<4>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, st);
 }
 
 void launch_gather(const LevelGeom& g, const float* cell, const float* base, const float* delta, const float* wf,

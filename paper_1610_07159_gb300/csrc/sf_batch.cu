@@ -19,6 +19,8 @@
 // vectors) are read with ordinary coherent loads; the non-coherent read-only
 // path is used only for the input images and for texels, which are written
 // once per launch before any read of them.
+#include <algorithm>
+
 #include "sf_launch.h"
 #include "sf_stages.cuh"
 
@@ -35,7 +37,7 @@ using TTB = TexF32;
 
 struct BShared {
     float sHB[BT * HB];
-    float sA[BT * 4];
+    __align__(16) float sW[BT * WROW];
     ff sred[BT / 32];
     ff res[PART_Q];
     DevParams P;
@@ -253,8 +255,8 @@ __device__ void pcg_cluster(const LevelGeom& g, const BLevel& B, int iters, floa
     }
 }
 
-template <int MAXOUT>
-__global__ void __launch_bounds__(BT, MAXOUT >= 16 ? 1 : 2) k_batch_frame(const BSeq* __restrict__ seqs,
+template <int MAXT>
+__global__ void __launch_bounds__(BT, 2) k_batch_frame(const BSeq* __restrict__ seqs,
                                                                           const int* __restrict__ order)
 {
     __shared__ BShared sm;
@@ -321,8 +323,8 @@ __global__ void __launch_bounds__(BT, MAXOUT >= 16 ? 1 : 2) k_batch_frame(const 
             float ep = 0.f, eg = 0.f;
             int nex = 0;
             for (int vb = rank; vb < B.n_groups; vb += T)
-                assemble_group<MAXOUT, TTB>(g, B.cpb, vb % B.gx, vb / B.gx, tex, B.base, B.delta, P, Wst, B.cell,
-                                            sm.sHB, sm.sA, ep, eg, nex);
+                assemble_group<MAXT, TTB>(g, B.cpb, vb % B.gx, vb / B.gx, tex, B.base, B.delta, P, Wst, B.cell,
+                                          sm.sHB, sm.sW, ep, eg, nex);
             cluster_sync_all();
             // node system with the priors; energy at the linearisation point
             float es = 0.f, ee = 0.f, em = 0.f;
@@ -421,7 +423,7 @@ __global__ void k_batch_args(BSeq* seqs, int nseq, const float* in, float* out)
     seqs[i].out = out + seqs[i].out_off;
 }
 
-template <int MAXOUT>
+template <int MAXT>
 cudaLaunchConfig_t batch_config(int nseq, int cluster, cudaStream_t st, cudaLaunchAttribute* attr)
 {
     cudaLaunchConfig_t cfg{};
@@ -438,32 +440,32 @@ cudaLaunchConfig_t batch_config(int nseq, int cluster, cudaStream_t st, cudaLaun
     return cfg;
 }
 
-template <int MAXOUT>
+template <int MAXT>
 void prepare_impl()
 {
-    cudaFuncSetAttribute(k_batch_frame<MAXOUT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_batch_frame<MAXT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
-template <int MAXOUT>
+template <int MAXT>
 int active_impl(int cluster)
 {
-    prepare_impl<MAXOUT>();
+    prepare_impl<MAXT>();
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = batch_config<MAXOUT>(1, cluster, nullptr, attr);
+    cudaLaunchConfig_t cfg = batch_config<MAXT>(1, cluster, nullptr, attr);
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_batch_frame<MAXOUT>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, k_batch_frame<MAXT>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return n;
 }
 
-template <int MAXOUT>
+template <int MAXT>
 cudaError_t launch_impl(const BSeq* seqs, const int* order, int nseq, int cluster, cudaStream_t st)
 {
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = batch_config<MAXOUT>(nseq, cluster, st, attr);
-    return cudaLaunchKernelEx(&cfg, k_batch_frame<MAXOUT>, seqs, order);
+    cudaLaunchConfig_t cfg = batch_config<MAXT>(nseq, cluster, st, attr);
+    return cudaLaunchKernelEx(&cfg, k_batch_frame<MAXT>, seqs, order);
 }
 
 } // namespace
@@ -472,15 +474,18 @@ int batch_cells_per_group(int s, int div)
 {
     int cpb = ETHREADS / (s * s);
     if (cpb < 1) cpb = 1;
-    while (cpb * CELL_VALS > 16 * ETHREADS) --cpb;
+    while (assemble_tasks_per_thread(cpb) > 4) --cpb;
     if (div > 1) cpb = (cpb + div - 1) / div;
     return cpb < 1 ? 1 : cpb;
 }
 
 int batch_maxout(int s)
 {
-    const int need = (batch_cells_per_group(s, 1) * CELL_VALS + ETHREADS - 1) / ETHREADS;
-    return need <= 1 ? 1 : need <= 4 ? 4 : 16;
+    // task slots per thread of the largest group any schedule uses
+    int need = 1;
+    for (int div = 1; div <= 4; ++div)
+        need = std::max(need, assemble_tasks_per_thread(batch_cells_per_group(s, div)));
+    return need <= 1 ? 1 : need <= 2 ? 2 : 4;
 }
 
 void batch_prepare(int cluster, int maxout)
@@ -488,24 +493,24 @@ void batch_prepare(int cluster, int maxout)
     (void)cluster;
     if (maxout == 1)
         prepare_impl<1>();
-    else if (maxout == 4)
-        prepare_impl<4>();
+    else if (maxout == 2)
+        prepare_impl<2>();
     else
-        prepare_impl<16>();
+        prepare_impl<4>();
 }
 
 int batch_active_clusters(int cluster, int maxout)
 {
     if (maxout == 1) return active_impl<1>(cluster);
-    if (maxout == 4) return active_impl<4>(cluster);
-    return active_impl<16>(cluster);
+    if (maxout == 2) return active_impl<2>(cluster);
+    return active_impl<4>(cluster);
 }
 
 cudaError_t launch_batch_frame(const BSeq* seqs, const int* order, int nseq, int cluster, int maxout, cudaStream_t st)
 {
     if (maxout == 1) return launch_impl<1>(seqs, order, nseq, cluster, st);
-    if (maxout == 4) return launch_impl<4>(seqs, order, nseq, cluster, st);
-    return launch_impl<16>(seqs, order, nseq, cluster, st);
+    if (maxout == 2) return launch_impl<2>(seqs, order, nseq, cluster, st);
+    return launch_impl<4>(seqs, order, nseq, cluster, st);
 }
 
 void launch_batch_args(BSeq* seqs, int nseq, const float* in, float* out, cudaStream_t st)

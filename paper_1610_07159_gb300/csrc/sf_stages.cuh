@@ -162,19 +162,85 @@ __device__ __forceinline__ void comp_sum(float& a, float& e, int lo, int hi, Ter
     }
 }
 
+// Cell reduction tasks. Per cell, 48 task kinds: kind 2e + h (e < 21) sums
+// entry e of H_p against the pair weights alpha_k alpha_l of pairs
+// 5h .. 5h + 4; kind 42 + c sums component c of b_p against the four corner
+// weights alpha_k. A task may cover only part `p` of P contiguous parts of
+// its cell's pixels; the parts meet at the end in a fixed order.
+constexpr int TASK_KINDS = 48;
+// per-pixel weight row in shared memory (16 floats, 16-byte aligned):
+// [0..3] pairs 0-3, [4..7] pairs 5-8, [8..11] corners 0-3, [12] pair 4, [13] pair 9
+constexpr int WROW = 16;
+
+__host__ __device__ constexpr int assemble_parts(int cpb) { return cpb * TASK_KINDS >= ETHREADS ? 1 : ETHREADS / (cpb * TASK_KINDS); }
+__host__ __device__ constexpr int assemble_tasks_per_thread(int cpb)
+{
+    return (cpb * TASK_KINDS * assemble_parts(cpb) + ETHREADS - 1) / ETHREADS;
+}
+
+// Compensated sums of n = 5 (H) or 4 (b) outputs over pixels [qa, qb):
+// runs of SUMRUN pixels are summed plainly, each run enters with one Kahan
+// step per output (the same scheme as comp_sum).
+template <int N>
+__device__ __forceinline__ void task_term(float* run, bool first, const float* sHB, int q, int hoff, const float* sW,
+                                          int w4, int w1)
+{
+    const float h = sHB[q * HB + hoff];
+    const float4 w = *reinterpret_cast<const float4*>(sW + q * WROW + w4);
+    const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) run[i] = first ? wv[i] * h : fmaf(wv[i], h, run[i]);
+    if (N == 5) {
+        const float w5 = sW[q * WROW + w1];
+        run[N - 1] = first ? w5 * h : fmaf(w5, h, run[N - 1]);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void kahan_add(float* a, float* e, const float* run)
+{
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const float y = run[i] - e[i];
+        const float t = a[i] + y;
+        e[i] = (t - a[i]) - y;
+        a[i] = t;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void task_sum(float* a, float* e, int qa, int qb, const float* sHB, int hoff,
+                                         const float* sW, int w4, int w1)
+{
+    float run[N];
+    int q = qa;
+    for (; q + SUMRUN <= qb; q += SUMRUN) {
+#pragma unroll
+        for (int r = 0; r < SUMRUN; ++r) task_term<N>(run, r == 0, sHB, q + r, hoff, sW, w4, w1);
+        kahan_add<N>(a, e, run);
+    }
+    for (; q < qb; ++q) {
+        task_term<N>(run, true, sHB, q, hoff, sW, w4, w1);
+        kahan_add<N>(a, e, run);
+    }
+}
+
 // Assembles the cells of one group: `cpb` consecutive cells of cell row
 // `by`, starting at cell bx * cpb. Pixels are enumerated cell-major (regular
-// cells s x ch, the row's last cell may be wider), processed in chunks of
-// ETHREADS; each thread owns up to MAXOUT of the cpb * CELL_VALS outputs and
-// sums its cell's pixels of every chunk. The pixel energies and the count of
-// excluded pixels are added to the thread's ep, eg, nex. sHB and sA are
-// ETHREADS * HB and ETHREADS * 4 floats of shared memory.
-template <int MAXOUT, class TT>
+// cells s x ch, the row's last cell may be wider) and processed in chunks of
+// ETHREADS: one pixel per thread computes H_p, b_p and its bilinear weights
+// into shared memory, then each thread runs up to MAXT reduction tasks
+// (above) over its cell's pixels of the chunk, five (or four) outputs at a
+// time from one load of the H_p (b_p) entry and one row of weights. The
+// pixel energies and the count of excluded pixels are added to the thread's
+// ep, eg, nex. sHB and sW are ETHREADS * HB and ETHREADS * WROW floats of
+// shared memory (sW 16-byte aligned).
+template <int MAXT, class TT>
 __device__ __forceinline__ void assemble_group(const LevelGeom& g, int cpb, int bx, int by,
                                                const typename TT::T* __restrict__ tex, const float* base,
                                                const float* delta, const DevParams& P,
                                                uint8_t* Wmask, float* cell, float* sHB,
-                                               float* sA, float& ep, float& eg, int& nex)
+                                               float* sW, float& ep, float& eg, int& nex)
 {
     const int tid = threadIdx.x;
     const int s = g.s;
@@ -186,11 +252,14 @@ __device__ __forceinline__ void assemble_group(const LevelGeom& g, int cpb, int 
     const int cw_last = (lastc == g.ncx - 1 ? g.w : (lastc + 1) * s) - lastc * s;
     const int per_reg = s * ch;
     const int total = (ncell - 1) * per_reg + cw_last * ch;
-    const int nout = ncell * CELL_VALS;
+    const int NP = assemble_parts(cpb);
+    const int ntask = ncell * TASK_KINDS * NP;
 
-    float acc[MAXOUT], cmp[MAXOUT]; // cmp: Kahan compensation of the cell sums
+    float acc[MAXT][5], cmp[MAXT][5]; // cmp: Kahan compensation of the cell sums
 #pragma unroll
-    for (int k = 0; k < MAXOUT; ++k) acc[k] = cmp[k] = 0.f;
+    for (int j = 0; j < MAXT; ++j)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) acc[j][i] = cmp[j][i] = 0.f;
 
     for (int c0 = 0; c0 < total; c0 += ETHREADS) {
         const int p = c0 + tid;
@@ -227,41 +296,86 @@ __device__ __forceinline__ void assemble_group(const LevelGeom& g, int cpb, int 
         for (int q = 0; q < NB; ++q) sHB[tid * HB + q] = H[q];
 #pragma unroll
         for (int q = 0; q < 6; ++q) sHB[tid * HB + NB + q] = bv[q];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) sA[tid * 4 + q] = al[q];
+        {
+            float* wr = sW + tid * WROW;
+            *reinterpret_cast<float4*>(wr) = make_float4(al[0] * al[0], al[0] * al[1], al[0] * al[2], al[0] * al[3]);
+            *reinterpret_cast<float4*>(wr + 4) = make_float4(al[1] * al[2], al[1] * al[3], al[2] * al[2], al[2] * al[3]);
+            *reinterpret_cast<float4*>(wr + 8) = make_float4(al[0], al[1], al[2], al[3]);
+            wr[12] = al[1] * al[1];
+            wr[13] = al[3] * al[3];
+        }
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < MAXOUT; ++k) {
-            const int o = tid + k * ETHREADS;
-            if (o < nout) {
-                const int c = o / CELL_VALS, r = o - c * CELL_VALS;
+        for (int j = 0; j < MAXT; ++j) {
+            const int t = tid + j * ETHREADS;
+            if (t < ntask) {
+                const int part = t % NP, r = t / NP, kind = r % TASK_KINDS, c = r / TASK_KINDS;
                 int lo = c * per_reg, hi = (c == ncell - 1) ? total : (c + 1) * per_reg;
                 lo = max(lo, c0) - c0;
                 hi = min(hi, c0 + ETHREADS) - c0;
-                float a = acc[k], e = cmp[k];
-                if (r < NPAIR * NB) {
-                    const int pr = r / NB, ee = r - pr * NB;
-                    const int kk = c_pair_k[pr], ll = c_pair_l[pr];
-                    comp_sum(a, e, lo, hi, [&](int q) { return sA[q * 4 + kk] * sA[q * 4 + ll] * sHB[q * HB + ee]; });
-                } else {
-                    const int rr = r - NPAIR * NB;
-                    const int kk = rr / 6, comp = rr - kk * 6;
-                    comp_sum(a, e, lo, hi, [&](int q) { return sA[q * 4 + kk] * sHB[q * HB + NB + comp]; });
+                if (hi > lo) {
+                    const int qa = lo + (hi - lo) * part / NP, qb = lo + (hi - lo) * (part + 1) / NP;
+                    if (kind < 2 * NB) {
+                        const int half = kind & 1;
+                        task_sum<5>(acc[j], cmp[j], qa, qb, sHB, kind >> 1, sW, half ? 4 : 0, half ? 13 : 12);
+                    } else {
+                        task_sum<4>(acc[j], cmp[j], qa, qb, sHB, NB + kind - 2 * NB, sW, 8, 0);
+                    }
                 }
-                cmp[k] = e;
-                acc[k] = a;
             }
         }
         __syncthreads();
     }
+    // outputs: r < 210 is entry ee of pair pr (r = pr * 21 + ee), r >= 210
+    // component comp of corner k (r = 210 + k * 6 + comp)
     const int ncell_tot = g.ncx * g.ncy;
+    const size_t cbase = (size_t)cj * g.ncx + ci0;
+    if (NP == 1) {
 #pragma unroll
-    for (int k = 0; k < MAXOUT; ++k) {
-        const int o = tid + k * ETHREADS;
-        if (o < nout) {
-            const int c = o / CELL_VALS, r = o - c * CELL_VALS;
-            cell[(size_t)r * ncell_tot + cj * g.ncx + ci0 + c] = acc[k] - cmp[k];
+        for (int j = 0; j < MAXT; ++j) {
+            const int t = tid + j * ETHREADS;
+            if (t < ntask) {
+                const int kind = t % TASK_KINDS, c = t / TASK_KINDS;
+                if (kind < 2 * NB) {
+                    const int ee = kind >> 1, half = kind & 1;
+#pragma unroll
+                    for (int i = 0; i < 5; ++i)
+                        cell[(size_t)((5 * half + i) * NB + ee) * ncell_tot + cbase + c] = acc[j][i] - cmp[j][i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        cell[(size_t)(NPAIR * NB + i * 6 + kind - 2 * NB) * ncell_tot + cbase + c] = acc[j][i] - cmp[j][i];
+                }
+            }
         }
+    } else {
+        // partial sums of the parts through shared memory, summed in part order
+        float* sp = sHB;
+#pragma unroll
+        for (int j = 0; j < MAXT; ++j) {
+            const int t = tid + j * ETHREADS;
+            if (t < ntask)
+#pragma unroll
+                for (int i = 0; i < 5; ++i) sp[t * 5 + i] = acc[j][i] - cmp[j][i];
+        }
+        __syncthreads();
+        for (int o = tid; o < ncell * CELL_VALS; o += ETHREADS) {
+            const int c = o / CELL_VALS, r = o - c * CELL_VALS;
+            int kind, i;
+            if (r < NPAIR * NB) {
+                const int pr = r / NB, ee = r - pr * NB;
+                kind = 2 * ee + (pr >= 5);
+                i = pr - 5 * (pr >= 5);
+            } else {
+                const int rr = r - NPAIR * NB;
+                kind = 2 * NB + rr % 6;
+                i = rr / 6;
+            }
+            float v = 0.f;
+            for (int part = 0; part < NP; ++part) v += sp[((c * TASK_KINDS + kind) * NP + part) * 5 + i];
+            cell[(size_t)r * ncell_tot + cbase + c] = v;
+        }
+        __syncthreads();
     }
 }
 
