@@ -322,6 +322,34 @@ def run_ours(args):
     dist, rank, world, local = dist_setup("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.arm == "batch8":
+        # profiling aid: 8 sequences of 640x480 in one launch per frame step, two frame steps
+        from paper_1610_07159_gb300 import scenes_device
+        b = sf.Batch([(WIDTH, HEIGHT)] * 8, [LEVELS] * 8, STRIDE,
+                     sf.preset(sf.PRESET_FIG2, gn_iters=[GN], pcg_iters=[PCG]))
+        b.set_schedule(8, 1)
+        v = [scenes_device.frames(scenes.SceneVideo(WIDTH, HEIGHT, 2, seed=5000 + i), 2, dev, dtype=torch.float32)
+             for i in range(8)]
+        o = torch.empty(b.out_total, device=dev, dtype=torch.float32)
+        for f in range(2):
+            b.solve(b.pack([x[f] for x in v]), o)
+        torch.cuda.synchronize()
+        print(json.dumps({"arm": "batch8", "energy": b.sequence(0).stats().energy}), flush=True)
+        return
+    if args.arm == "train":
+        # profiling aid: two training steps of the warm-start network, batch 256
+        from paper_1610_07159_gb300 import warmstart as ws
+        net = sf.Net(256)
+        net.set_params(ws.init_params(1))
+        g = torch.Generator(device=dev)
+        g.manual_seed(7)
+        x = torch.rand(256, 4, 60, 80, device=dev, generator=g)
+        y = 0.2 * torch.randn(256, 6, 8, 10, device=dev, generator=g)
+        for _ in range(2):
+            net.train_step(x, y, 1e-3)
+        net.status()
+        print(json.dumps({"arm": "train"}), flush=True)
+        return
     video = scenes.SceneVideo(WIDTH, HEIGHT, NFRAMES, seed=100 + rank).frames()
     frames_d = torch.from_numpy(video).to(dev)  # all frames resident in HBM (147 MB)
     flush = torch.empty(64 * 1024 * 1024, device=dev, dtype=torch.float32)  # 256 MB > L2
@@ -537,8 +565,9 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the batched, mixed and warm-start variants")
-    ap.add_argument("--arm", choices=("all", "video", "frames"), default="all",
-                    help="for profiling runs: only the pipelined video arm, or only the frame-by-frame arm")
+    ap.add_argument("--arm", choices=("all", "video", "frames", "batch8", "train"), default="all",
+                    help="for profiling runs: only the pipelined video arm, only the frame-by-frame arm, one "
+                         "8-sequence batched launch pair, or two training steps of the warm-start network")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
