@@ -85,12 +85,15 @@ enum { SF_FP32 = 0, SF_MIXED_BF16 = 1, SF_MIXED_FP16 = 2 };
 /* Columns of Table 1 (Appendix A). */
 enum { SF_PRESET_FIG2 = 0, SF_PRESET_FIG568 = 1, SF_PRESET_FIG79 = 2 };
 /* Schedule of the PCG solve, per level the first that fits: SF_PCG_DSM (one
- * thread-block cluster of up to 16 CTAs holding the level's system in
- * distributed shared memory, one barrier per iteration), then SF_PCG_CLUSTER
- * (one cluster, vectors in global memory), then SF_PCG_GRID (a cooperative
- * launch over the GPU). SF_PCG_DSM starts at the first, SF_PCG_AUTO and
- * SF_PCG_CLUSTER at the second, SF_PCG_GRID takes only the last. */
-enum { SF_PCG_AUTO = 0, SF_PCG_CLUSTER = 1, SF_PCG_GRID = 2, SF_PCG_DSM = 3 };
+ * cluster, the whole state in distributed shared memory, one barrier per
+ * iteration), then a single cluster with vectors in global memory, then a
+ * cooperative launch over the GPU. SF_PCG_DSM starts at the first, the others
+ * at the second; SF_PCG_GRID takes only the last. SF_PCG_CLUSTER and
+ * SF_PCG_GRID run the textbook loop (two reductions and two barriers per
+ * iteration); SF_PCG_AUTO and SF_PCG_ONE_REDUCTION run its Chronopoulos-Gear
+ * form (the same iterates in exact arithmetic, one fused reduction and one
+ * barrier per iteration). */
+enum { SF_PCG_AUTO = 0, SF_PCG_CLUSTER = 1, SF_PCG_GRID = 2, SF_PCG_DSM = 3, SF_PCG_ONE_REDUCTION = 4 };
 /* Kernel classes, for sf_params.profile_mask and sf_kernel_times. */
 enum {
     SF_K_PYRAMID = 0,  /* mip-map levels with gradient planes */
@@ -121,7 +124,7 @@ typedef struct sf_params {
     int max_backtracks;           /* step halvings tried before a step is rejected (4) */
     int use_graph;                /* 1: replay the frame as one captured CUDA graph */
     int profile_mask;             /* bit k set: time every launch of kernel class k with CUDA events */
-    int pcg_mode;                 /* SF_PCG_AUTO | SF_PCG_CLUSTER | SF_PCG_GRID | SF_PCG_DSM */
+    int pcg_mode;                 /* SF_PCG_AUTO | _CLUSTER | _GRID | _DSM | _ONE_REDUCTION */
     int video;                    /* 1: allocate the level pipeline of sf_solve_video */
 } sf_params;
 

@@ -31,6 +31,7 @@ struct LevelBuf {
     float *prev_delta = nullptr, *prev_total = nullptr;
     float *node = nullptr, *rhs = nullptr, *minv = nullptr;
     float *z = nullptr, *p0 = nullptr, *p1 = nullptr;
+    float* pub = nullptr; // one-reduction PCG: [2][r, w, s][6][G]
     float* cell = nullptr;
 };
 
@@ -262,7 +263,7 @@ int enqueue_level(sf_ctx* c, int l, const LevelIO& io, cudaStream_t st, int& nl)
                       st);
         prof_mark(c, SF_K_GATHER, false, st);
         prof_mark(c, SF_K_PCG, true, st);
-        cudaError_t e = launch_pcg(g, c->plan[l], b.node, b.rhs, b.minv, b.x, b.z, b.p0, b.p1, c->pcg_part[l],
+        cudaError_t e = launch_pcg(g, c->plan[l], b.node, b.rhs, b.minv, b.x, b.z, b.p0, b.p1, b.pub, c->pcg_part[l],
                                    c->bar + l, c->status, P.pcg_iters[l], 0, st);
         prof_mark(c, SF_K_PCG, false, st);
         if (e != cudaSuccess) return check_cuda(e);
@@ -563,7 +564,7 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
         p->grad_mode < 0 || p->grad_mode > 1 || p->wfeat_mode < 0 || p->wfeat_mode > 1 || p->temporal_mode < 0 ||
         p->temporal_mode > 2 || p->precision < SF_FP32 || p->precision > SF_MIXED_FP16 || !(p->wfeat_tau > 0.f) ||
         p->pcg_mode < 0 ||
-        p->pcg_mode > 3) {
+        p->pcg_mode > 4) {
         fail(SF_ERR_ARG);
         return nullptr;
     }
@@ -632,7 +633,7 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
              dalloc(c, &b.delta, G6) && dalloc(c, &b.x, G6) && dalloc(c, &b.wf, (size_t)g.G) &&
              dalloc(c, &b.prev_delta, G6) && dalloc(c, &b.prev_total, G6) &&
              dalloc(c, &b.node, (size_t)NODE_VALS * g.G) && dalloc(c, &b.rhs, G6) && dalloc(c, &b.minv, G6) &&
-             dalloc(c, &b.z, G6) && dalloc(c, &b.p0, G6) && dalloc(c, &b.p1, G6) &&
+             dalloc(c, &b.z, G6) && dalloc(c, &b.p0, G6) && dalloc(c, &b.p1, G6) && dalloc(c, &b.pub, 6 * G6) &&
              dalloc(c, &b.cell, (size_t)CELL_VALS * (g.ncx * g.ncy));
     }
     const size_t N0 = (size_t)width * height;
@@ -957,7 +958,7 @@ int sf_probe_pcg(sf_ctx* c, int level, int iters, float* x, void* stream)
     c->last_stream = st;
     const LevelGeom& g = c->geo[level];
     LevelBuf& b = c->lv[level];
-    int rc = check_cuda(launch_pcg(g, c->plan[level], b.node, b.rhs, b.minv, x, b.z, b.p0, b.p1,
+    int rc = check_cuda(launch_pcg(g, c->plan[level], b.node, b.rhs, b.minv, x, b.z, b.p0, b.p1, b.pub,
                                    c->pcg_part[level], c->bar + level, c->status, iters, 1, st));
     return rc ? fail(rc) : SF_OK;
 }

@@ -5,12 +5,14 @@
 //   C[M, N] = A[M, K] * B[N, K]^T      (both operands K-major, K % 64 == 0)
 //
 // One CTA of four warps computes a 128 x BN tile (BN <= 256, a multiple of
-// 16) over a range of K: per 64-wide K chunk the warps stage the A and B
-// tiles in shared memory in the tensor core's K-major layout without
-// swizzling (8-row x 16-byte core matrices, contiguous along K), one thread
-// issues four 128 x BN x 16 MMAs into a tensor-memory accumulator and commits
-// them to an mbarrier, and the next chunk is staged once the barrier reports
-// the MMAs done. The epilogue reads the accumulator lane by lane
+// 16) over a range of K: per 64-wide K chunk the warps copy the A and B tiles
+// into shared memory (cp.async, 16 bytes per copy, rows past the matrix
+// zero-filled) in the tensor core's K-major layout without swizzling (8-row x
+// 16-byte core matrices, contiguous along K), and one thread issues four
+// 128 x BN x 16 MMAs into a tensor-memory accumulator and commits them to the
+// stage's mbarrier. Two stages alternate: chunk k + 1 is copied while the
+// MMAs of chunk k run, and a stage is refilled once its mbarrier reports the
+// MMAs that read it done. The epilogue reads the accumulator lane by lane
 // (tcgen05.ld, warp w owns rows 32w .. 32w + 31) and applies one of the
 // epilogues below. Split-K (grid.y) writes FP32 partial products that a
 // fixed-order reduction sums, so results do not depend on scheduling.
@@ -36,35 +38,47 @@ constexpr uint32_t SBO = 8 * LBO;        // next 8-row group
 // byte offset of (row r, 16-byte vector v) of a tile in the K-major layout
 __device__ __forceinline__ uint32_t tile_off(int r, int v) { return (uint32_t)((r >> 3) * SBO + v * LBO + (r & 7) * 16); }
 
-// Stages rows [r0, r0 + rows) x K chunk kc of a row-major BF16 matrix; rows
-// at or past nrows are zero.
-__device__ __forceinline__ void stage(uint8_t* tile, const __nv_bfloat16* src, int ld, int r0, int rows, int nrows,
-                                      int kc)
+// Starts the copies of rows [r0, r0 + rows) x K chunk kc of a row-major BF16
+// matrix into a tile; rows at or past nrows are zero-filled.
+__device__ __forceinline__ void stage_async(uint32_t tile, const __nv_bfloat16* src, int ld, int r0, int rows, int nrows,
+                                            int kc)
 {
     for (int i = threadIdx.x; i < rows * 8; i += GT) {
         const int r = i >> 3, v = i & 7;
-        uint4 val = make_uint4(0u, 0u, 0u, 0u);
-        if (r0 + r < nrows) val = *reinterpret_cast<const uint4*>(src + (size_t)(r0 + r) * ld + kc * BK + v * 8);
-        *reinterpret_cast<uint4*>(tile + tile_off(r, v)) = val;
+        const bool ok = r0 + r < nrows;
+        const __nv_bfloat16* g = ok ? src + (size_t)(r0 + r) * ld + kc * BK + v * 8 : src;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tile + tile_off(r, v)), "l"(g),
+                     "r"(ok ? 16 : 0)
+                     : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 template <int EPI>
 __global__ void __launch_bounds__(GT, 1) k_gemm(GemmArgs a)
 {
     extern __shared__ uint8_t dsm[];
-    // A tile (16 KiB) then B tile (up to 32 KiB), 128-byte aligned
-    uint8_t* sA = dsm + ((128u - (tc::smem_u32(dsm) & 127u)) & 127u);
-    uint8_t* sB = sA + BM * BK * 2;
-    __shared__ __align__(8) uint64_t mbar;
+    // two stages, each an A tile (16 KiB) and a B tile (up to 32 KiB), 128-byte aligned
+    uint8_t* base = dsm + ((128u - (tc::smem_u32(dsm) & 127u)) & 127u);
+    constexpr uint32_t A_BYTES = BM * BK * 2, STAGE_BYTES = A_BYTES + 256 * BK * 2;
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.z * a.BN, split = blockIdx.y;
     const int bn = min(a.BN, a.N - n0); // a multiple of 16
     const uint32_t ncols = bn <= 32 ? 32u : bn <= 64 ? 64u : bn <= 128 ? 128u : 256u;
-    const uint32_t mbar_s = tc::smem_u32(&mbar);
+    const uint32_t mb[2] = {tc::smem_u32(&mbar[0]), tc::smem_u32(&mbar[1])};
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_sh), ncols);
-    if (tid == 0) tc::mbar_init(mbar_s, 1);
+    if (tid == 0) {
+        tc::mbar_init(mb[0], 1);
+        tc::mbar_init(mb[1], 1);
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -72,27 +86,41 @@ __global__ void __launch_bounds__(GT, 1) k_gemm(GemmArgs a)
     const uint32_t idesc = tc::idesc_bf16_f32(BM, bn);
     const int nkc = a.K / BK;
     const int kc0 = split * a.kc_per_split, kc1 = min(nkc, kc0 + a.kc_per_split);
-    const uint32_t sa = tc::smem_u32(sA), sb = tc::smem_u32(sB);
+    const uint32_t st0 = tc::smem_u32(base);
 
-    uint32_t parity = 0;
-    bool pending = false, failed = false, issued = false;
-    auto wait_pending = [&]() -> bool {
-        const bool w = tc::mbar_wait(mbar_s, parity);
+    uint32_t parity[2] = {0u, 0u};
+    bool pending[2] = {false, false};
+    bool failed = false, issued = false;
+    auto wait_stage = [&](int s) -> bool {
+        const bool w = tc::mbar_wait(mb[s], parity[s]);
         const bool any_fail = __syncthreads_or(!w) != 0;
         if (!any_fail) {
-            parity ^= 1u;
-            pending = false;
+            parity[s] ^= 1u;
+            pending[s] = false;
         }
         return !any_fail;
     };
+    if (kc0 < kc1) {
+        stage_async(st0, a.A, a.lda, m0, BM, a.M, kc0);
+        stage_async(st0 + A_BYTES, a.B, a.ldb, n0, bn, a.N, kc0);
+    }
     for (int kc = kc0; kc < kc1; ++kc) {
-        if (pending && !wait_pending()) {
-            failed = true;
-            break;
+        const int s = (kc - kc0) & 1;
+        const uint32_t sa = st0 + (uint32_t)s * STAGE_BYTES, sb = sa + A_BYTES;
+        if (kc + 1 < kc1) {
+            // the other stage is free once the MMAs of chunk kc - 1 are done
+            if (pending[s ^ 1] && !wait_stage(s ^ 1)) {
+                failed = true;
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t na = st0 + (uint32_t)(s ^ 1) * STAGE_BYTES;
+            stage_async(na, a.A, a.lda, m0, BM, a.M, kc + 1);
+            stage_async(na + A_BYTES, a.B, a.ldb, n0, bn, a.N, kc + 1);
+            cp_async_wait<2>(); // this thread's copies of chunk kc are in
+        } else {
+            cp_async_wait<0>();
         }
-        tc::fence_after_sync();
-        stage(sA, a.A, a.lda, m0, BM, a.M, kc);
-        stage(sB, a.B, a.ldb, n0, bn, a.N, kc);
         tc::fence_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -101,13 +129,17 @@ __global__ void __launch_bounds__(GT, 1) k_gemm(GemmArgs a)
             for (int j = 0; j < BK / 16; ++j)
                 tc::mma_bf16(tbase, tc::smem_desc(sa + 256u * j, LBO, SBO), tc::smem_desc(sb + 256u * j, LBO, SBO),
                              idesc, (kc > kc0 || j > 0) ? 1u : 0u);
-            tc::mma_commit(mbar_s);
+            tc::mma_commit(mb[s]);
         }
-        pending = true;
+        pending[s] = true;
         issued = true;
     }
-    if (!failed && pending && !wait_pending()) failed = true;
-    if (failed && pending) wait_pending(); // the MMAs still in flight, once more
+    cp_async_wait<0>(); // no copy outlives the loop
+    for (int s = 0; s < 2; ++s)
+        if (!failed && pending[s] && !wait_stage(s)) failed = true;
+    if (failed)
+        for (int s = 0; s < 2; ++s)
+            if (pending[s]) wait_stage(s); // the MMAs still in flight, once more
     tc::fence_after_sync();
 
     if (!failed) {
@@ -161,7 +193,7 @@ int gemm_check(const GemmArgs& a)
     return SF_OK;
 }
 
-constexpr int GEMM_SMEM = BM * BK * 2 + 256 * BK * 2 + 128;
+constexpr int GEMM_SMEM = 2 * (BM * BK * 2 + 256 * BK * 2) + 128;
 
 template <int EPI>
 void launch_epi(const GemmArgs& a, dim3 grid, cudaStream_t st)

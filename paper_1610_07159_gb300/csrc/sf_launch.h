@@ -60,12 +60,13 @@ struct PcgPlan {
     int blocks;  // CTAs of the launch
     int npt;     // nodes per four-lane group
     int cluster; // 2: one cluster, state in distributed shared memory;
-                 // 1: one cluster, vectors in global memory; 0: cooperative grid
+                 // 1: one cluster, vectors in global memory; 0: cooperative grid;
+                 // 3 / 4: grid / one cluster with one reduction per iteration
     int npc;     // nodes per CTA (cluster == 2)
 };
 PcgPlan pcg_plan(int G, int sm_count, int mode);
 cudaError_t launch_pcg(const LevelGeom& g, const PcgPlan& plan, const float* node, const float* rhs,
-                       const float* minv, float* x, float* z, float* p0, float* p1, float2* part,
+                       const float* minv, float* x, float* z, float* p0, float* p1, float* pub, float2* part,
                        unsigned long long* bar, int* status, int iters, int interleaved_out, cudaStream_t st);
 
 // sf_batch.cu: the frame solve of many independent sequences in one launch,

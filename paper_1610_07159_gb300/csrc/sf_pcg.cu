@@ -539,6 +539,238 @@ cudaError_t launch_grid(int blocks, const LevelGeom& g, const float* node, const
     return cudaLaunchCooperativeKernel((const void*)k_pcg<NPT, GridSync>, dim3(blocks), dim3(PT), args, 0, st);
 }
 
+// ---------------------------------------------------------------------------
+// PCG with one reduction per iteration (the Chronopoulos-Gear form: the same
+// iterates as the textbook loop in exact arithmetic), over the whole GPU or
+// one cluster, vectors in global memory. With u = M r and w = A u, the two
+// dot products gamma = r.u and delta = w.u come from one fused reduction;
+// every node publishes r, w and s = A p in one of two buffers (by iteration
+// parity), and a neighbour's u_{i+1} = M (r_i - alpha (w_i + beta s_{i-1}))
+// is formed on the fly from its published r_i, w_i and s_{i-1}. An iteration
+// has one matrix-vector product and one barrier, against two for k_pcg.
+// pub holds [2 parities][r, w, s][6][G].
+// ---------------------------------------------------------------------------
+template <class Sync>
+__device__ __forceinline__ void allreduce2(float a, float b, ff* sh, float2* part, int parity, Sync& sy,
+                                           unsigned long long* bar, int* status, bool& ok, ff& ra, ff& rb)
+{
+    __shared__ ff bc[2];
+    const int nb = gridDim.x;
+    float2* pa = part + (size_t)parity * 2 * nb;
+    float2* pb = pa + nb;
+    const ff sa = ff_block_sum_fast<PT>(a, sh);
+    const ff sb = ff_block_sum_fast<PT>(b, sh);
+    if (threadIdx.x == 0) {
+        pa[blockIdx.x] = make_float2(sa.hi, sa.lo);
+        pb[blockIdx.x] = make_float2(sb.hi, sb.lo);
+    }
+    ok = sy.sync(bar, status) && ok;
+    if (threadIdx.x < 32) {
+        const ff ta = ff_fixed_sum(pa, nb);
+        const ff tb = ff_fixed_sum(pb, nb);
+        if (threadIdx.x == 0) {
+            bc[0] = ta;
+            bc[1] = tb;
+        }
+    }
+    __syncthreads();
+    ra = bc[0];
+    rb = bc[1];
+    __syncthreads();
+}
+
+template <int NPT, class Sync>
+__global__ void __launch_bounds__(PT) k_pcg1(LevelGeom g, const float* __restrict__ node, const float* __restrict__ rhs,
+                                             const float* __restrict__ minv, float* __restrict__ xout, float* pub,
+                                             float2* part, unsigned long long* bar, int* status, int iters,
+                                             int interleaved, Sync sy)
+{
+    __shared__ ff sred[PT / 32];
+    sy.start(bar);
+    const int G = g.G, nx = g.nx, ny = g.ny;
+    const size_t G6 = (size_t)6 * G;
+    const int q4 = threadIdx.x & 3;
+    const int c0 = q4, c1 = q4 + 4;
+    const bool has1 = c1 < 6;
+    const int stride = gridDim.x * NPB;
+    const int slot0 = blockIdx.x * NPB + (threadIdx.x >> 2);
+    float xr[NPT][2], rr[NPT][2], ur[NPT][2], wr[NPT][2], sr[NPT][2], pr[NPT][2], mr[NPT][2];
+    int ni[NPT], nj[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int n = slot0 + k * stride;
+        nj[k] = n / nx;
+        ni[k] = n - nj[k] * nx;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = h ? c1 : c0;
+            const bool live = n < G && (h == 0 || has1);
+            const float r0 = live ? rhs[c * G + n] : 0.f;
+            mr[k][h] = live ? minv[c * G + n] : 0.f;
+            rr[k][h] = r0;
+            ur[k][h] = mr[k][h] * r0;
+            xr[k][h] = wr[k][h] = sr[k][h] = pr[k][h] = 0.f;
+            if (live) {
+                pub[0 * G6 + c * G + n] = r0;  // r_0 in buffer 0
+                pub[2 * G6 + c * G + n] = 0.f; // s_{-1} = 0
+            }
+        }
+    }
+    bool ok = sy.sync(bar, status);
+    float alpha = 0.f, beta = 0.f;
+    ff gam{0.f, 0.f};
+    int nred = 0;
+    for (int i = -1; i < iters && ok; ++i) {
+        // i = -1 is the set-up pass: w_0 = A u_0 and the first reduction
+        const int par = i < 0 ? 0 : (i & 1);
+        const int npar = i < 0 ? 0 : (par ^ 1);
+        const float* R = pub + (size_t)par * 3 * G6;
+        const float* Wv = R + G6;
+        const float* S = R + 2 * G6;
+        float* Rn = pub + (size_t)npar * 3 * G6;
+        float* Wn = Rn + G6;
+        float* Sn = Rn + 2 * G6;
+        if (i >= 0) {
+#pragma unroll
+            for (int k = 0; k < NPT; ++k)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    pr[k][h] = fmaf(beta, pr[k][h], ur[k][h]);
+                    sr[k][h] = fmaf(beta, sr[k][h], wr[k][h]);
+                    xr[k][h] = fmaf(alpha, pr[k][h], xr[k][h]);
+                    rr[k][h] = fmaf(-alpha, sr[k][h], rr[k][h]);
+                    ur[k][h] = mr[k][h] * rr[k][h];
+                }
+            if (i == iters - 1) break;
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int n = slot0 + k * stride;
+                if (n >= G) continue;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (!(h == 0 || has1)) continue;
+                    const int c = h ? c1 : c0;
+                    Rn[c * G + n] = rr[k][h];
+                    Sn[c * G + n] = sr[k][h];
+                }
+            }
+        }
+        float gp = 0.f, dp = 0.f;
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            const int n = slot0 + k * stride;
+            const bool live = n < G;
+            float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (live) {
+                const int ii = ni[k], jj = nj[k];
+#pragma unroll
+                for (int ss = 0; ss < 3; ++ss) {
+                    const int s = ss == 2 ? 8 : q4 + 4 * ss;
+                    if (ss == 2 && q4 != 0) continue;
+                    int owner, blk, pn;
+                    if (!stencil_slot(s, ii, jj, nx, ny, n, owner, blk, pn)) continue;
+                    float B[NB], u[6];
+#pragma unroll
+                    for (int e = 0; e < NB; ++e) B[e] = __ldg(node + (size_t)(blk * NB + e) * G + owner);
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        const float mm = __ldg(minv + c * G + pn);
+                        const float rv = __ldcg(R + c * G + pn);
+                        if (i >= 0) {
+                            const float wv = __ldcg(Wv + c * G + pn), sv = __ldcg(S + c * G + pn);
+                            u[c] = mm * fmaf(-alpha, fmaf(beta, sv, wv), rv);
+                        } else {
+                            u[c] = mm * rv;
+                        }
+                    }
+                    sym_matvec_acc(B, u, q);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                q[c] += __shfl_xor_sync(0xffffffffu, q[c], 1);
+                q[c] += __shfl_xor_sync(0xffffffffu, q[c], 2);
+            }
+            if (live) {
+                wr[k][0] = sel6(q, c0);
+                wr[k][1] = has1 ? sel6(q, c1) : 0.f;
+                Wn[c0 * G + n] = wr[k][0];
+                if (has1) Wn[c1 * G + n] = wr[k][1];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    gp = fmaf(rr[k][h], ur[k][h], gp);
+                    dp = fmaf(wr[k][h], ur[k][h], dp);
+                }
+            }
+        }
+        ff G2, D2;
+        allreduce2(gp, dp, sred, part, nred & 1, sy, bar, status, ok, G2, D2);
+        ++nred;
+        if (!ok) break;
+        if (i < 0) {
+            if (!(G2.hi > 1e-30f) || !(D2.hi > 1e-30f)) break; // x stays 0
+            alpha = G2.hi / D2.hi;
+            beta = 0.f;
+        } else {
+            const float bnew = G2.hi / gam.hi;
+            const float pap = D2.hi - bnew * G2.hi / alpha;
+            if (!(G2.hi > 1e-30f) || !(pap > 1e-30f)) break;
+            beta = bnew;
+            alpha = G2.hi / pap;
+        }
+        gam = G2;
+    }
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int n = slot0 + k * stride;
+        if (n >= G) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!(h == 0 || has1)) continue;
+            const int c = h ? c1 : c0;
+            if (interleaved)
+                xout[n * 6 + c] = xr[k][h];
+            else
+                xout[c * G + n] = xr[k][h];
+        }
+    }
+}
+
+template <int NPT>
+cudaError_t launch_grid1(int blocks, const LevelGeom& g, const float* node, const float* rhs, const float* minv,
+                         float* x, float* pub, float2* part, unsigned long long* bar, int* status, int iters,
+                         int interleaved, cudaStream_t st)
+{
+    LevelGeom gg = g;
+    GridSync sy{0ull};
+    void* args[] = {(void*)&gg, (void*)&node, (void*)&rhs, (void*)&minv, (void*)&x, (void*)&pub, (void*)&part,
+                    (void*)&bar, (void*)&status, (void*)&iters, (void*)&interleaved, (void*)&sy};
+    return cudaLaunchCooperativeKernel((const void*)k_pcg1<NPT, GridSync>, dim3(blocks), dim3(PT), args, 0, st);
+}
+
+template <int NPT>
+cudaError_t launch_cluster1(int blocks, const LevelGeom& g, const float* node, const float* rhs, const float* minv,
+                            float* x, float* pub, float2* part, unsigned long long* bar, int* status, int iters,
+                            int interleaved, cudaStream_t st)
+{
+    auto kern = k_pcg1<NPT, ClusterSync>;
+    if (blocks > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(PT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = blocks;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, g, node, rhs, minv, x, pub, part, bar, status, iters, interleaved,
+                              ClusterSync{});
+}
+
 int max_coop_blocks(int sm_count)
 {
     int per_sm = 0;
@@ -609,13 +841,15 @@ PcgPlan pcg_plan(int G, int sm_count, int mode)
             }
         }
     }
+    // AUTO takes the one-reduction form (measured faster at every level size)
+    const bool one = mode == SF_PCG_ONE_REDUCTION || mode == SF_PCG_AUTO;
     if (mode != SF_PCG_GRID) {
         for (int npt : {1, 2, 4}) {
             const int need = (G + NPB * npt - 1) / (NPB * npt);
             if (need <= maxc) {
                 p.blocks = need < 1 ? 1 : need;
                 p.npt = npt;
-                p.cluster = 1;
+                p.cluster = one ? 4 : 1;
                 return p;
             }
         }
@@ -627,7 +861,7 @@ PcgPlan pcg_plan(int G, int sm_count, int mode)
         if (need <= cap) {
             p.blocks = need < 1 ? 1 : need;
             p.npt = npt;
-            p.cluster = 0;
+            p.cluster = one ? 3 : 0;
             return p;
         }
     }
@@ -636,9 +870,20 @@ PcgPlan pcg_plan(int G, int sm_count, int mode)
 }
 
 cudaError_t launch_pcg(const LevelGeom& g, const PcgPlan& plan, const float* node, const float* rhs, const float* minv,
-                       float* x, float* z, float* p0, float* p1, float2* part, unsigned long long* bar, int* status,
-                       int iters, int interleaved_out, cudaStream_t st)
+                       float* x, float* z, float* p0, float* p1, float* pub, float2* part, unsigned long long* bar,
+                       int* status, int iters, int interleaved_out, cudaStream_t st)
 {
+    if (plan.cluster == 3 || plan.cluster == 4) {
+        const bool grid = plan.cluster == 3;
+        switch (plan.npt) {
+        case 1: return grid ? launch_grid1<1>(plan.blocks, g, node, rhs, minv, x, pub, part, bar, status, iters, interleaved_out, st)
+                            : launch_cluster1<1>(plan.blocks, g, node, rhs, minv, x, pub, part, bar, status, iters, interleaved_out, st);
+        case 2: return grid ? launch_grid1<2>(plan.blocks, g, node, rhs, minv, x, pub, part, bar, status, iters, interleaved_out, st)
+                            : launch_cluster1<2>(plan.blocks, g, node, rhs, minv, x, pub, part, bar, status, iters, interleaved_out, st);
+        default: return grid ? launch_grid1<4>(plan.blocks, g, node, rhs, minv, x, pub, part, bar, status, iters, interleaved_out, st)
+                             : launch_cluster1<4>(plan.blocks, g, node, rhs, minv, x, pub, part, bar, status, iters, interleaved_out, st);
+        }
+    }
     if (plan.cluster == 2) {
         switch (plan.npt) {
         case 1: return launch_dsm<1>(plan.blocks, plan.npc, g, node, rhs, minv, x, iters, interleaved_out, st);

@@ -103,7 +103,7 @@ def test_assemble_parity(w, h, s_, level, kw):
 
 
 @pytest.mark.parametrize("iters,mode", [(1, 0), (5, 0), (20, 0), (20, sf.PCG_CLUSTER), (20, sf.PCG_GRID),
-                                        (1, sf.PCG_DSM), (20, sf.PCG_DSM)])
+                                        (1, sf.PCG_DSM), (20, sf.PCG_DSM), (1, sf.PCG_ONE_REDUCTION), (20, sf.PCG_ONE_REDUCTION)])
 def test_pcg_parity_on_the_same_system(iters, mode):
     solver, lv, op = _level_setup(160, 120, 4, 3, 0, pcg_mode=mode)
     rng = np.random.default_rng(3)
@@ -115,6 +115,21 @@ def test_pcg_parity_on_the_same_system(iters, mode):
     x_ref, _, its = O.pcg(lv.nx, lv.ny, A, rhs.cpu().numpy().astype(np.float64), iters)
     assert its == iters
     assert rel_max(x_gpu, x_ref) < 2e-4 * iters
+
+
+@pytest.mark.parametrize("mode", [sf.PCG_GRID, sf.PCG_ONE_REDUCTION])
+def test_pcg_parity_grid_schedule_on_a_level_larger_than_a_cluster(mode):
+    """640x480 level 0 (4800 nodes) takes the cooperative-grid schedule."""
+    solver, lv, op = _level_setup(640, 480, 8, 4, 0, pcg_mode=mode)
+    rng = np.random.default_rng(4)
+    base, delta = _smooth_state(lv.G, rng)
+    wf = np.ones(lv.G, dtype=np.float32)
+    blocks, rhs, _, _ = solver.probe_assemble(0, _dev(base), _dev(delta), _dev(wf))
+    x_gpu = solver.probe_pcg(0, 20).cpu().numpy()
+    A = lib_blocks_to_oracle(blocks.cpu().numpy().astype(np.float64), lv.nx, lv.ny)
+    x_ref, _, its = O.pcg(lv.nx, lv.ny, A, rhs.cpu().numpy().astype(np.float64), 20)
+    assert its == 20
+    assert rel_max(x_gpu, x_ref) < 2e-4 * 20
 
 
 def test_energy_parity_with_given_and_computed_W():
@@ -190,7 +205,8 @@ def test_config1_frame_parity():
 
 @pytest.mark.parametrize("kw", [{"robust_mode": O.SQRT_PAPER}, {"grad_mode": O.GRAD_LITERAL},
                                 {"wfeat_mode": O.WFEAT_OFF, "eps_p": 0.0}, {"use_graph": 0},
-                                {"pcg_mode": sf.PCG_GRID}, {"pcg_mode": sf.PCG_CLUSTER}, {"pcg_mode": sf.PCG_DSM}])
+                                {"pcg_mode": sf.PCG_GRID}, {"pcg_mode": sf.PCG_CLUSTER}, {"pcg_mode": sf.PCG_DSM},
+                                {"pcg_mode": sf.PCG_ONE_REDUCTION}])
 def test_config1_frame_parity_modes(kw):
     q = scenes.plane_quadruple(seed=2)
     for r in _solve_both(q, 4, 3, [5], [10], **kw):
