@@ -371,6 +371,8 @@ def run_ours(args):
     # headline: the level-pipelined video solve, one step = one pass over the 30 frames
     solver = sf.Solver(WIDTH, HEIGHT, STRIDE, LEVELS,
                        sf.preset(sf.PRESET_FIG2, gn_iters=[GN], pcg_iters=[PCG], profile_mask=prof, video=1))
+    # set-up, outside the timed region: the PCG schedule of every level, picked by timing
+    pcg_schedules = solver.tune_pcg(frames_d[0])
     _, _, nx, ny = solver.dims(0)
     outs = torch.empty((NFRAMES, 6, ny, nx), device=dev, dtype=torch.float32)
     acc = {"ms": 0.0, sf.K_PCG: [0.0, 0], sf.K_ASSEMBLE: [0.0, 0]}
@@ -422,6 +424,7 @@ def run_ours(args):
 
     # plain FP32 frame by frame (one captured graph per frame), for comparison
     plain = sf.Solver(WIDTH, HEIGHT, STRIDE, LEVELS, sf.preset(sf.PRESET_FIG2, gn_iters=[GN], pcg_iters=[PCG]))
+    plain.tune_pcg(frames_d[0])  # the tuned schedules, from the per-process cache
     out1 = torch.empty((6, ny, nx), device=dev, dtype=torch.float32)
     passes = max(1, args.steps // 4)
     plain_ms, same = 0.0, True
@@ -445,6 +448,7 @@ def run_ours(args):
     host_outs = torch.empty((NFRAMES, 6, ny, nx), dtype=torch.float32).pin_memory()
     solver_e2e = sf.Solver(WIDTH, HEIGHT, STRIDE, LEVELS,
                            sf.preset(sf.PRESET_FIG2, gn_iters=[GN], pcg_iters=[PCG], video=1))
+    solver_e2e.tune_pcg(frames_d[0])
     for _ in range(args.warmup):
         solver_e2e.reset()
         solver_e2e.solve_video_host(host_frames, host_outs)
@@ -505,6 +509,8 @@ def run_ours(args):
         "gpu_launches": st.launches * frames_timed,
         "clocks": clk,
         "variants": {"frame_by_frame_graph_fps": plain_fps, "video_pipeline_fps": value,
+                     "pcg_schedules": [{"level": l, "kind": k, "ctas": b, "nodes_per_group": t}
+                                       for l, (k, b, t) in enumerate(pcg_schedules)],
                      "fields_identical": bool(same),
                      "note": "same FP32 kernels; the pipeline overlaps the levels of consecutive frames"},
         "energy_last_frame": st.energy,

@@ -206,6 +206,21 @@ SF_API int sf_get_stats(sf_ctx* ctx, sf_stats* out);
  * device buffers (6 x G floats each; either may be NULL). */
 SF_API int sf_get_state(sf_ctx* ctx, int level, float* delta, float* total, void* stream);
 
+/* PCG schedule autotuner: solves one frame of the given quadruple (device
+ * pointers), then times every PCG schedule that can run each level (one
+ * cluster or the whole GPU, one or two reductions per iteration, 1-4 nodes
+ * per four-lane group, distributed shared memory) on that level's last
+ * Gauss-Newton system, `reps` launches each after one warm-up, and keeps the
+ * fastest per level. Results are cached per process by the level's grid size,
+ * iteration count and SM count. Leaves the context reset (the next solve is a
+ * first frame) and captures the frame graph again on the next solve. */
+SF_API int sf_tune_pcg(sf_ctx* ctx, const float* L_t, const float* R_t, const float* L_t1, const float* R_t1, int reps,
+                       void* stream);
+/* The PCG schedule of a level: kind 0 grid / 1 cluster (two reductions per
+ * iteration), 3 grid / 4 cluster (one reduction), 2 distributed shared
+ * memory; CTAs; nodes per four-lane group. */
+SF_API int sf_pcg_schedule(const sf_ctx* ctx, int level, int* kind, int* blocks, int* npt);
+
 /* Device time of kernel class `klass` in the last frame: the sum over its
  * launches (ms) and their number. Needs the class in profile_mask; waits for
  * the context's work. */

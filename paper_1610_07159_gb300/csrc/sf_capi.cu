@@ -417,6 +417,7 @@ struct BatchSchedule {
 
 std::mutex g_tune_mu;
 std::map<std::string, BatchSchedule> g_tune_cache; // per process: shape key -> chosen schedule
+std::map<std::string, PcgPlan> g_pcg_tune;          // per process: level shape -> fastest PCG schedule
 
 void batch_free(sf_batch* b)
 {
@@ -1364,6 +1365,88 @@ int sf_warm_start(sf_net* n, sf_ctx* c, const float* L_t, const float* R_t, cons
     rc = net_forward(n->p, in, (long long)4 * NET_IN_H * NET_IN_W, (long long)NET_IN_H * NET_IN_W, 1, c->init_buf, st);
     if (rc) return fail(rc);
     c->pending_init = 1;
+    return SF_OK;
+}
+
+int sf_tune_pcg(sf_ctx* c, const float* L_t, const float* R_t, const float* L_t1, const float* R_t1, int reps,
+                void* stream)
+{
+    if (!c || !L_t || !R_t || !L_t1 || !R_t1 || reps < 1) return fail(SF_ERR_ARG);
+    cudaStream_t st = (cudaStream_t)stream;
+    // one frame leaves every level's last Gauss-Newton system in place
+    float* out = c->out_buf;
+    int rc = sf_solve(c, L_t, R_t, L_t1, R_t1, out, stream);
+    if (rc) return rc;
+    rc = check_cuda(cudaStreamSynchronize(st));
+    if (rc) return fail(rc);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(check_cuda(cudaErrorUnknown));
+    for (int l = 0; l < c->L && !rc; ++l) {
+        const LevelGeom& g = c->geo[l];
+        LevelBuf& b = c->lv[l];
+        const int iters = c->prm.pcg_iters[l];
+        if (iters < 1) continue;
+        const std::string key = std::to_string(g.nx) + "x" + std::to_string(g.ny) + "|" + std::to_string(iters) + "|" +
+                                std::to_string(c->sm_count);
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_pcg_tune.find(key);
+            if (it != g_pcg_tune.end()) {
+                c->plan[l] = it->second;
+                continue;
+            }
+        }
+        PcgPlan cand[16];
+        const int nc = pcg_candidates(g.G, c->sm_count, cand, 16);
+        float best = -1.f;
+        PcgPlan pick = c->plan[l];
+        for (int k = 0; k < nc && !rc; ++k) {
+            // a new block count starts its barrier counter from zero
+            rc = check_cuda(cudaMemsetAsync(c->bar + l, 0, sizeof(unsigned long long), st));
+            if (rc) break;
+            float ms = 0.f;
+            for (int r = 0; r <= reps && !rc; ++r) {
+                if (r == 1) cudaEventRecord(e0, st);
+                rc = check_cuda(launch_pcg(g, cand[k], b.node, b.rhs, b.minv, b.x, b.z, b.p0, b.p1, b.pub,
+                                           c->pcg_part[l], c->bar + l, c->status, iters, 0, st));
+            }
+            if (rc) break;
+            cudaEventRecord(e1, st);
+            rc = check_cuda(cudaEventSynchronize(e1));
+            if (!rc) rc = check_cuda(cudaEventElapsedTime(&ms, e0, e1));
+            int status = 0;
+            if (!rc) rc = check_cuda(cudaMemcpy(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+            if (!rc && status) rc = (status & DEV_TIMEOUT) ? SF_ERR_TIMEOUT : SF_ERR_NUMERIC;
+            if (!rc && (best < 0.f || ms < best)) {
+                best = ms;
+                pick = cand[k];
+            }
+        }
+        if (!rc) {
+            c->plan[l] = pick;
+            rc = check_cuda(cudaMemsetAsync(c->bar + l, 0, sizeof(unsigned long long), st));
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_pcg_tune[key] = pick;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(st));
+    // the frame graph holds the old schedules: capture again on the next solve
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->graph_tried = false;
+    int rc2 = sf_reset(c);
+    return rc ? fail(rc) : rc2;
+}
+
+int sf_pcg_schedule(const sf_ctx* c, int level, int* kind, int* blocks, int* npt)
+{
+    if (!c || level < 0 || level >= c->L) return fail(SF_ERR_ARG);
+    const PcgPlan& p = c->plan[level];
+    if (kind) *kind = p.cluster;
+    if (blocks) *blocks = p.blocks;
+    if (npt) *npt = p.npt;
     return SF_OK;
 }
 

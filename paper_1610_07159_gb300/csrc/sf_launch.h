@@ -65,6 +65,8 @@ struct PcgPlan {
     int npc;     // nodes per CTA (cluster == 2)
 };
 PcgPlan pcg_plan(int G, int sm_count, int mode);
+// every schedule that can run a level of G nodes (for the autotuner)
+int pcg_candidates(int G, int sm_count, PcgPlan* out, int max);
 cudaError_t launch_pcg(const LevelGeom& g, const PcgPlan& plan, const float* node, const float* rhs,
                        const float* minv, float* x, float* z, float* p0, float* p1, float* pub, float2* part,
                        unsigned long long* bar, int* status, int iters, int interleaved_out, cudaStream_t st);

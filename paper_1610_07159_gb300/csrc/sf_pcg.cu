@@ -855,7 +855,7 @@ PcgPlan pcg_plan(int G, int sm_count, int mode)
         }
     }
     int cap = max_coop_blocks(sm_count);
-    if (cap > MAX_PART) cap = MAX_PART;
+    if (cap > MAX_PART / 2) cap = MAX_PART / 2; // the one-reduction form keeps four partials per block
     for (int npt : {1, 2, 4}) {
         const int need = (G + NPB * npt - 1) / (NPB * npt);
         if (need <= cap) {
@@ -867,6 +867,39 @@ PcgPlan pcg_plan(int G, int sm_count, int mode)
     }
     p.blocks = -1; // too large for one launch
     return p;
+}
+
+int pcg_candidates(int G, int sm_count, PcgPlan* out, int max)
+{
+    int n = 0;
+    auto push = [&](PcgPlan p) {
+        if (n < max) out[n++] = p;
+    };
+    const int maxc = max_cluster_blocks();
+    int cap = max_coop_blocks(sm_count);
+    if (cap > MAX_PART / 2) cap = MAX_PART / 2;
+    for (int npt : {1, 2, 4}) {
+        const int need = std::max(1, (G + NPB * npt - 1) / (NPB * npt));
+        if (need <= maxc) {
+            push(PcgPlan{need, npt, 4, 0});
+            push(PcgPlan{need, npt, 1, 0});
+        }
+        if (need <= cap) {
+            push(PcgPlan{need, npt, 3, 0});
+            push(PcgPlan{need, npt, 0, 0});
+        }
+    }
+    const int dcap = dsm_max_npc();
+    for (int npt = 1; npt <= 3; ++npt) {
+        const int npc = std::min(CT_NPB * npt, dcap);
+        const int ctas0 = (G + npc - 1) / npc;
+        if (ctas0 <= maxc) {
+            const int even = (G + ctas0 - 1) / ctas0;
+            push(PcgPlan{(G + even - 1) / even, npt, 2, even});
+            break;
+        }
+    }
+    return n;
 }
 
 cudaError_t launch_pcg(const LevelGeom& g, const PcgPlan& plan, const float* node, const float* rhs, const float* minv,

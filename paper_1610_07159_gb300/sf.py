@@ -38,7 +38,7 @@ EXPORTED = (
     "sf_batch_get_schedule", "sf_batch_tune", "sf_batch_sequence", "sf_batch_reset", "sf_batch_destroy",
     "sf_probe_gemm_bf16", "sf_net_param_count", "sf_net_create", "sf_net_set_params", "sf_net_get_params",
     "sf_net_forward", "sf_net_gradients", "sf_net_train_step", "sf_net_status", "sf_net_destroy",
-    "sf_coarsest_images", "sf_warm_start",
+    "sf_coarsest_images", "sf_warm_start", "sf_tune_pcg", "sf_pcg_schedule",
 )
 STATIC_PCG_MAX_NODES = 4096
 
@@ -145,6 +145,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sf_net_destroy.restype = None
     L.sf_coarsest_images.argtypes = [vp, fp, fp, fp, fp, fp, vp]
     L.sf_warm_start.argtypes = [vp, vp, fp, fp, fp, fp, vp]
+    L.sf_tune_pcg.argtypes = [vp, fp, fp, fp, fp, i, vp]
+    L.sf_pcg_schedule.argtypes = [vp, i, ip, ip, ip]
     _lib = L
     return L
 
@@ -290,6 +292,20 @@ class Solver:
             raise SFError("solve_video_host takes contiguous host tensors")
         _check(self.L.sf_solve_video_host(self.ctx, frames.data_ptr(), int(frames.shape[0]), outs.data_ptr(),
                                           _stream()), "sf_solve_video_host")
+
+    def tune_pcg(self, imgs: torch.Tensor, reps: int = 5) -> list:
+        """Autotunes the PCG schedule of every level on one frame of imgs [4, h, w]; returns the schedules."""
+        base = _ptr(imgs, torch.float32)
+        n = self.width * self.height * 4
+        _check(self.L.sf_tune_pcg(self.ctx, base, base + n, base + 2 * n, base + 3 * n, int(reps), _stream()),
+               "sf_tune_pcg")
+        return [self.pcg_schedule(l) for l in range(self.levels)]
+
+    def pcg_schedule(self, level: int) -> tuple[int, int, int]:
+        k, b, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self.L.sf_pcg_schedule(self.ctx, int(level), ctypes.byref(k), ctypes.byref(b), ctypes.byref(t)),
+               "sf_pcg_schedule")
+        return k.value, b.value, t.value
 
     def set_init(self, coarsest_delta: torch.Tensor) -> None:
         _check(self.L.sf_set_init(self.ctx, _ptr(coarsest_delta, torch.float32), _stream()), "sf_set_init")

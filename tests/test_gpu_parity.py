@@ -213,6 +213,22 @@ def test_config1_frame_parity_modes(kw):
         _assert_frame_parity(*r)
 
 
+def test_pcg_autotuner_keeps_parity():
+    """The tuner picks a schedule per level by timing; every schedule runs the
+    same iterates, so the frame still matches the oracle."""
+    q = scenes.plane_quadruple(seed=3)
+    sp, op = make_params([5], [10])
+    solver = sf.Solver(160, 120, 4, 3, sp)
+    sched = solver.tune_pcg(_dev(q), reps=2)
+    assert all(k in (0, 1, 2, 3, 4) and b >= 1 and t in (1, 2, 3, 4) for k, b, t in sched)
+    fields = solver.solve(_dev(q)).cpu().numpy()
+    st = solver.stats()
+    assert st.status == sf.OK and st.frames == 1
+    ref = O.solve_frame(q.astype(np.float64), 4, 3, op, W_given=solver.wmasks())
+    own = O.solve_frame(q.astype(np.float64), 4, 3, op)
+    _assert_frame_parity(fields, st, ref, own, op, 3)
+
+
 def test_ragged_scene_parity_with_epipolar_prior():
     q = scenes.SceneVideo(150, 110, 1, seed=11, disparity=(2, 12), max_motion=4).frames(1)[0]
     for r in _solve_both(q, 4, 3, [4], [15], preset="fig568"):
