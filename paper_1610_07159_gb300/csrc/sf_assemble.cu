@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(ETHREADS, 2) k_assemble(LevelGeom g, int cpb, 
 }
 
 // Gather of the node system from the cell blocks plus the prior rows, the
-// Jacobi preconditioner, and (last block) the energy at this point.
+// Jacobi preconditioner, and (last block) the energy at this point; four
+// lanes per node.
 __global__ void __launch_bounds__(ETHREADS) k_gather(LevelGeom g, const float* __restrict__ cell,
                                                      const float* __restrict__ base, const float* __restrict__ delta,
                                                      const float* __restrict__ wf, DevParams P,
@@ -56,9 +57,10 @@ __global__ void __launch_bounds__(ETHREADS) k_gather(LevelGeom g, const float* _
 {
     __shared__ ff sred[ETHREADS / 32];
     __shared__ bool last_sh;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = t >> 2;
     float es = 0.f, ee = 0.f, em = 0.f;
-    if (n < g.G) gather_node(g, n, cell, base, delta, wf, P, node, rhs, minv, es, ee, em);
+    gather_node4(g, n < g.G ? n : g.G - 1, t & 3, n < g.G, cell, base, delta, wf, P, node, rhs, minv, es, ee, em);
     if (!ctrl) return;
     const ff ts = ff_block_sum_fast<ETHREADS>(es, sred);
     const ff te = ff_block_sum_fast<ETHREADS>(ee, sred);
@@ -248,7 +250,7 @@ void launch_gather(const LevelGeom& g, const float* cell, const float* base, con
                    const DevParams& P, float* node, float* rhs, float* minv, const Scratch& sc, StepCtrl* ctrl,
                    int n_asm_blocks, cudaStream_t st)
 {
-    const int blocks = (g.G + ETHREADS - 1) / ETHREADS;
+    const int blocks = (4 * g.G + ETHREADS - 1) / ETHREADS; // four lanes per node
     k_gather<<<blocks, ETHREADS, 0, st>>>(g, cell, base, delta, wf, P, node, rhs, minv, sc.gat_part, sc.asm_part,
                                           n_asm_blocks, sc.counters + 0, ctrl, sc.status);
 }

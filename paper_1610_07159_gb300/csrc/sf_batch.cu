@@ -328,8 +328,14 @@ __global__ void __launch_bounds__(BT, 2) k_batch_frame(const BSeq* __restrict__ 
             cluster_sync_all();
             // node system with the priors; energy at the linearisation point
             float es = 0.f, ee = 0.f, em = 0.f;
-            for (int n = gtid; n < g.G; n += gstride)
-                gather_node(g, n, B.cell, B.base, B.delta, B.wf, P, B.node, B.rhs, B.minv, es, ee, em);
+            // four lanes per node; the bound is a whole number of warps, so the
+            // lanes of a warp leave the loop together (gather_node4 shuffles)
+            const int lanes = 4 * ((g.G + 7) & ~7);
+            for (int t = gtid; t < lanes; t += gstride) {
+                const int n = t >> 2;
+                gather_node4(g, n < g.G ? n : g.G - 1, t & 3, n < g.G, B.cell, B.base, B.delta, B.wf, P, B.node,
+                             B.rhs, B.minv, es, ee, em);
+            }
             ff s6[6];
             {
                 const float v[6] = {ep, eg, (float)nex, es, ee, em};

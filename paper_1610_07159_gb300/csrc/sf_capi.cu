@@ -601,7 +601,8 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
         g.ncy = g.ny - 1;
         g.level = l;
         const int en_blocks = std::min((g.w * g.h + 255) / 256, 152 * 8) + (g.G + 255) / 256;
-        if (w < 2 || h < 2 || g.nx < 2 || g.ny < 2 || assemble_blocks(g, nullptr) > MAX_PART || en_blocks > MAX_PART) {
+        if (w < 2 || h < 2 || g.nx < 2 || g.ny < 2 || assemble_blocks(g, nullptr) > MAX_PART || en_blocks > MAX_PART ||
+            (4 * g.G + 255) / 256 > MAX_PART) {
             delete c;
             fail(SF_ERR_ARG);
             return nullptr;

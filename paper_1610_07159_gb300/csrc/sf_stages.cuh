@@ -466,39 +466,77 @@ __device__ __forceinline__ void node_prior_energy(const LevelGeom& g, const DevP
     em = m;
 }
 
-// Node n of the Gauss-Newton system: its five coupling blocks gathered from
-// the cell blocks of the (up to four) cells around it, plus the smoothness
-// (Eq. 14), epipolar (Eqs. 15-17) and magnitude (Eq. 18) rows, the
-// right-hand side and the Jacobi preconditioner; adds the node's prior
-// energies to es, ee, em.
-__device__ __forceinline__ void gather_node(const LevelGeom& g, int n, const float* cell,
-                                            const float* base, const float* delta,
-                                            const float* wf, const DevParams& P,
-                                            float* node, float* rhs,
-                                            float* minv, float& es, float& ee, float& em)
+// Node n of the Gauss-Newton system, shared by four consecutive lanes of a
+// warp (lane = lane id & 3; `live` false for the padding nodes past G, whose
+// lanes still take part in the shuffle): its five coupling blocks gathered
+// from the cell blocks of the (up to four) cells around it, plus the
+// smoothness (Eq. 14), epipolar (Eqs. 15-17) and magnitude (Eq. 18) rows, the
+// right-hand side and the Jacobi preconditioner. Lane 0 builds the node's own
+// block, the prior rows and the preconditioner and adds the node's prior
+// energies to es, ee, em; lane 1 the E block, lane 2 the S block, lane 3 the
+// SE and SW blocks and the cells' part of the right-hand side, which it hands
+// to lane 0 through a shuffle.
+__device__ __forceinline__ void gather_node4(const LevelGeom& g, int n, int lane, bool live, const float* cell,
+                                             const float* base, const float* delta, const float* wf,
+                                             const DevParams& P, float* node, float* rhs, float* minv, float& es,
+                                             float& ee, float& em)
 {
     const int i = n % g.nx, j = n / g.nx;
     const int ncx = g.ncx, ncy = g.ncy, G = g.G;
-    float Bs[NB], Be[NB], Bso[NB], Bse[NB], Bsw[NB], bb[6];
+    float bc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}; // cells' part of the right-hand side (lane 3)
+    if (live && lane == 3) {
+        float Bse[NB], Bsw[NB];
 #pragma unroll
-    for (int e = 0; e < NB; ++e) Bs[e] = Be[e] = Bso[e] = Bse[e] = Bsw[e] = 0.f;
+        for (int e = 0; e < NB; ++e) Bse[e] = Bsw[e] = 0.f;
+        // corners: 0 (ci,cj), 1 (ci+1,cj), 2 (ci,cj+1), 3 (ci+1,cj+1)
+        add_cell_pair(Bse, cell, ncx, ncy, i, j, pair_idx(0, 3));
+        add_cell_pair(Bsw, cell, ncx, ncy, i - 1, j, pair_idx(1, 2));
+        add_cell_rhs(bc, cell, ncx, ncy, i - 1, j - 1, 3);
+        add_cell_rhs(bc, cell, ncx, ncy, i, j - 1, 2);
+        add_cell_rhs(bc, cell, ncx, ncy, i - 1, j, 1);
+        add_cell_rhs(bc, cell, ncx, ncy, i, j, 0);
 #pragma unroll
-    for (int r = 0; r < 6; ++r) bb[r] = 0.f;
-    // corners: 0 (ci,cj), 1 (ci+1,cj), 2 (ci,cj+1), 3 (ci+1,cj+1)
+        for (int e = 0; e < NB; ++e) {
+            node[(size_t)(3 * NB + e) * G + n] = Bse[e];
+            node[(size_t)(4 * NB + e) * G + n] = Bsw[e];
+        }
+    }
+    const int src = (threadIdx.x & 31 & ~3) | 3;
+#pragma unroll
+    for (int u = 0; u < 6; ++u) bc[u] = __shfl_sync(0xffffffffu, bc[u], src);
+    if (!live) return;
+    if (lane == 1 || lane == 2) {
+        // E (lane 1) or S (lane 2) block, with the smoothness edge to that neighbour
+        float B[NB];
+#pragma unroll
+        for (int e = 0; e < NB; ++e) B[e] = 0.f;
+        if (lane == 1) {
+            add_cell_pair(B, cell, ncx, ncy, i, j - 1, pair_idx(2, 3));
+            add_cell_pair(B, cell, ncx, ncy, i, j, pair_idx(0, 1));
+        } else {
+            add_cell_pair(B, cell, ncx, ncy, i - 1, j, pair_idx(1, 3));
+            add_cell_pair(B, cell, ncx, ncy, i, j, pair_idx(0, 2));
+        }
+        const int mi = lane == 1 ? i + 1 : i, mj = lane == 1 ? j : j + 1;
+        if (mi < g.nx && mj < g.ny) {
+            const float ww = P.w_reg * P.w_smooth * (wf[n] + wf[mj * g.nx + mi]);
+#pragma unroll
+            for (int u = 0; u < 6; ++u) B[sym_idx(u, u)] -= ww * P.wfl[u >> 1];
+        }
+#pragma unroll
+        for (int e = 0; e < NB; ++e) node[(size_t)(lane * NB + e) * G + n] = B[e];
+        return;
+    }
+    if (lane != 0) return;
+    float Bs[NB], bb[6];
+#pragma unroll
+    for (int e = 0; e < NB; ++e) Bs[e] = 0.f;
+#pragma unroll
+    for (int r = 0; r < 6; ++r) bb[r] = bc[r];
     add_cell_pair(Bs, cell, ncx, ncy, i - 1, j - 1, pair_idx(3, 3));
     add_cell_pair(Bs, cell, ncx, ncy, i, j - 1, pair_idx(2, 2));
     add_cell_pair(Bs, cell, ncx, ncy, i - 1, j, pair_idx(1, 1));
     add_cell_pair(Bs, cell, ncx, ncy, i, j, pair_idx(0, 0));
-    add_cell_pair(Be, cell, ncx, ncy, i, j - 1, pair_idx(2, 3));
-    add_cell_pair(Be, cell, ncx, ncy, i, j, pair_idx(0, 1));
-    add_cell_pair(Bso, cell, ncx, ncy, i - 1, j, pair_idx(1, 3));
-    add_cell_pair(Bso, cell, ncx, ncy, i, j, pair_idx(0, 2));
-    add_cell_pair(Bse, cell, ncx, ncy, i, j, pair_idx(0, 3));
-    add_cell_pair(Bsw, cell, ncx, ncy, i - 1, j, pair_idx(1, 2));
-    add_cell_rhs(bb, cell, ncx, ncy, i - 1, j - 1, 3);
-    add_cell_rhs(bb, cell, ncx, ncy, i, j - 1, 2);
-    add_cell_rhs(bb, cell, ncx, ncy, i - 1, j, 1);
-    add_cell_rhs(bb, cell, ncx, ncy, i, j, 0);
 
     float T[6], d[6];
     node_total(base, delta, nullptr, 0.f, G, n, T, d);
@@ -520,8 +558,6 @@ __device__ __forceinline__ void gather_node(const LevelGeom& g, int n, const flo
             const float df = (base[u * g.G + n] - base[u * g.G + m]) + (d[u] - dm[u]);
             Bs[sym_idx(u, u)] += c;
             bb[u] -= c * df;
-            if (q == 0) Be[sym_idx(u, u)] -= c;
-            if (q == 1) Bso[sym_idx(u, u)] -= c;
         }
     }
     // epipolar (Eqs. 15-17)
@@ -544,13 +580,7 @@ __device__ __forceinline__ void gather_node(const LevelGeom& g, int n, const flo
         bb[u] -= cm * d[u];
     }
 #pragma unroll
-    for (int e = 0; e < NB; ++e) {
-        node[(size_t)(0 * NB + e) * G + n] = Bs[e];
-        node[(size_t)(1 * NB + e) * G + n] = Be[e];
-        node[(size_t)(2 * NB + e) * G + n] = Bso[e];
-        node[(size_t)(3 * NB + e) * G + n] = Bse[e];
-        node[(size_t)(4 * NB + e) * G + n] = Bsw[e];
-    }
+    for (int e = 0; e < NB; ++e) node[(size_t)e * G + n] = Bs[e];
 #pragma unroll
     for (int u = 0; u < 6; ++u) {
         rhs[u * G + n] = bb[u];
