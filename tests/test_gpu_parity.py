@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, through the C ABI, element by element.
 
-Bar (spec tolerance): fields within 1e-3 px max-abs and the final energy
+Bar: fields within 1e-3 px max-abs and the final energy
 within 1e-4 relative. Step-level stages use tolerances derived from FP32
 arithmetic on the same inputs (stated per test)."""
 
