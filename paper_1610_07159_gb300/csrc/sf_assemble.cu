@@ -192,6 +192,100 @@ __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, c
     }
 }
 
+// All backtracking trials of one Gauss-Newton step and the update in one
+// cooperative launch: for t = 1, 1/2, ... every block sums its share of the
+// pixel and node energies at delta + t x (W of the step), a bounded grid
+// barrier, then every warp forms the fixed-order totals, so all blocks take
+// the same decision; the first t whose energy does not exceed E_cur is taken
+// and applied (delta += t x). Replaces max_backtracks + 1 trial launches, most
+// of which found the step already taken, and the update launch.
+template <class TT>
+__global__ void __launch_bounds__(ETHREADS) k_trials(LevelGeom g, const typename TT::T* __restrict__ tex,
+                                                     const float* base, float* delta, const float* x,
+                                                     const float* __restrict__ wf, DevParams P,
+                                                     const uint8_t* __restrict__ Wmask, float2* part,
+                                                     unsigned long long* bar, int* status, StepCtrl* ctrl, int max_bt)
+{
+    __shared__ float sh[5][ETHREADS / 32];
+    unsigned long long target = grid_barrier_base(bar, gridDim.x);
+    const int nb = gridDim.x;
+    const int tid = blockIdx.x * ETHREADS + threadIdx.x, stride = nb * ETHREADS;
+    const double E_cur = ctrl->E_cur;
+    const int N = g.w * g.h;
+    float t = 1.f, t_acc = 0.f;
+    double E_acc = E_cur, terms_acc[5];
+    for (int q = 0; q < 5; ++q) terms_acc[q] = ctrl->terms_cur[q];
+    bool ok = true;
+    for (int j = 0; j <= max_bt && ok; ++j, t *= 0.5f) {
+        float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int p = tid; p < N; p += stride) {
+            const int y = p / g.w, xx = p - y * g.w;
+            int i0, j0;
+            float a, bb;
+            grid_cell(xx, y, g.s, g.nx, g.ny, i0, j0, a, bb);
+            float f[6];
+            pixel_fields(base, delta, x, t, g.G, j0 * g.nx + i0, g.nx, a, bb, f);
+            int Wi;
+            float Ep, Eg;
+            pixel_data<false, TT>(tex, g.w, g.h, xx, y, f, P, (int)Wmask[p], Wi, Ep, Eg, nullptr, nullptr);
+            v[0] += Ep;
+            v[1] += Eg;
+        }
+        for (int n = tid; n < g.G; n += stride) {
+            float a0, a1, a2;
+            node_prior_energy(g, P, base, delta, x, t, wf, n, a0, a1, a2);
+            v[2] += a0;
+            v[3] += a1;
+            v[4] += a2;
+        }
+        // block sums: FP32 within a warp, float-float across warps (thread 0, warp order)
+        float2* pj = part + (size_t)(j & 1) * 5 * nb;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) v[q] = warp_sum(v[q]);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) sh[q][threadIdx.x >> 5] = v[q];
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int q = 0; q < 5; ++q) {
+                ff tq{0.f, 0.f};
+                for (int w = 0; w < ETHREADS / 32; ++w) tq = ff_add(tq, ff_from(sh[q][w]));
+                pj[q * nb + blockIdx.x] = make_float2(tq.hi, tq.lo);
+            }
+        target += nb;
+        ok = grid_barrier(bar, status, target);
+        if (!ok) break;
+        double sq[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const ff tq = ff_fixed_sum(pj + q * nb, nb);
+            sq[q] = (double)tq.hi + tq.lo;
+        }
+        double terms[5];
+        terms[0] = P.w_photo * sq[0];
+        terms[1] = P.w_grad * sq[1];
+        terms[2] = (double)P.w_reg * P.w_smooth * sq[2];
+        terms[3] = (double)P.w_reg * P.w_epi * sq[3];
+        terms[4] = (double)P.w_reg * P.w_mag * sq[4];
+        const double E = terms[0] + terms[1] + terms[2] + terms[3] + terms[4];
+        if (E <= E_cur) {
+            t_acc = t;
+            E_acc = E;
+            for (int q = 0; q < 5; ++q) terms_acc[q] = terms[q];
+            break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctrl->E_acc = E_acc;
+        for (int q = 0; q < 5; ++q) ctrl->terms_acc[q] = terms_acc[q];
+        ctrl->t = t_acc;
+        ctrl->accepted = ok && t_acc > 0.f ? 1 : 0;
+    }
+    if (ok && t_acc > 0.f)
+        for (int k = tid; k < 6 * g.G; k += stride) delta[k] = fmaf(t_acc, x[k], delta[k]);
+}
+
 __global__ void k_apply_step(int n6, float* __restrict__ delta, const float* __restrict__ x,
                              const StepCtrl* __restrict__ ctrl)
 {
@@ -265,6 +359,48 @@ void launch_energy(const LevelGeom& g, const void* tex, int prec, const float* b
     SF_TEX_DISPATCH(prec, TT, k_energy<TT><<<npix + nnode, ETHREADS, 0, st>>>(
                                   g, npix, static_cast<const typename TT::T*>(tex), base, delta, x, t, wf, P, Wmask,
                                   wmode, sc.en_part, sc.counters + 1, ctrl, action, last, rec, sc.status));
+}
+
+template <class TT>
+int trials_blocks_impl(int sm_count)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trials<TT>, ETHREADS, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm * sm_count;
+}
+
+int trials_blocks(const LevelGeom& g, int prec, int sm_count)
+{
+    int cap = 0;
+    SF_TEX_DISPATCH(prec, TT, cap = trials_blocks_impl<TT>(sm_count));
+    // two CTAs per SM at most: room for the kernels of other levels running beside it
+    if (cap > 2 * sm_count) cap = 2 * sm_count;
+    const int want = (g.w * g.h + ETHREADS - 1) / ETHREADS;
+    int b = want < cap ? want : cap;
+    if (b > MAX_PART) b = MAX_PART;
+    return b < 1 ? 1 : b;
+}
+
+cudaError_t launch_trials(const LevelGeom& g, const void* tex, int prec, const float* base, float* delta, const float* x,
+                          const float* wf, const DevParams& P, const uint8_t* Wmask, const Scratch& sc,
+                          unsigned long long* bar, StepCtrl* ctrl, int max_bt, int blocks, cudaStream_t st)
+{
+    LevelGeom gg = g;
+    DevParams pp = P;
+    float2* part = sc.en_part;
+    int* status = sc.status;
+    void* args[] = {(void*)&gg, nullptr, (void*)&base, (void*)&delta, (void*)&x, (void*)&wf, (void*)&pp,
+                    (void*)&Wmask, (void*)&part, (void*)&bar, (void*)&status, (void*)&ctrl, (void*)&max_bt};
+    cudaError_t e = cudaSuccess;
+    SF_TEX_DISPATCH(prec, TT, {
+        const typename TT::T* tp = static_cast<const typename TT::T*>(tex);
+        args[1] = (void*)&tp;
+        e = cudaLaunchCooperativeKernel((const void*)k_trials<TT>, dim3(blocks), dim3(ETHREADS), args, 0, st);
+    });
+    return e;
 }
 
 void launch_apply_step(const LevelGeom& g, float* delta, const float* x, const StepCtrl* ctrl, cudaStream_t st)

@@ -57,11 +57,12 @@ struct sf_ctx {
     DevParams dp[SF_MAX_LEVELS]{};
     PcgPlan plan[SF_MAX_LEVELS]{};
     int asm_blocks[SF_MAX_LEVELS]{};
+    int trial_blocks[SF_MAX_LEVELS]{};   // CTAs of the cooperative trial launch
     int sm_count = 0;
     Scratch sc[SF_MAX_LEVELS]{};              // per level, so levels can run concurrently
     float2* pcg_part[SF_MAX_LEVELS]{};
     int* status = nullptr;                    // device status word shared by all levels
-    unsigned long long* bar = nullptr;        // per level: grid-barrier arrival counter
+    unsigned long long* bar = nullptr;        // grid-barrier arrival counters: [level] PCG, [SF_MAX_LEVELS + level] trials
     StepCtrl* ctrl = nullptr; // [SF_MAX_LEVELS * SF_MAX_GN + 1], the last one for probes
     double* rec = nullptr;    // [8] energy record
     DevArgs* args = nullptr;
@@ -269,11 +270,9 @@ int enqueue_level(sf_ctx* c, int l, const LevelIO& io, cudaStream_t st, int& nl)
         if (e != cudaSuccess) return check_cuda(e);
         nl += 3;
         prof_mark(c, SF_K_ENERGY, true, st);
-        float t = 1.f;
-        for (int j = 0; j <= P.max_backtracks; ++j, t *= 0.5f, ++nl)
-            launch_energy(g, io.tex, P.precision, b.base, b.delta, b.x, t, b.wf, c->dp[l], Wst, 0, sc, ctrl, 1,
-                          j == P.max_backtracks, nullptr, st);
-        launch_apply_step(g, b.delta, b.x, ctrl, st);
+        e = launch_trials(g, io.tex, P.precision, b.base, b.delta, b.x, b.wf, c->dp[l], Wst, sc,
+                          c->bar + SF_MAX_LEVELS + l, ctrl, P.max_backtracks, c->trial_blocks[l], st);
+        if (e != cudaSuccess) return check_cuda(e);
         ++nl;
         prof_mark(c, SF_K_ENERGY, false, st);
     }
@@ -619,6 +618,7 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
         return nullptr;
     }
     for (int l = 0; l < levels; ++l) {
+        c->trial_blocks[l] = trials_blocks(c->geo[l], p->precision, c->sm_count);
         c->plan[l] = pcg_plan(c->geo[l].G, c->sm_count, p->pcg_mode);
         if (c->plan[l].blocks < 1) {
             delete c;
@@ -661,7 +661,7 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
                 ok = dalloc(c, &c->vstate_delta[l][q], (size_t)6 * c->geo[l].G) &&
                      dalloc(c, &c->vstate_total[l][q], (size_t)6 * c->geo[l].G);
     }
-    ok = ok && dalloc(c, &c->bar, (size_t)SF_MAX_LEVELS) &&
+    ok = ok && dalloc(c, &c->bar, (size_t)2 * SF_MAX_LEVELS) &&
          dalloc(c, &c->ctrl, (size_t)SF_MAX_LEVELS * SF_MAX_GN + 1) && dalloc(c, &c->rec, 8) &&
          dalloc(c, &c->args, 1) && dalloc(c, &c->init_buf, (size_t)6 * c->geo[levels - 1].G) &&
          dalloc(c, &c->in_buf[0], N0) && dalloc(c, &c->in_buf[1], N0) && dalloc(c, &c->in_buf[2], N0) &&
@@ -798,7 +798,7 @@ int sf_reset(sf_ctx* c)
     c->pending_init = 0;
     int rc = check_cuda(cudaDeviceSynchronize());
     if (!rc) rc = check_cuda(cudaMemset(c->status, 0, 4 * sizeof(int)));
-    if (!rc) rc = check_cuda(cudaMemset(c->bar, 0, SF_MAX_LEVELS * sizeof(unsigned long long)));
+    if (!rc) rc = check_cuda(cudaMemset(c->bar, 0, 2 * SF_MAX_LEVELS * sizeof(unsigned long long)));
     for (int l = 0; l < c->L && !rc; ++l) rc = check_cuda(cudaMemset(c->sc[l].counters, 0, 8 * sizeof(unsigned)));
     if (!rc) rc = check_cuda(cudaDeviceSynchronize());
     return rc ? fail(rc) : SF_OK;

@@ -51,6 +51,12 @@ void launch_energy(const LevelGeom& g, const void* tex, int prec, const float* b
                    float t, const float* wf, const DevParams& P, uint8_t* Wmask, int wmode, const Scratch& sc,
                    StepCtrl* ctrl, int action, int last, double* rec, cudaStream_t st);
 void launch_apply_step(const LevelGeom& g, float* delta, const float* x, const StepCtrl* ctrl, cudaStream_t st);
+// all backtracking trials of a step and its update in one cooperative launch
+// of `blocks` CTAs (trials_blocks: all co-resident), on its own barrier counter
+int trials_blocks(const LevelGeom& g, int prec, int sm_count);
+cudaError_t launch_trials(const LevelGeom& g, const void* tex, int prec, const float* base, float* delta, const float* x,
+                          const float* wf, const DevParams& P, const uint8_t* Wmask, const Scratch& sc,
+                          unsigned long long* bar, StepCtrl* ctrl, int max_bt, int blocks, cudaStream_t st);
 void launch_unpack_blocks(const LevelGeom& g, const float* node, const float* rhs, float* blocks, float* rhs_out,
                           cudaStream_t st);
 

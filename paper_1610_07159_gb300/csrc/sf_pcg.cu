@@ -554,29 +554,31 @@ template <class Sync>
 __device__ __forceinline__ void allreduce2(float a, float b, ff* sh, float2* part, int parity, Sync& sy,
                                            unsigned long long* bar, int* status, bool& ok, ff& ra, ff& rb)
 {
-    __shared__ ff bc[2];
+    // block sums of both values in one pass (FP32 within a warp, float-float
+    // across warps, thread 0 in warp order); sh holds 2 * PT / 32 entries
     const int nb = gridDim.x;
     float2* pa = part + (size_t)parity * 2 * nb;
     float2* pb = pa + nb;
-    const ff sa = ff_block_sum_fast<PT>(a, sh);
-    const ff sb = ff_block_sum_fast<PT>(b, sh);
+    const float wa = warp_sum(a), wb = warp_sum(b);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        sh[2 * (threadIdx.x >> 5)] = ff_from(wa);
+        sh[2 * (threadIdx.x >> 5) + 1] = ff_from(wb);
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        pa[blockIdx.x] = make_float2(sa.hi, sa.lo);
-        pb[blockIdx.x] = make_float2(sb.hi, sb.lo);
+        ff ta{0.f, 0.f}, tb{0.f, 0.f};
+        for (int w = 0; w < PT / 32; ++w) {
+            ta = ff_add(ta, sh[2 * w]);
+            tb = ff_add(tb, sh[2 * w + 1]);
+        }
+        pa[blockIdx.x] = make_float2(ta.hi, ta.lo);
+        pb[blockIdx.x] = make_float2(tb.hi, tb.lo);
     }
     ok = sy.sync(bar, status) && ok;
-    if (threadIdx.x < 32) {
-        const ff ta = ff_fixed_sum(pa, nb);
-        const ff tb = ff_fixed_sum(pb, nb);
-        if (threadIdx.x == 0) {
-            bc[0] = ta;
-            bc[1] = tb;
-        }
-    }
-    __syncthreads();
-    ra = bc[0];
-    rb = bc[1];
-    __syncthreads();
+    // every warp forms the fixed-order sums itself: no broadcast through shared memory
+    ra = ff_fixed_sum(pa, nb);
+    rb = ff_fixed_sum(pb, nb);
 }
 
 template <int NPT, class Sync>
@@ -585,7 +587,7 @@ __global__ void __launch_bounds__(PT) k_pcg1(LevelGeom g, const float* __restric
                                              float2* part, unsigned long long* bar, int* status, int iters,
                                              int interleaved, Sync sy)
 {
-    __shared__ ff sred[PT / 32];
+    __shared__ ff sred[2 * (PT / 32)];
     sy.start(bar);
     const int G = g.G, nx = g.nx, ny = g.ny;
     const size_t G6 = (size_t)6 * G;
