@@ -108,20 +108,18 @@ __global__ void __launch_bounds__(ETHREADS) k_gather(LevelGeom g, const float* _
 }
 
 // Energy at base + delta (+ t x): pixel blocks first, then node blocks;
-// the last block to finish sums the partials in a fixed order and either
-// writes the record or takes the backtracking decision.
+// the last block to finish sums the partials in a fixed order and writes the
+// record (energy, the five weighted terms, excluded pixels).
 template <class TT>
 __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, const typename TT::T* __restrict__ tex,
                                                      const float* __restrict__ base, const float* __restrict__ delta,
                                                      const float* __restrict__ x, float t, const float* __restrict__ wf,
                                                      DevParams P, uint8_t* __restrict__ Wmask, int wmode,
                                                      float2* __restrict__ part, unsigned* counter,
-                                                     StepCtrl* __restrict__ ctrl, int action, int last,
                                                      double* __restrict__ rec, int* status)
 {
     __shared__ ff sred[ETHREADS / 32];
     __shared__ bool last_sh;
-    if (action == 1 && ld_acquire_s32(&ctrl->accepted)) return;
     float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if ((int)blockIdx.x < npixblk) {
         const int N = g.w * g.h;
@@ -170,22 +168,10 @@ __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, c
             terms[3] = (double)P.w_reg * P.w_epi * s[3];
             terms[4] = (double)P.w_reg * P.w_mag * s[4];
             const double E = terms[0] + terms[1] + terms[2] + terms[3] + terms[4];
-            if (action == 0) {
-                rec[0] = E;
-                for (int q = 0; q < 5; ++q) rec[1 + q] = terms[q];
-                rec[6] = s[5];
-            } else {
-                if (E <= ctrl->E_cur) {
-                    ctrl->E_acc = E;
-                    for (int q = 0; q < 5; ++q) ctrl->terms_acc[q] = terms[q];
-                    ctrl->t = t;
-                    __threadfence();
-                    atomicExch(&ctrl->accepted, 1);
-                } else if (last) {
-                    ctrl->t = 0.f; // rejected: keep delta, E_acc stays E_cur
-                }
-            }
-            if (!isfinite(E) && action == 0) atomicOr(status, DEV_NUMERIC);
+            rec[0] = E;
+            for (int q = 0; q < 5; ++q) rec[1 + q] = terms[q];
+            rec[6] = s[5];
+            if (!isfinite(E)) atomicOr(status, DEV_NUMERIC);
             __threadfence();
             *counter = 0u;
         }
@@ -286,14 +272,6 @@ __global__ void __launch_bounds__(ETHREADS) k_trials(LevelGeom g, const typename
         for (int k = tid; k < 6 * g.G; k += stride) delta[k] = fmaf(t_acc, x[k], delta[k]);
 }
 
-__global__ void k_apply_step(int n6, float* __restrict__ delta, const float* __restrict__ x,
-                             const StepCtrl* __restrict__ ctrl)
-{
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n6 || !ctrl->accepted) return;
-    delta[k] = fmaf(ctrl->t, x[k], delta[k]);
-}
-
 __global__ void k_unpack_blocks(int G, const float* __restrict__ node, const float* __restrict__ rhs,
                                 float* __restrict__ blocks, float* __restrict__ rhs_out)
 {
@@ -351,14 +329,14 @@ void launch_gather(const LevelGeom& g, const float* cell, const float* base, con
 
 void launch_energy(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta, const float* x,
                    float t, const float* wf, const DevParams& P, uint8_t* Wmask, int wmode, const Scratch& sc,
-                   StepCtrl* ctrl, int action, int last, double* rec, cudaStream_t st)
+                   double* rec, cudaStream_t st)
 {
     int npix = (g.w * g.h + ETHREADS - 1) / ETHREADS;
     if (npix > 152 * 8) npix = 152 * 8;
     const int nnode = (g.G + ETHREADS - 1) / ETHREADS;
     SF_TEX_DISPATCH(prec, TT, k_energy<TT><<<npix + nnode, ETHREADS, 0, st>>>(
                                   g, npix, static_cast<const typename TT::T*>(tex), base, delta, x, t, wf, P, Wmask,
-                                  wmode, sc.en_part, sc.counters + 1, ctrl, action, last, rec, sc.status));
+                                  wmode, sc.en_part, sc.counters + 1, rec, sc.status));
 }
 
 template <class TT>
@@ -401,12 +379,6 @@ cudaError_t launch_trials(const LevelGeom& g, const void* tex, int prec, const f
         e = cudaLaunchCooperativeKernel((const void*)k_trials<TT>, dim3(blocks), dim3(ETHREADS), args, 0, st);
     });
     return e;
-}
-
-void launch_apply_step(const LevelGeom& g, float* delta, const float* x, const StepCtrl* ctrl, cudaStream_t st)
-{
-    const int n6 = 6 * g.G;
-    k_apply_step<<<(n6 + 255) / 256, 256, 0, st>>>(n6, delta, x, ctrl);
 }
 
 void launch_unpack_blocks(const LevelGeom& g, const float* node, const float* rhs, float* blocks, float* rhs_out,

@@ -278,9 +278,7 @@ int enqueue_level(sf_ctx* c, int l, const LevelIO& io, cudaStream_t st, int& nl)
     }
     prof_mark(c, SF_K_LEVEL, true, st);
     if (l == 0 && P.gn_iters[0] == 0) {
-        launch_energy(g, io.tex, P.precision, b.base, b.delta, nullptr, 0.f, b.wf, c->dp[0], b.W, 1, sc, nullptr, 0, 0,
-                      c->rec,
-                      st);
+        launch_energy(g, io.tex, P.precision, b.base, b.delta, nullptr, 0.f, b.wf, c->dp[0], b.W, 1, sc, c->rec, st);
         ++nl;
     }
     launch_finish_level(g, b.base, b.delta, io.out_delta, io.out_total, io.args, l == 0, io.out_fields, st);
@@ -987,8 +985,7 @@ int sf_probe_energy(sf_ctx* c, int level, const float* base, const float* delta,
     if (W) rc = check_cuda(cudaMemcpyAsync(b.W, W, (size_t)g.w * g.h, cudaMemcpyDeviceToDevice, st));
     if (rc) return fail(rc);
     launch_energy(g, b.tex, c->prm.precision, base, delta, nullptr, 0.f, wfeat, c->dp[level], b.W, W ? 0 : 1,
-                  c->sc[level], nullptr, 0, 0, c->rec,
-                  st);
+                  c->sc[level], c->rec, st);
     rc = check_cuda(cudaMemcpyAsync(out6, c->rec, 6 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if (!rc) rc = check_cuda(cudaGetLastError());
     return rc ? fail(rc) : SF_OK;

@@ -44,13 +44,12 @@ void launch_assemble(const LevelGeom& g, const void* tex, int prec, const float*
 void launch_gather(const LevelGeom& g, const float* cell, const float* base, const float* delta, const float* wf,
                    const DevParams& P, float* node, float* rhs, float* minv, const Scratch& sc, StepCtrl* ctrl,
                    int n_asm_blocks, cudaStream_t st);
-// action: 0 = write the energy record `rec` only; 1 = backtracking trial
-// against ctrl (skips itself once a trial was accepted), `last` marks the
-// final trial. wmode: 0 = use Wmask, 1 = take W at the state and store it.
+// Energy at base + delta (+ t x) into the record `rec` (energy, five weighted
+// terms, excluded pixels). wmode: 0 = use Wmask, 1 = take W at the state and
+// store it.
 void launch_energy(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta, const float* x,
                    float t, const float* wf, const DevParams& P, uint8_t* Wmask, int wmode, const Scratch& sc,
-                   StepCtrl* ctrl, int action, int last, double* rec, cudaStream_t st);
-void launch_apply_step(const LevelGeom& g, float* delta, const float* x, const StepCtrl* ctrl, cudaStream_t st);
+                   double* rec, cudaStream_t st);
 // all backtracking trials of a step and its update in one cooperative launch
 // of `blocks` CTAs (trials_blocks: all co-resident), on its own barrier counter
 int trials_blocks(const LevelGeom& g, int prec, int sm_count);
