@@ -401,13 +401,6 @@ __device__ __forceinline__ void cluster_sync_all()
     asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ int ld_acquire_s32(const int* p)
 {
     int v;
@@ -424,10 +417,10 @@ __device__ __forceinline__ int ld_acquire_s32(const int* p)
 // launch waits for base + k*N arrivals. Arrivals are fire-and-forget
 // reductions (red.release.gpu), so N blocks do not queue behind returning
 // atomics. A waiter gives up after about one second (clock64 on the SM clock),
-// latches DEV_TIMEOUT and returns false; once the status word holds an error
-// every later barrier returns false at once, so the kernel unwinds instead of
-// hanging. After a timeout the counter is no longer a multiple of N: the
-// context resets it together with the status word.
+// latches DEV_TIMEOUT and returns false; a waiter that finds an error in the
+// status word (checked every 64 polls) returns false too, so the kernel
+// unwinds instead of hanging. After a timeout the counter is no longer a
+// multiple of N: the context resets it together with the status word.
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
 {
     unsigned long long v;
@@ -453,16 +446,22 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, int* statu
     __shared__ int ok_sh;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int ok = ld_acquire_s32(status) == 0;
-        if (ok) {
-            red_release_add_u64(ctr, 1ull);
-            const long long t0 = clock64();
-            while (ld_acquire_u64(ctr) < target) {
-                if (clock64() - t0 > 2000000000LL) {
-                    atomicOr(status, DEV_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
+        // arrive at once; the status word and the clock are read only every
+        // 64 polls, so the fast path has a single reduction and the polls
+        int ok = 1;
+        red_release_add_u64(ctr, 1ull);
+        const long long t0 = clock64();
+        unsigned k = 0;
+        while (ld_acquire_u64(ctr) < target) {
+            if ((++k & 63u) != 0u) continue;
+            if (ld_acquire_s32(status) != 0) {
+                ok = 0;
+                break;
+            }
+            if (clock64() - t0 > 2000000000LL) {
+                atomicOr(status, DEV_TIMEOUT);
+                ok = 0;
+                break;
             }
         }
         ok_sh = ok;
