@@ -317,3 +317,30 @@ def test_host_entry_point_matches_device_entry_point():
     out = torch.empty((6, 30, 40), dtype=torch.float32).pin_memory()
     b.solve_host(torch.from_numpy(q).pin_memory(), out)
     assert np.array_equal(Fd, out.numpy())
+
+
+def test_backtracking_trials_match_the_oracle_in_both_paths():
+    """The paper-literal square-root linearisation overshoots on this small
+    random scene, so steps are halved; the fused trial launch (one sequence)
+    and the batched kernel take the oracle's t at every step, and every step
+    keeps the energy monotone. The scene is deliberately ill-conditioned (four
+    unrelated textures, magnitude priors of 1e-4): the fields are held to the
+    energy bar and to 5e-2 px only, where FP32 and FP64 PCG part ways."""
+    q = scenes.random_quadruple(48, 40, 1, sigma=0.01)
+    sp, op = make_params([6], [30], m_s=1e-4, m_m=1e-4, m_d=1e-4, w_s=0.1, w_m=0.1, w_d=0.1,
+                         robust_mode=O.SQRT_PAPER)
+    solver = sf.Solver(48, 40, 4, 1, sp)
+    b = sf.Batch([(48, 40)], [1], 4, sp)
+    runs = [(solver.solve(_dev(q)).cpu().numpy(), solver),
+            (b.unpack(b.solve(b.pack([torch.from_numpy(q)])))[0].cpu().numpy(), b.sequence(0))]
+    for fields, view in runs:
+        st = view.stats()
+        assert st.status == sf.OK
+        ref = O.solve_frame(q.astype(np.float64), 4, 1, op, W_given=view.wmasks())
+        ts = [ref.step(0, g)[2] for g in range(6)]
+        assert any(0.0 < t < 1.0 for t in ts), ts
+        assert [st.step_t[0][g] for g in range(6)] == ts
+        for g in range(6):
+            assert st.step_accepted[0][g] <= st.step_energy[0][g]
+        assert abs(st.energy - ref.energy) <= ENERGY_TOL * abs(ref.energy), (st.energy, ref.energy)
+        assert np.max(np.abs(fields - ref.fields(0))) <= 5e-2
