@@ -562,7 +562,7 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
         p->grad_mode < 0 || p->grad_mode > 1 || p->wfeat_mode < 0 || p->wfeat_mode > 1 || p->temporal_mode < 0 ||
         p->temporal_mode > 2 || p->precision < SF_FP32 || p->precision > SF_MIXED_FP16 || !(p->wfeat_tau > 0.f) ||
         p->pcg_mode < 0 ||
-        p->pcg_mode > 4) {
+        p->pcg_mode > SF_PCG_ONE_REDUCTION) {
         fail(SF_ERR_ARG);
         return nullptr;
     }

@@ -18,7 +18,8 @@
 // Synchronisation: when the level fits in one thread-block cluster (up to 16
 // CTAs) the launch is a single cluster and the phases meet at the hardware
 // cluster barrier; larger levels use a cooperative launch over the whole GPU
-// and a bounded global-memory barrier.
+// and a bounded global-memory barrier, or, in the one-reduction kernels,
+// partial sums that carry their own tags (allreduce2_tagged).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -36,6 +37,7 @@ constexpr int PT = 256; // threads per block
 constexpr int NPB = PT / 4; // nodes per block and pass
 
 struct ClusterSync {
+    static constexpr bool kGrid = false;
     __device__ __forceinline__ void start(unsigned long long*) {}
     __device__ __forceinline__ bool sync(unsigned long long*, int*)
     {
@@ -45,6 +47,7 @@ struct ClusterSync {
 };
 
 struct GridSync {
+    static constexpr bool kGrid = true;
     unsigned long long target;
     __device__ __forceinline__ void start(unsigned long long* ctr) { target = grid_barrier_base(ctr, gridDim.x); }
     __device__ __forceinline__ bool sync(unsigned long long* ctr, int* status)
@@ -581,6 +584,136 @@ __device__ __forceinline__ void allreduce2(float a, float b, ff* sh, float2* par
     rb = ff_fixed_sum(pb, nb);
 }
 
+// The same reduction over a cooperative grid, with the barrier folded into
+// the data (the one-reduction kernels take it for every grid, whose plans are
+// capped at TAG_MAXB blocks): block b publishes its two float-float partials as four 64-bit words
+// (tag << 32 | value bits) in slot [tag & 1][b], and warp 0 of every block
+// polls all blocks' words until each carries the reduction's tag, then folds
+// them in the order of ff_fixed_sum (lane l takes blocks l, l + 32, ...), so
+// the sums are bit-identical to allreduce2's. A block waits for the polled
+// words instead of for a barrier counter and then the partials: one L2 round
+// trip less per reduction, and no arrivals queued on one address. The release
+// fence before the tagged stores and the acquire fence after the poll order
+// the block's published vectors exactly as the barrier does. Two slots by
+// tag parity suffice: a block writes tag k + 2 only after every block has
+// published tag k + 1, which each does after it has read tag k. Slots are
+// cleared (tag 0) before the launch's first barrier; tags start at 1. A poll
+// gives up like grid_barrier: on an error in the status word (checked every
+// 64 polls) or after ~1 s.
+constexpr int TAG_MAXB = 160; // at most 5 blocks per polling lane (152 SMs, one block each)
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ unsigned long long tag_word(unsigned tag, float v)
+{
+    return ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(v);
+}
+
+__device__ __forceinline__ void tagged_clear(unsigned long long* slots)
+{
+    if (threadIdx.x < 8) {
+        const int par = threadIdx.x >> 2, w = threadIdx.x & 3;
+        slots[((size_t)par * gridDim.x + blockIdx.x) * 4 + w] = 0ull;
+    }
+}
+
+__device__ __forceinline__ bool allreduce2_tagged(float a, float b, ff* sh, unsigned long long* slots, unsigned tag,
+                                                  int* status, ff& ra, ff& rb)
+{
+    __shared__ ff bc[2];
+    __shared__ int ok_sh;
+    const int nb = gridDim.x;
+    unsigned long long* sl = slots + (size_t)(tag & 1u) * 4 * nb;
+    const float wa = warp_sum(a), wb = warp_sum(b);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        sh[2 * (threadIdx.x >> 5)] = ff_from(wa);
+        sh[2 * (threadIdx.x >> 5) + 1] = ff_from(wb);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        if (lane == 0) {
+            ff ta{0.f, 0.f}, tb{0.f, 0.f};
+            for (int w = 0; w < PT / 32; ++w) {
+                ta = ff_add(ta, sh[2 * w]);
+                tb = ff_add(tb, sh[2 * w + 1]);
+            }
+            fence_acq_rel_gpu(); // the block's published vectors before its tag
+            unsigned long long* my = sl + (size_t)blockIdx.x * 4;
+            st_relaxed_u64(my + 0, tag_word(tag, ta.hi));
+            st_relaxed_u64(my + 1, tag_word(tag, ta.lo));
+            st_relaxed_u64(my + 2, tag_word(tag, tb.hi));
+            st_relaxed_u64(my + 3, tag_word(tag, tb.lo));
+        }
+        unsigned long long v[TAG_MAXB / 32][4];
+        int ok = 1;
+        const long long t0 = clock64();
+        for (unsigned k = 0;; ++k) {
+            bool ready = true;
+#pragma unroll
+            for (int j = 0; j < TAG_MAXB / 32; ++j) {
+                const int blk = lane + 32 * j;
+                if (blk < nb) {
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        v[j][w] = ld_relaxed_u64(sl + (size_t)blk * 4 + w);
+                        ready = ready && (unsigned)(v[j][w] >> 32) == tag;
+                    }
+                }
+            }
+            if (__all_sync(0xffffffffu, ready)) break;
+            if (((k + 1) & 63u) == 0u) {
+                bool fail = false;
+                if (lane == 0) {
+                    if (ld_acquire_s32(status) != 0) {
+                        fail = true;
+                    } else if (clock64() - t0 > 2000000000LL) {
+                        atomicOr(status, DEV_TIMEOUT);
+                        fail = true;
+                    }
+                }
+                if (__any_sync(0xffffffffu, fail)) {
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        fence_acq_rel_gpu(); // every block's published vectors after its tag
+        ff va{0.f, 0.f}, vb{0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < TAG_MAXB / 32; ++j) {
+            if (lane + 32 * j < nb) {
+                va = ff_add(va, ff{__uint_as_float((unsigned)v[j][0]), __uint_as_float((unsigned)v[j][1])});
+                vb = ff_add(vb, ff{__uint_as_float((unsigned)v[j][2]), __uint_as_float((unsigned)v[j][3])});
+            }
+        }
+        va = ff_warp_sum(va);
+        vb = ff_warp_sum(vb);
+        if (lane == 0) {
+            bc[0] = va;
+            bc[1] = vb;
+            ok_sh = ok;
+        }
+    }
+    __syncthreads();
+    ra = bc[0];
+    rb = bc[1];
+    return ok_sh != 0;
+}
+
 template <int NPT, class Sync>
 __global__ void __launch_bounds__(PT) k_pcg1(LevelGeom g, const float* __restrict__ node, const float* __restrict__ rhs,
                                              const float* __restrict__ minv, float* __restrict__ xout, float* pub,
@@ -618,6 +751,9 @@ __global__ void __launch_bounds__(PT) k_pcg1(LevelGeom g, const float* __restric
             }
         }
     }
+    // a grid (at most TAG_MAXB blocks) reduces through tagged words in part
+    unsigned long long* slots = reinterpret_cast<unsigned long long*>(part);
+    if constexpr (Sync::kGrid) tagged_clear(slots);
     bool ok = sy.sync(bar, status);
     float alpha = 0.f, beta = 0.f;
     ff gam{0.f, 0.f};
@@ -706,7 +842,10 @@ __global__ void __launch_bounds__(PT) k_pcg1(LevelGeom g, const float* __restric
             }
         }
         ff G2, D2;
-        allreduce2(gp, dp, sred, part, nred & 1, sy, bar, status, ok, G2, D2);
+        if constexpr (Sync::kGrid)
+            ok = allreduce2_tagged(gp, dp, sred, slots, (unsigned)nred + 1u, status, G2, D2) && ok;
+        else
+            allreduce2(gp, dp, sred, part, nred & 1, sy, bar, status, ok, G2, D2);
         ++nred;
         if (!ok) break;
         if (i < 0) {
@@ -743,6 +882,7 @@ cudaError_t launch_grid1(int blocks, const LevelGeom& g, const float* node, cons
                          float* x, float* pub, float2* part, unsigned long long* bar, int* status, int iters,
                          int interleaved, cudaStream_t st)
 {
+    if (blocks < 1 || blocks > TAG_MAXB) return cudaErrorInvalidValue; // the tagged reduction polls TAG_MAXB slots
     LevelGeom gg = g;
     GridSync sy{0ull};
     void* args[] = {(void*)&gg, (void*)&node, (void*)&rhs, (void*)&minv, (void*)&x, (void*)&pub, (void*)&part,
@@ -773,13 +913,23 @@ cudaError_t launch_cluster1(int blocks, const LevelGeom& g, const float* node, c
                               ClusterSync{});
 }
 
+// blocks of a cooperative launch that the GPU holds at once: the smallest
+// per-SM occupancy over the grid kernels, times the SMs
 int max_coop_blocks(int sm_count)
 {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<1, GridSync>, PT, 0) != cudaSuccess || per_sm < 1) {
-        cudaGetLastError();
-        per_sm = 1;
-    }
+    int per_sm = 1 << 20;
+    auto take = [&](const void* kern) {
+        int m = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, kern, PT, 0) != cudaSuccess) {
+            cudaGetLastError();
+            m = 1;
+        }
+        per_sm = std::min(per_sm, std::max(m, 1));
+    };
+    take((const void*)k_pcg<1, GridSync>);
+    take((const void*)k_pcg1<1, GridSync>);
+    take((const void*)k_pcg1<2, GridSync>);
+    take((const void*)k_pcg1<4, GridSync>);
     return per_sm * sm_count;
 }
 
@@ -857,7 +1007,8 @@ PcgPlan pcg_plan(int G, int sm_count, int mode)
         }
     }
     int cap = max_coop_blocks(sm_count);
-    if (cap > MAX_PART / 2) cap = MAX_PART / 2; // the one-reduction form keeps four partials per block
+    if (cap > MAX_PART / 2) cap = MAX_PART / 2;
+    if (one && cap > TAG_MAXB) cap = TAG_MAXB; // the one-reduction grid polls tagged words
     for (int npt : {1, 2, 4}) {
         const int need = (G + NPB * npt - 1) / (NPB * npt);
         if (need <= cap) {
@@ -886,10 +1037,8 @@ int pcg_candidates(int G, int sm_count, PcgPlan* out, int max)
             push(PcgPlan{need, npt, 4, 0});
             push(PcgPlan{need, npt, 1, 0});
         }
-        if (need <= cap) {
-            push(PcgPlan{need, npt, 3, 0});
-            push(PcgPlan{need, npt, 0, 0});
-        }
+        if (need <= cap && need <= TAG_MAXB) push(PcgPlan{need, npt, 3, 0});
+        if (need <= cap) push(PcgPlan{need, npt, 0, 0});
     }
     const int dcap = dsm_max_npc();
     for (int npt = 1; npt <= 3; ++npt) {

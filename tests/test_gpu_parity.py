@@ -118,9 +118,13 @@ def test_pcg_parity_on_the_same_system(iters, mode):
 
 
 @pytest.mark.parametrize("mode", [sf.PCG_GRID, sf.PCG_ONE_REDUCTION])
-def test_pcg_parity_grid_schedule_on_a_level_larger_than_a_cluster(mode):
-    """640x480 level 0 (4800 nodes) takes the cooperative-grid schedule."""
-    solver, lv, op = _level_setup(640, 480, 8, 4, 0, pcg_mode=mode)
+@pytest.mark.parametrize("w,h", [(640, 480), (800, 720), (1280, 720)])
+def test_pcg_parity_grid_schedule_on_a_level_larger_than_a_cluster(mode, w, h):
+    """Level 0 takes the cooperative-grid schedule: 640x480 (4800 nodes, 75
+    blocks), 800x720 (9000 nodes, 141 blocks, a ragged last block), 1280x720
+    (14400 nodes, 113 blocks of two nodes per lane group). The one-reduction
+    grid polls the tagged partials of up to five blocks per lane."""
+    solver, lv, op = _level_setup(w, h, 8, 4, 0, pcg_mode=mode)
     rng = np.random.default_rng(4)
     base, delta = _smooth_state(lv.G, rng)
     wf = np.ones(lv.G, dtype=np.float32)
