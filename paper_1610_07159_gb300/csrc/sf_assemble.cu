@@ -28,19 +28,18 @@ __global__ void __launch_bounds__(ETHREADS, 2) k_assemble(LevelGeom g, int cpb, 
 {
     __shared__ float sHB[ETHREADS * HB];
     __shared__ __align__(16) float sW[ETHREADS * WROW];
-    __shared__ ff sred[ETHREADS / 32];
+    __shared__ ff sred[3 * (ETHREADS / 32)];
     const int tid = threadIdx.x;
     float ep = 0.f, eg = 0.f;
     int nex = 0;
     assemble_group<MAXT, TT>(g, cpb, blockIdx.x, blockIdx.y, tex, base, delta, P, Wmask, cell, sHB, sW, ep, eg, nex);
     const int blk = blockIdx.y * gridDim.x + blockIdx.x;
-    const ff tp = ff_block_sum_fast<ETHREADS>(ep, sred);
-    const ff tg = ff_block_sum_fast<ETHREADS>(eg, sred);
-    const ff tn = ff_block_sum_fast<ETHREADS>((float)nex, sred);
+    const float v[3] = {ep, eg, (float)nex};
+    ff t[3];
+    ff_block_sum_fast_n<ETHREADS, 3>(v, sred, t);
     if (tid == 0) {
-        part[blk] = make_float2(tp.hi, tp.lo);
-        part[MAX_PART + blk] = make_float2(tg.hi, tg.lo);
-        part[2 * MAX_PART + blk] = make_float2(tn.hi, tn.lo);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) part[q * MAX_PART + blk] = make_float2(t[q].hi, t[q].lo);
     }
 }
 
@@ -55,20 +54,19 @@ __global__ void __launch_bounds__(ETHREADS) k_gather(LevelGeom g, const float* _
                                                      const float2* __restrict__ apart, int n_asm, unsigned* counter,
                                                      StepCtrl* __restrict__ ctrl, int* status)
 {
-    __shared__ ff sred[ETHREADS / 32];
+    __shared__ ff sred[6 * (ETHREADS / 32)];
     __shared__ bool last_sh;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = t >> 2;
     float es = 0.f, ee = 0.f, em = 0.f;
     gather_node4(g, n < g.G ? n : g.G - 1, t & 3, n < g.G, cell, base, delta, wf, P, node, rhs, minv, es, ee, em);
     if (!ctrl) return;
-    const ff ts = ff_block_sum_fast<ETHREADS>(es, sred);
-    const ff te = ff_block_sum_fast<ETHREADS>(ee, sred);
-    const ff tm = ff_block_sum_fast<ETHREADS>(em, sred);
+    const float v[3] = {es, ee, em};
+    ff tb[3];
+    ff_block_sum_fast_n<ETHREADS, 3>(v, sred, tb);
     if (threadIdx.x == 0) {
-        gpart[blockIdx.x] = make_float2(ts.hi, ts.lo);
-        gpart[MAX_PART + blockIdx.x] = make_float2(te.hi, te.lo);
-        gpart[2 * MAX_PART + blockIdx.x] = make_float2(tm.hi, tm.lo);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) gpart[q * MAX_PART + blockIdx.x] = make_float2(tb[q].hi, tb[q].lo);
         __threadfence();
         const unsigned done = atomicAdd(counter, 1u);
         last_sh = done == gridDim.x - 1;
@@ -77,12 +75,13 @@ __global__ void __launch_bounds__(ETHREADS) k_gather(LevelGeom g, const float* _
     if (!last_sh) return;
     __threadfence();
     {
-        const ff fp = ff_block_fixed_sum<ETHREADS>(apart, n_asm, sred);
-        const ff fg = ff_block_fixed_sum<ETHREADS>(apart + MAX_PART, n_asm, sred);
-        const ff fx = ff_block_fixed_sum<ETHREADS>(apart + 2 * MAX_PART, n_asm, sred);
-        const ff fs = ff_block_fixed_sum<ETHREADS>(gpart, gridDim.x, sred);
-        const ff fe = ff_block_fixed_sum<ETHREADS>(gpart + MAX_PART, gridDim.x, sred);
-        const ff fm = ff_block_fixed_sum<ETHREADS>(gpart + 2 * MAX_PART, gridDim.x, sred);
+        const float2* const parts[6] = {apart, apart + MAX_PART, apart + 2 * MAX_PART,
+                                        gpart, gpart + MAX_PART, gpart + 2 * MAX_PART};
+        const int nb = (int)gridDim.x;
+        const int cnt[6] = {n_asm, n_asm, n_asm, nb, nb, nb};
+        ff f[6];
+        ff_block_fixed_sum_n<ETHREADS, 6>(parts, cnt, sred, f);
+        const ff fp = f[0], fg = f[1], fx = f[2], fs = f[3], fe = f[4], fm = f[5];
         const double sp = (double)fp.hi + fp.lo, sg = (double)fg.hi + fg.lo, sx = (double)fx.hi + fx.lo;
         const double ss = (double)fs.hi + fs.lo, se = (double)fe.hi + fe.lo, sm = (double)fm.hi + fm.lo;
         if (threadIdx.x == 0) {
@@ -118,7 +117,7 @@ __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, c
                                                      float2* __restrict__ part, unsigned* counter,
                                                      double* __restrict__ rec, int* status)
 {
-    __shared__ ff sred[ETHREADS / 32];
+    __shared__ ff sred[6 * (ETHREADS / 32)];
     __shared__ bool last_sh;
     float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if ((int)blockIdx.x < npixblk) {
@@ -142,9 +141,13 @@ __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, c
         const int n = (blockIdx.x - npixblk) * ETHREADS + threadIdx.x;
         if (n < g.G) node_prior_energy(g, P, base, delta, x, t, wf, n, v[2], v[3], v[4]);
     }
-    for (int q = 0; q < 6; ++q) {
-        const ff sq = ff_block_sum_fast<ETHREADS>(v[q], sred);
-        if (threadIdx.x == 0) part[q * MAX_PART + blockIdx.x] = make_float2(sq.hi, sq.lo);
+    {
+        ff sq[6];
+        ff_block_sum_fast_n<ETHREADS, 6>(v, sred, sq);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) part[q * MAX_PART + blockIdx.x] = make_float2(sq[q].hi, sq[q].lo);
+        }
     }
     if (threadIdx.x == 0) {
         __threadfence();
@@ -155,11 +158,14 @@ __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, c
     if (!last_sh) return;
     __threadfence();
     {
+        const float2* const parts[6] = {part, part + MAX_PART, part + 2 * MAX_PART,
+                                        part + 3 * MAX_PART, part + 4 * MAX_PART, part + 5 * MAX_PART};
+        const int nb = (int)gridDim.x;
+        const int cnt[6] = {nb, nb, nb, nb, nb, nb};
+        ff f[6];
+        ff_block_fixed_sum_n<ETHREADS, 6>(parts, cnt, sred, f);
         double s[6];
-        for (int q = 0; q < 6; ++q) {
-            const ff t = ff_block_fixed_sum<ETHREADS>(part + q * MAX_PART, gridDim.x, sred);
-            s[q] = (double)t.hi + t.lo;
-        }
+        for (int q = 0; q < 6; ++q) s[q] = (double)f[q].hi + f[q].lo;
         if (threadIdx.x == 0) {
             double terms[5];
             terms[0] = P.w_photo * s[0];

@@ -395,6 +395,66 @@ __device__ __forceinline__ ff ff_block_fixed_sum(const float2* part, int n, ff* 
     return ff_block_sum<NT>(v, sh);
 }
 
+// K block sums at once: each result is bit-identical to ff_block_sum_fast
+// (or ff_block_sum, ff_block_fixed_sum) of that value alone, with two CTA
+// barriers in all instead of two per value. sh needs K * NT / 32 entries.
+template <int NT, int K>
+__device__ __forceinline__ void ff_block_sum_n(ff (&v)[K], ff* sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = ff_warp_sum(v[k]);
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh[k * (NT / 32) + warp] = v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = ff_warp_sum(lane < NT / 32 ? sh[k * (NT / 32) + lane] : ff{0.f, 0.f});
+}
+
+template <int NT, int K>
+__device__ __forceinline__ void ff_block_sum_fast_n(const float (&x)[K], ff* sh, ff (&out)[K])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float w[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) w[k] = warp_sum(x[k]);
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh[k * (NT / 32) + warp] = ff_from(w[k]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = ff_warp_sum(lane < NT / 32 ? sh[k * (NT / 32) + lane] : ff{0.f, 0.f});
+}
+
+// K fixed-order sums of partial arrays (part[k] holds n[k] float-float
+// partials), folded in the order of ff_block_fixed_sum with the K loads of
+// one index in flight together.
+template <int NT, int K>
+__device__ __forceinline__ void ff_block_fixed_sum_n(const float2* const (&part)[K], const int (&n)[K], ff* sh,
+                                                     ff (&out)[K])
+{
+    int nmax = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        out[k] = ff{0.f, 0.f};
+        nmax = n[k] > nmax ? n[k] : nmax;
+    }
+    for (int i = threadIdx.x; i < nmax; i += NT) {
+        float2 t[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) t[k] = i < n[k] ? __ldcg(part[k] + i) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (i < n[k]) out[k] = ff_add(out[k], ff{t[k].x, t[k].y});
+    }
+    ff_block_sum_n<NT, K>(out, sh);
+}
+
 __device__ __forceinline__ void cluster_sync_all()
 {
     asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
