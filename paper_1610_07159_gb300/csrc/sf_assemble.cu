@@ -187,8 +187,8 @@ __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, c
 // All backtracking trials of one Gauss-Newton step and the update in one
 // cooperative launch: for t = 1, 1/2, ... every block sums its share of the
 // pixel and node energies at delta + t x (W of the step), a bounded grid
-// barrier, then every warp forms the fixed-order totals, so all blocks take
-// the same decision; the first t whose energy does not exceed E_cur is taken
+// barrier, then warp 0 of every block forms the fixed-order totals, so all
+// blocks take the same decision; the first t whose energy does not exceed E_cur is taken
 // and applied (delta += t x). Replaces max_backtracks + 1 trial launches, most
 // of which found the step already taken, and the update launch.
 template <class TT>
@@ -199,6 +199,7 @@ __global__ void __launch_bounds__(ETHREADS) k_trials(LevelGeom g, const typename
                                                      unsigned long long* bar, int* status, StepCtrl* ctrl, int max_bt)
 {
     __shared__ float sh[5][ETHREADS / 32];
+    __shared__ double sq_sh[5];
     unsigned long long target = grid_barrier_base(bar, gridDim.x);
     const int nb = gridDim.x;
     const int tid = blockIdx.x * ETHREADS + threadIdx.x, stride = nb * ETHREADS;
@@ -248,12 +249,30 @@ __global__ void __launch_bounds__(ETHREADS) k_trials(LevelGeom g, const typename
         target += nb;
         ok = grid_barrier(bar, status, target);
         if (!ok) break;
+        // warp 0 forms the five fixed-order totals (the fold of ff_fixed_sum,
+        // the five values' loads of one index in flight together) and hands
+        // them to the block; sq_sh is next written after two more CTA barriers
+        if (threadIdx.x < 32) {
+            ff acc[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) acc[q] = ff{0.f, 0.f};
+            for (int i = threadIdx.x; i < nb; i += 32) {
+                float2 tv[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) tv[q] = __ldcg(pj + q * nb + i);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) acc[q] = ff_add(acc[q], ff{tv[q].x, tv[q].y});
+            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) acc[q] = ff_warp_sum(acc[q]);
+            if (threadIdx.x == 0)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) sq_sh[q] = (double)acc[q].hi + acc[q].lo;
+        }
+        __syncthreads();
         double sq[5];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            const ff tq = ff_fixed_sum(pj + q * nb, nb);
-            sq[q] = (double)tq.hi + tq.lo;
-        }
+        for (int q = 0; q < 5; ++q) sq[q] = sq_sh[q];
         double terms[5];
         terms[0] = P.w_photo * sq[0];
         terms[1] = P.w_grad * sq[1];
