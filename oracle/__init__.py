@@ -1,6 +1,6 @@
 """FP64 CPU oracle of the halfway-domain scene-flow solve (arXiv 1610.07159).
 
-TEST INFRASTRUCTURE ONLY. This package is the parity judge for the CUDA
+TEST INFRASTRUCTURE ONLY. This package is the parity reference for the CUDA
 library. Only the tests, the package's smoke check and the benchmark's CPU
 baseline leg import it; the product path never does. It shares no code with
 the CUDA path: the arithmetic lives in ``sfo.c`` (plain single-threaded C in

@@ -3,7 +3,7 @@
  * solve of Thies et al., "Real-time Halfway Domain Reconstruction of Motion
  * and Geometry" (arXiv 1610.07159).
  *
- * TEST INFRASTRUCTURE ONLY. This file is the parity judge for the CUDA
+ * TEST INFRASTRUCTURE ONLY. This file is the parity reference for the CUDA
  * library: it is called by the tests, by the package's smoke check and by the
  * benchmark's CPU-baseline leg, and by nothing on the product path. It shares
  * no code, header, table or constant generator with the CUDA path.
