@@ -11,14 +11,20 @@ Parity status of each function (what pins it, see the ``-m "not gpu"`` tests):
   sample, grid weights    pinned: scipy map_coordinates, partition of unity
   pixel terms (Eqs. 1-6)  pinned: closed forms on linear ramp images, FD Jacobian
   energy, assemble        pinned: b = -grad(E)/2 by finite differences, A by FD
-                          directional derivatives, closed-form priors
+                          directional derivatives (IRLS and the paper-literal
+                          square-root residuals), closed-form priors
   pcg                     pinned: dense Cholesky solve on tiny grids, monotone model
   upsample, temporal      pinned: constant and linear fields, closed forms
   solve_frame             pinned: static plane -> analytic disparity, rigid
                           translation -> m = v/2, stereo-only symmetry, identical
                           images -> zero, energy monotone per step
-  feature weight          parity unpinned against the paper (its constants are a
-                          reading); eigenvalue step pinned by numpy eigvalsh
+  halfway image           pinned: closed form on ramps at non-zero fields, exact
+                          shifted means at integer fields
+  feature weight          eigenvalue step pinned by numpy eigvalsh on the exact
+                          halfway image; its constants (gain 9, tau 1e-3) are a
+                          reading, since the paper gives none
+Every pin is itself checked: tests/test_oracle_mutations.py plants 22
+plausible mistakes in copies of sfo.c and each one fails a pin.
 """
 
 from __future__ import annotations
@@ -138,7 +144,9 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        path = build()
+        # SFO_LIB: a different build of sfo.c (the mutation tests load planted
+        # mistakes this way); by default the library built from sfo.c here
+        path = os.environ.get("SFO_LIB") or build()
         L = ctypes.CDLL(path)
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int)
@@ -154,6 +162,7 @@ def lib():
         L.sfo_pixel_terms.argtypes = [i, i, dp, d, d, dp, dp, dp, dp, dp]
         L.sfo_level_F.argtypes = [dp, i, dp]
         L.sfo_feature_weights.argtypes = [i, i, i, i, i, dp, dp, pp, dp]
+        L.sfo_halfway_image.argtypes = [i, i, i, i, i, dp, dp, dp]
         L.sfo_energy.argtypes = [i, i, i, i, i, i, dp, dp, dp, dp, up, pp, dp, up]
         L.sfo_energy.restype = d
         L.sfo_assemble.argtypes = [i, i, i, i, i, i, dp, dp, dp, dp, up, pp, dp, dp, up]
@@ -304,6 +313,14 @@ class Level:
     @property
     def G(self) -> int:
         return self.nx * self.ny
+
+
+def halfway_image(lv: Level, T: np.ndarray) -> np.ndarray:
+    """[h, w]: the mean of the four images warped by the totals T (6 x G)."""
+    T = _f64(T)
+    H = np.zeros((lv.h, lv.w))
+    lib().sfo_halfway_image(lv.w, lv.h, lv.s, lv.nx, lv.ny, _d(lv.planes), _d(T), _d(H))
+    return H
 
 
 def feature_weights(lv: Level, T: np.ndarray, p: Params) -> np.ndarray:

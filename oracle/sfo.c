@@ -323,6 +323,18 @@ static void epipolar_terms(const double Fl[9], double X, double Y, const double 
     }
 }
 
+/* Halfway image of a level at totals T (Section 3.1: the reference frame
+ * halfway between the four views): H(x) = mean of the four warped samples. */
+void sfo_halfway_image(int w, int h, int s, int nx, int ny, const double* planes, const double* T, double* H)
+{
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            double f[6];
+            pixel_fields(x, y, s, nx, ny, T, f);
+            H[y * w + x] = halfway_value(w, h, planes, x, y, f);
+        }
+}
+
 /* Feature weight w_i of every node (Section 4.3) [C10]: structure tensor of
  * the halfway image over the 3x3 pixels at the node, w = 1 + g exp(-lmin/tau). */
 void sfo_feature_weights(int w, int h, int s, int nx, int ny, const double* planes, const double* T,
@@ -334,12 +346,7 @@ void sfo_feature_weights(int w, int h, int s, int nx, int ny, const double* plan
         return;
     }
     double* H = (double*)malloc(sizeof(double) * w * h);
-    for (int y = 0; y < h; ++y)
-        for (int x = 0; x < w; ++x) {
-            double f[6];
-            pixel_fields(x, y, s, nx, ny, T, f);
-            H[y * w + x] = halfway_value(w, h, planes, x, y, f);
-        }
+    sfo_halfway_image(w, h, s, nx, ny, planes, T, H);
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             double a = 0.0, b = 0.0, c = 0.0;

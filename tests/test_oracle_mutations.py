@@ -1,0 +1,92 @@
+"""The oracle's pins are strong enough to catch plausible mistakes.
+
+Each case plants one mistake in a copy of oracle/sfo.c (a wrong sign, index,
+pairing, weight, dropped term, misplaced block, ...), builds the copy on the
+CPU, and runs the pin tests of tests/test_oracle_pins.py against it through
+the SFO_LIB override: every mutant must fail at least one pin. The planted
+mistakes live only in temporary copies; the oracle itself is not touched.
+"""
+
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "sfo.c")
+
+# name -> (text in sfo.c, planted replacement); each text occurs exactly once
+MUTANTS = {
+    "sign of s in image 1 (Eqs. 1-6)": ("    {+1.0, -1.0, -1.0},\n", "    {-1.0, -1.0, -1.0},\n"),
+    "check pair of d_0 swapped": ("{{1, 0}, {3, 2},", "{{0, 1}, {3, 2},"),
+    "gradient term dropped from E": ("Eg += psi_grad(", "Eg += 0.0 * psi_grad("),
+    "smoothness coupling in the mirrored slot": ("add_block(A, n, slot_of(i2 - i, j2 - j), u, u, -c);",
+                                                 "add_block(A, n, slot_of(i - i2, j - j2), u, u, -c);"),
+    "bilinear weights of corners 1 and 2 swapped": ("    wts[1] = a * (1 - b);\n    wts[2] = (1 - a) * b;\n",
+                                                    "    wts[1] = (1 - a) * b;\n    wts[2] = a * (1 - b);\n"),
+    "larger eigenvalue for w_i": ("0.5 * (a + c) - sqrt(", "0.5 * (a + c) + sqrt("),
+    "sign of the smoothness rhs": ("b[n * 6 + u] -= c * d;", "b[n * 6 + u] += c * d;"),
+    "prolongation without the factor 2": ("2.0 * grid_sample(nxc", "1.0 * grid_sample(nxc"),
+    "temporal transfer forward instead of back": ("(double)(i * s) - 2.0 * T_prev[2 * G + n]",
+                                                  "(double)(i * s) + 2.0 * T_prev[2 * G + n]"),
+    "backtracking accepts any step": ("if (Et <= Ecur) {", "if (Et == Et) {"),
+    "W threshold doubled": ("return mx < eps_p ? 1 : 0;", "return mx < 2.0 * eps_p ? 1 : 0;"),
+    "F of a level scaled on x only": ("ldexp(1.0, level), ldexp(1.0, level), 1.0", "ldexp(1.0, level), 1.0, 1.0"),
+    "halfway image with the sign of s flipped": (
+        "double px = x + SIGN[c][0] * f[0] + SIGN[c][1] * f[2] + SIGN[c][2] * f[4];\n"
+        "        double py = y + SIGN[c][0] * f[1] + SIGN[c][1] * f[3] + SIGN[c][2] * f[5];\n        acc +=",
+        "double px = x - SIGN[c][0] * f[0] + SIGN[c][1] * f[2] + SIGN[c][2] * f[4];\n"
+        "        double py = y - SIGN[c][0] * f[1] + SIGN[c][1] * f[3] + SIGN[c][2] * f[5];\n        acc +="),
+    "square-root photo block over 2 rho": ("gp[r] * gp[c] / (4.0 * rho_p)", "gp[r] * gp[c] / (2.0 * rho_p)"),
+    "square-root gradient block over 2 rho": ("gg[r] * gg[c] / (4.0 * rho_g)", "gg[r] * gg[c] / (2.0 * rho_g)"),
+    "IRLS weight without the 1/2": ("p->w_photo / (2.0 * phi(", "p->w_photo / (1.0 * phi("),
+    "epipolar Jacobian sign": ("SIGN[il][fld] * Fr[a] + SIGN[ir][fld] * Ftl[a]",
+                               "SIGN[il][fld] * Fr[a] - SIGN[ir][fld] * Ftl[a]"),
+    "magnitude prior on totals": ("double d = delta[(2 * fld + a) * G + n];", "double d = T[(2 * fld + a) * G + n];"),
+    "pyramid filter weight": ("dst[y * w2 + x] = 0.25 * acc;", "dst[y * w2 + x] = 0.3 * acc;"),
+    "gradient image without the 1/2": ("gx[y * w + x] = 0.5 * (img[y * w + xp] - img[y * w + xm]);",
+                                       "gx[y * w + x] = 1.0 * (img[y * w + xp] - img[y * w + xm]);"),
+    "bilinear x derivative with the rows' weights swapped": (
+        "*dpx = clx ? 0.0 : (1 - fy) * (p10 - p00) + fy * (p11 - p01);",
+        "*dpx = clx ? 0.0 : fy * (p10 - p00) + (1 - fy) * (p11 - p01);"),
+    "Jacobi preconditioner dropped": ("Minv[n * 6 + u] = d > 0.0 ? 1.0 / d : 1.0;", "Minv[n * 6 + u] = 1.0;"),
+}
+
+
+def _run_mutant(name, tmpdir):
+    text, planted = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(text) == 1, f"{name}: anchor text not unique in sfo.c"
+    tag = "".join(ch if ch.isalnum() else "_" for ch in name)
+    csrc = os.path.join(tmpdir, f"{tag}.c")
+    so = os.path.join(tmpdir, f"{tag}.so")
+    with open(csrc, "w") as f:
+        f.write(src.replace(text, planted))
+    subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", so, csrc, "-lm"])
+    env = dict(os.environ, SFO_LIB=so)
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x",
+                        "-q", "-p", "no:cacheprovider"], capture_output=True, text=True, env=env, cwd=ROOT)
+    return r.returncode, r.stdout[-400:]
+
+
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    names = sorted(MUTANTS)
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        results = dict(zip(names, ex.map(lambda n: _run_mutant(n, str(tmp_path)), names)))
+    missed = [n for n, (rc, _) in results.items() if rc == 0]
+    assert not missed, f"mutants that pass every pin: {missed}"
+    # a mutant must fail a test, not break the test run itself
+    broken = [n for n, (rc, out) in results.items() if rc not in (1,)]
+    assert not broken, {n: results[n][1] for n in broken}
+
+
+def test_the_unmutated_copy_passes(tmp_path):
+    """The harness itself: the oracle built from an unchanged copy passes every pin."""
+    so = os.path.join(str(tmp_path), "same.so")
+    subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", so, SRC, "-lm"])
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-q",
+                        "-p", "no:cacheprovider"], capture_output=True, text=True,
+                       env=dict(os.environ, SFO_LIB=so), cwd=ROOT)
+    assert r.returncode == 0, r.stdout[-2000:]

@@ -537,6 +537,128 @@ def test_feature_weight_eigenvalue_step():
     assert O.feature_weights(lv, T, O.Params(wfeat_mode=O.WFEAT_OFF)).max() == 1.0
 
 
+def _pixel_fields_closed_form(T, s, nx, ny, w, h):
+    """[6, h, w]: the bilinear interpolation of Eq. 7 written out (node (i, j)
+    at pixel (i s, j s); pixels past the last node clamp to it)."""
+    T = T.reshape(6, ny, nx)
+    ys, xs = np.mgrid[0:h, 0:w].astype(np.float64)
+    u, v = np.minimum(xs / s, nx - 1), np.minimum(ys / s, ny - 1)
+    i0, j0 = np.minimum(np.floor(u).astype(int), nx - 2), np.minimum(np.floor(v).astype(int), ny - 2)
+    a, b = u - i0, v - j0
+    return ((1 - a) * (1 - b) * T[:, j0, i0] + a * (1 - b) * T[:, j0, i0 + 1]
+            + (1 - a) * b * T[:, j0 + 1, i0] + a * b * T[:, j0 + 1, i0 + 1])
+
+
+def test_halfway_image_closed_form_on_ramps_at_nonzero_fields():
+    """H(x) = mean of the four images at the positions of Eqs. 1-6; on linear
+    ramps a x + b y + c bilinear sampling is exact, so H has a closed form."""
+    rng = np.random.default_rng(21)
+    w, h, s = 48, 40, 4
+    coefs = [(0.011, -0.007, 0.3), (-0.004, 0.013, 0.5), (0.009, 0.002, 0.1), (0.003, -0.012, 0.7)]
+    lv = O.Level(_ramp_planes(coefs, h=h, w=w), s)
+    T = rng.uniform(-2.5, 2.5, (6, lv.G))
+    H = O.halfway_image(lv, T.reshape(-1))
+    f = _pixel_fields_closed_form(T, s, lv.nx, lv.ny, w, h)
+    ys, xs = np.mgrid[0:h, 0:w].astype(np.float64)
+    S, M, D = f[0:2], f[2:4], f[4:6]
+    X = np.stack([xs, ys])
+    pos = [X - S - M + D, X + S - M - D, X - S + M - D, X + S + M + D]  # I_0^0, I_1^0, I_0^1, I_1^1
+    expect = sum(a * p[0] + b * p[1] + c for (a, b, c), p in zip(coefs, pos)) / 4.0
+    inside = np.all([(p[0] >= 0) & (p[0] <= w - 1) & (p[1] >= 0) & (p[1] <= h - 1) for p in pos], axis=0)
+    assert inside.mean() > 0.6
+    np.testing.assert_allclose(H[inside], expect[inside], atol=1e-12)
+
+
+def test_halfway_image_and_feature_weight_at_integer_fields():
+    """Integer s, m, d move every sample onto a pixel, so H is a mean of four
+    shifted images (exact on any image) and w_i follows from its structure
+    tensor in closed form (Section 4.3)."""
+    lv = _tiny_level(w=56, h=44, s=4, seed=31)
+    s, m, d = np.array([1.0, 0.0]), np.array([1.0, -1.0]), np.array([0.0, 1.0])
+    T = np.repeat(np.concatenate([s, m, d])[:, None], lv.G, axis=1)
+    H = O.halfway_image(lv, T.reshape(-1))
+    offs = [-s - m + d, s - m - d, -s + m - d, s + m + d]  # Eqs. 1-6 for I_0^0, I_1^0, I_0^1, I_1^1
+    r = int(max(np.abs(o).max() for o in offs))
+    ref = np.zeros((lv.h - 2 * r, lv.w - 2 * r))
+    for c, o in enumerate(offs):
+        ox, oy = int(o[0]), int(o[1])
+        ref += lv.planes[c, 0, r + oy:lv.h - r + oy, r + ox:lv.w - r + ox]
+    ref /= 4.0
+    np.testing.assert_allclose(H[r:lv.h - r, r:lv.w - r], ref, atol=1e-12)
+    # structure tensor of the exact H over the 3x3 pixels at interior nodes
+    Hy, Hx = np.gradient(H)
+    lmins, nodes = [], []
+    for j in range(lv.ny):
+        for i in range(lv.nx):
+            X, Y = i * lv.s, j * lv.s
+            if X - 2 < r or Y - 2 < r or X + 2 > lv.w - 1 - r or Y + 2 > lv.h - 1 - r:
+                continue
+            gx = Hx[Y - 1:Y + 2, X - 1:X + 2].reshape(-1)
+            gy = Hy[Y - 1:Y + 2, X - 1:X + 2].reshape(-1)
+            Mst = np.array([[gx @ gx, gx @ gy], [gx @ gy, gy @ gy]])
+            lmins.append(max(np.linalg.eigvalsh(Mst)[0], 0.0))
+            nodes.append(j * lv.nx + i)
+    assert len(nodes) >= 40
+    tau = float(np.median(lmins))  # so that exp(-lambda/tau) spreads over (0, 1)
+    wf = O.feature_weights(lv, T.reshape(-1), O.Params(wfeat_gain=9.0, wfeat_tau=tau))
+    expect = 1.0 + 9.0 * np.exp(-np.array(lmins) / tau)
+    assert np.ptp(expect) > 1.0
+    np.testing.assert_allclose(wf[nodes], expect, atol=1e-9)
+
+
+def test_sqrt_paper_system_matrix_is_the_gauss_newton_matrix_of_the_square_roots():
+    """Paper-literal linearisation (Section 5: one residual per pixel and term,
+    M = 2N + 14G): each pixel contributes the residuals sqrt(rho_photo) and
+    sqrt(rho_grad), rho the weighted sums of the six penalties, so
+    v^T A v = sum_px (D_v sqrt(rho_photo))^2 + (D_v sqrt(rho_grad))^2 + priors,
+    with D_v the directional derivative, here by central differences."""
+    lv = _tiny_level()
+    rng = np.random.default_rng(12)
+    base, delta = _smooth_state(lv, rng)
+    p = O.Params(eps_p=0.3, w_epi=0.0, w_s=0.05, w_m=0.05, w_d=0.05, m_s=0.01, m_m=0.01, m_d=0.01,
+                 robust_mode=O.SQRT_PAPER)
+    wf = 1.0 + rng.random(lv.G)
+    A, b, E, W = O.assemble(lv, base, delta, wf, p)
+    Ad = _dense(A, lv.nx, lv.ny)
+    np.testing.assert_allclose(Ad, Ad.T, atol=1e-12)
+    G = lv.G
+    hstep = 1e-6
+
+    def roots(out):
+        rp = p.w_photo * np.sqrt(out["e"] ** 2 + p.eps ** 2).sum()
+        rg = p.w_grad * np.sqrt((out["g"] ** 2).sum(axis=1) + p.eps ** 2).sum()
+        return np.sqrt(rp), np.sqrt(rg)
+
+    for trial in range(3):
+        v = rng.standard_normal(6 * G)
+        vi = v.reshape(6, G).T.reshape(-1)
+        T0 = (base + delta).reshape(6, G)
+        Tp, Tm = T0 + hstep * v.reshape(6, G), T0 - hstep * v.reshape(6, G)
+        quad = 0.0
+        for y in range(lv.h):
+            for x in range(lv.w):
+                if not W[y, x]:
+                    continue
+                nodes, wts = O.grid_weights(x, y, lv.s, lv.nx, lv.ny)
+                rp_p, rg_p = roots(O.pixel_terms(lv.planes, x, y, (Tp[:, nodes] * wts).sum(axis=1)))
+                rp_m, rg_m = roots(O.pixel_terms(lv.planes, x, y, (Tm[:, nodes] * wts).sum(axis=1)))
+                quad += ((rp_p - rp_m) / (2 * hstep)) ** 2 + ((rg_p - rg_m) / (2 * hstep)) ** 2
+        V = v.reshape(6, G)
+        wfl = [p.w_s, p.w_s, p.w_m, p.w_m, p.w_d, p.w_d]
+        mfl = [p.m_s, p.m_s, p.m_m, p.m_m, p.m_d, p.m_d]
+        for j in range(lv.ny):
+            for i in range(lv.nx):
+                n = j * lv.nx + i
+                for (i2, j2) in ((i + 1, j), (i, j + 1)):
+                    if i2 < lv.nx and j2 < lv.ny:
+                        mm = j2 * lv.nx + i2
+                        for u in range(6):
+                            quad += p.w_reg * p.w_smooth * (wf[n] + wf[mm]) * wfl[u] * (V[u, n] - V[u, mm]) ** 2
+                for u in range(6):
+                    quad += p.w_reg * p.w_mag * mfl[u] * V[u, n] ** 2
+        assert abs(vi @ Ad @ vi - quad) < 1e-5 * abs(quad)
+
+
 def test_backtracking_safeguard_is_exercised_and_keeps_energy_monotone():
     """The paper-literal square-root linearisation overshoots here; the safeguard halves t."""
     q = scenes.random_quadruple(48, 40, 1, sigma=0.01)
