@@ -50,10 +50,13 @@ WORKLOAD = (f"{WIDTH}x{HEIGHT} synthetic stereo video, {NFRAMES} frames, grid st
 FP32_LANES_PER_SM = 128
 
 # Algorithmic work per unit (derivations in the design notes):
-#   PCG (one reduction per iteration): per node 96 B (init) + 588 B per
-#   iteration (420 B of its five 6x6 blocks, 24 B of M, 72 B of published
+#   PCG, the byte model of the hot-path scope table: per node and iteration
+#   168 floats of stencil blocks (672 B) + about 8 vectors x 24 B = 860 B
+#   PCG, as the one-reduction kernel moves it: per node 96 B (init) + 588 B
+#   per iteration (420 B of its five 6x6 blocks, 24 B of M, 72 B of published
 #   r, w, s read, 72 B written) + 24 B (solution)
 #   assembly: 2250 FP32 flops per pixel
+PCG_MODEL_ITER_B = 860
 PCG_INIT_B, PCG_ITER_B, PCG_OUT_B = 96, 588, 24
 ASM_FLOPS_PER_PX = 2250
 
@@ -66,7 +69,11 @@ def level_sizes():
     return out
 
 
-def pcg_bytes_per_frame():
+def pcg_bytes_per_frame(model="survey"):
+    """Algorithmic PCG bytes of one frame: the 860 B/node/iteration model
+    ("survey") or the one-reduction kernel's own count ("one_reduction")."""
+    if model == "survey":
+        return sum(GN * nx * ny * PCG * PCG_MODEL_ITER_B for _, _, nx, ny in level_sizes())
     return sum(GN * nx * ny * (PCG_INIT_B + PCG * PCG_ITER_B + PCG_OUT_B) for _, _, nx, ny in level_sizes())
 
 
@@ -551,37 +558,82 @@ def run_ours(args):
     e2e_max = max_over_ranks(dist, e2e_ms, dev)
     e2e_value = aggregate_rate(world, frames_timed, e2e_max)
 
-    # roofline of the dominant kernel class, from the live per-kernel times of the profiled pass
+    # serialised pass for the roofline: the same frames, frame by frame on one stream (one captured graph
+    # per frame), with CUDA events recorded around every launch of the PCG and assembly classes inside the
+    # graph, so that no other kernel runs beside a timed one; L2 flushed before every frame
+    serial = sf.Solver(WIDTH, HEIGHT, STRIDE, LEVELS,
+                       sf.preset(sf.PRESET_FIG2, gn_iters=[GN], pcg_iters=[PCG], profile_mask=prof))
+    serial.tune_pcg(frames_d[0])
+    ser = {sf.K_PCG: [0.0, 0], sf.K_ASSEMBLE: [0.0, 0]}
+    ser_frame_ms, ser_worst_frac = 0.0, 0.0
+    for p_ in range(2):  # a warm pass, then the measured one
+        serial.reset()
+        for f in range(NFRAMES):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            serial.solve(frames_d[f], out1)
+            e.record(stream)
+            e.synchronize()
+            if p_:
+                fms = s.elapsed_time(e)
+                ser_frame_ms += fms
+                cls = 0.0
+                for kc in (sf.K_PCG, sf.K_ASSEMBLE):
+                    ms, n = serial.kernel_times(kc)
+                    ser[kc][0] += ms
+                    ser[kc][1] += n
+                    cls += ms
+                ser_worst_frac = max(ser_worst_frac, cls / fms)
+
+    # roofline of the dominant kernel class, from the serialised pass
     peaks, peak_src = measured_peaks()
-    pcg_ms, pcg_n = acc[sf.K_PCG]
-    asm_ms, asm_n = acc[sf.K_ASSEMBLE]
-    pcg_bytes_launch = pcg_bytes_per_frame() * frames_timed / max(pcg_n, 1)
-    asm_flops_launch = asm_flops_per_frame() * frames_timed / max(asm_n, 1)
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    alu_peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    fma_flops = sf.fma_rate()
+    alu_peak_tflops = fma_flops / 1e12
+    pcg_ms, pcg_n = ser[sf.K_PCG]
+    asm_ms, asm_n = ser[sf.K_ASSEMBLE]
+    pcg_s, asm_s = pcg_ms / 1e3, asm_ms / 1e3
+    pcg_model_bytes = pcg_bytes_per_frame("survey") * NFRAMES
+    pcg_kernel_bytes = pcg_bytes_per_frame("one_reduction") * NFRAMES
+    asm_flops = asm_flops_per_frame() * NFRAMES
+    hbm_peak = float(peaks["hbm_gbs"])
     kernels = {
         "pcg": {"launches": pcg_n, "ms_total": pcg_ms, "us_per_launch": 1e3 * pcg_ms / max(pcg_n, 1),
-                "bytes_per_launch": pcg_bytes_launch,
-                "GBps": pcg_bytes_launch / (pcg_ms / max(pcg_n, 1) / 1e3) / 1e9 if pcg_ms else None},
+                "bytes_per_launch_model_860B": pcg_model_bytes / max(pcg_n, 1),
+                "bytes_per_launch_kernel_588B": pcg_kernel_bytes / max(pcg_n, 1),
+                "GBps_model_860B": pcg_model_bytes / pcg_s / 1e9 if pcg_ms else None,
+                "GBps_kernel_588B": pcg_kernel_bytes / pcg_s / 1e9 if pcg_ms else None},
         "assemble": {"launches": asm_n, "ms_total": asm_ms, "us_per_launch": 1e3 * asm_ms / max(asm_n, 1),
-                     "flops_per_launch": asm_flops_launch,
-                     "TFLOPs": asm_flops_launch / (asm_ms / max(asm_n, 1) / 1e3) / 1e12 if asm_ms else None},
+                     "flops_per_launch": asm_flops / max(asm_n, 1),
+                     "TFLOPs": asm_flops / asm_s / 1e12 if asm_ms else None,
+                     "frac_of_measured_fp32_fma": asm_flops / asm_s / fma_flops if asm_ms else None},
+        "pipelined_pass": {"note": "the same classes inside the level pipeline, where launches of different "
+                                   "levels overlap, so these event times include shared time",
+                           "pcg_ms_per_step": acc[sf.K_PCG][0] / args.steps,
+                           "assemble_ms_per_step": acc[sf.K_ASSEMBLE][0] / args.steps},
     }
+    self_check = {"frames": NFRAMES, "frame_ms_total": ser_frame_ms, "class_ms_total": pcg_ms + asm_ms,
+                  "largest_class_share_of_a_frame": ser_worst_frac,
+                  "ok": bool(pcg_ms + asm_ms <= ser_frame_ms and ser_worst_frac <= 1.0)}
     if pcg_ms >= asm_ms:
-        ach = kernels["pcg"]["GBps"]
-        peak = float(peaks["hbm_gbs"])
-        roof = {"kernel": "k_pcg1", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak if ach else None, "traffic": recorded_traffic("k_pcg1"),
-                "peak_source": f"{peak_src} copy bandwidth"}
+        ach = kernels["pcg"]["GBps_model_860B"]
+        roof = {"kernel": "k_pcg1", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak if ach else None, "traffic": recorded_traffic("k_pcg1"),
+                "bytes_model": "860 B per node and PCG iteration (168 floats of stencil blocks + 8 vectors)",
+                "kernel_count": {"bytes_per_node_iteration": PCG_ITER_B,
+                                 "achieved": kernels["pcg"]["GBps_kernel_588B"],
+                                 "frac": kernels["pcg"]["GBps_kernel_588B"] / hbm_peak if pcg_ms else None},
+                "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json)"}
     else:
         ach = kernels["assemble"]["TFLOPs"]
         roof = {"kernel": "k_assemble", "bound": "alu", "achieved": ach, "peak": alu_peak_tflops, "unit": "TFLOP/s",
                 "frac": ach / alu_peak_tflops if ach else None, "traffic": recorded_traffic("k_assemble"),
-                "peak_source": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz"}
-    roof["timing"] = ("mean launch time from CUDA events recorded around every launch of the class, on its "
-                      f"stream, over a second timed pass of the same {args.steps} steps ({profiled_fps:.0f} frames/s "
-                      "with the events; the headline steps run without them)")
+                "peak_source": "FP32 FMA rate measured in this run (sf_probe_fma_rate)"}
+    roof["timing"] = ("CUDA events around every launch of the class inside the frame graph, over one serialised "
+                      f"pass of the {NFRAMES} frames on one stream (no other kernel runs beside a timed one; "
+                      "L2 flushed before every frame)")
+    roof["self_check"] = self_check
+    roof["fp32_fma_peak_tflops_measured"] = alu_peak_tflops
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -126,6 +126,7 @@ typedef struct sf_params {
     int profile_mask;             /* bit k set: time every launch of kernel class k with CUDA events */
     int pcg_mode;                 /* SF_PCG_AUTO | _CLUSTER | _GRID | _DSM | _ONE_REDUCTION */
     int video;                    /* 1: allocate the level pipeline of sf_solve_video */
+    int record_cells;             /* 1: record the bilinear cell decisions at cell edges (sf_probe_cells) */
 } sf_params;
 
 typedef struct sf_stats {
@@ -264,6 +265,29 @@ SF_API int sf_probe_wmask(sf_ctx* ctx, int level, int step, unsigned char* W, vo
  * weighted photo, grad, smooth, epi and mag parts. */
 SF_API int sf_probe_energy(sf_ctx* ctx, int level, const float* base, const float* delta, const float* wfeat,
                     const unsigned char* W, double* out6, void* stream);
+
+/* The bilinear cell decisions (reading C7: the cell of a sample at p is
+ * min(floor(p), w-2), the position clamped to the image) that the assembly
+ * of Gauss-Newton step `step` of `level` took in the last frame for every
+ * sample lying within 1e-3 px of a cell edge. A cell is an integer decision
+ * taken in FP32, and the analytic Jacobian of Section 5.1 (the derivative of
+ * the bilinear interpolant) jumps between cells, so a parity check in
+ * another precision replays these decisions like the outlier masks W. Needs
+ * params.record_cells = 1 at sf_create (SF_ERR_STATE otherwise; recording
+ * costs a few instructions per sample and an atomic per record). Waits for
+ * the context's work, writes *n (the number recorded) and copies up to
+ * max_recs records of two unsigned ints each, (pixel y*w + x, cell << 4 |
+ * clamped << 3 | image << 1 | axis), into the HOST buffer recs (may be NULL),
+ * in no particular order. SF_ERR_STATE also if more were recorded than the
+ * buffer held (8 per pixel). */
+SF_API int sf_probe_cells(sf_ctx* ctx, int level, int step, unsigned* recs, int max_recs, int* n);
+
+/* Measurement aid, no counterpart in the paper: the FP32 fused
+ * multiply-add rate of the current GPU (flops/s, an FMA counted as two), the
+ * roofline denominator of the ALU-bound assembly of Section 5.1. Runs a
+ * kernel of eight independent FMA chains per thread on every SM `reps` times
+ * (1..100) on `stream`, waits, and writes the best rate. */
+SF_API int sf_probe_fma_rate(int reps, double* flops_per_s, void* stream);
 
 /* C[s][M][N] = A[M, K] * B[N, K]^T over split s of K (K split into `splits`
  * contiguous ranges of 64-wide chunks; the splits' partial products are

@@ -42,12 +42,14 @@ _LIB_PATH = os.path.join(_HERE, "_build", "libsfo.so")
 
 MAX_LEVELS = 8
 MAX_GN = 16
-STATS_LEN = 16 + MAX_LEVELS * MAX_GN * 8
+STEP_STATS = 10
+STATS_LEN = 16 + MAX_LEVELS * MAX_GN * STEP_STATS
 
 IRLS, SQRT_PAPER = 0, 1
 GRAD_BROX, GRAD_LITERAL = 0, 1
 WFEAT_EIG, WFEAT_OFF = 0, 1
 TEMPORAL_PROPAGATE, TEMPORAL_COPY, TEMPORAL_ZERO = 0, 1, 2
+SOLVER_PCG, SOLVER_SCHWARZ = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -72,6 +74,8 @@ class _Params(ctypes.Structure):
         ("robust_mode", ctypes.c_int), ("grad_mode", ctypes.c_int), ("wfeat_mode", ctypes.c_int),
         ("wfeat_gain", ctypes.c_double), ("wfeat_tau", ctypes.c_double),
         ("temporal_mode", ctypes.c_int), ("max_backtracks", ctypes.c_int),
+        ("solver", ctypes.c_int), ("patch_iters", ctypes.c_int * MAX_LEVELS),
+        ("schwarz_tile", ctypes.c_int), ("schwarz_overlap", ctypes.c_int),
     ]
 
 
@@ -116,6 +120,10 @@ class Params:
     wfeat_tau: float = 1e-3
     temporal_mode: int = TEMPORAL_PROPAGATE
     max_backtracks: int = 4
+    solver: int = SOLVER_PCG
+    patch_iters: tuple = (5,) * MAX_LEVELS
+    schwarz_tile: int = 8
+    schwarz_overlap: int = 1
 
     @classmethod
     def preset(cls, name: str, **kw) -> "Params":
@@ -128,8 +136,11 @@ class Params:
         for k in ("w_reg", "w_photo", "w_grad", "w_epi", "w_smooth", "w_mag", "w_s", "w_m", "w_d",
                   "m_s", "m_m", "m_d", "eps", "eps_p", "wfeat_gain", "wfeat_tau"):
             setattr(p, k, float(getattr(self, k)))
-        for k in ("robust_mode", "grad_mode", "wfeat_mode", "temporal_mode", "max_backtracks"):
+        for k in ("robust_mode", "grad_mode", "wfeat_mode", "temporal_mode", "max_backtracks", "solver",
+                  "schwarz_tile", "schwarz_overlap"):
             setattr(p, k, int(getattr(self, k)))
+        qi = list(self.patch_iters) + [0] * MAX_LEVELS
+        p.patch_iters = (ctypes.c_int * MAX_LEVELS)(*[int(v) for v in qi[:MAX_LEVELS]])
         p.F = (ctypes.c_double * 9)(*[float(v) for v in self.F])
         gi = list(self.gn_iters) + [0] * MAX_LEVELS
         pi = list(self.pcg_iters) + [0] * MAX_LEVELS
@@ -170,11 +181,15 @@ def lib():
         L.sfo_apply.argtypes = [i, i, dp, dp, dp]
         L.sfo_pcg.argtypes = [i, i, dp, dp, i, dp, dp]
         L.sfo_pcg.restype = i
+        L.sfo_schwarz.argtypes = [i, i, dp, dp, i, i, i, i, dp]
+        L.sfo_schwarz.restype = i
         L.sfo_upsample.argtypes = [i, i, dp, i, i, dp]
         L.sfo_temporal.argtypes = [i, i, i, dp, dp, i, dp]
         L.sfo_packed_size.argtypes = [i, i, i, i]
         L.sfo_packed_size.restype = ctypes.c_long
-        L.sfo_solve_frame.argtypes = [i, i, i, i, pp, dp, dp, dp, dp, up, dp, dp, dp]
+        u32p = ctypes.POINTER(ctypes.c_uint)
+        lp = ctypes.POINTER(ctypes.c_long)
+        L.sfo_solve_frame.argtypes = [i, i, i, i, pp, dp, dp, dp, dp, up, u32p, lp, dp, dp, dp]
         L.sfo_solve_frame.restype = i
         _lib = L
     return _lib
@@ -372,6 +387,16 @@ def pcg(nx: int, ny: int, A: np.ndarray, b: np.ndarray, iters: int):
     return x, model[:its], its
 
 
+def schwarz(nx: int, ny: int, A: np.ndarray, b: np.ndarray, sweeps: int, patch_iters: int, tile: int = 8,
+            overlap: int = 1) -> np.ndarray:
+    """x [G, 6] after `sweeps` alternating Schwarz iterations (Section 5.2)."""
+    A, b = _f64(A), _f64(b)
+    x = np.zeros_like(b)
+    if lib().sfo_schwarz(nx, ny, _d(A), _d(b), int(sweeps), int(patch_iters), int(tile), int(overlap), _d(x)) != 0:
+        raise ValueError("invalid Schwarz tiling")
+    return x
+
+
 def upsample(Tc: np.ndarray, nxc: int, nyc: int, nx: int, ny: int) -> np.ndarray:
     Tc = _f64(Tc)
     base = np.zeros(6 * nx * ny)
@@ -406,16 +431,25 @@ class FrameResult:
         return self.delta[off:off + 6 * nx * ny].reshape(6, ny, nx)
 
     def step(self, level: int, g: int) -> np.ndarray:
-        i = 16 + (level * MAX_GN + g) * 8
-        return self.stats[i:i + 8]
+        """E at the linearisation point, E accepted, t, pixels with W = 0, PCG
+        iterations, replayed W decisions that differ from the oracle's own and
+        their largest margin, replayed cell decisions that differ and their
+        largest distance from an integer position."""
+        i = 16 + (level * MAX_GN + g) * STEP_STATS
+        return self.stats[i:i + STEP_STATS]
 
 
 def solve_frame(imgs4: np.ndarray, s: int, levels: int, p: Params, prev: FrameResult | None = None,
-                init_coarsest: np.ndarray | None = None, W_given: list | None = None) -> FrameResult:
+                init_coarsest: np.ndarray | None = None, W_given: list | None = None,
+                cells_given: list | None = None) -> FrameResult:
     """Algorithm 1 for one quadruple (without occlusion and illumination maps).
 
     W_given: optional outlier masks to use instead of taking W in FP64, as
-    W_given[level][step] arrays of the level's image shape."""
+    W_given[level][step] arrays of the level's image shape.
+    cells_given: optional bilinear cell decisions to use in the assembly of
+    each step instead of taking them in FP64, as cells_given[level][step]
+    uint32 arrays [n, 2] of (pixel y*w + x, cell << 4 | clamped << 3 |
+    image << 1 | axis), any order."""
     imgs4 = _f64(imgs4)
     _, h, w = imgs4.shape
     n = int(lib().sfo_packed_size(w, h, s, levels))
@@ -432,10 +466,27 @@ def solve_frame(imgs4: np.ndarray, s: int, levels: int, p: Params, prev: FrameRe
                 assert m.size == lw * lh
                 parts.append(m)
         wg = np.ascontiguousarray(np.concatenate(parts) if parts else np.zeros(1, np.uint8))
+    recs_p = offs_p = None
+    if cells_given is not None:
+        offs = np.zeros(MAX_LEVELS * MAX_GN + 1, dtype=np.int64)
+        parts, k = [], 0
+        for l in range(MAX_LEVELS):
+            for g in range(MAX_GN):
+                offs[l * MAX_GN + g] = k
+                if l < levels and l < len(cells_given) and g < len(cells_given[l]):
+                    r = np.asarray(cells_given[l][g], dtype=np.uint32).reshape(-1, 2)
+                    r = r[np.lexsort((r[:, 1], r[:, 0]))]
+                    parts.append(r)
+                    k += len(r)
+        offs[-1] = k
+        recs = np.ascontiguousarray(np.concatenate(parts) if parts else np.zeros((1, 2), np.uint32))
+        offs = np.ascontiguousarray(offs.astype(np.int_))
+        recs_p = recs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint))
+        offs_p = offs.ctypes.data_as(ctypes.POINTER(ctypes.c_long))
     rc = lib().sfo_solve_frame(w, h, s, levels, ctypes.byref(pc), _d(imgs4),
                                _d(prev.delta) if prev is not None else None,
                                _d(prev.total) if prev is not None else None,
-                               _d(ic), _u8(wg), _d(delta), _d(total), _d(stats))
+                               _d(ic), _u8(wg), recs_p, offs_p, _d(delta), _d(total), _d(stats))
     if rc != 0:
         raise ValueError("invalid sizes for the oracle solve")
     return FrameResult(delta, total, stats, packed_offsets(w, h, s, levels))

@@ -31,12 +31,14 @@
 
 #define SFO_MAX_LEVELS 8
 #define SFO_MAX_GN 16
-#define SFO_STATS_LEN (16 + SFO_MAX_LEVELS * SFO_MAX_GN * 8)
+#define SFO_STEP_STATS 10
+#define SFO_STATS_LEN (16 + SFO_MAX_LEVELS * SFO_MAX_GN * SFO_STEP_STATS)
 
 enum { SFO_IRLS = 0, SFO_SQRT_PAPER = 1 };
 enum { SFO_GRAD_BROX = 0, SFO_GRAD_LITERAL = 1 };
 enum { SFO_WFEAT_EIG = 0, SFO_WFEAT_OFF = 1 };
 enum { SFO_TEMPORAL_PROPAGATE = 0, SFO_TEMPORAL_COPY = 1, SFO_TEMPORAL_ZERO = 2 };
+enum { SFO_SOLVER_PCG = 0, SFO_SOLVER_SCHWARZ = 1 };
 
 typedef struct sfo_params {
     /* Table 1 (Appendix A) */
@@ -50,6 +52,14 @@ typedef struct sfo_params {
     int robust_mode, grad_mode, wfeat_mode;
     double wfeat_gain, wfeat_tau;
     int temporal_mode, max_backtracks;
+    /* linear solver of each Gauss-Newton step (Section 5.2) [C24]: global
+     * Jacobi-PCG with pcg_iters iterations, or alternating Schwarz with
+     * pcg_iters sweeps over square subdomains of schwarz_tile x schwarz_tile
+     * nodes plus schwarz_overlap nodes of overlap, each subdomain solved by
+     * patch_iters local PCG iterations */
+    int solver;
+    int patch_iters[SFO_MAX_LEVELS];
+    int schwarz_tile, schwarz_overlap;
 } sfo_params;
 
 /* Sign of stereo, motion and difference flow in each image's sample position
@@ -128,25 +138,54 @@ void sfo_level_planes(int w, int h, const double* imgs4, double* planes)
 
 /* Bilinear interpolation of plane P (w x h) at (px, py); the position is
  * clamped to [0, w-1] x [0, h-1]; the cell is min(floor(p), w-2). The
- * derivative is that of the bilinear interpolant, 0 along a clamped axis. */
-double sfo_sample(int w, int h, const double* P, double px, double py, double* dpx, double* dpy)
+ * derivative is that of the bilinear interpolant, 0 along a clamped axis.
+ *
+ * The cell decision of one axis: position p on [0, n-1] -> clamped position,
+ * cell min(floor(p), n-2) and whether p was clamped. */
+static void axis_decision(int n, double p, double* cp, int* cell, int* clamped)
 {
-    int clx = 0, cly = 0;
-    double cx = px, cy = py;
-    if (cx < 0.0) { cx = 0.0; clx = 1; }
-    if (cx > w - 1) { cx = w - 1; clx = 1; }
-    if (cy < 0.0) { cy = 0.0; cly = 1; }
-    if (cy > h - 1) { cy = h - 1; cly = 1; }
-    int ix = (int)floor(cx), iy = (int)floor(cy);
-    if (ix > w - 2) ix = w - 2;
-    if (iy > h - 2) iy = h - 2;
+    *clamped = 0;
+    *cp = p;
+    if (p < 0.0) { *cp = 0.0; *clamped = 1; }
+    if (p > n - 1) { *cp = n - 1; *clamped = 1; }
+    *cell = (int)floor(*cp);
+    if (*cell > n - 2) *cell = n - 2;
+}
+
+/* A cell decision given from outside (a record of another implementation,
+ * see sfo_solve_frame): code = cell << 1 | clamped, or -1 for none. With a
+ * given decision the interpolant of that cell is used: a clamped axis takes
+ * the cell's edge value and derivative 0; otherwise the fraction p - cell
+ * (slightly outside [0, 1] when the two decisions part). */
+static double sample_decided(int w, int h, const double* P, double px, double py, int gx, int gy, double* dpx,
+                             double* dpy)
+{
+    int clx, cly, ix, iy;
+    double cx, cy;
+    axis_decision(w, px, &cx, &ix, &clx);
+    axis_decision(h, py, &cy, &iy, &cly);
     double fx = cx - ix, fy = cy - iy;
+    if (gx >= 0) {
+        ix = gx >> 1;
+        clx = gx & 1;
+        fx = clx ? (ix == 0 && px < 0.5 * (w - 1) ? 0.0 : 1.0) : px - ix;
+    }
+    if (gy >= 0) {
+        iy = gy >> 1;
+        cly = gy & 1;
+        fy = cly ? (iy == 0 && py < 0.5 * (h - 1) ? 0.0 : 1.0) : py - iy;
+    }
     double p00 = P[iy * w + ix], p10 = P[iy * w + ix + 1];
     double p01 = P[(iy + 1) * w + ix], p11 = P[(iy + 1) * w + ix + 1];
     double v = (1 - fx) * (1 - fy) * p00 + fx * (1 - fy) * p10 + (1 - fx) * fy * p01 + fx * fy * p11;
     if (dpx) *dpx = clx ? 0.0 : (1 - fy) * (p10 - p00) + fy * (p11 - p01);
     if (dpy) *dpy = cly ? 0.0 : (1 - fx) * (p01 - p00) + fx * (p11 - p10);
     return v;
+}
+
+double sfo_sample(int w, int h, const double* P, double px, double py, double* dpx, double* dpy)
+{
+    return sample_decided(w, h, P, px, py, -1, -1, dpx, dpy);
 }
 
 /* Same rule on a node grid (nx x ny): used by prolongation and the temporal
@@ -201,17 +240,20 @@ static void pixel_fields(int x, int y, int s, int nx, int ny, const double* T, d
 /* For pixel (x, y) with fields f = (s, m, d): the six brightness checks e[k],
  * the six gradient-constancy 2-vectors g[2k], g[2k+1] (difference of the
  * warped image gradients [C2]) and their Jacobians w.r.t. the six pixel
- * fields (Je[k][u], Jg[2k+a][u], u = sx, sy, mx, my, dx, dy). */
-void sfo_pixel_terms(int w, int h, const double* planes, double x, double y, const double f[6],
-                     double e[6], double g[12], double Je[36], double Jg[72])
+ * fields (Je[k][u], Jg[2k+a][u], u = sx, sy, mx, my, dx, dy). dec is NULL or
+ * gives, per image c, a cell decision for x (dec[2c]) and y (dec[2c+1]) as
+ * sample_decided takes it (-1: the oracle's own). */
+static void pixel_terms_decided(int w, int h, const double* planes, double x, double y, const double f[6],
+                                const int dec[8], double e[6], double g[12], double Je[36], double Jg[72])
 {
     size_t n = (size_t)w * h;
     double val[4][3], dx[4][3], dy[4][3];
     for (int c = 0; c < 4; ++c) {
         double px = x + SIGN[c][0] * f[0] + SIGN[c][1] * f[2] + SIGN[c][2] * f[4];
         double py = y + SIGN[c][0] * f[1] + SIGN[c][1] * f[3] + SIGN[c][2] * f[5];
+        int gx = dec ? dec[2 * c] : -1, gy = dec ? dec[2 * c + 1] : -1;
         for (int p = 0; p < 3; ++p)
-            val[c][p] = sfo_sample(w, h, planes + (size_t)(c * 3 + p) * n, px, py, &dx[c][p], &dy[c][p]);
+            val[c][p] = sample_decided(w, h, planes + (size_t)(c * 3 + p) * n, px, py, gx, gy, &dx[c][p], &dy[c][p]);
     }
     for (int k = 0; k < 6; ++k) {
         int F = CHECK[k][0], S = CHECK[k][1];
@@ -233,6 +275,12 @@ void sfo_pixel_terms(int w, int h, const double* planes, double x, double y, con
             }
         }
     }
+}
+
+void sfo_pixel_terms(int w, int h, const double* planes, double x, double y, const double f[6],
+                     double e[6], double g[12], double Je[36], double Jg[72])
+{
+    pixel_terms_decided(w, h, planes, x, y, f, NULL, e, g, Je, Jg);
 }
 
 /* Halfway image: mean of the four warped samples (used by the feature weight). */
@@ -446,12 +494,25 @@ static int slot_of(int di, int dj) { return 3 * (dj + 1) + (di + 1); }
 
 static void add_block(double* A, int n, int slot, int r, int c, double v) { A[((size_t)n * 9 + slot) * 36 + r * 6 + c] += v; }
 
-/* Assembles A dx = b at the state base + delta, with W taken at this state
- * (written to Wout) unless W is given. Returns the energy at the state. */
-double sfo_assemble(int w, int h, int s, int nx, int ny, int level, const double* planes,
-                    const double* base, const double* delta, const double* wf, const unsigned char* Win,
-                    const sfo_params* p, double* A, double* b, unsigned char* Wout)
+/* Sample position of image c along axis a (0: x, 1: y) for fields f
+ * (Eqs. 1-6). */
+static double sample_position(int c, int a, double x, double y, const double f[6])
 {
+    return (a == 0 ? x : y) + SIGN[c][0] * f[a] + SIGN[c][1] * f[2 + a] + SIGN[c][2] * f[4 + a];
+}
+
+/* Assembles A dx = b at the state base + delta, with W taken at this state
+ * (written to Wout) unless W is given. Returns the energy at the state.
+ * recs/nrec: cell decisions given for some samples (record format of
+ * sfo_solve_frame, sorted by pixel), or NULL; *ndis and *margin then count
+ * the given decisions that differ from this oracle's own and the largest
+ * distance of such a sample's own position from the nearest integer. */
+static double assemble_impl(int w, int h, int s, int nx, int ny, int level, const double* planes,
+                            const double* base, const double* delta, const double* wf, const unsigned char* Win,
+                            const sfo_params* p, double* A, double* b, unsigned char* Wout, const unsigned* recs,
+                            long nrec, int* ndis, double* margin)
+{
+    long cur = 0;
     int G = nx * ny;
     memset(A, 0, sizeof(double) * (size_t)G * 9 * 36);
     memset(b, 0, sizeof(double) * (size_t)G * 6);
@@ -465,7 +526,26 @@ double sfo_assemble(int w, int h, int s, int nx, int ny, int level, const double
             double al[4];
             sfo_grid_weights(x, y, s, nx, ny, nd, al);
             pixel_fields(x, y, s, nx, ny, T, f);
-            sfo_pixel_terms(w, h, planes, x, y, f, e, g, Je, Jg);
+            int dec[8] = {-1, -1, -1, -1, -1, -1, -1, -1}, have = 0;
+            const unsigned pix = (unsigned)(y * w + x);
+            while (recs && cur < nrec && recs[2 * cur] < pix) ++cur;
+            while (recs && cur < nrec && recs[2 * cur] == pix) {
+                const unsigned code = recs[2 * cur + 1];
+                const int img = (code >> 1) & 3, ax = code & 1;
+                dec[2 * img + ax] = (int)((code >> 4) << 1 | ((code >> 3) & 1));
+                have = 1;
+                /* does the oracle's own decision differ? */
+                double pos = sample_position(img, ax, x, y, f), cp;
+                int cell, cl;
+                axis_decision(ax == 0 ? w : h, pos, &cp, &cell, &cl);
+                if ((cell << 1 | cl) != dec[2 * img + ax]) {
+                    double dist = fabs(pos - floor(pos + 0.5));
+                    ++*ndis;
+                    if (dist > *margin) *margin = dist;
+                }
+                ++cur;
+            }
+            pixel_terms_decided(w, h, planes, x, y, f, have ? dec : NULL, e, g, Je, Jg);
             int Wi = Win ? Win[y * w + x] : outlier_weight(e, p->eps_p);
             if (Wout) Wout[y * w + x] = (unsigned char)Wi;
             if (!Wi) continue;
@@ -570,6 +650,16 @@ double sfo_assemble(int w, int h, int s, int nx, int ny, int level, const double
     return sfo_energy(w, h, s, nx, ny, level, planes, base, delta, wf, Win ? Win : Wout, p, NULL, NULL);
 }
 
+double sfo_assemble(int w, int h, int s, int nx, int ny, int level, const double* planes,
+                    const double* base, const double* delta, const double* wf, const unsigned char* Win,
+                    const sfo_params* p, double* A, double* b, unsigned char* Wout)
+{
+    int ndis = 0;
+    double margin = 0.0;
+    return assemble_impl(w, h, s, nx, ny, level, planes, base, delta, wf, Win, p, A, b, Wout, NULL, 0, &ndis,
+                         &margin);
+}
+
 /* y = A x for the block system; vectors interleaved per node (n*6 + r). */
 void sfo_apply(int nx, int ny, const double* A, const double* x, double* y)
 {
@@ -647,6 +737,77 @@ int sfo_pcg(int nx, int ny, const double* A, const double* b, int iters, double*
     free(q);
     free(Minv);
     return it;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Domain decomposition (Section 5.2): alternating Schwarz [C24]            */
+/* ------------------------------------------------------------------------ */
+
+/* Solves A x = b from x = 0 by `sweeps` data-parallel Schwarz iterations. The
+ * grid is cut into square tiles of `tile` x `tile` nodes (the last row and
+ * column of tiles ragged); a subdomain is a tile grown by `overlap` nodes on
+ * every side (clipped to the grid). In each sweep, from the same iterate x:
+ * the residual r = b - A x; for every subdomain, the local system (the rows
+ * and columns of A of the subdomain's nodes; couplings to nodes outside it
+ * dropped, those nodes held at x) is solved for a correction e by
+ * `patch_iters` Jacobi-PCG iterations from e = 0 (sfo_pcg on the local block
+ * grid); then every node takes x + e from the subdomain whose tile holds it
+ * (restricted additive Schwarz). The exchange between subdomains is the
+ * global iterate. Returns 0, or -1 for an invalid tiling. */
+int sfo_schwarz(int nx, int ny, const double* A, const double* b, int sweeps, int patch_iters, int tile, int overlap,
+                double* x)
+{
+    if (tile < 1 || overlap < 0) return -1;
+    int N = nx * ny * 6;
+    double* r = (double*)malloc(sizeof(double) * N);
+    double* xn = (double*)malloc(sizeof(double) * N);
+    int ext = tile + 2 * overlap;
+    double* Al = (double*)malloc(sizeof(double) * (size_t)ext * ext * 9 * 36);
+    double* rl = (double*)malloc(sizeof(double) * ext * ext * 6);
+    double* el = (double*)malloc(sizeof(double) * ext * ext * 6);
+    for (int a = 0; a < N; ++a) x[a] = 0.0;
+    for (int sw = 0; sw < sweeps; ++sw) {
+        sfo_apply(nx, ny, A, x, r);
+        for (int a = 0; a < N; ++a) r[a] = b[a] - r[a];
+        memcpy(xn, x, sizeof(double) * N);
+        for (int tj = 0; tj * tile < ny; ++tj)
+            for (int ti = 0; ti * tile < nx; ++ti) {
+                /* the subdomain: nodes [i0, i1) x [j0, j1) */
+                int i0 = ti * tile - overlap, j0 = tj * tile - overlap;
+                int i1 = (ti + 1) * tile + overlap, j1 = (tj + 1) * tile + overlap;
+                if (i0 < 0) i0 = 0;
+                if (j0 < 0) j0 = 0;
+                if (i1 > nx) i1 = nx;
+                if (j1 > ny) j1 = ny;
+                int lx = i1 - i0, ly = j1 - j0;
+                /* local block grid: the couplings inside the subdomain */
+                memset(Al, 0, sizeof(double) * (size_t)lx * ly * 9 * 36);
+                for (int j = j0; j < j1; ++j)
+                    for (int i = i0; i < i1; ++i) {
+                        int nl = (j - j0) * lx + (i - i0), n = j * nx + i;
+                        for (int q = 0; q < 9; ++q) {
+                            int di = q % 3 - 1, dj = q / 3 - 1;
+                            if (i + di < i0 || i + di >= i1 || j + dj < j0 || j + dj >= j1) continue;
+                            memcpy(Al + ((size_t)nl * 9 + q) * 36, A + ((size_t)n * 9 + q) * 36, sizeof(double) * 36);
+                        }
+                        for (int u = 0; u < 6; ++u) rl[nl * 6 + u] = r[n * 6 + u];
+                    }
+                sfo_pcg(lx, ly, Al, rl, patch_iters, el, NULL);
+                /* restricted update: the tile's own nodes only */
+                for (int j = tj * tile; j < (tj + 1) * tile && j < ny; ++j)
+                    for (int i = ti * tile; i < (ti + 1) * tile && i < nx; ++i) {
+                        int nl = (j - j0) * lx + (i - i0), n = j * nx + i;
+                        for (int u = 0; u < 6; ++u) xn[n * 6 + u] = x[n * 6 + u] + el[nl * 6 + u];
+                    }
+            }
+        memcpy(x, xn, sizeof(double) * N);
+    }
+    free(r);
+    free(xn);
+    free(Al);
+    free(rl);
+    free(el);
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -742,16 +903,32 @@ long sfo_packed_size(int w0, int h0, int s, int levels)
  *   W_given       optional outlier masks to use instead of taking W here:
  *                 for l = 0..L-1 and g = 0..gn_iters[l]-1 one w_l*h_l byte
  *                 mask each, in that order; NULL to take W at each state
+ *   cell_recs,    optional bilinear cell decisions to use instead of taking
+ *   cell_offs     them here, for the assembly of each Gauss-Newton step:
+ *                 records of two unsigned each, (pixel y*w + x, code) with
+ *                 code = cell << 4 | clamped << 3 | image << 1 | axis
+ *                 (axis 0 = x), sorted by pixel; the records of level l and
+ *                 step g are [cell_offs[l*16+g], cell_offs[l*16+g+1]); NULL
+ *                 to take every decision here. A decision is an integer
+ *                 taken in floating point (the cell min(floor(p), w-2) of
+ *                 reading C7), like W; replaying another implementation's
+ *                 decisions for samples at a cell edge isolates the
+ *                 continuous error of the rest.
  *   stats         SFO_STATS_LEN doubles: [0] final energy, [1..5] its terms,
  *                 [6] pixels with W = 0 in the last step; at 16 + (l*16+g)*8:
  *                 E at the linearisation point, E accepted, step t (0 if
- *                 rejected), pixels with W = 0, PCG iterations run, and with
+ *                 rejected), pixels with W = 0, PCG iterations run, with
  *                 W_given the pixels whose given W differs from the one taken
- *                 here and the largest | max_k |e_k| - eps_p | among them.
+ *                 here and the largest | max_k |e_k| - eps_p | among them,
+ *                 and with cell_recs the given cell decisions that differ from
+ *                 the ones taken here and the largest distance of such a
+ *                 sample's position from the nearest integer (SFO_STEP_STATS
+ *                 values per step at 16 + (l*16+g)*SFO_STEP_STATS).
  * Returns 0, or -1 for invalid sizes. */
 int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const double* imgs,
                     const double* prev_delta, const double* prev_total, const double* init_coarsest,
-                    const unsigned char* W_given, double* out_delta, double* out_total, double* stats)
+                    const unsigned char* W_given, const unsigned* cell_recs, const long* cell_offs,
+                    double* out_delta, double* out_total, double* stats)
 {
     if (L < 1 || L > SFO_MAX_LEVELS || s < 1) return -1;
     int W[SFO_MAX_LEVELS], H[SFO_MAX_LEVELS], NX[SFO_MAX_LEVELS], NY[SFO_MAX_LEVELS];
@@ -812,11 +989,27 @@ int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const dou
             int ndis = 0;
             double margin = 0.0;
             if (Wg) ndis = w_disagreement(w, h, s, nx, ny, planes, base, delta, Wg, p, &margin);
-            double Ecur = sfo_assemble(w, h, s, nx, ny, l, planes, base, delta, wf, Wg, p, A, b, Wm);
+            const unsigned* rg = NULL;
+            long nrg = 0;
+            if (cell_recs && cell_offs) {
+                rg = cell_recs + 2 * cell_offs[l * SFO_MAX_GN + g];
+                nrg = cell_offs[l * SFO_MAX_GN + g + 1] - cell_offs[l * SFO_MAX_GN + g];
+            }
+            int ncdis = 0;
+            double cmargin = 0.0;
+            double Ecur = assemble_impl(w, h, s, nx, ny, l, planes, base, delta, wf, Wg, p, A, b, Wm, rg, nrg,
+                                        &ncdis, &cmargin);
             have_W = 1;
             int nexcl = 0;
             for (int a = 0; a < w * h; ++a) nexcl += Wm[a] == 0;
-            int its = sfo_pcg(nx, ny, A, b, p->pcg_iters[l], x, NULL);
+            int its = p->pcg_iters[l];
+            if (p->solver == SFO_SOLVER_SCHWARZ) {
+                if (sfo_schwarz(nx, ny, A, b, p->pcg_iters[l], p->patch_iters[l], p->schwarz_tile,
+                                p->schwarz_overlap, x) != 0)
+                    memset(x, 0, sizeof(double) * G * 6);
+            } else {
+                its = sfo_pcg(nx, ny, A, b, p->pcg_iters[l], x, NULL);
+            }
             /* backtracking safeguard [C18]: first t in {1, 1/2, ...} that does
              * not raise the energy (W frozen at this step's value) */
             double t = 1.0, Eacc = Ecur, tacc = 0.0;
@@ -832,7 +1025,7 @@ int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const dou
                 }
             }
             if (stats) {
-                double* st = stats + 16 + (l * SFO_MAX_GN + g) * 8;
+                double* st = stats + 16 + (l * SFO_MAX_GN + g) * SFO_STEP_STATS;
                 st[0] = Ecur;
                 st[1] = Eacc;
                 st[2] = tacc;
@@ -840,6 +1033,8 @@ int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const dou
                 st[4] = its;
                 st[5] = ndis;
                 st[6] = margin;
+                st[7] = ncdis;
+                st[8] = cmargin;
             }
         }
         if (l == 0 && stats) {

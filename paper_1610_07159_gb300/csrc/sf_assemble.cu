@@ -20,11 +20,12 @@ namespace sfk {
 namespace {
 
 // One CTA per cell group (assemble_group), then the block's energy partials.
-template <int MAXT, class TT>
+// REC: also record the cell decisions of samples at a cell edge (test aid).
+template <int MAXT, class TT, bool REC>
 __global__ void __launch_bounds__(ETHREADS, 2) k_assemble(LevelGeom g, int cpb, const typename TT::T* __restrict__ tex,
                                                        const float* __restrict__ base, const float* __restrict__ delta,
                                                        DevParams P, uint8_t* __restrict__ Wmask,
-                                                       float* __restrict__ cell, float2* __restrict__ part)
+                                                       float* __restrict__ cell, float2* __restrict__ part, CellLog log)
 {
     __shared__ float sHB[ETHREADS * HB];
     __shared__ __align__(16) float sW[ETHREADS * WROW];
@@ -32,7 +33,8 @@ __global__ void __launch_bounds__(ETHREADS, 2) k_assemble(LevelGeom g, int cpb, 
     const int tid = threadIdx.x;
     float ep = 0.f, eg = 0.f;
     int nex = 0;
-    assemble_group<MAXT, TT>(g, cpb, blockIdx.x, blockIdx.y, tex, base, delta, P, Wmask, cell, sHB, sW, ep, eg, nex);
+    assemble_group<MAXT, TT, REC>(g, cpb, blockIdx.x, blockIdx.y, tex, base, delta, P, Wmask, cell, sHB, sW, ep, eg,
+                                  nex, &log);
     const int blk = blockIdx.y * gridDim.x + blockIdx.x;
     const float v[3] = {ep, eg, (float)nex};
     ff t[3];
@@ -311,11 +313,18 @@ __global__ void k_unpack_blocks(int G, const float* __restrict__ node, const flo
 
 template <int MAXT>
 void assemble_impl(const LevelGeom& g, int cpb, const void* tex, int prec, const float* base, const float* delta,
-                   const DevParams& P, uint8_t* Wmask, float* cell, float2* part, cudaStream_t st)
+                   const DevParams& P, uint8_t* Wmask, float* cell, float2* part, const CellLog* log, cudaStream_t st)
 {
     dim3 grid((g.ncx + cpb - 1) / cpb, g.ncy);
-    SF_TEX_DISPATCH(prec, TT, k_assemble<MAXT, TT><<<grid, ETHREADS, 0, st>>>(
-                                  g, cpb, static_cast<const typename TT::T*>(tex), base, delta, P, Wmask, cell, part));
+    if (log) {
+        SF_TEX_DISPATCH(prec, TT, k_assemble<MAXT, TT, true><<<grid, ETHREADS, 0, st>>>(
+                                      g, cpb, static_cast<const typename TT::T*>(tex), base, delta, P, Wmask, cell,
+                                      part, *log));
+    } else {
+        SF_TEX_DISPATCH(prec, TT, k_assemble<MAXT, TT, false><<<grid, ETHREADS, 0, st>>>(
+                                      g, cpb, static_cast<const typename TT::T*>(tex), base, delta, P, Wmask, cell,
+                                      part, CellLog{nullptr, nullptr, 0}));
+    }
 }
 
 } // namespace
@@ -330,17 +339,18 @@ int assemble_blocks(const LevelGeom& g, int* cpb_out)
 }
 
 void launch_assemble(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta,
-                     const DevParams& P, uint8_t* Wmask, float* cell, const Scratch& sc, cudaStream_t st)
+                     const DevParams& P, uint8_t* Wmask, float* cell, const Scratch& sc, cudaStream_t st,
+                     const CellLog* log)
 {
     int cpb;
     assemble_blocks(g, &cpb);
     const int need = assemble_tasks_per_thread(cpb);
     if (need <= 1)
-        assemble_impl<1>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, st);
+        assemble_impl<1>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, log, st);
     else if (need <= 2)
-        assemble_impl<2>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, st);
+        assemble_impl<2>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, log, st);
     else
-        assemble_impl<4>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, st);
+        assemble_impl<4>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, log, st);
 }
 
 void launch_gather(const LevelGeom& g, const float* cell, const float* base, const float* delta, const float* wf,

@@ -33,6 +33,9 @@ struct LevelBuf {
     float *z = nullptr, *p0 = nullptr, *p1 = nullptr;
     float* pub = nullptr; // one-reduction PCG: [2][r, w, s][6][G]
     float* cell = nullptr;
+    uint2* cellrec = nullptr;  // [gn][cellcap] cell decisions at cell edges (record_cells)
+    unsigned* celln = nullptr; // [gn] records per step
+    int cellcap = 0;
 };
 
 __global__ void k_set_args(DevArgs* a, const float* i0, const float* i1, const float* i2, const float* i3, float* out,
@@ -257,7 +260,13 @@ int enqueue_level(sf_ctx* c, int l, const LevelIO& io, cudaStream_t st, int& nl)
         StepCtrl* ctrl = c->ctrl + l * SF_MAX_GN + gi;
         uint8_t* Wst = b.W + (size_t)gi * g.w * g.h; // this step's outlier mask, kept for inspection
         prof_mark(c, SF_K_ASSEMBLE, true, st);
-        launch_assemble(g, io.tex, P.precision, b.base, b.delta, c->dp[l], Wst, b.cell, sc, st);
+        if (b.cellrec) {
+            cudaMemsetAsync(b.celln + gi, 0, sizeof(unsigned), st);
+            const CellLog log{b.cellrec + (size_t)gi * b.cellcap, b.celln + gi, b.cellcap};
+            launch_assemble(g, io.tex, P.precision, b.base, b.delta, c->dp[l], Wst, b.cell, sc, st, &log);
+        } else {
+            launch_assemble(g, io.tex, P.precision, b.base, b.delta, c->dp[l], Wst, b.cell, sc, st);
+        }
         prof_mark(c, SF_K_ASSEMBLE, false, st);
         prof_mark(c, SF_K_GATHER, true, st);
         launch_gather(g, b.cell, b.base, b.delta, b.wf, c->dp[l], b.node, b.rhs, b.minv, sc, ctrl, c->asm_blocks[l],
@@ -635,6 +644,12 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
              dalloc(c, &b.node, (size_t)NODE_VALS * g.G) && dalloc(c, &b.rhs, G6) && dalloc(c, &b.minv, G6) &&
              dalloc(c, &b.z, G6) && dalloc(c, &b.p0, G6) && dalloc(c, &b.p1, G6) && dalloc(c, &b.pub, 6 * G6) &&
              dalloc(c, &b.cell, (size_t)CELL_VALS * (g.ncx * g.ncy));
+        if (ok && p->record_cells) {
+            // every sample of a pixel can sit on a cell edge (zero fields put all of them there)
+            b.cellcap = (int)std::min<size_t>(8 * N, (size_t)1 << 30);
+            const size_t steps = (size_t)std::max(1, p->gn_iters[l]);
+            ok = dalloc(c, &b.cellrec, steps * b.cellcap) && dalloc(c, &b.celln, steps);
+        }
     }
     const size_t N0 = (size_t)width * height;
     ok = ok && dalloc(c, &c->status, 4);
@@ -991,6 +1006,26 @@ int sf_probe_energy(sf_ctx* c, int level, const float* base, const float* delta,
     return rc ? fail(rc) : SF_OK;
 }
 
+int sf_probe_cells(sf_ctx* c, int level, int step, unsigned* recs, int max_recs, int* n)
+{
+    if (!c || !n || level < 0 || level >= c->L || step < 0 || step >= std::max(1, c->prm.gn_iters[level]) ||
+        max_recs < 0)
+        return fail(SF_ERR_ARG);
+    const LevelBuf& b = c->lv[level];
+    if (!b.cellrec) return fail(SF_ERR_STATE);
+    int rc = check_cuda(cudaDeviceSynchronize());
+    unsigned cnt = 0;
+    if (!rc) rc = check_cuda(cudaMemcpy(&cnt, b.celln + step, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (rc) return fail(rc);
+    *n = (int)std::min<unsigned>(cnt, (unsigned)INT32_MAX);
+    const size_t k = std::min<size_t>({(size_t)cnt, (size_t)b.cellcap, (size_t)max_recs});
+    if (recs && k)
+        rc = check_cuda(cudaMemcpy(recs, b.cellrec + (size_t)step * b.cellcap, k * sizeof(uint2),
+                                   cudaMemcpyDeviceToHost));
+    if (rc) return fail(rc);
+    return cnt > (unsigned)b.cellcap ? fail(SF_ERR_STATE) : SF_OK;
+}
+
 int sf_batch_create(int n, const int* widths, const int* heights, const int* levels, int grid_stride,
                     const sf_params* p, sf_batch** out)
 {
@@ -1008,6 +1043,7 @@ int sf_batch_create(int n, const int* widths, const int* heights, const int* lev
     sf_params q = *p;
     q.use_graph = 0;
     q.video = 0;
+    q.record_cells = 0;
     q.profile_mask = 0;
     std::string key = std::to_string(n) + "|" + std::to_string(grid_stride);
     for (int i = 0; i < n; ++i) {

@@ -160,6 +160,32 @@ __device__ __forceinline__ void axis_cell(int x, float o, int w, int& ix, float&
     }
 }
 
+// Record of the bilinear cell decisions taken by the assembly (a test aid,
+// off on the solve path): every sample whose position lies within
+// CELL_LOG_MARGIN px of a cell edge appends (pixel y*w + x, cell << 4 |
+// clamped << 3 | image << 1 | axis). A cell is an integer decision taken in
+// FP32 (reading C7); an FP64 implementation at a slightly different state can
+// take the other cell there, and the analytic Jacobian of the bilinear
+// interpolant jumps between cells. `n` may exceed `cap` (records past cap are
+// dropped, the count still grows).
+constexpr float CELL_LOG_MARGIN = 1e-3f;
+struct CellLog {
+    uint2* buf;
+    unsigned* n;
+    int cap;
+};
+
+__device__ __forceinline__ void log_cell(const CellLog* log, int pix, float o, int ix, bool clamped, int img, int axis)
+{
+    o = fminf(fmaxf(o, -1.0e7f), 1.0e7f);
+    const float fr = o - floorf(o);
+    if (fr >= CELL_LOG_MARGIN && fr <= 1.f - CELL_LOG_MARGIN) return;
+    const unsigned k = atomicAdd(log->n, 1u);
+    if (k < (unsigned)log->cap)
+        log->buf[k] = make_uint2((unsigned)pix, ((unsigned)ix << 4) | ((clamped ? 1u : 0u) << 3) |
+                                                     ((unsigned)img << 1) | (unsigned)axis);
+}
+
 // Texel storage: FP32 (float4) or 16-bit (four halves or bfloat16s in 8
 // bytes). Loads convert to FP32; all arithmetic after the load is FP32.
 struct TexF32 {
@@ -224,15 +250,19 @@ struct Tap {
     float v[3], dx[3], dy[3];
 };
 
-template <class TT>
+template <class TT, bool REC = false>
 __device__ __forceinline__ void tap4(const typename TT::T* __restrict__ T, int w, int h, int x, int y, float ox,
-                                     float oy, Tap& o)
+                                     float oy, Tap& o, const CellLog* log = nullptr, int img = 0)
 {
     int ix, iy;
     float fx, fy;
     bool clx, cly;
     axis_cell(x, ox, w, ix, fx, clx);
     axis_cell(y, oy, h, iy, fy, cly);
+    if (REC) {
+        log_cell(log, y * w + x, ox, ix, clx, img, 0);
+        log_cell(log, y * w + x, oy, iy, cly, img, 1);
+    }
     const typename TT::T* r0 = T + (size_t)iy * w + ix;
     const float4 a = TT::ld(r0), b = TT::ld(r0 + 1), c = TT::ld(r0 + w), d = TT::ld(r0 + w + 1);
     const float av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z}, cv[3] = {c.x, c.y, c.z}, dv[3] = {d.x, d.y, d.z};

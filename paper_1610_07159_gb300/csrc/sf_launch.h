@@ -39,8 +39,10 @@ struct Scratch {
     int* status;
 };
 int assemble_blocks(const LevelGeom& g, int* cpb_out);
+// log: record the cell decisions of samples at a cell edge (test aid), or null
 void launch_assemble(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta,
-                     const DevParams& P, uint8_t* Wmask, float* cell, const Scratch& sc, cudaStream_t st);
+                     const DevParams& P, uint8_t* Wmask, float* cell, const Scratch& sc, cudaStream_t st,
+                     const CellLog* log = nullptr);
 void launch_gather(const LevelGeom& g, const float* cell, const float* base, const float* delta, const float* wf,
                    const DevParams& P, float* node, float* rhs, float* minv, const Scratch& sc, StepCtrl* ctrl,
                    int n_asm_blocks, cudaStream_t st);

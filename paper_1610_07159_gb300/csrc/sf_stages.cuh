@@ -28,10 +28,10 @@ __constant__ int c_pair_l[NPAIR] = {0, 1, 2, 3, 1, 2, 3, 2, 3, 3};
 // Data terms of one pixel at fields f (Eqs. 1-6, 11-13). Returns the
 // unweighted photometric and gradient penalties; with ASSEMBLE also the
 // pixel's 6x6 normal-equation block H (packed) and right-hand side b.
-template <bool ASSEMBLE, class TT>
+template <bool ASSEMBLE, class TT, bool REC = false>
 __device__ __forceinline__ void pixel_data(const typename TT::T* __restrict__ tex, int w, int h, int x, int y, const float f[6],
                                            const DevParams& P, int Wgiven, int& Wout, float& Ep, float& Eg, float* H,
-                                           float* b)
+                                           float* b, const CellLog* log = nullptr)
 {
     const size_t plane = (size_t)w * h;
     Tap tp[4];
@@ -39,7 +39,7 @@ __device__ __forceinline__ void pixel_data(const typename TT::T* __restrict__ te
     for (int c = 0; c < 4; ++c) {
         const float ox = sgn(c, 0) * f[0] + sgn(c, 1) * f[2] + sgn(c, 2) * f[4];
         const float oy = sgn(c, 0) * f[1] + sgn(c, 1) * f[3] + sgn(c, 2) * f[5];
-        tap4<TT>(tex + c * plane, w, h, x, y, ox, oy, tp[c]);
+        tap4<TT, REC>(tex + c * plane, w, h, x, y, ox, oy, tp[c], log, c);
     }
     float e[6];
 #pragma unroll
@@ -235,12 +235,13 @@ __device__ __forceinline__ void task_sum(float* a, float* e, int qa, int qb, con
 // pixel energies and the count of excluded pixels are added to the thread's
 // ep, eg, nex. sHB and sW are ETHREADS * HB and ETHREADS * WROW floats of
 // shared memory (sW 16-byte aligned).
-template <int MAXT, class TT>
+template <int MAXT, class TT, bool REC = false>
 __device__ __forceinline__ void assemble_group(const LevelGeom& g, int cpb, int bx, int by,
                                                const typename TT::T* __restrict__ tex, const float* base,
                                                const float* delta, const DevParams& P,
                                                uint8_t* Wmask, float* cell, float* sHB,
-                                               float* sW, float& ep, float& eg, int& nex)
+                                               float* sW, float& ep, float& eg, int& nex,
+                                               const CellLog* log = nullptr)
 {
     const int tid = threadIdx.x;
     const int s = g.s;
@@ -282,7 +283,7 @@ __device__ __forceinline__ void assemble_group(const LevelGeom& g, int cpb, int 
             pixel_fields(base, delta, nullptr, 0.f, g.G, j0 * g.nx + i0, g.nx, a, bb, f);
             int Wi;
             float Ep, Eg;
-            pixel_data<true, TT>(tex, g.w, g.h, x, y, f, P, -1, Wi, Ep, Eg, H, bv);
+            pixel_data<true, TT, REC>(tex, g.w, g.h, x, y, f, P, -1, Wi, Ep, Eg, H, bv, log);
             Wmask[y * g.w + x] = (uint8_t)Wi;
             ep += Ep;
             eg += Eg;

@@ -34,6 +34,7 @@ EXPORTED = (
     "sf_grid_dims", "sf_set_init", "sf_reset",
     "sf_get_stats", "sf_get_state", "sf_kernel_times", "sf_destroy", "sf_status_string", "sf_last_error", "sf_probe_pyramid",
     "sf_probe_feature_weights", "sf_probe_assemble", "sf_probe_pcg", "sf_probe_wmask", "sf_probe_energy",
+    "sf_probe_cells", "sf_probe_fma_rate",
     "sf_pcg_static", "sf_batch_create", "sf_batch_layout", "sf_batch_solve", "sf_batch_set_schedule",
     "sf_batch_get_schedule", "sf_batch_tune", "sf_batch_sequence", "sf_batch_reset", "sf_batch_destroy",
     "sf_probe_gemm_bf16", "sf_net_param_count", "sf_net_create", "sf_net_set_params", "sf_net_get_params",
@@ -59,7 +60,7 @@ class Params(ctypes.Structure):
         ("wfeat_gain", ctypes.c_float), ("wfeat_tau", ctypes.c_float),
         ("temporal_mode", ctypes.c_int), ("precision", ctypes.c_int), ("max_backtracks", ctypes.c_int),
         ("use_graph", ctypes.c_int), ("profile_mask", ctypes.c_int), ("pcg_mode", ctypes.c_int),
-        ("video", ctypes.c_int),
+        ("video", ctypes.c_int), ("record_cells", ctypes.c_int),
     ]
 
 
@@ -119,6 +120,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sf_probe_pcg.argtypes = [vp, i, i, fp, vp]
     L.sf_probe_wmask.argtypes = [vp, i, i, fp, vp]
     L.sf_probe_energy.argtypes = [vp, i, fp, fp, fp, fp, fp, vp]
+    L.sf_probe_cells.argtypes = [vp, i, i, ctypes.POINTER(ctypes.c_uint), i, ip]
+    L.sf_probe_fma_rate.argtypes = [i, ctypes.POINTER(ctypes.c_double), vp]
     L.sf_pcg_static.argtypes = [i, i, fp, fp, i, fp, vp]
     sz = ctypes.POINTER(ctypes.c_size_t)
     L.sf_batch_create.argtypes = [i, ip, ip, ip, i, ctypes.POINTER(Params), ctypes.POINTER(vp)]
@@ -186,6 +189,13 @@ def _ptr(t: torch.Tensor | None, dtype: torch.dtype | None = None) -> int | None
 
 def _stream() -> int:
     return torch.cuda.current_stream().cuda_stream
+
+
+def fma_rate(reps: int = 5) -> float:
+    """The FP32 FMA rate of the current GPU in flops/s (measurement aid)."""
+    out = ctypes.c_double()
+    _check(load().sf_probe_fma_rate(int(reps), ctypes.byref(out), _stream()), "sf_probe_fma_rate")
+    return out.value
 
 
 def gemm_bf16(A: torch.Tensor, B: torch.Tensor, BN: int = 256, splits: int = 1) -> torch.Tensor:
@@ -378,6 +388,24 @@ class Solver:
         """The outlier masks of every Gauss-Newton step of the last frame, [level][step]."""
         return [[self.probe_wmask(l, g).cpu().numpy() for g in range(self.params.gn_iters[l])]
                 for l in range(self.levels)]
+
+    def cell_records(self) -> list:
+        """The bilinear cell decisions at cell edges of every Gauss-Newton step
+        of the last frame, [level][step] uint32 arrays [n, 2] (needs
+        record_cells=1 at creation)."""
+        import numpy as np
+        out = []
+        for l in range(self.levels):
+            per = []
+            for g in range(self.params.gn_iters[l]):
+                n = ctypes.c_int()
+                _check(self.L.sf_probe_cells(self.ctx, l, g, None, 0, ctypes.byref(n)), "sf_probe_cells")
+                buf = np.zeros((max(n.value, 1), 2), dtype=np.uint32)
+                _check(self.L.sf_probe_cells(self.ctx, l, g, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint)),
+                                             n.value, ctypes.byref(n)), "sf_probe_cells")
+                per.append(buf[:n.value])
+            out.append(per)
+        return out
 
     def probe_energy(self, level: int, base: torch.Tensor, delta: torch.Tensor, wfeat: torch.Tensor,
                      W: torch.Tensor | None = None) -> torch.Tensor:

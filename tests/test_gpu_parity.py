@@ -205,6 +205,15 @@ def test_config1_frame_parity():
         for l in range(3):
             for g in range(5):
                 assert r[1].step_t[l][g] == r[2].step(l, g)[2]
+        # against the oracle's OWN outlier decisions (no replay), reported: the
+        # replay above removes only the pixels whose W parts at the threshold
+        fields, st, ref, own = r[0], r[1], r[2], r[3]
+        err_own = np.max(np.abs(fields - own.fields(0)), axis=(1, 2))
+        err_rep = np.max(np.abs(fields - ref.fields(0)), axis=(1, 2))
+        print("\nconfig 1 max-abs px, W replayed: %s; oracle's own W: %s; energy rel (own W) %.2e" % (
+            np.array2string(err_rep, precision=2), np.array2string(err_own, precision=2),
+            abs(st.energy - own.energy) / abs(own.energy)))
+        assert np.all(err_own <= FIELD_TOL), err_own
 
 
 @pytest.mark.parametrize("kw", [{"robust_mode": O.SQRT_PAPER}, {"grad_mode": O.GRAD_LITERAL},

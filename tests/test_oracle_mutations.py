@@ -52,6 +52,14 @@ MUTANTS = {
         "*dpx = clx ? 0.0 : (1 - fy) * (p10 - p00) + fy * (p11 - p01);",
         "*dpx = clx ? 0.0 : fy * (p10 - p00) + (1 - fy) * (p11 - p01);"),
     "Jacobi preconditioner dropped": ("Minv[n * 6 + u] = d > 0.0 ? 1.0 / d : 1.0;", "Minv[n * 6 + u] = 1.0;"),
+    "Schwarz residual sign": ("for (int a = 0; a < N; ++a) r[a] = b[a] - r[a];",
+                              "for (int a = 0; a < N; ++a) r[a] = b[a] + r[a];"),
+    "Schwarz update not restricted to the tile": (
+        "for (int j = tj * tile; j < (tj + 1) * tile && j < ny; ++j)\n"
+        "                    for (int i = ti * tile; i < (ti + 1) * tile && i < nx; ++i) {",
+        "for (int j = j0; j < j1; ++j)\n                    for (int i = i0; i < i1; ++i) {"),
+    "Schwarz subdomain without its overlap": ("int i0 = ti * tile - overlap, j0 = tj * tile - overlap;",
+                                               "int i0 = ti * tile, j0 = tj * tile;"),
 }
 
 
@@ -65,7 +73,8 @@ def _run_mutant(name, tmpdir):
     with open(csrc, "w") as f:
         f.write(src.replace(text, planted))
     subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", so, csrc, "-lm"])
-    env = dict(os.environ, SFO_LIB=so)
+    # one BLAS thread per mutant run: the runs go in parallel
+    env = dict(os.environ, SFO_LIB=so, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x",
                         "-q", "-p", "no:cacheprovider"], capture_output=True, text=True, env=env, cwd=ROOT)
     return r.returncode, r.stdout[-400:]

@@ -426,6 +426,64 @@ def test_pcg_matches_dense_cholesky_and_decreases_model():
 # hierarchy and temporal transfer
 # --------------------------------------------------------------------------- #
 
+def _tiny_system(seed=13, w=40, h=28, s=4):
+    lv = _tiny_level(w=w, h=h, s=s, seed=seed)
+    rng = np.random.default_rng(seed)
+    base, delta = _smooth_state(lv, rng)
+    A, b, _, _ = O.assemble(lv, base, delta, 1.0 + rng.random(lv.G), O.Params(eps_p=0.3))
+    return lv, A, b
+
+
+def test_schwarz_with_one_subdomain_is_plain_pcg():
+    """A single subdomain holding the whole grid, one sweep: the local solve
+    is the global Jacobi-PCG from zero (Section 5.2 reduces to Section 5.1)."""
+    lv, A, b = _tiny_system()
+    for it in (1, 4, 12):
+        x_pcg, _, _ = O.pcg(lv.nx, lv.ny, A, b, it)
+        x_sw = O.schwarz(lv.nx, lv.ny, A, b, 1, it, tile=max(lv.nx, lv.ny), overlap=0)
+        np.testing.assert_allclose(x_sw, x_pcg, rtol=0, atol=1e-13 * np.abs(x_pcg).max())
+
+
+@pytest.mark.parametrize("tile,overlap", [(2, 0), (3, 1), (4, 2)])
+def test_schwarz_with_exact_local_solves_is_restricted_additive_schwarz(tile, overlap):
+    """With enough patch iterations the local PCG solves exactly, and each
+    sweep is x <- x + sum_k R~_k^T A_k^-1 R_k (b - A x) with A_k the dense
+    subdomain block (numpy.linalg.solve) and R~_k keeping the tile's own
+    nodes: restricted additive Schwarz, written out here on the dense matrix."""
+    lv, A, b = _tiny_system()
+    nx, ny = lv.nx, lv.ny
+    D = _dense(A, nx, ny)
+    bb = b.reshape(-1)
+    x = np.zeros_like(bb)
+    sweeps = 3
+    for _ in range(sweeps):
+        r = bb - D @ x
+        xn = x.copy()
+        for tj in range(0, ny, tile):
+            for ti in range(0, nx, tile):
+                ext = [(i, j) for j in range(max(tj - overlap, 0), min(tj + tile + overlap, ny))
+                       for i in range(max(ti - overlap, 0), min(ti + tile + overlap, nx))]
+                idx = np.array([6 * (j * nx + i) + u for (i, j) in ext for u in range(6)])
+                e = np.linalg.solve(D[np.ix_(idx, idx)], r[idx])
+                for k, (i, j) in enumerate(ext):
+                    if ti <= i < ti + tile and tj <= j < tj + tile:
+                        n = j * nx + i
+                        xn[6 * n:6 * n + 6] = x[6 * n:6 * n + 6] + e[6 * k:6 * k + 6]
+        x = xn
+    x_sw = O.schwarz(nx, ny, A, b, sweeps, 400, tile=tile, overlap=overlap).reshape(-1)
+    np.testing.assert_allclose(x_sw, x, rtol=0, atol=1e-9 * np.abs(x).max())
+
+
+def test_schwarz_sweeps_converge_to_the_dense_solution():
+    lv, A, b = _tiny_system()
+    D = _dense(A, lv.nx, lv.ny)
+    x_star = np.linalg.solve(D, b.reshape(-1))
+    errs = [np.abs(O.schwarz(lv.nx, lv.ny, A, b, k, 10, tile=3, overlap=1).reshape(-1) - x_star).max()
+            for k in (1, 4, 16, 64)]
+    assert all(e2 < e1 for e1, e2 in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-8 * np.abs(x_star).max()
+
+
 def test_upsample_constant_and_linear_fields():
     nxc, nyc, nx, ny = 6, 5, 12, 9
     Tc = np.repeat(np.arange(1.0, 7.0)[:, None], nxc * nyc, axis=1)
