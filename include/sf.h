@@ -94,6 +94,17 @@ enum { SF_PRESET_FIG2 = 0, SF_PRESET_FIG568 = 1, SF_PRESET_FIG79 = 2 };
  * form (the same iterates in exact arithmetic, one fused reduction and one
  * barrier per iteration). */
 enum { SF_PCG_AUTO = 0, SF_PCG_CLUSTER = 1, SF_PCG_GRID = 2, SF_PCG_DSM = 3, SF_PCG_ONE_REDUCTION = 4 };
+/* Linear solver of each Gauss-Newton step. SF_SOLVER_PCG: Jacobi-PCG on the
+ * whole level (Section 5.1), pcg_iters iterations. SF_SOLVER_SCHWARZ: the
+ * domain decomposition of Section 5.2, data-parallel alternating Schwarz
+ * sweeps over square subdomains of schwarz_tile x schwarz_tile grid nodes
+ * plus schwarz_overlap nodes of overlap on each side; every sweep solves each
+ * subdomain's system by patch_iters Jacobi-PCG iterations in shared memory
+ * (the paper's "PCG iterations with patch iterations each": pcg_iters is the
+ * number of sweeps), and the subdomains exchange the iterate through global
+ * memory. Restricted additive Schwarz: each node takes the correction of the
+ * subdomain whose tile holds it. */
+enum { SF_SOLVER_PCG = 0, SF_SOLVER_SCHWARZ = 1 };
 /* Kernel classes, for sf_params.profile_mask and sf_kernel_times. */
 enum {
     SF_K_PYRAMID = 0,  /* mip-map levels with gradient planes */
@@ -127,6 +138,10 @@ typedef struct sf_params {
     int pcg_mode;                 /* SF_PCG_AUTO | _CLUSTER | _GRID | _DSM | _ONE_REDUCTION */
     int video;                    /* 1: allocate the level pipeline of sf_solve_video */
     int record_cells;             /* 1: record the bilinear cell decisions at cell edges (sf_probe_cells) */
+    int solver;                   /* SF_SOLVER_PCG | SF_SOLVER_SCHWARZ */
+    int patch_iters[SF_MAX_LEVELS]; /* Schwarz: local PCG iterations per sweep (5) */
+    int schwarz_tile;             /* Schwarz: tile side in grid nodes (8: 16 px at the paper's stride 2) */
+    int schwarz_overlap;          /* Schwarz: overlap in grid nodes on each side (1: the paper's 2 px) */
 } sf_params;
 
 typedef struct sf_stats {
@@ -255,6 +270,13 @@ SF_API int sf_probe_assemble(sf_ctx* ctx, int level, const float* base, const fl
 /* Runs `iters` PCG iterations on the system last assembled for `level`
  * (by sf_probe_assemble) and writes the solution (G x 6). */
 SF_API int sf_probe_pcg(sf_ctx* ctx, int level, int iters, float* x, void* stream);
+
+/* Runs `sweeps` alternating Schwarz sweeps of `patch` local PCG iterations
+ * (Section 5.2, SF_SOLVER_SCHWARZ with the context's tile and overlap) on the
+ * system last assembled for `level` (by sf_probe_assemble) and writes the
+ * solution (G x 6). SF_ERR_ARG if the tiling cannot run on one CTA per
+ * subdomain (six threads per node of an extended subdomain, at most 640). */
+SF_API int sf_probe_schwarz(sf_ctx* ctx, int level, int sweeps, int patch, float* x, void* stream);
 
 /* Copies the outlier mask W (Section 4.1) that Gauss-Newton step `step` of
  * `level` used in the last frame (h*w bytes, 1 = kept, 0 = pruned). */

@@ -59,13 +59,15 @@ struct sf_ctx {
     LevelBuf lv[SF_MAX_LEVELS];
     DevParams dp[SF_MAX_LEVELS]{};
     PcgPlan plan[SF_MAX_LEVELS]{};
+    SchwarzPlan splan[SF_MAX_LEVELS]{};
     int asm_blocks[SF_MAX_LEVELS]{};
     int trial_blocks[SF_MAX_LEVELS]{};   // CTAs of the cooperative trial launch
     int sm_count = 0;
     Scratch sc[SF_MAX_LEVELS]{};              // per level, so levels can run concurrently
     float2* pcg_part[SF_MAX_LEVELS]{};
     int* status = nullptr;                    // device status word shared by all levels
-    unsigned long long* bar = nullptr;        // grid-barrier arrival counters: [level] PCG, [SF_MAX_LEVELS + level] trials
+    unsigned long long* bar = nullptr;        // grid-barrier arrival counters: [level] PCG, [SF_MAX_LEVELS + level]
+                                              // trials, [2 * SF_MAX_LEVELS + level] Schwarz
     StepCtrl* ctrl = nullptr; // [SF_MAX_LEVELS * SF_MAX_GN + 1], the last one for probes
     double* rec = nullptr;    // [8] energy record
     DevArgs* args = nullptr;
@@ -273,8 +275,12 @@ int enqueue_level(sf_ctx* c, int l, const LevelIO& io, cudaStream_t st, int& nl)
                       st);
         prof_mark(c, SF_K_GATHER, false, st);
         prof_mark(c, SF_K_PCG, true, st);
-        cudaError_t e = launch_pcg(g, c->plan[l], b.node, b.rhs, b.minv, b.x, b.z, b.p0, b.p1, b.pub, c->pcg_part[l],
-                                   c->bar + l, c->status, P.pcg_iters[l], 0, st);
+        cudaError_t e = P.solver == SF_SOLVER_SCHWARZ
+                            ? launch_schwarz(g, c->splan[l], b.node, b.rhs, b.minv, b.x, b.z,
+                                             c->bar + 2 * SF_MAX_LEVELS + l, c->status, P.pcg_iters[l],
+                                             P.patch_iters[l], 0, st)
+                            : launch_pcg(g, c->plan[l], b.node, b.rhs, b.minv, b.x, b.z, b.p0, b.p1, b.pub,
+                                         c->pcg_part[l], c->bar + l, c->status, P.pcg_iters[l], 0, st);
         prof_mark(c, SF_K_PCG, false, st);
         if (e != cudaSuccess) return check_cuda(e);
         nl += 3;
@@ -559,6 +565,10 @@ int sf_params_preset(sf_params* p, int preset)
     p->precision = SF_FP32;
     p->max_backtracks = 4;
     p->use_graph = 1;
+    p->solver = SF_SOLVER_PCG;
+    for (int l = 0; l < SF_MAX_LEVELS; ++l) p->patch_iters[l] = 5;
+    p->schwarz_tile = 8;
+    p->schwarz_overlap = 1;
     return SF_OK;
 }
 
@@ -570,13 +580,15 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
         p->max_backtracks < 0 || p->max_backtracks > 8 || p->robust_mode < 0 || p->robust_mode > 1 ||
         p->grad_mode < 0 || p->grad_mode > 1 || p->wfeat_mode < 0 || p->wfeat_mode > 1 || p->temporal_mode < 0 ||
         p->temporal_mode > 2 || p->precision < SF_FP32 || p->precision > SF_MIXED_FP16 || !(p->wfeat_tau > 0.f) ||
-        p->pcg_mode < 0 ||
-        p->pcg_mode > SF_PCG_ONE_REDUCTION) {
+        p->pcg_mode < 0 || p->pcg_mode > SF_PCG_ONE_REDUCTION || p->solver < SF_SOLVER_PCG ||
+        p->solver > SF_SOLVER_SCHWARZ || (p->solver == SF_SOLVER_SCHWARZ && (p->schwarz_tile < 1 ||
+                                                                               p->schwarz_overlap < 0))) {
         fail(SF_ERR_ARG);
         return nullptr;
     }
     for (int l = 0; l < levels; ++l)
-        if (p->gn_iters[l] < 0 || p->gn_iters[l] > SF_MAX_GN || p->pcg_iters[l] < 0 || p->pcg_iters[l] > 100000) {
+        if (p->gn_iters[l] < 0 || p->gn_iters[l] > SF_MAX_GN || p->pcg_iters[l] < 0 || p->pcg_iters[l] > 100000 ||
+            (p->solver == SF_SOLVER_SCHWARZ && (p->patch_iters[l] < 0 || p->patch_iters[l] > 100000))) {
             fail(SF_ERR_ARG);
             return nullptr;
         }
@@ -627,7 +639,10 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
     for (int l = 0; l < levels; ++l) {
         c->trial_blocks[l] = trials_blocks(c->geo[l], p->precision, c->sm_count);
         c->plan[l] = pcg_plan(c->geo[l].G, c->sm_count, p->pcg_mode);
-        if (c->plan[l].blocks < 1) {
+        // a level needs the plan of the solver it runs (the global PCG has a size limit, Schwarz does not)
+        if ((p->solver == SF_SOLVER_PCG && c->plan[l].blocks < 1) ||
+            (p->solver == SF_SOLVER_SCHWARZ &&
+             schwarz_plan(c->geo[l], p->schwarz_tile, p->schwarz_overlap, c->sm_count, &c->splan[l]) != 0)) {
             delete c;
             fail(SF_ERR_ARG);
             return nullptr;
@@ -674,7 +689,7 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
                 ok = dalloc(c, &c->vstate_delta[l][q], (size_t)6 * c->geo[l].G) &&
                      dalloc(c, &c->vstate_total[l][q], (size_t)6 * c->geo[l].G);
     }
-    ok = ok && dalloc(c, &c->bar, (size_t)2 * SF_MAX_LEVELS) &&
+    ok = ok && dalloc(c, &c->bar, (size_t)3 * SF_MAX_LEVELS) &&
          dalloc(c, &c->ctrl, (size_t)SF_MAX_LEVELS * SF_MAX_GN + 1) && dalloc(c, &c->rec, 8) &&
          dalloc(c, &c->args, 1) && dalloc(c, &c->init_buf, (size_t)6 * c->geo[levels - 1].G) &&
          dalloc(c, &c->in_buf[0], N0) && dalloc(c, &c->in_buf[1], N0) && dalloc(c, &c->in_buf[2], N0) &&
@@ -811,7 +826,7 @@ int sf_reset(sf_ctx* c)
     c->pending_init = 0;
     int rc = check_cuda(cudaDeviceSynchronize());
     if (!rc) rc = check_cuda(cudaMemset(c->status, 0, 4 * sizeof(int)));
-    if (!rc) rc = check_cuda(cudaMemset(c->bar, 0, 2 * SF_MAX_LEVELS * sizeof(unsigned long long)));
+    if (!rc) rc = check_cuda(cudaMemset(c->bar, 0, 3 * SF_MAX_LEVELS * sizeof(unsigned long long)));
     for (int l = 0; l < c->L && !rc; ++l) rc = check_cuda(cudaMemset(c->sc[l].counters, 0, 8 * sizeof(unsigned)));
     if (!rc) rc = check_cuda(cudaDeviceSynchronize());
     return rc ? fail(rc) : SF_OK;
@@ -968,13 +983,27 @@ int sf_probe_assemble(sf_ctx* c, int level, const float* base, const float* delt
 
 int sf_probe_pcg(sf_ctx* c, int level, int iters, float* x, void* stream)
 {
-    if (!c || !x || level < 0 || level >= c->L || iters < 0) return fail(SF_ERR_ARG);
+    if (!c || !x || level < 0 || level >= c->L || iters < 0 || c->plan[level].blocks < 1) return fail(SF_ERR_ARG);
     cudaStream_t st = (cudaStream_t)stream;
     c->last_stream = st;
     const LevelGeom& g = c->geo[level];
     LevelBuf& b = c->lv[level];
     int rc = check_cuda(launch_pcg(g, c->plan[level], b.node, b.rhs, b.minv, x, b.z, b.p0, b.p1, b.pub,
                                    c->pcg_part[level], c->bar + level, c->status, iters, 1, st));
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_probe_schwarz(sf_ctx* c, int level, int sweeps, int patch, float* x, void* stream)
+{
+    if (!c || !x || level < 0 || level >= c->L || sweeps < 0 || patch < 0) return fail(SF_ERR_ARG);
+    SchwarzPlan plan{};
+    if (schwarz_plan(c->geo[level], c->prm.schwarz_tile, c->prm.schwarz_overlap, c->sm_count, &plan) != 0)
+        return fail(SF_ERR_ARG);
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    LevelBuf& b = c->lv[level];
+    int rc = check_cuda(launch_schwarz(c->geo[level], plan, b.node, b.rhs, b.minv, x, b.z,
+                                       c->bar + 2 * SF_MAX_LEVELS + level, c->status, sweeps, patch, 1, st));
     return rc ? fail(rc) : SF_OK;
 }
 
@@ -1032,7 +1061,7 @@ int sf_batch_create(int n, const int* widths, const int* heights, const int* lev
     g_last_error = SF_OK;
     if (!out) return fail(SF_ERR_ARG);
     *out = nullptr;
-    if (n < 1 || n > (1 << 16) || !widths || !heights || !levels || !p || p->precision != SF_FP32 ||
+    if (n < 1 || n > (1 << 16) || !widths || !heights || !levels || !p || p->precision != SF_FP32 || p->solver != SF_SOLVER_PCG ||
         p->gn_iters[0] < 1)
         return fail(SF_ERR_ARG);
     sf_batch* b = new (std::nothrow) sf_batch();
@@ -1419,7 +1448,7 @@ int sf_tune_pcg(sf_ctx* c, const float* L_t, const float* R_t, const float* L_t1
         const LevelGeom& g = c->geo[l];
         LevelBuf& b = c->lv[l];
         const int iters = c->prm.pcg_iters[l];
-        if (iters < 1) continue;
+        if (iters < 1 || c->prm.solver == SF_SOLVER_SCHWARZ) continue;
         const std::string key = std::to_string(g.nx) + "x" + std::to_string(g.ny) + "|" + std::to_string(iters) + "|" +
                                 std::to_string(c->sm_count);
         {

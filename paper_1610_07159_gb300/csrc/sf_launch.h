@@ -78,6 +78,26 @@ cudaError_t launch_pcg(const LevelGeom& g, const PcgPlan& plan, const float* nod
                        const float* minv, float* x, float* z, float* p0, float* p1, float* pub, float2* part,
                        unsigned long long* bar, int* status, int iters, int interleaved_out, cudaStream_t st);
 
+// sf_schwarz.cu: the normal equations solved by restricted additive Schwarz
+// sweeps over square subdomains with local PCG in shared memory (Section 5.2).
+struct SchwarzPlan {
+    int tile, overlap; // nodes
+    int nsub;          // subdomains
+    int emax;          // nodes of the largest extended subdomain
+    int es;            // shared-memory stride (a compiled bound >= emax)
+    int threads;       // per CTA (six per node)
+    int smem;          // dynamic shared memory per CTA (bytes)
+    int blocks;        // CTAs of the cooperative launch (all co-resident)
+};
+// 0, or -1 if the tiling cannot run (too large for one CTA)
+int schwarz_plan(const LevelGeom& g, int tile, int overlap, int sm_count, SchwarzPlan* out);
+// x (component-major [6][G], or interleaved [G][6] with interleaved_out) after
+// `sweeps` sweeps of `patch` local iterations; xtmp is a second [6][G] buffer;
+// bar a grid-barrier counter used only by this kernel
+cudaError_t launch_schwarz(const LevelGeom& g, const SchwarzPlan& plan, const float* node, const float* rhs,
+                           const float* minv, float* x, float* xtmp, unsigned long long* bar, int* status, int sweeps,
+                           int patch, int interleaved_out, cudaStream_t st);
+
 // sf_batch.cu: the frame solve of many independent sequences in one launch,
 // one thread-block cluster per sequence. Descriptors live in device memory
 // and are read-only during a launch (the per-frame input and output pointers

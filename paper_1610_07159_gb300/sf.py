@@ -27,6 +27,7 @@ TEMPORAL_PROPAGATE, TEMPORAL_COPY, TEMPORAL_ZERO = 0, 1, 2
 FP32, MIXED_BF16, MIXED_FP16 = 0, 1, 2
 K_PYRAMID, K_LEVEL, K_ASSEMBLE, K_GATHER, K_PCG, K_ENERGY = range(6)
 PCG_AUTO, PCG_CLUSTER, PCG_GRID, PCG_DSM, PCG_ONE_REDUCTION = 0, 1, 2, 3, 4
+SOLVER_PCG, SOLVER_SCHWARZ = 0, 1
 PRESET_FIG2, PRESET_FIG568, PRESET_FIG79 = 0, 1, 2
 
 EXPORTED = (
@@ -34,7 +35,7 @@ EXPORTED = (
     "sf_grid_dims", "sf_set_init", "sf_reset",
     "sf_get_stats", "sf_get_state", "sf_kernel_times", "sf_destroy", "sf_status_string", "sf_last_error", "sf_probe_pyramid",
     "sf_probe_feature_weights", "sf_probe_assemble", "sf_probe_pcg", "sf_probe_wmask", "sf_probe_energy",
-    "sf_probe_cells", "sf_probe_fma_rate",
+    "sf_probe_cells", "sf_probe_fma_rate", "sf_probe_schwarz",
     "sf_pcg_static", "sf_batch_create", "sf_batch_layout", "sf_batch_solve", "sf_batch_set_schedule",
     "sf_batch_get_schedule", "sf_batch_tune", "sf_batch_sequence", "sf_batch_reset", "sf_batch_destroy",
     "sf_probe_gemm_bf16", "sf_net_param_count", "sf_net_create", "sf_net_set_params", "sf_net_get_params",
@@ -61,6 +62,8 @@ class Params(ctypes.Structure):
         ("temporal_mode", ctypes.c_int), ("precision", ctypes.c_int), ("max_backtracks", ctypes.c_int),
         ("use_graph", ctypes.c_int), ("profile_mask", ctypes.c_int), ("pcg_mode", ctypes.c_int),
         ("video", ctypes.c_int), ("record_cells", ctypes.c_int),
+        ("solver", ctypes.c_int), ("patch_iters", ctypes.c_int * MAX_LEVELS),
+        ("schwarz_tile", ctypes.c_int), ("schwarz_overlap", ctypes.c_int),
     ]
 
 
@@ -118,6 +121,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sf_probe_feature_weights.argtypes = [vp, i, fp, fp, vp]
     L.sf_probe_assemble.argtypes = [vp, i, fp, fp, fp, fp, fp, fp, fp, vp]
     L.sf_probe_pcg.argtypes = [vp, i, i, fp, vp]
+    L.sf_probe_schwarz.argtypes = [vp, i, i, i, fp, vp]
     L.sf_probe_wmask.argtypes = [vp, i, i, fp, vp]
     L.sf_probe_energy.argtypes = [vp, i, fp, fp, fp, fp, fp, vp]
     L.sf_probe_cells.argtypes = [vp, i, i, ctypes.POINTER(ctypes.c_uint), i, ip]
@@ -167,7 +171,7 @@ def preset(which: int = PRESET_FIG2, **kw) -> Params:
     p = Params()
     _check(load().sf_params_preset(ctypes.byref(p), int(which)), "sf_params_preset")
     for k, v in kw.items():
-        if k in ("gn_iters", "pcg_iters"):
+        if k in ("gn_iters", "pcg_iters", "patch_iters"):
             vals = list(v) + [list(v)[-1]] * MAX_LEVELS
             setattr(p, k, (ctypes.c_int * MAX_LEVELS)(*[int(x) for x in vals[:MAX_LEVELS]]))
         elif k == "F":
@@ -376,6 +380,13 @@ class Solver:
         _, _, nx, ny = self.dims(level)
         x = torch.empty((nx * ny, 6), device="cuda", dtype=torch.float32)
         _check(self.L.sf_probe_pcg(self.ctx, int(level), int(iters), _ptr(x), _stream()), "sf_probe_pcg")
+        return x
+
+    def probe_schwarz(self, level: int, sweeps: int, patch: int) -> torch.Tensor:
+        _, _, nx, ny = self.dims(level)
+        x = torch.empty((nx * ny, 6), device="cuda", dtype=torch.float32)
+        _check(self.L.sf_probe_schwarz(self.ctx, int(level), int(sweeps), int(patch), _ptr(x), _stream()),
+               "sf_probe_schwarz")
         return x
 
     def probe_wmask(self, level: int, step: int) -> torch.Tensor:

@@ -19,6 +19,8 @@ def make_params(gn, pcg, preset: str = "fig2", **kw):
     d = dict(O.TABLE1[preset])
     lib_only = {k: kw.pop(k) for k in ("use_graph", "precision", "pcg_mode", "profile_mask", "video",
                                        "record_cells") if k in kw}
+    if "patch_iters" in kw:  # per level, like gn and pcg
+        kw["patch_iters"] = tuple(list(kw["patch_iters"]) + [kw["patch_iters"][-1]] * 8)[:8]
     d.update(kw)
     op = O.Params(gn_iters=tuple(list(gn) + [gn[-1]] * 8)[:8], pcg_iters=tuple(list(pcg) + [pcg[-1]] * 8)[:8], **d)
     sp = sf.preset(PRESET_IDS[preset], gn_iters=list(gn), pcg_iters=list(pcg), **{**kw, **lib_only})
