@@ -76,6 +76,8 @@ class _Params(ctypes.Structure):
         ("temporal_mode", ctypes.c_int), ("max_backtracks", ctypes.c_int),
         ("solver", ctypes.c_int), ("patch_iters", ctypes.c_int * MAX_LEVELS),
         ("schwarz_tile", ctypes.c_int), ("schwarz_overlap", ctypes.c_int),
+        ("occlusion", ctypes.c_int), ("occ_tau", ctypes.c_double),
+        ("illumination", ctypes.c_int), ("illum_sigma", ctypes.c_double),
     ]
 
 
@@ -124,6 +126,10 @@ class Params:
     patch_iters: tuple = (5,) * MAX_LEVELS
     schwarz_tile: int = 8
     schwarz_overlap: int = 1
+    occlusion: int = 0
+    occ_tau: float = 0.5
+    illumination: int = 0
+    illum_sigma: float = 3.2
 
     @classmethod
     def preset(cls, name: str, **kw) -> "Params":
@@ -134,10 +140,10 @@ class Params:
     def to_c(self) -> _Params:
         p = _Params()
         for k in ("w_reg", "w_photo", "w_grad", "w_epi", "w_smooth", "w_mag", "w_s", "w_m", "w_d",
-                  "m_s", "m_m", "m_d", "eps", "eps_p", "wfeat_gain", "wfeat_tau"):
+                  "m_s", "m_m", "m_d", "eps", "eps_p", "wfeat_gain", "wfeat_tau", "occ_tau", "illum_sigma"):
             setattr(p, k, float(getattr(self, k)))
         for k in ("robust_mode", "grad_mode", "wfeat_mode", "temporal_mode", "max_backtracks", "solver",
-                  "schwarz_tile", "schwarz_overlap"):
+                  "schwarz_tile", "schwarz_overlap", "occlusion", "illumination"):
             setattr(p, k, int(getattr(self, k)))
         qi = list(self.patch_iters) + [0] * MAX_LEVELS
         p.patch_iters = (ctypes.c_int * MAX_LEVELS)(*[int(v) for v in qi[:MAX_LEVELS]])
@@ -189,7 +195,16 @@ def lib():
         L.sfo_packed_size.restype = ctypes.c_long
         u32p = ctypes.POINTER(ctypes.c_uint)
         lp = ctypes.POINTER(ctypes.c_long)
-        L.sfo_solve_frame.argtypes = [i, i, i, i, pp, dp, dp, dp, dp, up, u32p, lp, dp, dp, dp]
+        L.sfo_solve_frame.argtypes = [i, i, i, i, pp, dp, dp, dp, dp, up, u32p, lp, up, dp, dp, dp]
+        L.sfo_occlusion_map.argtypes = [i, i, i, i, i, dp, d, up]
+        L.sfo_vis_upsample.argtypes = [i, i, up, i, i, up]
+        L.sfo_illum_residual.argtypes = [i, i, i, i, i, dp, dp, dp]
+        L.sfo_gauss_blur.argtypes = [i, i, dp, d, dp]
+        L.sfo_illum_upsample.argtypes = [i, i, dp, i, i, dp]
+        L.sfo_energy_maps.argtypes = [i, i, i, i, i, i, dp, dp, dp, dp, up, pp, up, dp, dp, up]
+        L.sfo_energy_maps.restype = d
+        L.sfo_assemble_maps.argtypes = [i, i, i, i, i, i, dp, dp, dp, dp, up, pp, up, dp, dp, dp, up]
+        L.sfo_assemble_maps.restype = d
         L.sfo_solve_frame.restype = i
         _lib = L
     return _lib
@@ -371,6 +386,85 @@ def assemble(lv: Level, base, delta, wf, p: Params, W: np.ndarray | None = None)
     return A, b, E, (Win if Win is not None else Wout).reshape(lv.h, lv.w)
 
 
+def _maps(lv: Level, V, Lmap):
+    Vc = None if V is None else np.ascontiguousarray(V, dtype=np.uint8).reshape(-1)
+    Lc = None if Lmap is None else _f64(Lmap).reshape(-1)
+    if Vc is not None:
+        assert Vc.size == lv.w * lv.h
+    if Lc is not None:
+        assert Lc.size == 2 * lv.w * lv.h
+    return Vc, Lc
+
+
+def energy_maps(lv: Level, base, delta, wf, p: Params, V=None, Lmap=None, W=None):
+    """energy() with a level's occlusion map V [h, w] and illumination
+    differences Lmap [2, h, w] (either may be None)."""
+    base, delta, wf = _f64(base), _f64(delta), _f64(wf)
+    Vc, Lc = _maps(lv, V, Lmap)
+    terms = np.zeros(5)
+    Wout = np.zeros(lv.w * lv.h, dtype=np.uint8)
+    Win = None if W is None else np.ascontiguousarray(W, dtype=np.uint8).reshape(-1)
+    pc = p.to_c()
+    E = lib().sfo_energy_maps(lv.w, lv.h, lv.s, lv.nx, lv.ny, lv.level, _d(lv.planes), _d(base), _d(delta),
+                              _d(wf), _u8(Win), ctypes.byref(pc), _u8(Vc), _d(Lc), _d(terms), _u8(Wout))
+    return E, terms, (Win if Win is not None else Wout).reshape(lv.h, lv.w)
+
+
+def assemble_maps(lv: Level, base, delta, wf, p: Params, V=None, Lmap=None, W=None):
+    """assemble() with a level's occlusion map and illumination differences."""
+    base, delta, wf = _f64(base), _f64(delta), _f64(wf)
+    Vc, Lc = _maps(lv, V, Lmap)
+    A = np.zeros((lv.G, 9, 6, 6))
+    b = np.zeros((lv.G, 6))
+    Wout = np.zeros(lv.w * lv.h, dtype=np.uint8)
+    Win = None if W is None else np.ascontiguousarray(W, dtype=np.uint8).reshape(-1)
+    pc = p.to_c()
+    E = lib().sfo_assemble_maps(lv.w, lv.h, lv.s, lv.nx, lv.ny, lv.level, _d(lv.planes), _d(base), _d(delta),
+                                _d(wf), _u8(Win), ctypes.byref(pc), _u8(Vc), _d(Lc), _d(A), _d(b), _u8(Wout))
+    return A, b, E, (Win if Win is not None else Wout).reshape(lv.h, lv.w)
+
+
+def occlusion_map(w: int, h: int, s: int, T: np.ndarray, tau: float = 0.5) -> np.ndarray:
+    """[h, w] uint8 visibility of a level at totals T (6 x G)."""
+    nx, ny = grid_dims(w, h, s)
+    T = _f64(T)
+    assert T.size == 6 * nx * ny
+    O = np.zeros(w * h, dtype=np.uint8)
+    lib().sfo_occlusion_map(w, h, s, nx, ny, _d(T), float(tau), _u8(O))
+    return O.reshape(h, w)
+
+
+def vis_upsample(Oc: np.ndarray, w: int, h: int) -> np.ndarray:
+    Oc = np.ascontiguousarray(Oc, dtype=np.uint8)
+    hc, wc = Oc.shape
+    V = np.zeros(w * h, dtype=np.uint8)
+    lib().sfo_vis_upsample(wc, hc, _u8(Oc.reshape(-1)), w, h, _u8(V))
+    return V.reshape(h, w)
+
+
+def illum_residual(lv: Level, T: np.ndarray) -> np.ndarray:
+    """[2, h, w] stereo intensity residuals (right - left at times 0 and 1)."""
+    r = np.zeros(2 * lv.w * lv.h)
+    lib().sfo_illum_residual(lv.w, lv.h, lv.s, lv.nx, lv.ny, _d(lv.planes), _d(_f64(T)), _d(r))
+    return r.reshape(2, lv.h, lv.w)
+
+
+def gauss_blur(img: np.ndarray, sigma: float = 3.2) -> np.ndarray:
+    img = _f64(img)
+    h, w = img.shape
+    out = np.zeros_like(img)
+    lib().sfo_gauss_blur(w, h, _d(img), float(sigma), _d(out))
+    return out
+
+
+def illum_upsample(Rc: np.ndarray, w: int, h: int) -> np.ndarray:
+    Rc = _f64(Rc)
+    _, hc, wc = Rc.shape
+    out = np.zeros(2 * w * h)
+    lib().sfo_illum_upsample(wc, hc, _d(Rc), w, h, _d(out))
+    return out.reshape(2, h, w)
+
+
 def apply(nx: int, ny: int, A: np.ndarray, x: np.ndarray) -> np.ndarray:
     A, x = _f64(A), _f64(x)
     y = np.zeros_like(x)
@@ -441,7 +535,7 @@ class FrameResult:
 
 def solve_frame(imgs4: np.ndarray, s: int, levels: int, p: Params, prev: FrameResult | None = None,
                 init_coarsest: np.ndarray | None = None, W_given: list | None = None,
-                cells_given: list | None = None) -> FrameResult:
+                cells_given: list | None = None, V_given: list | None = None) -> FrameResult:
     """Algorithm 1 for one quadruple (without occlusion and illumination maps).
 
     W_given: optional outlier masks to use instead of taking W in FP64, as
@@ -449,7 +543,9 @@ def solve_frame(imgs4: np.ndarray, s: int, levels: int, p: Params, prev: FrameRe
     cells_given: optional bilinear cell decisions to use in the assembly of
     each step instead of taking them in FP64, as cells_given[level][step]
     uint32 arrays [n, 2] of (pixel y*w + x, cell << 4 | clamped << 3 |
-    image << 1 | axis), any order."""
+    image << 1 | axis), any order.
+    V_given: optional occlusion maps to use instead of the oracle's own
+    prolongated ones, as V_given[level] arrays of the level's image shape."""
     imgs4 = _f64(imgs4)
     _, h, w = imgs4.shape
     n = int(lib().sfo_packed_size(w, h, s, levels))
@@ -483,10 +579,19 @@ def solve_frame(imgs4: np.ndarray, s: int, levels: int, p: Params, prev: FrameRe
         offs = np.ascontiguousarray(offs.astype(np.int_))
         recs_p = recs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint))
         offs_p = offs.ctypes.data_as(ctypes.POINTER(ctypes.c_long))
+    vg = None
+    if V_given is not None:
+        parts = []
+        for l in range(levels):
+            lw, lh = level_dims(w, h, l)
+            m = np.ascontiguousarray(V_given[l], dtype=np.uint8).reshape(-1)
+            assert m.size == lw * lh
+            parts.append(m)
+        vg = np.ascontiguousarray(np.concatenate(parts))
     rc = lib().sfo_solve_frame(w, h, s, levels, ctypes.byref(pc), _d(imgs4),
                                _d(prev.delta) if prev is not None else None,
                                _d(prev.total) if prev is not None else None,
-                               _d(ic), _u8(wg), recs_p, offs_p, _d(delta), _d(total), _d(stats))
+                               _d(ic), _u8(wg), recs_p, offs_p, _u8(vg), _d(delta), _d(total), _d(stats))
     if rc != 0:
         raise ValueError("invalid sizes for the oracle solve")
     return FrameResult(delta, total, stats, packed_offsets(w, h, s, levels))

@@ -60,7 +60,24 @@ typedef struct sfo_params {
     int solver;
     int patch_iters[SFO_MAX_LEVELS];
     int schwarz_tile, schwarz_overlap;
+    /* per-level maps of Algorithm 1, computed after a level's solve and
+     * prolongated to the next finer level: occlusion maps V (Section 4.1,
+     * Section 5.3) [C25] with the closeness tolerance occ_tau (level pixels
+     * of disparity), and illumination correction maps (Section 5.3) [C26]
+     * with the Gaussian's sigma (level pixels) */
+    int occlusion;
+    double occ_tau;
+    int illumination;
+    double illum_sigma;
 } sfo_params;
+
+/* The maps a level's data terms use (NULL members: V = 1, no correction):
+ * V[h][w] visibility, L[2][h][w] the illumination difference of the right
+ * camera at times 0 and 1, in the level's reference frame. */
+typedef struct sfo_maps {
+    const unsigned char* V;
+    const double* L;
+} sfo_maps;
 
 /* Sign of stereo, motion and difference flow in each image's sample position
  * (Eqs. 1-6): image 0 at x-s-m+d, 1 at x+s-m-d, 2 at x-s+m-d, 3 at x+s+m+d. */
@@ -242,9 +259,12 @@ static void pixel_fields(int x, int y, int s, int nx, int ny, const double* T, d
  * warped image gradients [C2]) and their Jacobians w.r.t. the six pixel
  * fields (Je[k][u], Jg[2k+a][u], u = sx, sy, mx, my, dx, dy). dec is NULL or
  * gives, per image c, a cell decision for x (dec[2c]) and y (dec[2c+1]) as
- * sample_decided takes it (-1: the oracle's own). */
+ * sample_decided takes it (-1: the oracle's own). corr is NULL or the
+ * illumination difference (time 0, time 1) at this pixel, subtracted from the
+ * right images' intensities (a constant of the level: the Jacobians keep). */
 static void pixel_terms_decided(int w, int h, const double* planes, double x, double y, const double f[6],
-                                const int dec[8], double e[6], double g[12], double Je[36], double Jg[72])
+                                const int dec[8], const double* corr, double e[6], double g[12], double Je[36],
+                                double Jg[72])
 {
     size_t n = (size_t)w * h;
     double val[4][3], dx[4][3], dy[4][3];
@@ -254,6 +274,12 @@ static void pixel_terms_decided(int w, int h, const double* planes, double x, do
         int gx = dec ? dec[2 * c] : -1, gy = dec ? dec[2 * c + 1] : -1;
         for (int p = 0; p < 3; ++p)
             val[c][p] = sample_decided(w, h, planes + (size_t)(c * 3 + p) * n, px, py, gx, gy, &dx[c][p], &dy[c][p]);
+    }
+    if (corr) {
+        /* illumination correction [C26]: the right images (1 at time 0, 3 at
+         * time 1) less the right camera's illumination difference */
+        val[1][0] -= corr[0];
+        val[3][0] -= corr[1];
     }
     for (int k = 0; k < 6; ++k) {
         int F = CHECK[k][0], S = CHECK[k][1];
@@ -280,7 +306,16 @@ static void pixel_terms_decided(int w, int h, const double* planes, double x, do
 void sfo_pixel_terms(int w, int h, const double* planes, double x, double y, const double f[6],
                      double e[6], double g[12], double Je[36], double Jg[72])
 {
-    pixel_terms_decided(w, h, planes, x, y, f, NULL, e, g, Je, Jg);
+    pixel_terms_decided(w, h, planes, x, y, f, NULL, NULL, e, g, Je, Jg);
+}
+
+/* The correction of pixel p from the maps (NULL without illumination maps). */
+static const double* pixel_corr(const sfo_maps* mp, int w, int h, int p, double buf[2])
+{
+    if (!mp || !mp->L) return NULL;
+    buf[0] = mp->L[p];
+    buf[1] = mp->L[(size_t)w * h + p];
+    return buf;
 }
 
 /* Halfway image: mean of the four warped samples (used by the feature weight). */
@@ -425,9 +460,9 @@ void sfo_feature_weights(int w, int h, int s, int nx, int ny, const double* plan
 /* terms[0..4] = E_photo, E_grad, E_smooth, E_epi, E_mag (unweighted sums as
  * in Eqs. 11, 13, 14, 15, 18); returns the weighted total of Eqs. 8-10.
  * If W is NULL it is computed at this state (and written to Wout if given). */
-double sfo_energy(int w, int h, int s, int nx, int ny, int level, const double* planes,
-                  const double* base, const double* delta, const double* wf, const unsigned char* W,
-                  const sfo_params* p, double terms[5], unsigned char* Wout)
+static double energy_impl(int w, int h, int s, int nx, int ny, int level, const double* planes,
+                          const double* base, const double* delta, const double* wf, const unsigned char* W,
+                          const sfo_params* p, double terms[5], unsigned char* Wout, const sfo_maps* mp)
 {
     int G = nx * ny;
     double* T = (double*)malloc(sizeof(double) * 6 * G);
@@ -435,12 +470,13 @@ double sfo_energy(int w, int h, int s, int nx, int ny, int level, const double* 
     double Ep = 0.0, Eg = 0.0, Es = 0.0, Ee = 0.0, Em = 0.0;
     for (int y = 0; y < h; ++y)
         for (int x = 0; x < w; ++x) {
-            double f[6], e[6], g[12];
+            double f[6], e[6], g[12], cb[2];
             pixel_fields(x, y, s, nx, ny, T, f);
-            sfo_pixel_terms(w, h, planes, x, y, f, e, g, NULL, NULL);
+            pixel_terms_decided(w, h, planes, x, y, f, NULL, pixel_corr(mp, w, h, y * w + x, cb), e, g, NULL, NULL);
             int Wi = W ? W[y * w + x] : outlier_weight(e, p->eps_p);
             if (Wout) Wout[y * w + x] = (unsigned char)Wi;
-            if (!Wi) continue; /* V = 1 [C12] */
+            if (!Wi) continue;
+            if (mp && mp->V && !mp->V[y * w + x]) continue; /* V of Eqs. 11 and 13 [C25] */
             for (int k = 0; k < 6; ++k) {
                 Ep += phi(e[k], p->eps);
                 Eg += psi_grad(g[2 * k] * g[2 * k] + g[2 * k + 1] * g[2 * k + 1], p->eps, p->grad_mode);
@@ -486,6 +522,23 @@ double sfo_energy(int w, int h, int s, int nx, int ny, int level, const double* 
     return p->w_photo * Ep + p->w_grad * Eg + p->w_reg * (p->w_smooth * Es + p->w_epi * Ee + p->w_mag * Em);
 }
 
+double sfo_energy(int w, int h, int s, int nx, int ny, int level, const double* planes,
+                  const double* base, const double* delta, const double* wf, const unsigned char* W,
+                  const sfo_params* p, double terms[5], unsigned char* Wout)
+{
+    return energy_impl(w, h, s, nx, ny, level, planes, base, delta, wf, W, p, terms, Wout, NULL);
+}
+
+/* The energy with a level's maps (V: h*w bytes or NULL; L: 2*h*w or NULL). */
+double sfo_energy_maps(int w, int h, int s, int nx, int ny, int level, const double* planes,
+                       const double* base, const double* delta, const double* wf, const unsigned char* W,
+                       const sfo_params* p, const unsigned char* V, const double* L, double terms[5],
+                       unsigned char* Wout)
+{
+    sfo_maps mp = {V, L};
+    return energy_impl(w, h, s, nx, ny, level, planes, base, delta, wf, W, p, terms, Wout, &mp);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Gauss-Newton normal equations (Section 5.1, Eqs. 19-24) [C3]               */
 /* ------------------------------------------------------------------------ */
@@ -510,7 +563,7 @@ static double sample_position(int c, int a, double x, double y, const double f[6
 static double assemble_impl(int w, int h, int s, int nx, int ny, int level, const double* planes,
                             const double* base, const double* delta, const double* wf, const unsigned char* Win,
                             const sfo_params* p, double* A, double* b, unsigned char* Wout, const unsigned* recs,
-                            long nrec, int* ndis, double* margin)
+                            long nrec, int* ndis, double* margin, const sfo_maps* mp)
 {
     long cur = 0;
     int G = nx * ny;
@@ -545,10 +598,13 @@ static double assemble_impl(int w, int h, int s, int nx, int ny, int level, cons
                 }
                 ++cur;
             }
-            pixel_terms_decided(w, h, planes, x, y, f, have ? dec : NULL, e, g, Je, Jg);
+            double cb[2];
+            pixel_terms_decided(w, h, planes, x, y, f, have ? dec : NULL, pixel_corr(mp, w, h, (int)pix, cb), e, g, Je,
+                                Jg);
             int Wi = Win ? Win[y * w + x] : outlier_weight(e, p->eps_p);
             if (Wout) Wout[y * w + x] = (unsigned char)Wi;
             if (!Wi) continue;
+            if (mp && mp->V && !mp->V[pix]) continue; /* V [C25] */
             /* pixel-level 6x6 H_p and 6-vector b_p */
             double Hp[36] = {0}, bp[6] = {0};
             if (p->robust_mode == SFO_IRLS) {
@@ -647,7 +703,7 @@ static double assemble_impl(int w, int h, int s, int nx, int ny, int level, cons
             }
         }
     free(T);
-    return sfo_energy(w, h, s, nx, ny, level, planes, base, delta, wf, Win ? Win : Wout, p, NULL, NULL);
+    return energy_impl(w, h, s, nx, ny, level, planes, base, delta, wf, Win ? Win : Wout, p, NULL, NULL, mp);
 }
 
 double sfo_assemble(int w, int h, int s, int nx, int ny, int level, const double* planes,
@@ -657,7 +713,21 @@ double sfo_assemble(int w, int h, int s, int nx, int ny, int level, const double
     int ndis = 0;
     double margin = 0.0;
     return assemble_impl(w, h, s, nx, ny, level, planes, base, delta, wf, Win, p, A, b, Wout, NULL, 0, &ndis,
-                         &margin);
+                         &margin, NULL);
+}
+
+/* The Gauss-Newton system with a level's maps (V: h*w bytes or NULL; L: 2*h*w
+ * or NULL). */
+double sfo_assemble_maps(int w, int h, int s, int nx, int ny, int level, const double* planes,
+                         const double* base, const double* delta, const double* wf, const unsigned char* Win,
+                         const sfo_params* p, const unsigned char* V, const double* L, double* A, double* b,
+                         unsigned char* Wout)
+{
+    int ndis = 0;
+    double margin = 0.0;
+    sfo_maps mp = {V, L};
+    return assemble_impl(w, h, s, nx, ny, level, planes, base, delta, wf, Win, p, A, b, Wout, NULL, 0, &ndis,
+                         &margin, &mp);
 }
 
 /* y = A x for the block system; vectors interleaved per node (n*6 + r). */
@@ -848,12 +918,185 @@ void sfo_temporal(int s, int nx, int ny, const double* delta_prev, const double*
         }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Occlusion maps (Section 5.3, V of Eqs. 11 and 13) [C25]                   */
+/* ------------------------------------------------------------------------ */
+
+/* Closeness of the surface point with fields f at time t (0 or 1): the
+ * horizontal disparity of that time's stereo pair, the left camera's sample
+ * position less the right camera's (Eqs. 1-6: 2 d_x - 2 s_x at time 0,
+ * -2 s_x - 2 d_x at time 1). Depth falls as it grows: a larger value is
+ * nearer the cameras. */
+static double closeness(int t, const double f[6])
+{
+    int il = t == 0 ? 0 : 2, ir = il + 1;
+    double ol = SIGN[il][0] * f[0] + SIGN[il][1] * f[2] + SIGN[il][2] * f[4];
+    double orr = SIGN[ir][0] * f[0] + SIGN[ir][1] * f[2] + SIGN[ir][2] * f[4];
+    return ol - orr;
+}
+
+/* Twice the signed area of (a, b, p): > 0 when p lies left of a -> b. */
+static double edge_fn(double ax, double ay, double bx, double by, double px, double py)
+{
+    return (bx - ax) * (py - ay) - (by - ay) * (px - ax);
+}
+
+/* Occlusion map O (h*w bytes, 1 = visible) of a level at totals T: the
+ * triangulated warp grid (every cell split into the triangles (i,j) (i+1,j)
+ * (i+1,j+1) and (i,j) (i+1,j+1) (i,j+1)) is rendered into each of the four
+ * images at its nodes' sample positions (Eqs. 1-6), keeping per image pixel
+ * the largest closeness (a z-buffer; a pixel centre on a triangle's edge
+ * counts as covered; degenerate triangles draw nothing). A reference pixel
+ * is visible when, in every image, its sample position rounded to the
+ * nearest pixel lies in the image and its own closeness is at least that
+ * pixel's z-buffer value less tau. */
+void sfo_occlusion_map(int w, int h, int s, int nx, int ny, const double* T, double tau, unsigned char* O)
+{
+    int G = nx * ny;
+    size_t N = (size_t)w * h;
+    double* Z = (double*)malloc(sizeof(double) * 4 * N);
+    for (size_t a = 0; a < 4 * N; ++a) Z[a] = -INFINITY;
+    for (int c = 0; c < 4; ++c) {
+        int t = c / 2;
+        for (int j = 0; j + 1 < ny; ++j)
+            for (int i = 0; i + 1 < nx; ++i)
+                for (int tri = 0; tri < 2; ++tri) {
+                    int vi[3] = {i, i + 1, tri == 0 ? i + 1 : i};
+                    int vj[3] = {j, tri == 0 ? j : j + 1, j + 1};
+                    double X[3], Y[3], K[3];
+                    for (int v = 0; v < 3; ++v) {
+                        int n = vj[v] * nx + vi[v];
+                        double f[6];
+                        for (int q = 0; q < 6; ++q) f[q] = T[q * G + n];
+                        X[v] = vi[v] * s + SIGN[c][0] * f[0] + SIGN[c][1] * f[2] + SIGN[c][2] * f[4];
+                        Y[v] = vj[v] * s + SIGN[c][0] * f[1] + SIGN[c][1] * f[3] + SIGN[c][2] * f[5];
+                        K[v] = closeness(t, f);
+                    }
+                    double area = edge_fn(X[0], Y[0], X[1], Y[1], X[2], Y[2]);
+                    if (area == 0.0) continue;
+                    double xmin = fmin(X[0], fmin(X[1], X[2])), xmax = fmax(X[0], fmax(X[1], X[2]));
+                    double ymin = fmin(Y[0], fmin(Y[1], Y[2])), ymax = fmax(Y[0], fmax(Y[1], Y[2]));
+                    int x0 = (int)ceil(fmax(xmin, 0.0)), x1 = (int)floor(fmin(xmax, w - 1.0));
+                    int y0 = (int)ceil(fmax(ymin, 0.0)), y1 = (int)floor(fmin(ymax, h - 1.0));
+                    for (int py = y0; py <= y1; ++py)
+                        for (int px = x0; px <= x1; ++px) {
+                            double b0 = edge_fn(X[1], Y[1], X[2], Y[2], px, py);
+                            double b1 = edge_fn(X[2], Y[2], X[0], Y[0], px, py);
+                            double b2 = edge_fn(X[0], Y[0], X[1], Y[1], px, py);
+                            if (area < 0.0) {
+                                b0 = -b0;
+                                b1 = -b1;
+                                b2 = -b2;
+                            }
+                            if (b0 < 0.0 || b1 < 0.0 || b2 < 0.0) continue;
+                            double k = (b0 * K[0] + b1 * K[1] + b2 * K[2]) / fabs(area);
+                            double* z = Z + (size_t)c * N + (size_t)py * w + px;
+                            if (k > *z) *z = k;
+                        }
+                }
+    }
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            double f[6];
+            pixel_fields(x, y, s, nx, ny, T, f);
+            int vis = 1;
+            for (int c = 0; c < 4 && vis; ++c) {
+                double px = x + SIGN[c][0] * f[0] + SIGN[c][1] * f[2] + SIGN[c][2] * f[4];
+                double py = y + SIGN[c][0] * f[1] + SIGN[c][1] * f[3] + SIGN[c][2] * f[5];
+                double qx = floor(px + 0.5), qy = floor(py + 0.5);
+                if (qx < 0.0 || qx > w - 1.0 || qy < 0.0 || qy > h - 1.0) {
+                    vis = 0;
+                    break;
+                }
+                double z = Z[(size_t)c * N + (size_t)qy * w + (size_t)qx];
+                if (!(closeness(c / 2, f) >= z - tau)) vis = 0;
+            }
+            O[y * w + x] = (unsigned char)vis;
+        }
+    free(Z);
+}
+
+/* Prolongation of a coarse occlusion map to the next finer level: fine pixel
+ * (x, y) interpolates the coarse map bilinearly at (x/2, y/2) and is visible
+ * when the result is at least 1/2. */
+void sfo_vis_upsample(int wc, int hc, const unsigned char* Oc, int w, int h, unsigned char* V)
+{
+    double* P = (double*)malloc(sizeof(double) * wc * hc);
+    for (int a = 0; a < wc * hc; ++a) P[a] = Oc[a] ? 1.0 : 0.0;
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) V[y * w + x] = sfo_sample(wc, hc, P, 0.5 * x, 0.5 * y, NULL, NULL) >= 0.5;
+    free(P);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Illumination correction maps (Section 5.3) [C26]                          */
+/* ------------------------------------------------------------------------ */
+
+/* Stereo intensity residuals of a level at totals T in the reference frame:
+ * r[t][y][x] = I_1^t(p) - I_0^t(p') at the pixel's sample positions in the
+ * right and left image of time t (Eqs. 1-6, checks d_0 and d_1). */
+void sfo_illum_residual(int w, int h, int s, int nx, int ny, const double* planes, const double* T, double* r)
+{
+    size_t N = (size_t)w * h;
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            double f[6], e[6], g[12];
+            pixel_fields(x, y, s, nx, ny, T, f);
+            sfo_pixel_terms(w, h, planes, x, y, f, e, g, NULL, NULL);
+            r[(size_t)y * w + x] = e[0];
+            r[N + (size_t)y * w + x] = e[1];
+        }
+}
+
+/* Gaussian low-pass of an image: weights exp(-k^2 / (2 sigma^2)) for
+ * |k| <= R = ceil(3 sigma) along each axis, normalised to sum 1, edges
+ * clamped; written as the plain 2D sum over the (2R+1)^2 window. */
+void sfo_gauss_blur(int w, int h, const double* src, double sigma, double* dst)
+{
+    int R = (int)ceil(3.0 * sigma);
+    double* g = (double*)malloc(sizeof(double) * (2 * R + 1));
+    double sum = 0.0;
+    for (int k = -R; k <= R; ++k) {
+        g[k + R] = exp(-(double)k * k / (2.0 * sigma * sigma));
+        sum += g[k + R];
+    }
+    for (int k = 0; k <= 2 * R; ++k) g[k] /= sum;
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            double acc = 0.0;
+            for (int dy = -R; dy <= R; ++dy)
+                for (int dx = -R; dx <= R; ++dx) {
+                    int xx = x + dx, yy = y + dy;
+                    xx = xx < 0 ? 0 : (xx > w - 1 ? w - 1 : xx);
+                    yy = yy < 0 ? 0 : (yy > h - 1 ? h - 1 : yy);
+                    acc += g[dx + R] * g[dy + R] * src[(size_t)yy * w + xx];
+                }
+            dst[(size_t)y * w + x] = acc;
+        }
+    free(g);
+}
+
+/* Box prolongation to the next finer level: fine pixel (x, y) takes coarse
+ * pixel (x/2, y/2) (integer division), for both times. */
+void sfo_illum_upsample(int wc, int hc, const double* Rc, int w, int h, double* L)
+{
+    for (int t = 0; t < 2; ++t)
+        for (int y = 0; y < h; ++y)
+            for (int x = 0; x < w; ++x) {
+                int xc = x / 2, yc = y / 2;
+                if (xc > wc - 1) xc = wc - 1;
+                if (yc > hc - 1) yc = hc - 1;
+                L[(size_t)t * w * h + (size_t)y * w + x] = Rc[(size_t)t * wc * hc + (size_t)yc * wc + xc];
+            }
+}
+
 /* Compares a given outlier mask with the one this oracle takes at the state
  * base + delta: returns the number of pixels that differ and, in *margin, the
  * largest distance | max_k |e_k| - eps_p | among them (how far from the
  * threshold the two decisions part). */
 static int w_disagreement(int w, int h, int s, int nx, int ny, const double* planes, const double* base,
-                          const double* delta, const unsigned char* Wg, const sfo_params* p, double* margin)
+                          const double* delta, const unsigned char* Wg, const sfo_params* p, double* margin,
+                          const sfo_maps* mp)
 {
     int G = nx * ny, n = 0;
     double* T = (double*)malloc(sizeof(double) * 6 * G);
@@ -861,9 +1104,9 @@ static int w_disagreement(int w, int h, int s, int nx, int ny, const double* pla
     *margin = 0.0;
     for (int y = 0; y < h; ++y)
         for (int x = 0; x < w; ++x) {
-            double f[6], e[6], g[12];
+            double f[6], e[6], g[12], cb[2];
             pixel_fields(x, y, s, nx, ny, T, f);
-            sfo_pixel_terms(w, h, planes, x, y, f, e, g, NULL, NULL);
+            pixel_terms_decided(w, h, planes, x, y, f, NULL, pixel_corr(mp, w, h, y * w + x, cb), e, g, NULL, NULL);
             if (outlier_weight(e, p->eps_p) != Wg[y * w + x]) {
                 double mx = 0.0;
                 for (int k = 0; k < 6; ++k)
@@ -877,7 +1120,7 @@ static int w_disagreement(int w, int h, int s, int nx, int ny, const double* pla
 }
 
 /* ------------------------------------------------------------------------ */
-/* One frame: Algorithm 1 without the occlusion and illumination maps        */
+/* One frame: Algorithm 1                                                     */
 /* ------------------------------------------------------------------------ */
 
 /* Packed per-level node arrays: level l starts at 6 * sum_{k<l} G_k. */
@@ -914,6 +1157,9 @@ long sfo_packed_size(int w0, int h0, int s, int levels)
  *                 reading C7), like W; replaying another implementation's
  *                 decisions for samples at a cell edge isolates the
  *                 continuous error of the rest.
+ *   V_given       optional occlusion maps to use instead of prolongating this
+ *                 oracle's own (p->occlusion): for l = 0..L-1 one w_l*h_l
+ *                 byte map each (level L-1's is all ones); NULL to compute
  *   stats         SFO_STATS_LEN doubles: [0] final energy, [1..5] its terms,
  *                 [6] pixels with W = 0 in the last step; at 16 + (l*16+g)*8:
  *                 E at the linearisation point, E accepted, step t (0 if
@@ -923,17 +1169,19 @@ long sfo_packed_size(int w0, int h0, int s, int levels)
  *                 and with cell_recs the given cell decisions that differ from
  *                 the ones taken here and the largest distance of such a
  *                 sample's position from the nearest integer (SFO_STEP_STATS
- *                 values per step at 16 + (l*16+g)*SFO_STEP_STATS).
+ *                 values per step at 16 + (l*16+g)*SFO_STEP_STATS); with
+ *                 V_given, stats[8 + l] counts the pixels of level l whose
+ *                 given V differs from this oracle's own prolongated map.
  * Returns 0, or -1 for invalid sizes. */
 int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const double* imgs,
                     const double* prev_delta, const double* prev_total, const double* init_coarsest,
                     const unsigned char* W_given, const unsigned* cell_recs, const long* cell_offs,
-                    double* out_delta, double* out_total, double* stats)
+                    const unsigned char* V_given, double* out_delta, double* out_total, double* stats)
 {
     if (L < 1 || L > SFO_MAX_LEVELS || s < 1) return -1;
     int W[SFO_MAX_LEVELS], H[SFO_MAX_LEVELS], NX[SFO_MAX_LEVELS], NY[SFO_MAX_LEVELS];
-    long off[SFO_MAX_LEVELS], woff[SFO_MAX_LEVELS];
-    long acc = 0, wacc = 0;
+    long off[SFO_MAX_LEVELS], woff[SFO_MAX_LEVELS], poff[SFO_MAX_LEVELS];
+    long acc = 0, wacc = 0, pacc = 0;
     for (int l = 0; l < L; ++l) {
         sfo_level_dims(w0, h0, l, &W[l], &H[l]);
         NX[l] = (W[l] + s - 1) / s;
@@ -943,6 +1191,8 @@ int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const dou
         acc += 6L * NX[l] * NY[l];
         woff[l] = wacc;
         wacc += (long)p->gn_iters[l] * W[l] * H[l];
+        poff[l] = pacc;
+        pacc += (long)W[l] * H[l];
     }
     if (stats) memset(stats, 0, sizeof(double) * SFO_STATS_LEN);
 
@@ -955,10 +1205,26 @@ int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const dou
             sfo_downsample(W[l - 1], H[l - 1], lvl_imgs[l - 1] + (size_t)c * W[l - 1] * H[l - 1],
                            lvl_imgs[l] + (size_t)c * W[l] * H[l]);
 
+    /* the maps each level takes from the next coarser one (Algorithm 1):
+     * none at the coarsest level, then prolongated after every solve */
+    unsigned char* Vown = (unsigned char*)malloc(pacc);   /* this oracle's own prolongated V, per level */
+    double* Lmap = (double*)malloc(sizeof(double) * 2 * pacc); /* illumination differences, per level */
+    memset(Vown, 1, pacc);
+    memset(Lmap, 0, sizeof(double) * 2 * pacc);
     for (int l = L - 1; l >= 0; --l) {
         int w = W[l], h = H[l], nx = NX[l], ny = NY[l], G = nx * ny;
         double* planes = (double*)malloc(sizeof(double) * 12 * w * h);
         sfo_level_planes(w, h, lvl_imgs[l], planes);
+        sfo_maps maps = {NULL, NULL};
+        if (p->occlusion) {
+            maps.V = V_given ? V_given + poff[l] : Vown + poff[l];
+            if (V_given && stats) {
+                int nd = 0;
+                for (long a = 0; a < (long)w * h; ++a) nd += (V_given[poff[l] + a] != 0) != (Vown[poff[l] + a] != 0);
+                stats[8 + l] = nd;
+            }
+        }
+        if (p->illumination) maps.L = Lmap + 2 * poff[l];
         double* base = out_total + off[l]; /* reuse the output as scratch for the base */
         double* delta = out_delta + off[l];
         if (l == L - 1) {
@@ -988,7 +1254,7 @@ int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const dou
             const unsigned char* Wg = W_given ? W_given + woff[l] + (long)g * w * h : NULL;
             int ndis = 0;
             double margin = 0.0;
-            if (Wg) ndis = w_disagreement(w, h, s, nx, ny, planes, base, delta, Wg, p, &margin);
+            if (Wg) ndis = w_disagreement(w, h, s, nx, ny, planes, base, delta, Wg, p, &margin, &maps);
             const unsigned* rg = NULL;
             long nrg = 0;
             if (cell_recs && cell_offs) {
@@ -998,7 +1264,7 @@ int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const dou
             int ncdis = 0;
             double cmargin = 0.0;
             double Ecur = assemble_impl(w, h, s, nx, ny, l, planes, base, delta, wf, Wg, p, A, b, Wm, rg, nrg,
-                                        &ncdis, &cmargin);
+                                        &ncdis, &cmargin, &maps);
             have_W = 1;
             int nexcl = 0;
             for (int a = 0; a < w * h; ++a) nexcl += Wm[a] == 0;
@@ -1016,7 +1282,7 @@ int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const dou
             for (int bt = 0; bt <= p->max_backtracks; ++bt, t *= 0.5) {
                 for (int n = 0; n < G; ++n)
                     for (int c = 0; c < 6; ++c) trial[c * G + n] = delta[c * G + n] + t * x[n * 6 + c];
-                double Et = sfo_energy(w, h, s, nx, ny, l, planes, base, trial, wf, Wm, p, NULL, NULL);
+                double Et = energy_impl(w, h, s, nx, ny, l, planes, base, trial, wf, Wm, p, NULL, NULL, &maps);
                 if (Et <= Ecur) {
                     memcpy(delta, trial, sizeof(double) * 6 * G);
                     Eacc = Et;
@@ -1040,8 +1306,8 @@ int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const dou
         if (l == 0 && stats) {
             /* final energy: with the last step's W, or W at this state */
             double terms[5];
-            double E = sfo_energy(w, h, s, nx, ny, l, planes, base, delta, wf, have_W ? Wm : NULL, p, terms,
-                                  have_W ? NULL : Wm);
+            double E = energy_impl(w, h, s, nx, ny, l, planes, base, delta, wf, have_W ? Wm : NULL, p, terms,
+                                   have_W ? NULL : Wm, &maps);
             stats[0] = E;
             stats[1] = p->w_photo * terms[0];
             stats[2] = p->w_grad * terms[1];
@@ -1053,6 +1319,25 @@ int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const dou
             stats[6] = nexcl;
         }
         for (int a = 0; a < 6 * G; ++a) base[a] += delta[a]; /* the slot now holds the total T_l */
+        if (l > 0 && p->occlusion) {
+            /* occlusion map of this level, prolongated to the next finer one */
+            unsigned char* O = (unsigned char*)malloc((size_t)w * h);
+            sfo_occlusion_map(w, h, s, nx, ny, base, p->occ_tau, O);
+            sfo_vis_upsample(w, h, O, W[l - 1], H[l - 1], Vown + poff[l - 1]);
+            free(O);
+        }
+        if (l > 0 && p->illumination) {
+            /* illumination differences of this level, low-passed, box-prolongated */
+            size_t N = (size_t)w * h;
+            double* r = (double*)malloc(sizeof(double) * 2 * N);
+            double* R = (double*)malloc(sizeof(double) * 2 * N);
+            sfo_illum_residual(w, h, s, nx, ny, planes, base, r);
+            sfo_gauss_blur(w, h, r, p->illum_sigma, R);
+            sfo_gauss_blur(w, h, r + N, p->illum_sigma, R + N);
+            sfo_illum_upsample(w, h, R, W[l - 1], H[l - 1], Lmap + 2 * poff[l - 1]);
+            free(r);
+            free(R);
+        }
         free(T);
         free(wf);
         free(A);
@@ -1063,5 +1348,7 @@ int sfo_solve_frame(int w0, int h0, int s, int L, const sfo_params* p, const dou
         free(planes);
     }
     for (int l = 0; l < L; ++l) free(lvl_imgs[l]);
+    free(Vown);
+    free(Lmap);
     return 0;
 }

@@ -2,8 +2,8 @@
 
 Each case plants one mistake in a copy of oracle/sfo.c (a wrong sign, index,
 pairing, weight, dropped term, misplaced block, ...), builds the copy on the
-CPU, and runs the pin tests of tests/test_oracle_pins.py against it through
-the SFO_LIB override: every mutant must fail at least one pin. The planted
+CPU, and runs the pin tests of tests/test_oracle_pins.py and
+tests/test_oracle_maps.py against it through the SFO_LIB override: every mutant must fail at least one pin. The planted
 mistakes live only in temporary copies; the oracle itself is not touched.
 """
 
@@ -16,6 +16,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "sfo.c")
+PIN_FILES = [os.path.join(ROOT, "tests", f) for f in ("test_oracle_pins.py", "test_oracle_maps.py")]
 
 # name -> (text in sfo.c, planted replacement); each text occurs exactly once
 MUTANTS = {
@@ -60,6 +61,22 @@ MUTANTS = {
         "for (int j = j0; j < j1; ++j)\n                    for (int i = i0; i < i1; ++i) {"),
     "Schwarz subdomain without its overlap": ("int i0 = ti * tile - overlap, j0 = tj * tile - overlap;",
                                                "int i0 = ti * tile, j0 = tj * tile;"),
+    "closeness with the wrong sign": ("    return ol - orr;\n", "    return orr - ol;\n"),
+    "occlusion tolerance added": ("if (!(closeness(c / 2, f) >= z - tau)) vis = 0;",
+                                  "if (!(closeness(c / 2, f) >= z + tau)) vis = 0;"),
+    "z-buffer lookup truncates instead of rounding": ("double qx = floor(px + 0.5), qy = floor(py + 0.5);",
+                                                      "double qx = floor(px), qy = floor(py);"),
+    "second triangle of a cell misplaced": ("int vj[3] = {j, tri == 0 ? j : j + 1, j + 1};",
+                                            "int vj[3] = {j, j, j + 1};"),
+    "visibility prolongation threshold": ("sfo_sample(wc, hc, P, 0.5 * x, 0.5 * y, NULL, NULL) >= 0.5;",
+                                          "sfo_sample(wc, hc, P, 0.5 * x, 0.5 * y, NULL, NULL) > 0.5;"),
+    "Gaussian not normalised": ("for (int k = 0; k <= 2 * R; ++k) g[k] /= sum;",
+                                "for (int k = 0; k <= 2 * R; ++k) g[k] /= 2.0;"),
+    "Gaussian radius 2 sigma": ("int R = (int)ceil(3.0 * sigma);", "int R = (int)ceil(2.0 * sigma);"),
+    "illumination correction on the left image": ("val[1][0] -= corr[0];", "val[0][0] -= corr[0];"),
+    "box prolongation shifted": ("int xc = x / 2, yc = y / 2;", "int xc = (x + 1) / 2, yc = y / 2;"),
+    "stereo residual of time 1 from the wrong check": ("r[N + (size_t)y * w + x] = e[1];",
+                                                       "r[N + (size_t)y * w + x] = e[3];"),
 }
 
 
@@ -75,8 +92,8 @@ def _run_mutant(name, tmpdir):
     subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", so, csrc, "-lm"])
     # one BLAS thread per mutant run: the runs go in parallel
     env = dict(os.environ, SFO_LIB=so, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x",
-                        "-q", "-p", "no:cacheprovider"], capture_output=True, text=True, env=env, cwd=ROOT)
+    r = subprocess.run([sys.executable, "-m", "pytest", *PIN_FILES, "-x", "-q", "-p", "no:cacheprovider"],
+                       capture_output=True, text=True, env=env, cwd=ROOT)
     return r.returncode, r.stdout[-400:]
 
 
@@ -95,7 +112,6 @@ def test_the_unmutated_copy_passes(tmp_path):
     """The harness itself: the oracle built from an unchanged copy passes every pin."""
     so = os.path.join(str(tmp_path), "same.so")
     subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", so, SRC, "-lm"])
-    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-q",
-                        "-p", "no:cacheprovider"], capture_output=True, text=True,
-                       env=dict(os.environ, SFO_LIB=so), cwd=ROOT)
+    r = subprocess.run([sys.executable, "-m", "pytest", *PIN_FILES, "-q", "-p", "no:cacheprovider"],
+                       capture_output=True, text=True, env=dict(os.environ, SFO_LIB=so), cwd=ROOT)
     assert r.returncode == 0, r.stdout[-2000:]
