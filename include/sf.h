@@ -10,8 +10,8 @@
  * consistency of the six checks of Eqs. 1-6 under the pseudo-Huber penalty of
  * Eq. 12, smoothness, epipolar and magnitude priors) with robust Gauss-Newton
  * and preconditioned conjugate gradients (Section 5.1), coarse to fine on a
- * hierarchy that stores delta flows between levels (Section 5.3, Algorithm 1
- * without the occlusion and illumination maps).
+ * hierarchy that stores delta flows between levels (Section 5.3, Algorithm 1;
+ * its occlusion and illumination maps on request).
  *
  * Every step runs in CUDA kernels of this library on one GPU; there is no CPU
  * path. All calls are plain C: pointers, sizes and status codes.
@@ -142,6 +142,24 @@ typedef struct sf_params {
     int patch_iters[SF_MAX_LEVELS]; /* Schwarz: local PCG iterations per sweep (5) */
     int schwarz_tile;             /* Schwarz: tile side in grid nodes (8: 16 px at the paper's stride 2) */
     int schwarz_overlap;          /* Schwarz: overlap in grid nodes on each side (1: the paper's 2 px) */
+    /* Per-level maps of Algorithm 1 (Section 5.3), computed after each level's
+     * solve and prolongated to the next finer level; the coarsest level uses
+     * none. Occlusion maps: the triangulated warp grid is rendered into each
+     * of the four views with a z-buffer of closeness (the stereo pair's
+     * horizontal disparity, larger = nearer); a reference pixel is visible
+     * when, in every view, its rounded sample position lies in the image and
+     * its closeness is at least the z-buffer's there less occ_tau; the map is
+     * interpolated bilinearly to the next level and thresholded at 1/2, and
+     * V = 0 removes the pixel from Eqs. 11 and 13. Illumination maps: the
+     * right-minus-left intensity residual of each time's stereo pair in the
+     * reference frame, low-passed by a Gaussian of illum_sigma level pixels
+     * (truncated at ceil(3 sigma), at most 16; edges clamped), box-prolongated,
+     * and subtracted from the right images' intensity samples of the next
+     * level. Not with the batched solve. */
+    int occlusion;                /* 1: occlusion maps on */
+    float occ_tau;                /* closeness tolerance, level pixels of disparity (0.5) */
+    int illumination;             /* 1: illumination correction maps on */
+    float illum_sigma;            /* Gaussian sigma, level pixels (3.2) */
 } sf_params;
 
 typedef struct sf_stats {
@@ -277,6 +295,23 @@ SF_API int sf_probe_pcg(sf_ctx* ctx, int level, int iters, float* x, void* strea
  * solution (G x 6). SF_ERR_ARG if the tiling cannot run on one CTA per
  * subdomain (six threads per node of an extended subdomain, at most 640). */
 SF_API int sf_probe_schwarz(sf_ctx* ctx, int level, int sweeps, int patch, float* x, void* stream);
+
+/* The occlusion map V that `level` used in the last frame (h*w bytes, device;
+ * 1 = visible): the prolongated map of level + 1, all ones at the coarsest
+ * level. Needs params.occlusion = 1 (SF_ERR_STATE otherwise). Frame-by-frame
+ * solves only (sf_solve). */
+SF_API int sf_probe_vmask(sf_ctx* ctx, int level, unsigned char* V, void* stream);
+
+/* The occlusion map of `level` at totals T (6 x G device floats, the fields
+ * layout): O (h*w bytes, device), before prolongation. Needs
+ * params.occlusion = 1. */
+SF_API int sf_probe_occlusion(sf_ctx* ctx, int level, const float* T, unsigned char* O, void* stream);
+
+/* The low-passed stereo residuals of `level` at totals T on the context's
+ * current pyramid (built by sf_probe_pyramid or a solve): R (2 x h x w
+ * device floats, time 0 then time 1), before prolongation. Needs
+ * params.illumination = 1. */
+SF_API int sf_probe_illum(sf_ctx* ctx, int level, const float* T, float* R, void* stream);
 
 /* Copies the outlier mask W (Section 4.1) that Gauss-Newton step `step` of
  * `level` used in the last frame (h*w bytes, 1 = kept, 0 = pruned). */

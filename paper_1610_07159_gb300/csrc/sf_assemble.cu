@@ -24,7 +24,7 @@ namespace {
 template <int MAXT, class TT, bool REC>
 __global__ void __launch_bounds__(ETHREADS, 2) k_assemble(LevelGeom g, int cpb, const typename TT::T* __restrict__ tex,
                                                        const float* __restrict__ base, const float* __restrict__ delta,
-                                                       DevParams P, uint8_t* __restrict__ Wmask,
+                                                       DevParams P, LevelMaps M, uint8_t* __restrict__ Wmask,
                                                        float* __restrict__ cell, float2* __restrict__ part, CellLog log)
 {
     __shared__ float sHB[ETHREADS * HB];
@@ -33,8 +33,8 @@ __global__ void __launch_bounds__(ETHREADS, 2) k_assemble(LevelGeom g, int cpb, 
     const int tid = threadIdx.x;
     float ep = 0.f, eg = 0.f;
     int nex = 0;
-    assemble_group<MAXT, TT, REC>(g, cpb, blockIdx.x, blockIdx.y, tex, base, delta, P, Wmask, cell, sHB, sW, ep, eg,
-                                  nex, &log);
+    assemble_group<MAXT, TT, REC>(g, cpb, blockIdx.x, blockIdx.y, tex, base, delta, P, M, Wmask, cell, sHB, sW, ep,
+                                  eg, nex, &log);
     const int blk = blockIdx.y * gridDim.x + blockIdx.x;
     const float v[3] = {ep, eg, (float)nex};
     ff t[3];
@@ -115,7 +115,7 @@ template <class TT>
 __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, const typename TT::T* __restrict__ tex,
                                                      const float* __restrict__ base, const float* __restrict__ delta,
                                                      const float* __restrict__ x, float t, const float* __restrict__ wf,
-                                                     DevParams P, uint8_t* __restrict__ Wmask, int wmode,
+                                                     DevParams P, LevelMaps M, uint8_t* __restrict__ Wmask, int wmode,
                                                      float2* __restrict__ part, unsigned* counter,
                                                      double* __restrict__ rec, int* status)
 {
@@ -133,7 +133,8 @@ __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, c
             pixel_fields(base, delta, x, t, g.G, j0 * g.nx + i0, g.nx, a, bb, f);
             int Wi;
             float Ep, Eg;
-            pixel_data<false, TT>(tex, g.w, g.h, xx, y, f, P, wmode ? -1 : (int)Wmask[p], Wi, Ep, Eg, nullptr, nullptr);
+            pixel_data<false, TT>(tex, g.w, g.h, xx, y, f, P, M, wmode ? -1 : (int)Wmask[p], Wi, Ep, Eg, nullptr,
+                                  nullptr);
             if (wmode) Wmask[p] = (uint8_t)Wi;
             v[0] += Ep;
             v[1] += Eg;
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, c
 template <class TT>
 __global__ void __launch_bounds__(ETHREADS) k_trials(LevelGeom g, const typename TT::T* __restrict__ tex,
                                                      const float* base, float* delta, const float* x,
-                                                     const float* __restrict__ wf, DevParams P,
+                                                     const float* __restrict__ wf, DevParams P, LevelMaps M,
                                                      const uint8_t* __restrict__ Wmask, float2* part,
                                                      unsigned long long* bar, int* status, StepCtrl* ctrl, int max_bt)
 {
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(ETHREADS) k_trials(LevelGeom g, const typename
             pixel_fields(base, delta, x, t, g.G, j0 * g.nx + i0, g.nx, a, bb, f);
             int Wi;
             float Ep, Eg;
-            pixel_data<false, TT>(tex, g.w, g.h, xx, y, f, P, (int)Wmask[p], Wi, Ep, Eg, nullptr, nullptr);
+            pixel_data<false, TT>(tex, g.w, g.h, xx, y, f, P, M, (int)Wmask[p], Wi, Ep, Eg, nullptr, nullptr);
             v[0] += Ep;
             v[1] += Eg;
         }
@@ -313,16 +314,17 @@ __global__ void k_unpack_blocks(int G, const float* __restrict__ node, const flo
 
 template <int MAXT>
 void assemble_impl(const LevelGeom& g, int cpb, const void* tex, int prec, const float* base, const float* delta,
-                   const DevParams& P, uint8_t* Wmask, float* cell, float2* part, const CellLog* log, cudaStream_t st)
+                   const DevParams& P, const LevelMaps& M, uint8_t* Wmask, float* cell, float2* part,
+                   const CellLog* log, cudaStream_t st)
 {
     dim3 grid((g.ncx + cpb - 1) / cpb, g.ncy);
     if (log) {
         SF_TEX_DISPATCH(prec, TT, k_assemble<MAXT, TT, true><<<grid, ETHREADS, 0, st>>>(
-                                      g, cpb, static_cast<const typename TT::T*>(tex), base, delta, P, Wmask, cell,
+                                      g, cpb, static_cast<const typename TT::T*>(tex), base, delta, P, M, Wmask, cell,
                                       part, *log));
     } else {
         SF_TEX_DISPATCH(prec, TT, k_assemble<MAXT, TT, false><<<grid, ETHREADS, 0, st>>>(
-                                      g, cpb, static_cast<const typename TT::T*>(tex), base, delta, P, Wmask, cell,
+                                      g, cpb, static_cast<const typename TT::T*>(tex), base, delta, P, M, Wmask, cell,
                                       part, CellLog{nullptr, nullptr, 0}));
     }
 }
@@ -340,17 +342,17 @@ int assemble_blocks(const LevelGeom& g, int* cpb_out)
 
 void launch_assemble(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta,
                      const DevParams& P, uint8_t* Wmask, float* cell, const Scratch& sc, cudaStream_t st,
-                     const CellLog* log)
+                     const CellLog* log, const LevelMaps& M)
 {
     int cpb;
     assemble_blocks(g, &cpb);
     const int need = assemble_tasks_per_thread(cpb);
     if (need <= 1)
-        assemble_impl<1>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, log, st);
+        assemble_impl<1>(g, cpb, tex, prec, base, delta, P, M, Wmask, cell, sc.asm_part, log, st);
     else if (need <= 2)
-        assemble_impl<2>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, log, st);
+        assemble_impl<2>(g, cpb, tex, prec, base, delta, P, M, Wmask, cell, sc.asm_part, log, st);
     else
-        assemble_impl<4>(g, cpb, tex, prec, base, delta, P, Wmask, cell, sc.asm_part, log, st);
+        assemble_impl<4>(g, cpb, tex, prec, base, delta, P, M, Wmask, cell, sc.asm_part, log, st);
 }
 
 void launch_gather(const LevelGeom& g, const float* cell, const float* base, const float* delta, const float* wf,
@@ -364,14 +366,14 @@ void launch_gather(const LevelGeom& g, const float* cell, const float* base, con
 
 void launch_energy(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta, const float* x,
                    float t, const float* wf, const DevParams& P, uint8_t* Wmask, int wmode, const Scratch& sc,
-                   double* rec, cudaStream_t st)
+                   double* rec, cudaStream_t st, const LevelMaps& M)
 {
     int npix = (g.w * g.h + ETHREADS - 1) / ETHREADS;
     if (npix > 152 * 8) npix = 152 * 8;
     const int nnode = (g.G + ETHREADS - 1) / ETHREADS;
     SF_TEX_DISPATCH(prec, TT, k_energy<TT><<<npix + nnode, ETHREADS, 0, st>>>(
-                                  g, npix, static_cast<const typename TT::T*>(tex), base, delta, x, t, wf, P, Wmask,
-                                  wmode, sc.en_part, sc.counters + 1, rec, sc.status));
+                                  g, npix, static_cast<const typename TT::T*>(tex), base, delta, x, t, wf, P, M,
+                                  Wmask, wmode, sc.en_part, sc.counters + 1, rec, sc.status));
 }
 
 template <class TT>
@@ -399,13 +401,15 @@ int trials_blocks(const LevelGeom& g, int prec, int sm_count)
 
 cudaError_t launch_trials(const LevelGeom& g, const void* tex, int prec, const float* base, float* delta, const float* x,
                           const float* wf, const DevParams& P, const uint8_t* Wmask, const Scratch& sc,
-                          unsigned long long* bar, StepCtrl* ctrl, int max_bt, int blocks, cudaStream_t st)
+                          unsigned long long* bar, StepCtrl* ctrl, int max_bt, int blocks, cudaStream_t st,
+                          const LevelMaps& M)
 {
     LevelGeom gg = g;
     DevParams pp = P;
+    LevelMaps mm = M;
     float2* part = sc.en_part;
     int* status = sc.status;
-    void* args[] = {(void*)&gg, nullptr, (void*)&base, (void*)&delta, (void*)&x, (void*)&wf, (void*)&pp,
+    void* args[] = {(void*)&gg, nullptr, (void*)&base, (void*)&delta, (void*)&x, (void*)&wf, (void*)&pp, (void*)&mm,
                     (void*)&Wmask, (void*)&part, (void*)&bar, (void*)&status, (void*)&ctrl, (void*)&max_bt};
     cudaError_t e = cudaSuccess;
     SF_TEX_DISPATCH(prec, TT, {

@@ -323,7 +323,8 @@ __global__ void __launch_bounds__(BT, 2) k_batch_frame(const BSeq* __restrict__ 
             float ep = 0.f, eg = 0.f;
             int nex = 0;
             for (int vb = rank; vb < B.n_groups; vb += T)
-                assemble_group<MAXT, TTB>(g, B.cpb, vb % B.gx, vb / B.gx, tex, B.base, B.delta, P, Wst, B.cell,
+                assemble_group<MAXT, TTB>(g, B.cpb, vb % B.gx, vb / B.gx, tex, B.base, B.delta, P,
+                                          LevelMaps{nullptr, nullptr}, Wst, B.cell,
                                           sm.sHB, sm.sW, ep, eg, nex);
             cluster_sync_all();
             // node system with the priors; energy at the linearisation point
@@ -365,7 +366,8 @@ __global__ void __launch_bounds__(BT, 2) k_batch_frame(const BSeq* __restrict__ 
                     pixel_fields(B.base, B.delta, B.x, t, g.G, j0 * g.nx + i0, g.nx, a, bb, f);
                     int Wi;
                     float Ep, Eg;
-                    pixel_data<false, TTB>(tex, g.w, g.h, xx, y, f, P, (int)Wst[p], Wi, Ep, Eg, nullptr, nullptr);
+                    pixel_data<false, TTB>(tex, g.w, g.h, xx, y, f, P, LevelMaps{nullptr, nullptr}, (int)Wst[p], Wi,
+                                           Ep, Eg, nullptr, nullptr);
                     v[0] += Ep;
                     v[1] += Eg;
                 }

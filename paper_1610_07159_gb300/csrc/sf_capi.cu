@@ -36,6 +36,14 @@ struct LevelBuf {
     uint2* cellrec = nullptr;  // [gn][cellcap] cell decisions at cell edges (record_cells)
     unsigned* celln = nullptr; // [gn] records per step
     int cellcap = 0;
+    // per-level maps of Algorithm 1: the maps this level uses ([frame parity], the video pipeline
+    // alternates them), and the scratch that computes this level's own for the next finer level
+    uint8_t* vis[2] = {nullptr, nullptr}; // [h][w] occlusion map V used here
+    float* illum[2] = {nullptr, nullptr}; // [2][h][w] illumination differences used here
+    int* zbuf = nullptr;                  // [4][h][w] z-buffer
+    uint8_t* occ = nullptr;               // [h][w] this level's occlusion map
+    float* illr = nullptr;                // [2][h][w] stereo residuals, then low-passed
+    float* illt = nullptr;                // [2][h][w] scratch of the separable blur
 };
 
 __global__ void k_set_args(DevArgs* a, const float* i0, const float* i1, const float* i2, const float* i3, float* out,
@@ -76,6 +84,7 @@ struct sf_ctx {
     float* in_buf[4] = {nullptr, nullptr, nullptr, nullptr};
     float* out_buf = nullptr;
     int frames = 0;
+    GaussW gauss{};                           // weights of the illumination maps' low-pass
     cudaGraphExec_t gexec = nullptr;
     bool graph_tried = false;
     cudaStream_t cap = nullptr;
@@ -175,7 +184,7 @@ DevParams make_dev_params(const sf_params& p, int level)
 bool finite_params(const sf_params& p)
 {
     const float v[] = {p.w_reg, p.w_photo, p.w_grad, p.w_epi, p.w_smooth, p.w_mag, p.w_s, p.w_m, p.w_d,
-                       p.m_s, p.m_m, p.m_d, p.eps, p.eps_p, p.wfeat_gain, p.wfeat_tau};
+                       p.m_s, p.m_m, p.m_d, p.eps, p.eps_p, p.wfeat_gain, p.wfeat_tau, p.occ_tau, p.illum_sigma};
     for (float x : v)
         if (!std::isfinite(x)) return false;
     for (float x : p.F)
@@ -218,6 +227,10 @@ void prof_mark(sf_ctx* c, int k, bool begin, cudaStream_t st)
 // Inputs and outputs of one level's solve.
 struct LevelIO {
     const void* tex;                                   // the level's texels
+    const uint8_t* vis_in;                             // occlusion map of this level (null: none)
+    const float* illum_in;                             // illumination differences of this level (null: none)
+    uint8_t* vis_out;                                  // the next finer level's, made here (null: none)
+    float* illum_out;
     const float* coarse_base;                          // coarse totals (base + delta, or the
     const float* coarse_delta;                         // totals alone when delta is null); null at the top
     const float* prev_delta, *prev_total;              // temporal state of the previous frame
@@ -258,6 +271,8 @@ int enqueue_level(sf_ctx* c, int l, const LevelIO& io, cudaStream_t st, int& nl)
         nl += 2;
     }
     prof_mark(c, SF_K_LEVEL, false, st);
+    const bool finer = l < c->L - 1; // the coarsest level takes no maps
+    const LevelMaps M{P.occlusion && finer ? io.vis_in : nullptr, P.illumination && finer ? io.illum_in : nullptr};
     for (int gi = 0; gi < P.gn_iters[l]; ++gi) {
         StepCtrl* ctrl = c->ctrl + l * SF_MAX_GN + gi;
         uint8_t* Wst = b.W + (size_t)gi * g.w * g.h; // this step's outlier mask, kept for inspection
@@ -265,9 +280,9 @@ int enqueue_level(sf_ctx* c, int l, const LevelIO& io, cudaStream_t st, int& nl)
         if (b.cellrec) {
             cudaMemsetAsync(b.celln + gi, 0, sizeof(unsigned), st);
             const CellLog log{b.cellrec + (size_t)gi * b.cellcap, b.celln + gi, b.cellcap};
-            launch_assemble(g, io.tex, P.precision, b.base, b.delta, c->dp[l], Wst, b.cell, sc, st, &log);
+            launch_assemble(g, io.tex, P.precision, b.base, b.delta, c->dp[l], Wst, b.cell, sc, st, &log, M);
         } else {
-            launch_assemble(g, io.tex, P.precision, b.base, b.delta, c->dp[l], Wst, b.cell, sc, st);
+            launch_assemble(g, io.tex, P.precision, b.base, b.delta, c->dp[l], Wst, b.cell, sc, st, nullptr, M);
         }
         prof_mark(c, SF_K_ASSEMBLE, false, st);
         prof_mark(c, SF_K_GATHER, true, st);
@@ -286,15 +301,28 @@ int enqueue_level(sf_ctx* c, int l, const LevelIO& io, cudaStream_t st, int& nl)
         nl += 3;
         prof_mark(c, SF_K_ENERGY, true, st);
         e = launch_trials(g, io.tex, P.precision, b.base, b.delta, b.x, b.wf, c->dp[l], Wst, sc,
-                          c->bar + SF_MAX_LEVELS + l, ctrl, P.max_backtracks, c->trial_blocks[l], st);
+                          c->bar + SF_MAX_LEVELS + l, ctrl, P.max_backtracks, c->trial_blocks[l], st, M);
         if (e != cudaSuccess) return check_cuda(e);
         ++nl;
         prof_mark(c, SF_K_ENERGY, false, st);
     }
     prof_mark(c, SF_K_LEVEL, true, st);
     if (l == 0 && P.gn_iters[0] == 0) {
-        launch_energy(g, io.tex, P.precision, b.base, b.delta, nullptr, 0.f, b.wf, c->dp[0], b.W, 1, sc, c->rec, st);
+        launch_energy(g, io.tex, P.precision, b.base, b.delta, nullptr, 0.f, b.wf, c->dp[0], b.W, 1, sc, c->rec, st,
+                      M);
         ++nl;
+    }
+    // this level's maps for the next finer level (Algorithm 1: occlusion maps, illumination maps,
+    // prolongation), from its final totals base + delta
+    if (l > 0 && P.occlusion && io.vis_out) {
+        launch_occlusion(g, b.base, b.delta, P.occ_tau, b.zbuf, b.occ, st);
+        launch_vis_up(g.w, g.h, b.occ, c->geo[l - 1].w, c->geo[l - 1].h, io.vis_out, st);
+        nl += 4;
+    }
+    if (l > 0 && P.illumination && io.illum_out) {
+        launch_illum(g, io.tex, P.precision, b.base, b.delta, c->gauss, b.illr, b.illt, st);
+        launch_illum_up(g.w, g.h, b.illr, c->geo[l - 1].w, c->geo[l - 1].h, io.illum_out, st);
+        nl += 4;
     }
     launch_finish_level(g, b.base, b.delta, io.out_delta, io.out_total, io.args, l == 0, io.out_fields, st);
     ++nl;
@@ -313,8 +341,10 @@ int enqueue_frame(sf_ctx* c, cudaStream_t st)
     for (int l = c->L - 1; l >= 0; --l) {
         const bool has_c = l < c->L - 1;
         LevelBuf& b = c->lv[l];
-        LevelIO io{b.tex, has_c ? c->lv[l + 1].base : nullptr, has_c ? c->lv[l + 1].delta : nullptr,
-                   b.prev_delta, b.prev_total, b.prev_delta, b.prev_total, nullptr, c->args, 0, 0};
+        LevelIO io{b.tex, b.vis[0], b.illum[0], l > 0 ? c->lv[l - 1].vis[0] : nullptr,
+                   l > 0 ? c->lv[l - 1].illum[0] : nullptr, has_c ? c->lv[l + 1].base : nullptr,
+                   has_c ? c->lv[l + 1].delta : nullptr, b.prev_delta, b.prev_total, b.prev_delta, b.prev_total,
+                   nullptr, c->args, 0, 0};
         int rc = enqueue_level(c, l, io, st, nl);
         if (rc) return rc;
     }
@@ -370,7 +400,11 @@ int enqueue_video(sf_ctx* c, const float* frames, const float* host_in, int n, f
             const bool has_c = l < L - 1;
             float* out = nullptr;
             if (l == 0) out = host_out ? c->vout[slot] : outs + (size_t)fl * G6;
-            LevelIO io{c->ring_tex[slot][l], has_c ? c->vstate_total[l + 1][fg & 1] : nullptr, nullptr,
+            // the maps of frame fg pass from level l + 1 to level l in the pipeline's previous step; the
+            // next frame's are written meanwhile into the buffer of the other parity
+            LevelIO io{c->ring_tex[slot][l], c->lv[l].vis[fg & 1], c->lv[l].illum[fg & 1],
+                       l > 0 ? c->lv[l - 1].vis[fg & 1] : nullptr, l > 0 ? c->lv[l - 1].illum[fg & 1] : nullptr,
+                       has_c ? c->vstate_total[l + 1][fg & 1] : nullptr, nullptr,
                        c->vstate_delta[l][(fg + 1) & 1], c->vstate_total[l][(fg + 1) & 1],
                        c->vstate_delta[l][fg & 1], c->vstate_total[l][fg & 1], out, nullptr, fg,
                        (l == L - 1 && fl == 0) ? c->pending_init : 0};
@@ -569,6 +603,10 @@ int sf_params_preset(sf_params* p, int preset)
     for (int l = 0; l < SF_MAX_LEVELS; ++l) p->patch_iters[l] = 5;
     p->schwarz_tile = 8;
     p->schwarz_overlap = 1;
+    p->occlusion = 0;
+    p->occ_tau = 0.5f;
+    p->illumination = 0;
+    p->illum_sigma = 3.2f;
     return SF_OK;
 }
 
@@ -582,7 +620,9 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
         p->temporal_mode > 2 || p->precision < SF_FP32 || p->precision > SF_MIXED_FP16 || !(p->wfeat_tau > 0.f) ||
         p->pcg_mode < 0 || p->pcg_mode > SF_PCG_ONE_REDUCTION || p->solver < SF_SOLVER_PCG ||
         p->solver > SF_SOLVER_SCHWARZ || (p->solver == SF_SOLVER_SCHWARZ && (p->schwarz_tile < 1 ||
-                                                                               p->schwarz_overlap < 0))) {
+                                                                               p->schwarz_overlap < 0)) ||
+        p->occlusion < 0 || p->occlusion > 1 || !(p->occ_tau >= 0.f) || p->illumination < 0 ||
+        p->illumination > 1 || (p->illumination && !(p->illum_sigma > 0.f && 3.f * p->illum_sigma <= GAUSS_MAX_R))) {
         fail(SF_ERR_ARG);
         return nullptr;
     }
@@ -659,6 +699,15 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
              dalloc(c, &b.node, (size_t)NODE_VALS * g.G) && dalloc(c, &b.rhs, G6) && dalloc(c, &b.minv, G6) &&
              dalloc(c, &b.z, G6) && dalloc(c, &b.p0, G6) && dalloc(c, &b.p1, G6) && dalloc(c, &b.pub, 6 * G6) &&
              dalloc(c, &b.cell, (size_t)CELL_VALS * (g.ncx * g.ncy));
+        if (ok && (p->occlusion || p->illumination)) {
+            const int nbuf = p->video ? 2 : 1;
+            for (int q = 0; q < nbuf && ok; ++q) {
+                if (p->occlusion) ok = dalloc(c, &b.vis[q], N);
+                if (ok && p->illumination) ok = dalloc(c, &b.illum[q], 2 * N);
+            }
+            if (ok && p->occlusion) ok = dalloc(c, &b.zbuf, 4 * N) && dalloc(c, &b.occ, N);
+            if (ok && p->illumination) ok = dalloc(c, &b.illr, 2 * N) && dalloc(c, &b.illt, 2 * N);
+        }
         if (ok && p->record_cells) {
             // every sample of a pixel can sit on a cell edge (zero fields put all of them there)
             b.cellcap = (int)std::min<size_t>(8 * N, (size_t)1 << 30);
@@ -701,6 +750,11 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
     }
     if (p->wfeat_mode == SF_WFEAT_OFF)
         for (int l = 0; l < levels; ++l) launch_fill(c->lv[l].wf, 1.f, (size_t)c->geo[l].G, 0);
+    if (p->illumination) c->gauss = gauss_weights(p->illum_sigma);
+    // the coarsest level sees no maps: all visible (its illumination buffers stay zero)
+    for (int q = 0; q < 2; ++q)
+        if (c->lv[levels - 1].vis[q])
+            cudaMemset(c->lv[levels - 1].vis[q], 1, (size_t)c->geo[levels - 1].w * c->geo[levels - 1].h);
     bool sok = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess;
     if (sok && c->video) {
         sok = cudaEventCreateWithFlags(&c->vfork, cudaEventDisableTiming) == cudaSuccess;
@@ -1007,6 +1061,41 @@ int sf_probe_schwarz(sf_ctx* c, int level, int sweeps, int patch, float* x, void
     return rc ? fail(rc) : SF_OK;
 }
 
+int sf_probe_vmask(sf_ctx* c, int level, unsigned char* V, void* stream)
+{
+    if (!c || !V || level < 0 || level >= c->L) return fail(SF_ERR_ARG);
+    if (!c->prm.occlusion) return fail(SF_ERR_STATE);
+    const size_t N = (size_t)c->geo[level].w * c->geo[level].h;
+    int rc = check_cuda(cudaMemcpyAsync(V, c->lv[level].vis[0], N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_probe_occlusion(sf_ctx* c, int level, const float* T, unsigned char* O, void* stream)
+{
+    if (!c || !T || !O || level < 0 || level >= c->L) return fail(SF_ERR_ARG);
+    if (!c->prm.occlusion) return fail(SF_ERR_STATE);
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    launch_occlusion(c->geo[level], T, nullptr, c->prm.occ_tau, c->lv[level].zbuf, O, st);
+    int rc = check_cuda(cudaGetLastError());
+    return rc ? fail(rc) : SF_OK;
+}
+
+int sf_probe_illum(sf_ctx* c, int level, const float* T, float* R, void* stream)
+{
+    if (!c || !T || !R || level < 0 || level >= c->L) return fail(SF_ERR_ARG);
+    if (!c->prm.illumination) return fail(SF_ERR_STATE);
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    const LevelGeom& g = c->geo[level];
+    LevelBuf& b = c->lv[level];
+    launch_illum(g, b.tex, c->prm.precision, T, nullptr, c->gauss, b.illr, b.illt, st);
+    int rc = check_cuda(cudaMemcpyAsync(R, b.illr, (size_t)2 * g.w * g.h * sizeof(float), cudaMemcpyDeviceToDevice,
+                                        st));
+    if (!rc) rc = check_cuda(cudaGetLastError());
+    return rc ? fail(rc) : SF_OK;
+}
+
 int sf_probe_wmask(sf_ctx* c, int level, int step, unsigned char* W, void* stream)
 {
     if (!c || !W || level < 0 || level >= c->L || step < 0 || step >= std::max(1, c->prm.gn_iters[level]))
@@ -1061,8 +1150,8 @@ int sf_batch_create(int n, const int* widths, const int* heights, const int* lev
     g_last_error = SF_OK;
     if (!out) return fail(SF_ERR_ARG);
     *out = nullptr;
-    if (n < 1 || n > (1 << 16) || !widths || !heights || !levels || !p || p->precision != SF_FP32 || p->solver != SF_SOLVER_PCG ||
-        p->gn_iters[0] < 1)
+    if (n < 1 || n > (1 << 16) || !widths || !heights || !levels || !p || p->precision != SF_FP32 ||
+        p->solver != SF_SOLVER_PCG || p->occlusion || p->illumination || p->gn_iters[0] < 1)
         return fail(SF_ERR_ARG);
     sf_batch* b = new (std::nothrow) sf_batch();
     if (!b) return fail(SF_ERR_OOM);

@@ -59,6 +59,15 @@ struct DevParams {
     float wfeat_gain, wfeat_tau;
 };
 
+// The maps a level's data terms take from the next coarser level (Algorithm
+// 1, Section 5.3): V[h][w] the occlusion map (1 = visible; null: all
+// visible) and L[2][h][w] the illumination difference of the right camera at
+// times 0 and 1 in the reference frame (null: none).
+struct LevelMaps {
+    const uint8_t* V;
+    const float* L;
+};
+
 // Control record of one Gauss-Newton step (one per level and step).
 struct StepCtrl {
     double E_cur;        // energy at the linearisation point

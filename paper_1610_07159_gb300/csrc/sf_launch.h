@@ -42,7 +42,7 @@ int assemble_blocks(const LevelGeom& g, int* cpb_out);
 // log: record the cell decisions of samples at a cell edge (test aid), or null
 void launch_assemble(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta,
                      const DevParams& P, uint8_t* Wmask, float* cell, const Scratch& sc, cudaStream_t st,
-                     const CellLog* log = nullptr);
+                     const CellLog* log = nullptr, const LevelMaps& M = LevelMaps{nullptr, nullptr});
 void launch_gather(const LevelGeom& g, const float* cell, const float* base, const float* delta, const float* wf,
                    const DevParams& P, float* node, float* rhs, float* minv, const Scratch& sc, StepCtrl* ctrl,
                    int n_asm_blocks, cudaStream_t st);
@@ -51,13 +51,14 @@ void launch_gather(const LevelGeom& g, const float* cell, const float* base, con
 // store it.
 void launch_energy(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta, const float* x,
                    float t, const float* wf, const DevParams& P, uint8_t* Wmask, int wmode, const Scratch& sc,
-                   double* rec, cudaStream_t st);
+                   double* rec, cudaStream_t st, const LevelMaps& M = LevelMaps{nullptr, nullptr});
 // all backtracking trials of a step and its update in one cooperative launch
 // of `blocks` CTAs (trials_blocks: all co-resident), on its own barrier counter
 int trials_blocks(const LevelGeom& g, int prec, int sm_count);
 cudaError_t launch_trials(const LevelGeom& g, const void* tex, int prec, const float* base, float* delta, const float* x,
                           const float* wf, const DevParams& P, const uint8_t* Wmask, const Scratch& sc,
-                          unsigned long long* bar, StepCtrl* ctrl, int max_bt, int blocks, cudaStream_t st);
+                          unsigned long long* bar, StepCtrl* ctrl, int max_bt, int blocks, cudaStream_t st,
+                          const LevelMaps& M = LevelMaps{nullptr, nullptr});
 void launch_unpack_blocks(const LevelGeom& g, const float* node, const float* rhs, float* blocks, float* rhs_out,
                           cudaStream_t st);
 
@@ -77,6 +78,26 @@ int pcg_candidates(int G, int sm_count, PcgPlan* out, int max);
 cudaError_t launch_pcg(const LevelGeom& g, const PcgPlan& plan, const float* node, const float* rhs,
                        const float* minv, float* x, float* z, float* p0, float* p1, float* pub, float2* part,
                        unsigned long long* bar, int* status, int iters, int interleaved_out, cudaStream_t st);
+
+// sf_maps.cu: the per-level maps of Algorithm 1 (Section 5.3).
+constexpr int GAUSS_MAX_R = 16;
+struct GaussW {
+    int R;                        // radius ceil(3 sigma), at most GAUSS_MAX_R
+    float w[2 * GAUSS_MAX_R + 1]; // normalised weights exp(-k^2 / (2 sigma^2))
+};
+GaussW gauss_weights(float sigma);
+// occlusion map O (h*w bytes) of a level at totals base + delta (delta may be
+// null); Z is a 4*h*w int scratch z-buffer
+void launch_occlusion(const LevelGeom& g, const float* base, const float* delta, float tau, int* Z, uint8_t* O,
+                      cudaStream_t st);
+// V of the next finer level (w x h) from a coarse map O (wc x hc)
+void launch_vis_up(int wc, int hc, const uint8_t* O, int w, int h, uint8_t* V, cudaStream_t st);
+// the low-passed stereo residuals R[2][h][w] of a level, written to r (tmp:
+// a second 2*h*w scratch)
+void launch_illum(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta,
+                  const GaussW& gw, float* r, float* tmp, cudaStream_t st);
+// L[2][h][w] of the next finer level from R[2][hc][wc] (box prolongation)
+void launch_illum_up(int wc, int hc, const float* R, int w, int h, float* L, cudaStream_t st);
 
 // sf_schwarz.cu: the normal equations solved by restricted additive Schwarz
 // sweeps over square subdomains with local PCG in shared memory (Section 5.2).

@@ -30,8 +30,8 @@ __constant__ int c_pair_l[NPAIR] = {0, 1, 2, 3, 1, 2, 3, 2, 3, 3};
 // pixel's 6x6 normal-equation block H (packed) and right-hand side b.
 template <bool ASSEMBLE, class TT, bool REC = false>
 __device__ __forceinline__ void pixel_data(const typename TT::T* __restrict__ tex, int w, int h, int x, int y, const float f[6],
-                                           const DevParams& P, int Wgiven, int& Wout, float& Ep, float& Eg, float* H,
-                                           float* b, const CellLog* log = nullptr)
+                                           const DevParams& P, const LevelMaps& M, int Wgiven, int& Wout, float& Ep,
+                                           float& Eg, float* H, float* b, const CellLog* log = nullptr)
 {
     const size_t plane = (size_t)w * h;
     Tap tp[4];
@@ -40,6 +40,13 @@ __device__ __forceinline__ void pixel_data(const typename TT::T* __restrict__ te
         const float ox = sgn(c, 0) * f[0] + sgn(c, 1) * f[2] + sgn(c, 2) * f[4];
         const float oy = sgn(c, 0) * f[1] + sgn(c, 1) * f[3] + sgn(c, 2) * f[5];
         tap4<TT, REC>(tex + c * plane, w, h, x, y, ox, oy, tp[c], log, c);
+    }
+    const int pix = y * w + x;
+    if (M.L) {
+        // illumination correction: the right images (1 at time 0, 3 at time 1) less the right camera's
+        // difference at this pixel (a constant of the level: the Jacobian keeps)
+        tp[1].v[0] -= __ldg(M.L + pix);
+        tp[3].v[0] -= __ldg(M.L + plane + pix);
     }
     float e[6];
 #pragma unroll
@@ -65,6 +72,7 @@ __device__ __forceinline__ void pixel_data(const typename TT::T* __restrict__ te
         for (int q = 0; q < 6; ++q) b[q] = 0.f;
     }
     if (!Wi) return;
+    if (M.V && !__ldg(M.V + pix)) return; // occluded in a view: V = 0 in Eqs. 11 and 13
     const float eps2 = P.eps * P.eps;
     const bool literal = P.grad_mode == SF_GRAD_LITERAL;
     const bool irls = P.robust_mode == SF_IRLS;
@@ -238,7 +246,7 @@ __device__ __forceinline__ void task_sum(float* a, float* e, int qa, int qb, con
 template <int MAXT, class TT, bool REC = false>
 __device__ __forceinline__ void assemble_group(const LevelGeom& g, int cpb, int bx, int by,
                                                const typename TT::T* __restrict__ tex, const float* base,
-                                               const float* delta, const DevParams& P,
+                                               const float* delta, const DevParams& P, const LevelMaps& M,
                                                uint8_t* Wmask, float* cell, float* sHB,
                                                float* sW, float& ep, float& eg, int& nex,
                                                const CellLog* log = nullptr)
@@ -283,7 +291,7 @@ __device__ __forceinline__ void assemble_group(const LevelGeom& g, int cpb, int 
             pixel_fields(base, delta, nullptr, 0.f, g.G, j0 * g.nx + i0, g.nx, a, bb, f);
             int Wi;
             float Ep, Eg;
-            pixel_data<true, TT, REC>(tex, g.w, g.h, x, y, f, P, -1, Wi, Ep, Eg, H, bv, log);
+            pixel_data<true, TT, REC>(tex, g.w, g.h, x, y, f, P, M, -1, Wi, Ep, Eg, H, bv, log);
             Wmask[y * g.w + x] = (uint8_t)Wi;
             ep += Ep;
             eg += Eg;

@@ -35,7 +35,8 @@ EXPORTED = (
     "sf_grid_dims", "sf_set_init", "sf_reset",
     "sf_get_stats", "sf_get_state", "sf_kernel_times", "sf_destroy", "sf_status_string", "sf_last_error", "sf_probe_pyramid",
     "sf_probe_feature_weights", "sf_probe_assemble", "sf_probe_pcg", "sf_probe_wmask", "sf_probe_energy",
-    "sf_probe_cells", "sf_probe_fma_rate", "sf_probe_schwarz",
+    "sf_probe_cells", "sf_probe_fma_rate", "sf_probe_schwarz", "sf_probe_vmask", "sf_probe_occlusion",
+    "sf_probe_illum",
     "sf_pcg_static", "sf_batch_create", "sf_batch_layout", "sf_batch_solve", "sf_batch_set_schedule",
     "sf_batch_get_schedule", "sf_batch_tune", "sf_batch_sequence", "sf_batch_reset", "sf_batch_destroy",
     "sf_probe_gemm_bf16", "sf_net_param_count", "sf_net_create", "sf_net_set_params", "sf_net_get_params",
@@ -64,6 +65,8 @@ class Params(ctypes.Structure):
         ("video", ctypes.c_int), ("record_cells", ctypes.c_int),
         ("solver", ctypes.c_int), ("patch_iters", ctypes.c_int * MAX_LEVELS),
         ("schwarz_tile", ctypes.c_int), ("schwarz_overlap", ctypes.c_int),
+        ("occlusion", ctypes.c_int), ("occ_tau", ctypes.c_float),
+        ("illumination", ctypes.c_int), ("illum_sigma", ctypes.c_float),
     ]
 
 
@@ -122,6 +125,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sf_probe_assemble.argtypes = [vp, i, fp, fp, fp, fp, fp, fp, fp, vp]
     L.sf_probe_pcg.argtypes = [vp, i, i, fp, vp]
     L.sf_probe_schwarz.argtypes = [vp, i, i, i, fp, vp]
+    L.sf_probe_vmask.argtypes = [vp, i, fp, vp]
+    L.sf_probe_occlusion.argtypes = [vp, i, fp, fp, vp]
+    L.sf_probe_illum.argtypes = [vp, i, fp, fp, vp]
     L.sf_probe_wmask.argtypes = [vp, i, i, fp, vp]
     L.sf_probe_energy.argtypes = [vp, i, fp, fp, fp, fp, fp, vp]
     L.sf_probe_cells.argtypes = [vp, i, i, ctypes.POINTER(ctypes.c_uint), i, ip]
@@ -388,6 +394,30 @@ class Solver:
         _check(self.L.sf_probe_schwarz(self.ctx, int(level), int(sweeps), int(patch), _ptr(x), _stream()),
                "sf_probe_schwarz")
         return x
+
+    def probe_vmask(self, level: int) -> torch.Tensor:
+        w, h, _, _ = self.dims(level)
+        V = torch.empty((h, w), device="cuda", dtype=torch.uint8)
+        _check(self.L.sf_probe_vmask(self.ctx, int(level), _ptr(V), _stream()), "sf_probe_vmask")
+        return V
+
+    def vmasks(self) -> list:
+        """The occlusion maps every level used in the last frame (needs occlusion=1)."""
+        return [self.probe_vmask(l).cpu().numpy() for l in range(self.levels)]
+
+    def probe_occlusion(self, level: int, T: torch.Tensor) -> torch.Tensor:
+        w, h, _, _ = self.dims(level)
+        O = torch.empty((h, w), device="cuda", dtype=torch.uint8)
+        _check(self.L.sf_probe_occlusion(self.ctx, int(level), _ptr(T, torch.float32), _ptr(O), _stream()),
+               "sf_probe_occlusion")
+        return O
+
+    def probe_illum(self, level: int, T: torch.Tensor) -> torch.Tensor:
+        w, h, _, _ = self.dims(level)
+        R = torch.empty((2, h, w), device="cuda", dtype=torch.float32)
+        _check(self.L.sf_probe_illum(self.ctx, int(level), _ptr(T, torch.float32), _ptr(R), _stream()),
+               "sf_probe_illum")
+        return R
 
     def probe_wmask(self, level: int, step: int) -> torch.Tensor:
         w, h, _, _ = self.dims(level)
