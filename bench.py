@@ -374,6 +374,49 @@ def variant_schwarz(dev, frames_d, pcg_energies, pcg_fps, reps=3):
             "note": "best of a few passes of the level pipeline each; energies frame by frame from the same frames"}
 
 
+STEREO_W, STEREO_H, STEREO_LEVELS = 4288, 2848, 7
+
+
+def variant_stereo_12mp(dev, reps=3):
+    """The paper's 12 MP stereo-only workload (Section 6): one seeded synthetic
+    4288x2848 stereo pair (disparities 30-200 px) used at both times, stride 8,
+    7 levels, 3 Gauss-Newton steps per level, the Figures 7/9 column of Table
+    1. The level-0 grid (536 x 356 nodes) is solved by the Schwarz
+    decomposition of Section 5.2 (tile 7 nodes, overlap 1, 6 sweeps x 6 patch
+    iterations); the global PCG does not hold a grid that large in one launch.
+    The paper reports 700 ms per pair on its 2016 GPU (context only)."""
+    import numpy as np
+    import torch
+
+    from paper_1610_07159_gb300 import scenes, scenes_device, sf
+
+    video = scenes.SceneVideo(STEREO_W, STEREO_H, 1, seed=700, disparity=(30.0, 200.0), max_motion=0.0)
+    q = scenes_device.stereo_pair_quadruple(video, dev)
+    p = sf.preset(sf.PRESET_FIG79, gn_iters=[GN], pcg_iters=[6], patch_iters=[6], solver=sf.SOLVER_SCHWARZ,
+                  schwarz_tile=7, schwarz_overlap=1)
+    s = sf.Solver(STEREO_W, STEREO_H, STRIDE, STEREO_LEVELS, p)
+    out = s.solve(q)  # warm-up (captures the frame graph)
+    times = []
+    for _ in range(reps):
+        s.reset()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        s.solve(q, out)
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    st = s.stats()
+    f = out.cpu().numpy()
+    s.close()
+    ms = min(times)
+    return {"workload": f"{STEREO_W}x{STEREO_H} stereo pair at both times, stride {STRIDE}, {STEREO_LEVELS} levels, "
+                        f"{GN} GN per level, Schwarz 6 sweeps x 6 patch iterations (tile 7, overlap 1), Figures 7/9 "
+                        "weights, FP32",
+            "ms_per_pair": ms, "pairs_per_s": 1e3 / ms, "launches": st.launches,
+            "max_abs_motion_and_difference_px": float(np.max(np.abs(f[2:]))),
+            "energy": st.energy, "paper_context_ms_per_pair": 700.0}
+
+
 def variant_mixed(dev, frames_d):
     """The headline video in the 16-bit texel modes, with the final energy of
     the last frame against FP32."""
@@ -716,6 +759,7 @@ def run_ours(args):
     }
     if rank == 0 and not args.no_variants:
         line["variants"]["schwarz_640x480"] = variant_schwarz(dev, frames_d, plain_energies, value)
+        line["variants"]["stereo_only_4288x2848"] = variant_stereo_12mp(dev)
         line["variants"]["batched_640x480"] = variant_batched_640(dev, frames_d)
         line["variants"]["batched_640x480"]["vs_plain_fp32_video"] = \
             line["variants"]["batched_640x480"]["frames_per_s"] / value

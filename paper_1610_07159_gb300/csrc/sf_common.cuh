@@ -32,7 +32,7 @@ constexpr int CELL_VALS = NPAIR * NB + 24; // 234
 constexpr int NODE_BLKS = 5;               // self, E, S, SE, SW
 constexpr int NODE_VALS = NODE_BLKS * NB;  // 105
 constexpr int ASM_THREADS = 256;
-constexpr int MAX_PART = 16384;            // partial-sum slots per reduction
+constexpr int MAX_PART = 65536;            // partial-sum slots per reduction (per-block partials of a level)
 
 // device status bits
 constexpr int DEV_TIMEOUT = 1;

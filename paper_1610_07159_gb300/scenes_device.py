@@ -190,3 +190,16 @@ def frames(video: SceneVideo, n: int, device, noise_seed: int | None = None, dty
     out[:, 0:2] = noisy[0:n]
     out[:, 2:4] = noisy[1:n + 1]
     return out
+
+
+def stereo_pair_quadruple(video: SceneVideo, device, t: float = 0.0, noise_seed: int | None = None,
+                          dtype=torch.float32) -> torch.Tensor:
+    """A stereo-only quadruple [4, H, W] (float32 on device): the stereo pair
+    of time t used at both times (L, R, L, R), as in the paper's experiments on
+    still stereo pairs, where the motion and difference flows vanish."""
+    clean = render_cameras(video, [(float(t), 0), (float(t), 1)], device, dtype).to(torch.float64)
+    g = torch.Generator(device=device)
+    g.manual_seed(video.seed if noise_seed is None else int(noise_seed))
+    noisy = (clean + video.sigma * torch.randn(clean.shape, generator=g, device=device, dtype=torch.float64))
+    pair = noisy.to(torch.float32)
+    return torch.stack([pair[0], pair[1], pair[0], pair[1]])
