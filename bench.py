@@ -417,6 +417,95 @@ def variant_stereo_12mp(dev, reps=3):
             "energy": st.energy, "paper_context_ms_per_pair": 700.0}
 
 
+HR_W, HR_H, HR_STRIDE, HR_LEVELS, HR_FRAMES = 1920, 1080, 16, 6, 20
+PREC_NAMES = (("fp32", 0), ("fp16", 2), ("bf16", 1))  # sf.FP32, sf.MIXED_FP16, sf.MIXED_BF16
+
+
+def variant_high_resolution(dev, reps=2):
+    """The 1920x1080 video (20 frames, disparities up to 96 px, motion up to
+    40 px; stride 16, 6 levels, 3 GN x 20 PCG, the Figures 5/6/8 weights) in
+    FP32, FP16 and BF16 texels through the level pipeline: frames/s and the
+    last frame's energy. Also keeps, per precision, frame 0's fields and the
+    integer decisions of its solve (W masks; the cell decisions in FP32), for
+    the per-field comparison with the FP64 oracle in the CPU leg."""
+    import torch
+
+    from paper_1610_07159_gb300 import scenes, scenes_device, sf
+
+    video = scenes.SceneVideo(HR_W, HR_H, HR_FRAMES, seed=300, disparity=(15.0, 96.0), max_motion=40.0)
+    frames = scenes_device.frames(video, HR_FRAMES, dev, dtype=torch.float32)
+    nx, ny = -(-HR_W // HR_STRIDE), -(-HR_H // HR_STRIDE)
+    outs = torch.empty((HR_FRAMES, 6, ny, nx), device=dev, dtype=torch.float32)
+    res, keep = {}, {}
+    for name, prec in PREC_NAMES:
+        kw = dict(gn_iters=[GN], pcg_iters=[PCG], precision=prec)
+        v = sf.Solver(HR_W, HR_H, HR_STRIDE, HR_LEVELS, sf.preset(sf.PRESET_FIG568, video=1, **kw))
+        v.tune_pcg(frames[0])
+        v.solve_video(frames, outs)
+        best = None
+        for _ in range(reps):
+            v.reset()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            v.solve_video(frames, outs)
+            b.record()
+            b.synchronize()
+            best = a.elapsed_time(b) if best is None else min(best, a.elapsed_time(b))
+        res[name] = {"fps": HR_FRAMES * 1e3 / best, "energy_last_frame": v.stats().energy}
+        v.close()
+        one = sf.Solver(HR_W, HR_H, HR_STRIDE, HR_LEVELS,
+                        sf.preset(sf.PRESET_FIG568, record_cells=1 if prec == 0 else 0, **kw))
+        f0 = one.solve(frames[0]).cpu().numpy()
+        keep[name] = {"fields": f0, "energy": one.stats().energy, "W": one.wmasks(),
+                      "cells": one.cell_records() if prec == 0 else None}
+        one.close()
+    for name in ("fp16", "bf16"):
+        res[name]["energy_rel_vs_fp32"] = (res[name]["energy_last_frame"] - res["fp32"]["energy_last_frame"]) / \
+            res["fp32"]["energy_last_frame"]
+        res[name]["vs_fp32_fps"] = res[name]["fps"] / res["fp32"]["fps"]
+    res["workload"] = (f"{HR_W}x{HR_H} synthetic stereo video, {HR_FRAMES} frames, disparities up to 96 px, motion up "
+                       f"to 40 px, stride {HR_STRIDE}, {HR_LEVELS} levels, {GN} GN x {PCG} PCG, Figures 5/6/8 weights")
+    return res, {"frame0": frames[0].cpu().numpy(), "runs": keep}
+
+
+def webcam_frame0_runs(frames_d):
+    """Frame 0 of the headline video in the three texel precisions: fields and
+    the integer decisions of the solve, for the per-field oracle comparison."""
+    from paper_1610_07159_gb300 import sf
+
+    keep = {}
+    for name, prec in PREC_NAMES:
+        one = sf.Solver(WIDTH, HEIGHT, STRIDE, LEVELS,
+                        sf.preset(sf.PRESET_FIG2, gn_iters=[GN], pcg_iters=[PCG], precision=prec,
+                                  record_cells=1 if prec == 0 else 0))
+        f0 = one.solve(frames_d[0]).cpu().numpy()
+        keep[name] = {"fields": f0, "energy": one.stats().energy, "W": one.wmasks(),
+                      "cells": one.cell_records() if prec == 0 else None}
+        one.close()
+    return {"frame0": frames_d[0].cpu().numpy(), "runs": keep}
+
+
+def per_field_errors(saved, w, h, stride, levels, preset):
+    """CPU leg: every output field of the GPU's frame 0 against the FP64
+    oracle solving the same quadruple with the GPU's W masks replayed (and its
+    cell decisions at cell edges in FP32): max-abs px per field, energy."""
+    import numpy as np
+
+    import oracle as O
+
+    names = ("s_x", "s_y", "m_x", "m_y", "d_x", "d_y")
+    p = O.Params.preset(preset, gn_iters=(GN,) * 8, pcg_iters=(PCG,) * 8)
+    q = saved["frame0"].astype(np.float64)
+    out = {}
+    for name, run in saved["runs"].items():
+        ref = O.solve_frame(q, stride, levels, p, W_given=run["W"], cells_given=run["cells"])
+        err = np.max(np.abs(run["fields"] - ref.fields(0)), axis=(1, 2))
+        out[name] = {**{n: float(e) for n, e in zip(names, err)},
+                     "energy_rel": abs(run["energy"] - ref.energy) / abs(ref.energy),
+                     "replayed": "W and cell decisions" if run["cells"] is not None else "W"}
+    return out
+
+
 def variant_mixed(dev, frames_d):
     """The headline video in the 16-bit texel modes, with the final energy of
     the last frame against FP32."""
@@ -765,11 +854,20 @@ def run_ours(args):
             line["variants"]["batched_640x480"]["frames_per_s"] / value
         line["variants"]["batched_64_uneven"] = variant_batched(dev)
         line["variants"]["mixed_precision"] = variant_mixed(dev, frames_d)
+        hr, hr_saved = variant_high_resolution(dev)
+        line["variants"]["mixed_precision_1920x1080"] = hr
+        webcam_saved = webcam_frame0_runs(frames_d)
         line["variants"]["learned_warm_start"] = variant_warm_start(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(video)
         if not args.no_variants:
             line["variants"]["cpu_oracle_all_cores"] = cpu_baseline_all_cores()
+            # every output field against the FP64 oracle (the oracle runs in this CPU leg only)
+            line["variants"]["per_field_error_vs_fp64_oracle"] = {
+                "note": "frame 0; max-abs px per field on the finest level; the oracle replays the GPU's W masks (and "
+                        "its cell decisions at cell edges in FP32), integer decisions taken in floating point",
+                f"{WIDTH}x{HEIGHT}": per_field_errors(webcam_saved, WIDTH, HEIGHT, STRIDE, LEVELS, "fig2"),
+                f"{HR_W}x{HR_H}": per_field_errors(hr_saved, HR_W, HR_H, HR_STRIDE, HR_LEVELS, "fig568")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -778,8 +876,9 @@ def run_ours(args):
 
 
 def run_reference(args):
-    """The FP64 CPU oracle as the reference arm: each step solves one 160x240
-    tile (1/8 of a 640x480 frame, same levels, stride and iterations)."""
+    """The FP64 CPU oracle as the reference arm, on the headline workload itself:
+    each step solves the next whole 640x480 frame of the same video from the
+    previous frame's state (the temporal chain), single-threaded."""
     import numpy as np
 
     import oracle as O
@@ -788,25 +887,26 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    video = scenes.SceneVideo(WIDTH, HEIGHT, 2, seed=100).frames(2)
-    tw, th = WIDTH // 4, HEIGHT // 2
-    tiles = [video[f][:, ty * th:(ty + 1) * th, tx * tw:(tx + 1) * tw].astype(np.float64)
-             for f in range(2) for ty in range(2) for tx in range(4)]
+    n = args.warmup + args.steps
+    video = scenes.SceneVideo(WIDTH, HEIGHT, NFRAMES, seed=100).frames(min(n, NFRAMES))
     p = O.Params.preset("fig2", gn_iters=(GN,) * 8, pcg_iters=(PCG,) * 8)
+    prev = None
     for k in range(args.warmup):
-        O.solve_frame(tiles[k % len(tiles)], STRIDE, LEVELS, p)
+        prev = O.solve_frame(video[k % NFRAMES].astype(np.float64), STRIDE, LEVELS, p, prev=prev)
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        O.solve_frame(tiles[k % len(tiles)], STRIDE, LEVELS, p)
+    for k in range(args.warmup, n):
+        prev = O.solve_frame(video[k % NFRAMES].astype(np.float64), STRIDE, LEVELS, p, prev=prev)
     dt = time.perf_counter() - t0
-    value = args.steps / 8.0 / dt
-    sample = (f"each step solves one {tw}x{th} tile (1/8 of a {WIDTH}x{HEIGHT} frame: {LEVELS} levels, stride "
-              f"{STRIDE}, {GN} GN x {PCG} PCG) with the single-threaded FP64 C oracle; frames/s = steps / 8 / time")
+    value = args.steps / dt
+    sample = (f"frames {args.warmup + 1}-{n} of the same {WIDTH}x{HEIGHT} video (frames 1-{args.warmup} as warm-up), "
+              "each from the previous frame's state, with the single-threaded FP64 C oracle on one host core; "
+              "frames/s = timed frames / time")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded ray-cast stereo video)",
-        "config": {"workload": WORKLOAD, "global_batch": 1, "seq_len": NFRAMES, "parallelism": "single host core"},
+        "config": {"workload": WORKLOAD, "step": "one frame of the video (temporal chain)", "global_batch": 1,
+                   "seq_len": NFRAMES, "parallelism": "single host core"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }

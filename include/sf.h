@@ -346,6 +346,27 @@ SF_API int sf_probe_cells(sf_ctx* ctx, int level, int step, unsigned* recs, int 
  * (1..100) on `stream`, waits, and writes the best rate. */
 SF_API int sf_probe_fma_rate(int reps, double* flops_per_s, void* stream);
 
+/* ---- failure detection, exercised without a fault ---------------------
+ * The device-wide waits of this library (the grid barriers of the PCG,
+ * Schwarz and trial kernels, the mbarrier waits of the tensor-core GEMM) are
+ * bounded: a wait that runs out latches a status bit and returns, so a lost
+ * block never hangs the GPU. These two calls run the same wait code with a
+ * short limit on a condition that a test controls; they have no counterpart
+ * in the paper.
+ *
+ * sf_probe_barrier_timeout: a cooperative launch of one block per SM passes
+ * one grid barrier (the library's own, limit `limit_cycles` SM clocks);
+ * block `skip_block` never arrives (-1: every block arrives). Waits for the
+ * launch and writes the latched status (*status: SF_OK, or SF_ERR_TIMEOUT
+ * when the barrier ran out) and the number of blocks that came back from the
+ * barrier (*returned). Allocates its own small device buffers. */
+SF_API int sf_probe_barrier_timeout(int skip_block, long long limit_cycles, int* status, int* returned);
+/* sf_probe_mbarrier_timeout: one block waits on a shared-memory mbarrier of
+ * arrival count 1 (the GEMM's wait, limit `limit_cycles`); with arrive = 1
+ * one thread arrives first, with arrive = 0 nothing does. *completed: 1 if
+ * the wait saw the phase complete, 0 if it ran out. */
+SF_API int sf_probe_mbarrier_timeout(int arrive, long long limit_cycles, int* completed);
+
 /* C[s][M][N] = A[M, K] * B[N, K]^T over split s of K (K split into `splits`
  * contiguous ranges of 64-wide chunks; the splits' partial products are
  * written separately), on the tensor cores: A and B device BF16, row-major
@@ -390,7 +411,11 @@ SF_API int sf_net_gradients(sf_net* n, const float* imgs, const float* target, i
  * 0.999, epsilon 1e-8, bias-corrected) with learning rate lr. */
 SF_API int sf_net_train_step(sf_net* n, const float* imgs, const float* target, int batch, float lr, float* loss,
                              void* stream);
-/* Waits for the device; SF_ERR_TIMEOUT if a tensor-core wait timed out. */
+/* Waits for the device; SF_ERR_TIMEOUT if a tensor-core wait timed out. A
+ * timed-out tile waits once more for its tensor-core work in flight; if that
+ * also gives up, the work may still be running on memory the tile released,
+ * and the CUDA context is to be treated as poisoned: the caller should stop
+ * launching work on it (destroy it, or end the process). */
 SF_API int sf_net_status(sf_net* n);
 SF_API void sf_net_destroy(sf_net* n);
 /* The coarsest-level intensities of a quadruple (device FP32 [4][h][w] of
@@ -475,7 +500,10 @@ SF_API void sf_batch_destroy(sf_batch* b);
  * every GPU that loads the library until exit; a larger G returns SF_ERR_ARG
  * without touching the GPU. The first call on a device looks the array's
  * device address up (cudaGetSymbolAddress) with that device current, so make
- * that first call before any stream capture. All calls share the array and
+ * that first call before any stream capture. The looked-up address is kept
+ * for the rest of the process: after cudaDeviceReset on a device, do not call
+ * sf_pcg_static on that device again in the same process (the reloaded
+ * library image may sit elsewhere). All calls share the array and
  * every call writes what it reads before reading it; calls that overlap on
  * the GPU (other streams, other host threads) race on it. */
 #define SF_STATIC_PCG_MAX_NODES 4096

@@ -519,7 +519,8 @@ __device__ __forceinline__ int ld_acquire_s32(const int* p)
 // latches DEV_TIMEOUT and returns false; a waiter that finds an error in the
 // status word (checked every 64 polls) returns false too, so the kernel
 // unwinds instead of hanging. After a timeout the counter is no longer a
-// multiple of N: the context resets it together with the status word.
+// multiple of N: the context resets it together with the status word. The
+// limit is a parameter so that a test can run it out in a millisecond.
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
 {
     unsigned long long v;
@@ -540,7 +541,8 @@ __device__ __forceinline__ unsigned long long grid_barrier_base(unsigned long lo
     return base_sh;
 }
 
-__device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, int* status, unsigned long long target)
+__device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, int* status, unsigned long long target,
+                                             long long limit_cycles = 2000000000LL)
 {
     __shared__ int ok_sh;
     __syncthreads();
@@ -557,7 +559,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, int* statu
                 ok = 0;
                 break;
             }
-            if (clock64() - t0 > 2000000000LL) {
+            if (clock64() - t0 > limit_cycles) {
                 atomicOr(status, DEV_TIMEOUT);
                 ok = 0;
                 break;

@@ -19,8 +19,13 @@
 //
 // Every mbarrier wait gives up after about one second; the CTA then waits
 // once more for its MMAs in flight, frees its tensor memory, raises the
-// error word and returns.
+// error word (bit 0) and returns. If that second wait gives up too, MMAs may
+// still be writing the tensor memory and reading the shared memory that the
+// CTA released: bit 1 is raised as well, and the CUDA context is to be
+// treated as poisoned (the process should not launch further work on it).
 #include <cuda_bf16.h>
+
+#include <mutex>
 
 #include "sf_launch.h"
 #include "sf_tc.cuh"
@@ -137,9 +142,11 @@ __global__ void __launch_bounds__(GT, 1) k_gemm(GemmArgs a)
     cp_async_wait<0>(); // no copy outlives the loop
     for (int s = 0; s < 2; ++s)
         if (!failed && pending[s] && !wait_stage(s)) failed = true;
+    bool drained = true; // every committed MMA group has completed
     if (failed)
         for (int s = 0; s < 2; ++s)
-            if (pending[s]) wait_stage(s); // the MMAs still in flight, once more
+            if (pending[s] && !wait_stage(s)) drained = false; // the MMAs still in flight, once more
+    if (!drained && tid == 0) atomicOr(a.err, 2); // MMAs may still run: the context is poisoned
     tc::fence_after_sync();
 
     if (!failed) {
@@ -198,10 +205,15 @@ constexpr int GEMM_SMEM = 2 * (BM * BK * 2 + 256 * BK * 2) + 128;
 template <int EPI>
 void launch_epi(const GemmArgs& a, dim3 grid, cudaStream_t st)
 {
-    static bool attr = false; // set once per process (idempotent)
-    if (!attr) {
-        cudaFuncSetAttribute(k_gemm<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
-        attr = true;
+    // the dynamic shared-memory limit is a function attribute of each device: set once per device
+    static std::mutex mu;
+    static bool attr[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!attr[dev] &&
+            cudaFuncSetAttribute(k_gemm<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM) == cudaSuccess)
+            attr[dev] = true;
     }
     k_gemm<EPI><<<grid, GT, GEMM_SMEM, st>>>(a);
 }

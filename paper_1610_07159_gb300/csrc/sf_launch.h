@@ -180,7 +180,8 @@ struct GemmArgs {
     float* C;            // GEMM_F32, GEMM_BIAS_NCHW_F32
     __nv_bfloat16* Cb;   // GEMM_BIAS_RELU_BF16
     const float* bias;
-    int* err;            // set to 1 if an mbarrier wait timed out
+    int* err;            // bit 0: an mbarrier wait timed out; bit 1: MMAs may still be in flight after it
+                         // (their shared and tensor memory were released: treat the CUDA context as poisoned)
 };
 int gemm_check(const GemmArgs& a);
 cudaError_t launch_gemm(const GemmArgs& a, int epi, int splits, cudaStream_t st);

@@ -33,7 +33,9 @@ constexpr size_t ST_FLOATS = 3 * ST_VEC + 4 * ST_MAX_CTAS;
 static __device__ __align__(256) float g_static_scratch[ST_FLOATS];
 
 // Device address of g_static_scratch per device, looked up once with that
-// device current (in host code the symbol is only a host-side stand-in).
+// device current (in host code the symbol is only a host-side stand-in). The
+// cache is not refreshed after cudaDeviceReset, which unloads the module: a
+// process that resets a device must not call sf_pcg_static on it afterwards.
 float* g_scratch_addr[64] = {nullptr};
 std::mutex g_scratch_mu;
 

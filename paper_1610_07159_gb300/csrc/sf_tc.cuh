@@ -96,13 +96,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t saddr, uint32_t parity)
     return ok != 0;
 }
 
-// Waits for the phase with the given parity to complete, for at most about
-// one second of SM clock; returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t saddr, uint32_t parity)
+// Waits for the phase with the given parity to complete, for at most
+// limit_cycles of SM clock (about one second by default); returns false on
+// timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t saddr, uint32_t parity, long long limit_cycles = 2000000000LL)
 {
     const long long t0 = clock64();
     while (!mbar_try_wait(saddr, parity))
-        if (clock64() - t0 > 2000000000LL) return false;
+        if (clock64() - t0 > limit_cycles) return false;
     return true;
 }
 

@@ -1,5 +1,5 @@
 """sf_pcg_static, the PCG entry point that allocates nothing, against the
-context's PCG (sf_probe_pcg) on the same systems.
+context's PCG (sf_probe_pcg) and the FP64 oracle's PCG on the same systems.
 
 It serves callers that cannot allocate device memory where they solve: code
 inside a CUDA graph capture (cudaMalloc is not allowed there), real-time loops
@@ -15,8 +15,9 @@ import numpy as np
 import pytest
 import torch
 
+import oracle as O
 from paper_1610_07159_gb300 import scenes, sf
-from tests.gpu_common import make_params, rel_max
+from tests.gpu_common import lib_blocks_to_oracle, make_params, rel_max
 
 pytestmark = pytest.mark.gpu
 
@@ -53,6 +54,10 @@ def test_static_pcg_matches_the_context_pcg_on_consecutive_calls():
         x_static = sf.pcg_static(nx, ny, blocks, rhs, ITERS)
         torch.cuda.synchronize()
         assert rel_max(x_static.cpu().numpy(), x_ctx.cpu().numpy()) < TOL
+        # and against the FP64 oracle's PCG on the same blocks and right-hand side
+        A = lib_blocks_to_oracle(blocks.cpu().numpy().astype(np.float64), nx, ny)
+        x_ref, _, its = O.pcg(nx, ny, A, rhs.cpu().numpy().astype(np.float64), ITERS)
+        assert its == ITERS and rel_max(x_static.cpu().numpy(), x_ref) < TOL
         results.append(x_static.cpu().numpy())
     assert np.array_equal(results[0], results[1])  # deterministic across calls
 
