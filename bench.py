@@ -293,6 +293,7 @@ def variant_batched_640(dev, frames_d, n_seq=32, steps=3):
     others = [scenes_device.frames(scenes.SceneVideo(WIDTH, HEIGHT, steps + 1, seed=6000 + i), steps + 1, dev,
                                    dtype=torch.float32) for i in range(1, n_seq)]
     packed = [b.pack([frames_d[f]] + [v[f] for v in others]) for f in range(steps + 1)]
+    b_in_off = list(b.in_offsets)
     del others
     out = torch.empty(b.out_total, device=dev, dtype=torch.float32)
     b.tune(packed[0], out, steps=2)
@@ -315,8 +316,44 @@ def variant_batched_640(dev, frames_d, n_seq=32, steps=3):
     res = {"sequences": n_seq, "frames_per_s": n_seq * steps * 1e3 / ms, "ms_per_frame_step": ms / steps,
            "schedule": {"cluster_ctas": b.schedule()[0], "cpb_div": b.schedule()[1]},
            "energy_rel_vs_plain_max": max(rel), "frames_compared": len(rel)}
+    batched_energies = [b.sequence(i).stats().energy for i in range(n_seq)]
     b.close()
     plain.close()
+    # the throughput baseline: the same n_seq sequences through n_seq plain FP32 contexts, each replaying its
+    # frame graph on its own stream, all streams running at once
+    ctxs = [sf.Solver(WIDTH, HEIGHT, STRIDE, LEVELS, sf.preset(sf.PRESET_FIG2, gn_iters=[GN], pcg_iters=[PCG]))
+            for _ in range(n_seq)]
+    for c in ctxs:
+        c.tune_pcg(frames_d[0])  # the cached per-level schedules
+    streams = [torch.cuda.Stream() for _ in range(n_seq)]
+    outs = [torch.empty((6, HEIGHT // STRIDE, WIDTH // STRIDE), device=dev, dtype=torch.float32) for _ in range(n_seq)]
+    seq_frames = [[frames_d[f] for f in range(steps + 1)]] + \
+        [[packed[f][b_in_off[i]:b_in_off[i] + 4 * WIDTH * HEIGHT].view(4, HEIGHT, WIDTH) for f in range(steps + 1)]
+         for i in range(1, n_seq)]
+    main = torch.cuda.current_stream()
+    ms_ms = 0.0
+    for f in range(steps + 1):
+        s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(main)
+        for i, c in enumerate(ctxs):
+            streams[i].wait_event(s0)
+            with torch.cuda.stream(streams[i]):
+                c.solve(seq_frames[i][f], outs[i])
+        for st in streams:
+            main.wait_stream(st)
+        e0.record(main)
+        e0.synchronize()
+        if f > 0:
+            ms_ms += s0.elapsed_time(e0)
+    ms_energies = [c.stats().energy for c in ctxs]
+    for c in ctxs:
+        c.close()
+    ms_fps = n_seq * steps * 1e3 / ms_ms
+    res["plain_fp32_multistream"] = {
+        "contexts": n_seq, "frames_per_s": ms_fps, "ms_per_frame_step": ms_ms / steps,
+        "note": "one plain context per sequence, each replaying its frame graph on its own stream",
+        "energy_rel_vs_batched_max": max(abs(a - bb) / abs(bb) for a, bb in zip(ms_energies, batched_energies))}
+    res["vs_plain_fp32_multistream"] = res["frames_per_s"] / ms_fps
     return res
 
 
@@ -571,10 +608,14 @@ def variant_warm_start(dev, n_videos=8):
         s.close()
         return len(quads) * 1e3 / tot
 
+    tte = ws.evaluate_time_to_energy(net, 32, seed0=970000)
     res = {"frames": n_videos, "cold_schedule": list(ws.FULL), "cold_first_frame_fps": fps(ws.FULL, False),
+           "time_to_cold_energy_1e-4": {k: tte[k] for k in ("frames", "bar", "cold_full_cost", "warm_accepted")},
            "accepted_at_1e-4": ev["cheapest_warm"],
            "per_schedule": [{k: r[k] for k in ("gn", "cost", "warm_mean_rel", "warm_max_rel", "cold_mean_rel",
                                                 "cold_max_rel", "warm_accepted")} for r in ev["schedules"]]}
+    for start, r in tte["starts"].items():
+        res["time_to_cold_energy_1e-4"][start] = {k: r[k] for k in ("reached", "mean_cost", "frames_per_s_to_reach")}
     if pick:
         res.update({"warm_schedule": pick["gn"], "warm_first_frame_fps": fps(pick["gn"], True),
                     "warm_mean_rel_energy": pick["warm_mean_rel"], "warm_max_rel_energy": pick["warm_max_rel"]})

@@ -22,6 +22,11 @@ coarsest level is 80 x 60 pixels with an 8 x 10 warp grid.
   solve with the full schedule against warm-started solves with cheaper
   schedules (fewer Gauss-Newton steps per level). A schedule is accepted when
   every evaluation frame ends within 1e-4 relative of its cold-start energy.
+* Time to energy: per frame, the cheapest schedule of a family (more or
+  fewer Gauss-Newton steps per level) whose final energy reaches the cold
+  start's within 1e-4, from the zero start, from the network's prediction,
+  and from the prediction kept only where it lowers the coarsest level's
+  energy (guarded); the Gauss-Newton cost and frames/s to get there.
 """
 
 from __future__ import annotations
@@ -147,6 +152,95 @@ def evaluate(net: sf.Net | None, n_videos: int, seed0: int, schedules=SCHEDULES,
     res["cheapest_warm"] = min(acc_w, key=lambda r: r["cost"])["gn"] if acc_w else None
     res["cheapest_cold"] = min(acc_z, key=lambda r: r["cost"])["gn"] if acc_z else None
     return res
+
+
+# the schedule family of the time-to-energy evaluation, cheapest first by cost
+# (Gauss-Newton steps weighted by level pixels): the schedules above and ones
+# with more steps on the finest level
+TTE_SCHEDULES = tuple(sorted(set(SCHEDULES) | {(g0,) + tail for g0 in range(4, 9)
+                                               for tail in ((3, 3, 3), (2, 2, 1), (1, 1, 0), (2, 2, 0))},
+                             key=schedule_cost))
+
+
+def guarded_init(net: sf.Net, solver: sf.Solver, q: torch.Tensor) -> bool:
+    """Predicts the coarsest initial delta and keeps it only where it lowers
+    the coarsest level's energy against the zero start (both with W taken at
+    their own state and the feature weights of the zero start); returns
+    whether the prediction was kept. The same safeguard as the step
+    acceptance of the solve, applied to the start."""
+    img = sf.coarsest_images(solver, q)  # also builds the context's pyramid
+    pred = net.forward(img[None].contiguous())[0].contiguous()
+    lc = solver.levels - 1
+    _, _, nx, ny = solver.dims(lc)
+    zero = torch.zeros((6, ny * nx), device="cuda", dtype=torch.float32)
+    wf = solver.probe_feature_weights(lc, zero)
+    e_pred = solver.probe_energy(lc, zero, pred.view(6, -1).contiguous(), wf)[0].item()
+    e_zero = solver.probe_energy(lc, zero, zero, wf)[0].item()
+    if e_pred < e_zero:
+        solver.set_init(pred.view(6, -1).contiguous())
+        return True
+    return False
+
+
+def evaluate_time_to_energy(net: sf.Net, n_videos: int, seed0: int, schedules=TTE_SCHEDULES, device="cuda",
+                            rel=ACCEPT_REL):
+    """The spec evaluation of the warm start: on the first frames of
+    n_videos held-out videos, E_cold is the final energy of the cold start
+    with the full schedule; for each start (zero, network, guarded network)
+    and frame, the cheapest schedule of the family whose final energy is
+    within `rel` of E_cold (E <= (1 + rel) E_cold), its cost (Gauss-Newton
+    steps weighted by level pixels) and its solve time (CUDA events, the
+    network's pass included). A frame that no schedule brings there counts as
+    not reached."""
+    quads = [scenes_device.frames(scenes.SceneVideo(W0, H0, 1, seed=seed0 + v), 1, device)[0] for v in range(n_videos)]
+    solvers = {gn: sf.Solver(W0, H0, STRIDE, LEVELS, solver_params(gn)) for gn in set(schedules) | {FULL}}
+
+    def run(gn, q, start):
+        s = solvers[gn]
+        s.reset()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        if start == "warm":
+            net.warm_start(s, q)
+        elif start == "guarded":
+            guarded_init(net, s, q)
+        s.solve(q)
+        b.record()
+        b.synchronize()
+        return s.stats().energy, a.elapsed_time(b)
+
+    for q in quads[:2]:  # warm-up (graph capture of every schedule)
+        for gn in solvers:
+            run(gn, q, "zero")
+    e_cold = [run(FULL, q, "zero")[0] for q in quads]
+    out = {"frames": n_videos, "bar": f"E <= (1 + {rel:g}) E_cold, E_cold the cold start with {list(FULL)}",
+           "family": [list(gn) for gn in schedules], "cold_full_cost": schedule_cost(FULL), "starts": {}}
+    for start in ("zero", "warm", "guarded"):
+        costs, times, reached, picks = [], [], 0, []
+        for q, ec in zip(quads, e_cold):
+            pick = None
+            for gn in schedules:
+                e, ms = run(gn, q, start)
+                if e <= (1.0 + rel) * ec:
+                    pick = (gn, ms)
+                    break
+            if pick is not None:
+                reached += 1
+                costs.append(schedule_cost(pick[0]))
+                times.append(pick[1])
+                picks.append(list(pick[0]))
+            else:
+                picks.append(None)
+        out["starts"][start] = {
+            "reached": reached, "mean_cost": float(np.mean(costs)) if costs else None,
+            "frames_per_s_to_reach": len(times) * 1e3 / float(np.sum(times)) if times else None,
+            "schedules": picks}
+    for s in solvers.values():
+        s.close()
+    z, w = out["starts"]["zero"], out["starts"]["warm"]
+    out["warm_accepted"] = bool(w["reached"] == n_videos and z["mean_cost"] is not None and
+                                w["mean_cost"] is not None and w["mean_cost"] < z["mean_cost"])
+    return out
 
 
 def main(argv=None) -> None:

@@ -74,3 +74,26 @@ def test_warm_start_replaces_the_zero_start_of_the_first_frame_only():
     s.solve(q[1])  # the next frame takes the temporal transfer again
     d_next, _ = s.state(3)
     assert not torch.allclose(d_next, pred)
+
+
+def test_time_to_cold_energy_evaluation():
+    """The evaluation the warm start is judged by: per held-out first frame,
+    the cheapest schedule that reaches the full cold start's energy within
+    1e-4. The zero start always gets there (the full schedule is in the
+    family); every reported schedule is one of the family; the guarded start
+    never does worse than zero at the coarsest level by construction."""
+    d = np.load(WEIGHTS)
+    net = sf.Net(1)
+    net.set_params(torch.from_numpy(d["params"]).cuda())
+    fam = ((1, 1, 1, 0), (2, 2, 1, 0), (3, 3, 3, 0), (3, 3, 3, 3), (5, 2, 2, 0))
+    res = ws.evaluate_time_to_energy(net, 4, seed0=975000, schedules=fam)
+    z = res["starts"]["zero"]
+    assert z["reached"] == 4 and z["mean_cost"] <= ws.schedule_cost((3, 3, 3, 3)) + 1e-9
+    for start in ("zero", "warm", "guarded"):
+        r = res["starts"][start]
+        assert 0 <= r["reached"] <= 4
+        assert all(p is None or tuple(p) in fam for p in r["schedules"])
+        if r["reached"]:
+            assert r["frames_per_s_to_reach"] > 0
+    print("\ntime to cold energy:", {k: (v["reached"], v["mean_cost"]) for k, v in res["starts"].items()})
+
