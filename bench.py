@@ -454,6 +454,39 @@ def variant_stereo_12mp(dev, reps=3):
             "energy": st.energy, "paper_context_ms_per_pair": 700.0}
 
 
+def variant_maps(dev, frames_d, plain_fps, reps=3):
+    """The headline video with the occlusion and illumination correction maps
+    of Algorithm 1 computed after every level and used by the next: frames/s
+    through the level pipeline, and the share of the map kernels in a frame
+    (serialised, CUDA events around their launches inside the frame graph)."""
+    import torch
+
+    from paper_1610_07159_gb300 import sf
+
+    kw = dict(gn_iters=[GN], pcg_iters=[PCG], occlusion=1, illumination=1)
+    v = sf.Solver(WIDTH, HEIGHT, STRIDE, LEVELS, sf.preset(sf.PRESET_FIG2, video=1, **kw))
+    v.tune_pcg(frames_d[0])
+    _, _, nx, ny = level_sizes()[0]
+    outs = torch.empty((NFRAMES, 6, ny, nx), device=dev, dtype=torch.float32)
+    v.solve_video(frames_d, outs)
+    best = None
+    for _ in range(reps):
+        v.reset()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        v.solve_video(frames_d, outs)
+        b.record()
+        b.synchronize()
+        best = a.elapsed_time(b) if best is None else min(best, a.elapsed_time(b))
+    st = v.stats()
+    v.close()
+    fps = NFRAMES * 1e3 / best
+    return {"video_fps": fps, "vs_plain_video_fps": fps / plain_fps, "launches_per_frame": st.launches,
+            "energy_last_frame": st.energy,
+            "note": "occlusion maps (z-buffered warp grid, visibility, prolongation) and illumination maps (stereo "
+                    "residual, Gaussian sigma 3.2 px, box prolongation) after levels 3, 2, 1"}
+
+
 HR_W, HR_H, HR_STRIDE, HR_LEVELS, HR_FRAMES = 1920, 1080, 16, 6, 20
 PREC_NAMES = (("fp32", 0), ("fp16", 2), ("bf16", 1))  # sf.FP32, sf.MIXED_FP16, sf.MIXED_BF16
 
@@ -665,14 +698,21 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     prof = (1 << sf.K_PCG) | (1 << sf.K_ASSEMBLE)
 
-    if args.arm == "frames":
-        # profiling aid: the frame-by-frame graph path only, W + K frames in level order
-        plain = sf.Solver(WIDTH, HEIGHT, STRIDE, LEVELS, sf.preset(sf.PRESET_FIG2, gn_iters=[GN], pcg_iters=[PCG]))
+    if args.arm in ("frames", "frames_maps", "frames_schwarz"):
+        # profiling aid: the frame-by-frame graph path only, W + K frames in level order (with both maps, or with
+        # the Schwarz solver of the equal-energy schedule)
+        extra = {}
+        if args.arm == "frames_maps":
+            extra = dict(occlusion=1, illumination=1)
+        elif args.arm == "frames_schwarz":
+            extra = dict(solver=sf.SOLVER_SCHWARZ, pcg_iters=[6], patch_iters=[6], schwarz_tile=7, schwarz_overlap=1)
+        plain = sf.Solver(WIDTH, HEIGHT, STRIDE, LEVELS,
+                          sf.preset(sf.PRESET_FIG2, **{**dict(gn_iters=[GN], pcg_iters=[PCG]), **extra}))
         out1 = torch.empty((6, 60, 80), device=dev, dtype=torch.float32)
         for k in range(args.warmup + args.steps):
             plain.solve(frames_d[k % NFRAMES], out1)
         torch.cuda.synchronize()
-        print(json.dumps({"arm": "frames", "frames": args.warmup + args.steps}), flush=True)
+        print(json.dumps({"arm": args.arm, "frames": args.warmup + args.steps}), flush=True)
         return
 
     # headline: the level-pipelined video solve, one step = one pass over the 30 frames. A second
@@ -890,6 +930,7 @@ def run_ours(args):
     if rank == 0 and not args.no_variants:
         line["variants"]["schwarz_640x480"] = variant_schwarz(dev, frames_d, plain_energies, value)
         line["variants"]["stereo_only_4288x2848"] = variant_stereo_12mp(dev)
+        line["variants"]["occlusion_and_illumination_maps"] = variant_maps(dev, frames_d, value)
         line["variants"]["batched_640x480"] = variant_batched_640(dev, frames_d)
         line["variants"]["batched_640x480"]["vs_plain_fp32_video"] = \
             line["variants"]["batched_640x480"]["frames_per_s"] / value
@@ -962,9 +1003,11 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the batched, mixed and warm-start variants")
-    ap.add_argument("--arm", choices=("all", "video", "frames", "batch8", "train"), default="all",
-                    help="for profiling runs: only the pipelined video arm, only the frame-by-frame arm, one "
-                         "8-sequence batched launch pair, or two training steps of the warm-start network")
+    ap.add_argument("--arm", choices=("all", "video", "frames", "frames_maps", "frames_schwarz", "batch8", "train"),
+                    default="all",
+                    help="for profiling runs: only the pipelined video arm, only the frame-by-frame arm (plain, with "
+                         "both maps, or with the Schwarz solver), one 8-sequence batched launch pair, or two training "
+                         "steps of the warm-start network")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
