@@ -9,8 +9,9 @@
 //     shared memory; the paper precomputes these alignment blocks once per
 //     step and reads them on demand (Section 5.2);
 //   * per node: gather of the cell blocks plus the smoothness (Eq. 14),
-//     epipolar (Eqs. 15-17) and magnitude (Eq. 18) rows, the Jacobi
-//     preconditioner and the energy at the linearisation point;
+//     epipolar (Eqs. 15-17) and magnitude (Eq. 18) rows (entry-parallel), the
+//     right-hand side, the Jacobi preconditioner and the energy at the
+//     linearisation point (component-parallel);
 //   * energies of trial steps with the backtracking decision and the update.
 #include "sf_launch.h"
 #include "sf_stages.cuh"
@@ -45,23 +46,140 @@ __global__ void __launch_bounds__(ETHREADS, 2) k_assemble(LevelGeom g, int cpb, 
     }
 }
 
-// Gather of the node system from the cell blocks plus the prior rows, the
-// Jacobi preconditioner, and (last block) the energy at this point; four
-// lanes per node.
-__global__ void __launch_bounds__(ETHREADS) k_gather(LevelGeom g, const float* __restrict__ cell,
-                                                     const float* __restrict__ base, const float* __restrict__ delta,
-                                                     const float* __restrict__ wf, DevParams P,
-                                                     float* __restrict__ node, float* __restrict__ rhs,
-                                                     float* __restrict__ minv, float2* __restrict__ gpart,
-                                                     const float2* __restrict__ apart, int n_asm, unsigned* counter,
-                                                     StepCtrl* __restrict__ ctrl, int* status)
+// Row and column (r <= c) of entry e of a packed symmetric 6x6 block.
+__constant__ unsigned char c_sym_r[NB] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3, 4, 4, 5};
+__constant__ unsigned char c_sym_c[NB] = {0, 1, 2, 3, 4, 5, 1, 2, 3, 4, 5, 2, 3, 4, 5, 3, 4, 5, 4, 5, 5};
+
+__device__ __forceinline__ float cell_entry(const float* __restrict__ cell, int ncx, int ncy, int ci, int cj, int v)
+{
+    if (ci < 0 || cj < 0 || ci >= ncx || cj >= ncy) return 0.f;
+    return __ldg(cell + (size_t)v * ncx * ncy + cj * ncx + ci);
+}
+
+// The node blocks of the Gauss-Newton system, one thread per (entry, node):
+// entry v = b * 21 + e of node n is the sum of its cells' pair blocks (the
+// chain rule of Eq. 7), plus for the node's own block the smoothness
+// (Eq. 14), epipolar (Eqs. 15-17) and magnitude (Eq. 18) rows and for the E
+// and S blocks the smoothness coupling, added in the order gather_node4
+// adds them, so the values are the same bit for bit. Entry-parallel: every
+// thread has a few independent loads, where a node-parallel gather waits on
+// long chains of them.
+__global__ void __launch_bounds__(ETHREADS) k_gather_blocks(LevelGeom g, const float* __restrict__ cell,
+                                                            const float* __restrict__ base,
+                                                            const float* __restrict__ delta,
+                                                            const float* __restrict__ wf, DevParams P,
+                                                            float* __restrict__ node)
+{
+    const int t = blockIdx.x * ETHREADS + threadIdx.x;
+    if (t >= NODE_VALS * g.G) return;
+    const int v = t / g.G, n = t - v * g.G;
+    const int b = v / NB, e = v - b * NB;
+    const int i = n % g.nx, j = n / g.nx;
+    const int ncx = g.ncx, ncy = g.ncy;
+    const int r = c_sym_r[e], c = c_sym_c[e];
+    const bool diag = r == c;
+    float acc = 0.f;
+    if (b == 0) {
+        acc += cell_entry(cell, ncx, ncy, i - 1, j - 1, pair_idx(3, 3) * NB + e);
+        acc += cell_entry(cell, ncx, ncy, i, j - 1, pair_idx(2, 2) * NB + e);
+        acc += cell_entry(cell, ncx, ncy, i - 1, j, pair_idx(1, 1) * NB + e);
+        acc += cell_entry(cell, ncx, ncy, i, j, pair_idx(0, 0) * NB + e);
+        const float wn = wf[n];
+        if (diag) {
+            const int nbi[4] = {i + 1, i, i - 1, i};
+            const int nbj[4] = {j, j + 1, j, j - 1};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (nbi[q] < 0 || nbj[q] < 0 || nbi[q] >= g.nx || nbj[q] >= g.ny) continue;
+                const float ww = P.w_reg * P.w_smooth * (wn + wf[nbj[q] * g.nx + nbi[q]]);
+                acc += ww * P.wfl[r >> 1];
+            }
+        }
+        const float ce = P.w_reg * P.w_epi;
+        if (ce != 0.f) {
+            float T[6], d[6], rr[2], J[12];
+            node_total(base, delta, nullptr, 0.f, g.G, n, T, d);
+            epipolar(P.Fl, (float)(i * g.s), (float)(j * g.s), T, rr, J);
+            acc = fmaf(ce * J[r], J[c], acc);
+            acc = fmaf(ce * J[6 + r], J[6 + c], acc);
+        }
+        if (diag) acc += P.w_reg * P.w_mag * P.mfl[r >> 1];
+    } else if (b == 1 || b == 2) {
+        if (b == 1) {
+            acc += cell_entry(cell, ncx, ncy, i, j - 1, pair_idx(2, 3) * NB + e);
+            acc += cell_entry(cell, ncx, ncy, i, j, pair_idx(0, 1) * NB + e);
+        } else {
+            acc += cell_entry(cell, ncx, ncy, i - 1, j, pair_idx(1, 3) * NB + e);
+            acc += cell_entry(cell, ncx, ncy, i, j, pair_idx(0, 2) * NB + e);
+        }
+        const int mi = b == 1 ? i + 1 : i, mj = b == 1 ? j : j + 1;
+        if (diag && mi < g.nx && mj < g.ny) {
+            const float ww = P.w_reg * P.w_smooth * (wf[n] + wf[mj * g.nx + mi]);
+            acc -= ww * P.wfl[r >> 1];
+        }
+    } else if (b == 3) {
+        acc += cell_entry(cell, ncx, ncy, i, j, pair_idx(0, 3) * NB + e);
+    } else {
+        acc += cell_entry(cell, ncx, ncy, i - 1, j, pair_idx(1, 2) * NB + e);
+    }
+    node[t] = acc;
+}
+
+// The right-hand side and Jacobi preconditioner, one thread per (component,
+// node) (the cells' part of b plus the prior rows, in gather_node4's order),
+// and the prior energies at the linearisation point (the thread of component
+// 0); the last block to finish forms the step's record from the assembly's
+// and these partials in a fixed order.
+__global__ void __launch_bounds__(ETHREADS) k_gather_rhs(LevelGeom g, const float* __restrict__ cell,
+                                                         const float* __restrict__ base,
+                                                         const float* __restrict__ delta,
+                                                         const float* __restrict__ wf, DevParams P,
+                                                         const float* __restrict__ node, float* __restrict__ rhs,
+                                                         float* __restrict__ minv, float2* __restrict__ gpart,
+                                                         const float2* __restrict__ apart, int n_asm,
+                                                         unsigned* counter, StepCtrl* __restrict__ ctrl, int* status)
 {
     __shared__ ff sred[6 * (ETHREADS / 32)];
     __shared__ bool last_sh;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = t >> 2;
+    const int t = blockIdx.x * ETHREADS + threadIdx.x;
+    const int G = g.G;
     float es = 0.f, ee = 0.f, em = 0.f;
-    gather_node4(g, n < g.G ? n : g.G - 1, t & 3, n < g.G, cell, base, delta, wf, P, node, rhs, minv, es, ee, em);
+    if (t < 6 * G) {
+        const int u = t / G, n = t - u * G;
+        const int i = n % g.nx, j = n / g.nx;
+        const int ncx = g.ncx, ncy = g.ncy;
+        const int rc = NPAIR * NB + u; // component u of corner k's rhs at rc + 6 k
+        float bb = 0.f;
+        bb += cell_entry(cell, ncx, ncy, i - 1, j - 1, rc + 6 * 3);
+        bb += cell_entry(cell, ncx, ncy, i, j - 1, rc + 6 * 2);
+        bb += cell_entry(cell, ncx, ncy, i - 1, j, rc + 6 * 1);
+        bb += cell_entry(cell, ncx, ncy, i, j, rc + 6 * 0);
+        const float du = delta[u * G + n];
+        const float wn = wf[n];
+        const int nbi[4] = {i + 1, i, i - 1, i};
+        const int nbj[4] = {j, j + 1, j, j - 1};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (nbi[q] < 0 || nbj[q] < 0 || nbi[q] >= g.nx || nbj[q] >= g.ny) continue;
+            const int m = nbj[q] * g.nx + nbi[q];
+            const float ww = P.w_reg * P.w_smooth * (wn + wf[m]);
+            const float cf = ww * P.wfl[u >> 1];
+            const float df = (base[u * G + n] - base[u * G + m]) + (du - delta[u * G + m]);
+            bb -= cf * df;
+        }
+        const float ce = P.w_reg * P.w_epi;
+        if (ce != 0.f) {
+            float T[6], d[6], r[2], J[12];
+            node_total(base, delta, nullptr, 0.f, G, n, T, d);
+            epipolar(P.Fl, (float)(i * g.s), (float)(j * g.s), T, r, J);
+            bb -= ce * (r[0] * J[u] + r[1] * J[6 + u]);
+        }
+        bb -= P.w_reg * P.w_mag * P.mfl[u >> 1] * du;
+        rhs[u * G + n] = bb;
+        const float dg = node[(size_t)sym_idx(u, u) * G + n];
+        minv[u * G + n] = dg > 0.f ? 1.f / dg : 1.f;
+        if (u == 0) node_prior_energy(g, P, base, delta, nullptr, 0.f, wf, n, es, ee, em);
+    }
     if (!ctrl) return;
     const float v[3] = {es, ee, em};
     ff tb[3];
@@ -87,21 +205,21 @@ __global__ void __launch_bounds__(ETHREADS) k_gather(LevelGeom g, const float* _
         const double sp = (double)fp.hi + fp.lo, sg = (double)fg.hi + fg.lo, sx = (double)fx.hi + fx.lo;
         const double ss = (double)fs.hi + fs.lo, se = (double)fe.hi + fe.lo, sm = (double)fm.hi + fm.lo;
         if (threadIdx.x == 0) {
-            StepCtrl c;
-            c.terms_cur[0] = P.w_photo * sp;
-            c.terms_cur[1] = P.w_grad * sg;
-            c.terms_cur[2] = (double)P.w_reg * P.w_smooth * ss;
-            c.terms_cur[3] = (double)P.w_reg * P.w_epi * se;
-            c.terms_cur[4] = (double)P.w_reg * P.w_mag * sm;
-            c.E_cur = c.terms_cur[0] + c.terms_cur[1] + c.terms_cur[2] + c.terms_cur[3] + c.terms_cur[4];
-            c.E_acc = c.E_cur;
-            for (int q = 0; q < 5; ++q) c.terms_acc[q] = c.terms_cur[q];
-            c.t = 0.f;
-            c.accepted = 0;
-            c.n_excluded = (int)sx;
-            c.pad = 0;
-            *ctrl = c;
-            if (!isfinite(c.E_cur)) atomicOr(status, DEV_NUMERIC);
+            StepCtrl cr;
+            cr.terms_cur[0] = P.w_photo * sp;
+            cr.terms_cur[1] = P.w_grad * sg;
+            cr.terms_cur[2] = (double)P.w_reg * P.w_smooth * ss;
+            cr.terms_cur[3] = (double)P.w_reg * P.w_epi * se;
+            cr.terms_cur[4] = (double)P.w_reg * P.w_mag * sm;
+            cr.E_cur = cr.terms_cur[0] + cr.terms_cur[1] + cr.terms_cur[2] + cr.terms_cur[3] + cr.terms_cur[4];
+            cr.E_acc = cr.E_cur;
+            for (int q = 0; q < 5; ++q) cr.terms_acc[q] = cr.terms_cur[q];
+            cr.t = 0.f;
+            cr.accepted = 0;
+            cr.n_excluded = (int)sx;
+            cr.pad = 0;
+            *ctrl = cr;
+            if (!isfinite(cr.E_cur)) atomicOr(status, DEV_NUMERIC);
             __threadfence();
             *counter = 0u;
         }
@@ -359,9 +477,12 @@ void launch_gather(const LevelGeom& g, const float* cell, const float* base, con
                    const DevParams& P, float* node, float* rhs, float* minv, const Scratch& sc, StepCtrl* ctrl,
                    int n_asm_blocks, cudaStream_t st)
 {
-    const int blocks = (4 * g.G + ETHREADS - 1) / ETHREADS; // four lanes per node
-    k_gather<<<blocks, ETHREADS, 0, st>>>(g, cell, base, delta, wf, P, node, rhs, minv, sc.gat_part, sc.asm_part,
-                                          n_asm_blocks, sc.counters + 0, ctrl, sc.status);
+    // the node blocks entry by entry, then the right-hand side, preconditioner and energy component by component
+    const int bblocks = (NODE_VALS * g.G + ETHREADS - 1) / ETHREADS;
+    k_gather_blocks<<<bblocks, ETHREADS, 0, st>>>(g, cell, base, delta, wf, P, node);
+    const int rblocks = (6 * g.G + ETHREADS - 1) / ETHREADS;
+    k_gather_rhs<<<rblocks, ETHREADS, 0, st>>>(g, cell, base, delta, wf, P, node, rhs, minv, sc.gat_part,
+                                               sc.asm_part, n_asm_blocks, sc.counters + 0, ctrl, sc.status);
 }
 
 void launch_energy(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta, const float* x,

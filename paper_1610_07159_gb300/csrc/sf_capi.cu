@@ -298,7 +298,7 @@ int enqueue_level(sf_ctx* c, int l, const LevelIO& io, cudaStream_t st, int& nl)
                                          c->pcg_part[l], c->bar + l, c->status, P.pcg_iters[l], 0, st);
         prof_mark(c, SF_K_PCG, false, st);
         if (e != cudaSuccess) return check_cuda(e);
-        nl += 3;
+        nl += 4; // assembly, the two gather passes, the linear solve
         prof_mark(c, SF_K_ENERGY, true, st);
         e = launch_trials(g, io.tex, P.precision, b.base, b.delta, b.x, b.wf, c->dp[l], Wst, sc,
                           c->bar + SF_MAX_LEVELS + l, ctrl, P.max_backtracks, c->trial_blocks[l], st, M);
@@ -660,7 +660,7 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
         g.level = l;
         const int en_blocks = std::min((g.w * g.h + 255) / 256, 152 * 8) + (g.G + 255) / 256;
         if (w < 2 || h < 2 || g.nx < 2 || g.ny < 2 || assemble_blocks(g, nullptr) > MAX_PART || en_blocks > MAX_PART ||
-            (4 * g.G + 255) / 256 > MAX_PART) {
+            (6 * g.G + 255) / 256 > MAX_PART) {
             delete c;
             fail(SF_ERR_ARG);
             return nullptr;
