@@ -109,16 +109,21 @@ __device__ __forceinline__ void weigh_terms(const DevParams& P, double sp, doubl
     terms[4] = (double)P.w_reg * P.w_mag * sm;
 }
 
-// Jacobi-preconditioned CG on one level's block system, the cluster's CTAs
-// sharing the nodes: four lanes per node (lane q applies stencil slots q and
-// q + 4, lane 0 also slot 8; two shuffle rounds combine them), vectors in
-// global memory, two cluster sums per iteration. A neighbour's p_k is formed
-// from its z_k and p_{k-1} (double-buffered), as in the single-sequence
-// solver, so an iteration needs no third barrier.
+// Jacobi-preconditioned CG on one level's block system in the one-reduction
+// form of Chronopoulos and Gear, the cluster's CTAs sharing the nodes: four
+// lanes per node (lane q applies stencil slots q and q + 4, lane 0 also slot
+// 8; two shuffle rounds combine them). An owner keeps its iterate x and
+// direction p in global memory and publishes r_k, w_k = A u_k and
+// s_{k-1} = A p_{k-1} in the buffers of iteration k's parity; a neighbour's
+// u_{k+1} = M (r_k - alpha_k (w_k + beta_k s_{k-1})) is formed from those, in
+// the same operations as its owner forms it, so one sweep over the nodes
+// (update, then w_{k+1} = A u_{k+1}) and one cluster sum of (r, u) and (w, u)
+// make an iteration.
 __device__ void pcg_cluster(const LevelGeom& g, const BLevel& B, int iters, float2* part, int& phase, BShared& sm,
                             int rank, int T)
 {
     const int G = g.G, nx = g.nx, ny = g.ny;
+    const size_t G6 = (size_t)6 * G;
     const int q4 = threadIdx.x & 3, c0 = q4, c1 = q4 + 4;
     const bool has1 = c1 < 6;
     const int grp = rank * BNPB + (threadIdx.x >> 2);
@@ -128,82 +133,77 @@ __device__ void pcg_cluster(const LevelGeom& g, const BLevel& B, int iters, floa
     const int wgrp = rank * BNPB + ((threadIdx.x >> 5) << 3);
     const int nk = wgrp < G ? (G - 1 - wgrp) / stride + 1 : 0;
     float* x = B.x;
-    float* r = B.r;
-    float* z = B.z;
-    float* p0 = B.p0;
-    float* p1 = B.p1;
-    float* qv = B.q;
+    float* pd = B.p;
     const float* node = B.node;
     const float* rhs = B.rhs;
     const float* minv = B.minv;
 
-    float acc = 0.f;
-    for (int k = 0; k < nk; ++k) {
-        const int n = grp + k * stride;
-        if (n >= G) continue;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (h == 1 && !has1) continue;
-            const int c = h ? c1 : c0;
-            const float rr = rhs[c * G + n];
-            const float zz = minv[c * G + n] * rr;
-            r[c * G + n] = rr;
-            z[c * G + n] = zz;
-            p0[c * G + n] = zz;
-            x[c * G + n] = 0.f;
-            acc = fmaf(rr, zz, acc);
-        }
-    }
-    ff red[1];
-    {
-        const float v[1] = {acc};
-        cl_sum<1>(v, red, part, phase, sm, rank, T);
-    }
-    ff rz = red[0];
-    float beta = 0.f;
-    for (int it = 0; it < iters; ++it) {
-        if (!(rz.hi > 1e-30f)) break;
-        const bool first = it == 0;
-        const float* pprev = (it & 1) ? p0 : p1; // p_{it-1} sits in buffer (it-1) & 1
-        float* pcur = (it & 1) ? p1 : p0;
-        acc = 0.f;
+    float alpha = 0.f, beta = 0.f;
+    ff gam{0.f, 0.f};
+    for (int i = -1; i < iters; ++i) {
+        // i = -1 sets up: r_0 = b, s_{-1} = 0, w_0 = A M b and the first sums
+        const int par = i < 0 ? 0 : (i & 1);
+        const int npar = i < 0 ? 0 : (par ^ 1);
+        const float* R = B.pub + (size_t)par * 3 * G6;
+        const float* Wv = R + G6;
+        const float* S = R + 2 * G6;
+        float* Rn = B.pub + (size_t)npar * 3 * G6;
+        float* Wn = Rn + G6;
+        float* Sn = Rn + 2 * G6;
+        const bool last = i == iters - 1; // the update of x only
+        float gp = 0.f, dp = 0.f;
         for (int k = 0; k < nk; ++k) {
             const int n = grp + k * stride;
             const bool live = n < G;
-            float pn0 = 0.f, pn1 = 0.f;
-            float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float rn[2] = {0.f, 0.f}, un[2] = {0.f, 0.f};
             if (live) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     if (h == 1 && !has1) continue;
-                    const int c = h ? c1 : c0;
-                    float pv = z[c * G + n];
-                    if (!first) {
-                        pv = fmaf(beta, pprev[c * G + n], pv);
-                        pcur[c * G + n] = pv;
+                    const int o = (h ? c1 : c0) * G + n;
+                    const float m = minv[o];
+                    float r1, s;
+                    if (i < 0) {
+                        r1 = rhs[o];
+                        s = 0.f;
+                        x[o] = 0.f;
+                        pd[o] = 0.f;
+                    } else {
+                        const float r = R[o];
+                        const float p = fmaf(beta, pd[o], m * r);
+                        s = fmaf(beta, S[o], Wv[o]);
+                        x[o] = fmaf(alpha, p, x[o]);
+                        pd[o] = p;
+                        r1 = fmaf(-alpha, s, r);
                     }
-                    if (h == 0)
-                        pn0 = pv;
-                    else
-                        pn1 = pv;
+                    rn[h] = r1;
+                    un[h] = m * r1;
+                    if (!last) {
+                        Rn[o] = r1;
+                        Sn[o] = s;
+                    }
                 }
-                const int j = n / nx, i = n - j * nx;
+            }
+            if (last) continue;
+            float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (live) {
+                const int j = n / nx, ii = n - j * nx;
 #pragma unroll
                 for (int ss = 0; ss < 3; ++ss) {
                     const int s = ss == 2 ? 8 : q4 + 4 * ss;
                     if (ss == 2 && q4 != 0) continue;
                     int owner, blk, pnode;
-                    if (!stencil_slot(s, i, j, nx, ny, n, owner, blk, pnode)) continue;
-                    float Bk[NB], pm[6];
+                    if (!stencil_slot(s, ii, j, nx, ny, n, owner, blk, pnode)) continue;
+                    float Bk[NB], u[6];
 #pragma unroll
                     for (int e = 0; e < NB; ++e) Bk[e] = node[(size_t)(blk * NB + e) * G + owner];
 #pragma unroll
-                    for (int u = 0; u < 6; ++u) {
-                        float v = z[u * G + pnode];
-                        if (!first) v = fmaf(beta, pprev[u * G + pnode], v);
-                        pm[u] = v;
+                    for (int c = 0; c < 6; ++c) {
+                        const int o = c * G + pnode;
+                        const float m = minv[o];
+                        u[c] = i < 0 ? m * rhs[o] : m * fmaf(-alpha, fmaf(beta, S[o], Wv[o]), R[o]);
                     }
-                    sym_matvec_acc(Bk, pm, q);
+                    sym_matvec_acc(Bk, u, q);
                 }
             }
 #pragma unroll
@@ -212,47 +212,41 @@ __device__ void pcg_cluster(const LevelGeom& g, const BLevel& B, int iters, floa
                 q[u] += __shfl_xor_sync(0xffffffffu, q[u], 2);
             }
             if (live) {
-                const float qa = sel6(q, c0);
-                qv[c0 * G + n] = qa;
-                acc = fmaf(pn0, qa, acc);
+                const float wa = sel6(q, c0);
+                Wn[c0 * G + n] = wa;
+                gp = fmaf(rn[0], un[0], gp);
+                dp = fmaf(wa, un[0], dp);
                 if (has1) {
-                    const float qb = sel6(q, c1);
-                    qv[c1 * G + n] = qb;
-                    acc = fmaf(pn1, qb, acc);
+                    const float wb = sel6(q, c1);
+                    Wn[c1 * G + n] = wb;
+                    gp = fmaf(rn[1], un[1], gp);
+                    dp = fmaf(wb, un[1], dp);
                 }
             }
         }
+        if (last) break;
+        ff red[2];
         {
-            const float v[1] = {acc};
-            cl_sum<1>(v, red, part, phase, sm, rank, T);
+            const float v[2] = {gp, dp};
+            cl_sum<2>(v, red, part, phase, sm, rank, T);
         }
-        const ff pq = red[0];
-        if (!(pq.hi > 1e-30f)) break;
-        const float alpha = rz.hi / pq.hi;
-        acc = 0.f;
-        for (int k = 0; k < nk; ++k) {
-            const int n = grp + k * stride;
-            if (n >= G) continue;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (h == 1 && !has1) continue;
-                const int c = h ? c1 : c0;
-                const int o = c * G + n;
-                x[o] = fmaf(alpha, pcur[o], x[o]);
-                const float rr = fmaf(-alpha, qv[o], r[o]);
-                const float zz = minv[o] * rr;
-                r[o] = rr;
-                z[o] = zz;
-                acc = fmaf(rr, zz, acc);
-            }
+        const ff G2 = red[0], D2 = red[1];
+        if (i < 0) {
+            if (!(G2.hi > 1e-30f) || !(D2.hi > 1e-30f)) break; // x stays 0
+            alpha = G2.hi / D2.hi;
+            beta = 0.f;
+        } else {
+            const float bnew = G2.hi / gam.hi;
+            const float pap = D2.hi - bnew * G2.hi / alpha;
+            if (!(G2.hi > 1e-30f) || !(pap > 1e-30f)) break;
+            beta = bnew;
+            alpha = G2.hi / pap;
         }
-        {
-            const float v[1] = {acc};
-            cl_sum<1>(v, red, part, phase, sm, rank, T);
-        }
-        beta = red[0].hi / rz.hi;
-        rz = red[0];
+        gam = G2;
     }
+    // the last update of x has no cluster sum behind it; the trials read x
+    // of every node
+    cluster_sync_all();
 }
 
 template <int MAXT>

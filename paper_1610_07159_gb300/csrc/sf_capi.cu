@@ -1225,15 +1225,12 @@ int sf_batch_create(int n, const int* widths, const int* heights, const int* lev
             B.node = lb.node;
             B.rhs = lb.rhs;
             B.minv = lb.minv;
-            B.z = lb.z;
-            B.p0 = lb.p0;
-            B.p1 = lb.p1;
+            B.p = lb.p0;
+            B.pub = lb.pub;
             B.cell = lb.cell;
             B.ctrl = c->ctrl + l * SF_MAX_GN;
             B.gn = c->prm.gn_iters[l];
             B.pcg = c->prm.pcg_iters[l];
-            const size_t G6 = (size_t)6 * c->geo[l].G;
-            ok = dalloc(c, &B.r, G6) && dalloc(c, &B.q, G6);
         }
     }
     // longest sequences first, so the last clusters to start are short ones

@@ -131,7 +131,7 @@ struct BLevel {
     float* H;          // halfway image [h][w]
     float *base, *delta, *x, *wf, *prev_delta, *prev_total; // [6][G] (wf: [G])
     float *node, *rhs, *minv;                               // [105][G], [6][G], [6][G]
-    float *r, *z, *p0, *p1, *q;                             // PCG vectors [6][G]
+    float *p, *pub;    // PCG direction [6][G]; r, w, s of both parities [2][3][6][G]
     float* cell;       // [234][ncells]
     StepCtrl* ctrl;    // [SF_MAX_GN]
     int gn, pcg;       // Gauss-Newton steps and PCG iterations of the level
