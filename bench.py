@@ -709,10 +709,15 @@ def run_ours(args):
         plain = sf.Solver(WIDTH, HEIGHT, STRIDE, LEVELS,
                           sf.preset(sf.PRESET_FIG2, **{**dict(gn_iters=[GN], pcg_iters=[PCG]), **extra}))
         out1 = torch.empty((6, 60, 80), device=dev, dtype=torch.float32)
+        if args.tune_pcg:
+            plain.tune_pcg(frames_d[0])  # the headline's per-level PCG schedules
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("frames")  # ncu --nvtx --nvtx-include "frames/" skips the set-up launches
         for k in range(args.warmup + args.steps):
             plain.solve(frames_d[k % NFRAMES], out1)
         torch.cuda.synchronize()
-        print(json.dumps({"arm": args.arm, "frames": args.warmup + args.steps}), flush=True)
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"arm": args.arm, "frames": args.warmup + args.steps, "tuned_pcg": args.tune_pcg}), flush=True)
         return
 
     # headline: the level-pipelined video solve, one step = one pass over the 30 frames. A second
@@ -1003,6 +1008,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the batched, mixed and warm-start variants")
+    ap.add_argument("--tune-pcg", action="store_true",
+                    help="frames arms: pick the per-level PCG schedules by timing first, as the headline does")
     ap.add_argument("--arm", choices=("all", "video", "frames", "frames_maps", "frames_schwarz", "batch8", "train"),
                     default="all",
                     help="for profiling runs: only the pipelined video arm, only the frame-by-frame arm (plain, with "

@@ -614,7 +614,13 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+// One-sided fences: fence.release before the relaxed tag stores makes them
+// release stores, a relaxed poll followed by fence.acquire an acquire read
+// (the PTX memory model's fence-based release and acquire patterns); cheaper
+// than two full fence.acq_rel.
+__device__ __forceinline__ void fence_release_gpu() { asm volatile("fence.release.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acquire.gpu;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned long long tag_word(unsigned tag, float v)
 {
@@ -651,7 +657,7 @@ __device__ __forceinline__ bool allreduce2_tagged(float a, float b, ff* sh, unsi
                 ta = ff_add(ta, sh[2 * w]);
                 tb = ff_add(tb, sh[2 * w + 1]);
             }
-            fence_acq_rel_gpu(); // the block's published vectors before its tag
+            fence_release_gpu(); // the block's published vectors before its tag
             unsigned long long* my = sl + (size_t)blockIdx.x * 4;
             st_relaxed_u64(my + 0, tag_word(tag, ta.hi));
             st_relaxed_u64(my + 1, tag_word(tag, ta.lo));
@@ -691,7 +697,7 @@ __device__ __forceinline__ bool allreduce2_tagged(float a, float b, ff* sh, unsi
                 }
             }
         }
-        fence_acq_rel_gpu(); // every block's published vectors after its tag
+        fence_acquire_gpu(); // every block's published vectors after its tag
         ff va{0.f, 0.f}, vb{0.f, 0.f};
 #pragma unroll
         for (int j = 0; j < TAG_MAXB / 32; ++j) {
