@@ -254,6 +254,13 @@ SF_API int sf_tune_pcg(sf_ctx* ctx, const float* L_t, const float* R_t, const fl
  * iteration), 3 grid / 4 cluster (one reduction), 2 distributed shared
  * memory; CTAs; nodes per four-lane group. */
 SF_API int sf_pcg_schedule(const sf_ctx* ctx, int level, int* kind, int* blocks, int* npt);
+/* Sets the PCG schedule of a level (kind, CTAs, nodes per group as
+ * sf_pcg_schedule reports them), for a schedule kept from an earlier tuning
+ * or picked by the caller's own measure. Only a schedule that sf_tune_pcg
+ * would consider for the level is taken; anything else returns SF_ERR_ARG
+ * and leaves the context unchanged. Waits for the device; the next solve
+ * captures the frame graph again. */
+SF_API int sf_set_pcg_schedule(sf_ctx* ctx, int level, int kind, int blocks, int npt);
 
 /* Device time of kernel class `klass` in the last frame: the sum over its
  * launches (ms) and their number. Needs the class in profile_mask; waits for

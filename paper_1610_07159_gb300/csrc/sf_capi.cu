@@ -1589,6 +1589,25 @@ int sf_tune_pcg(sf_ctx* c, const float* L_t, const float* R_t, const float* L_t1
     return rc ? fail(rc) : rc2;
 }
 
+int sf_set_pcg_schedule(sf_ctx* c, int level, int kind, int blocks, int npt)
+{
+    if (!c || level < 0 || level >= c->L) return fail(SF_ERR_ARG);
+    PcgPlan cand[16];
+    const int nc = pcg_candidates(c->geo[level].G, c->sm_count, cand, 16);
+    int k = 0;
+    while (k < nc && !(cand[k].cluster == kind && cand[k].blocks == blocks && cand[k].npt == npt)) ++k;
+    if (k == nc) return fail(SF_ERR_ARG);
+    if (check_cuda(cudaDeviceSynchronize())) return fail(SF_ERR_CUDA);
+    c->plan[level] = cand[k];
+    // a new block count starts its barrier counter from zero; the frame graph
+    // holds the old schedule: capture again on the next solve
+    if (check_cuda(cudaMemset(c->bar + level, 0, sizeof(unsigned long long)))) return fail(SF_ERR_CUDA);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->graph_tried = false;
+    return SF_OK;
+}
+
 int sf_pcg_schedule(const sf_ctx* c, int level, int* kind, int* blocks, int* npt)
 {
     if (!c || level < 0 || level >= c->L) return fail(SF_ERR_ARG);

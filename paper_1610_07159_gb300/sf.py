@@ -41,7 +41,7 @@ EXPORTED = (
     "sf_batch_get_schedule", "sf_batch_tune", "sf_batch_sequence", "sf_batch_reset", "sf_batch_destroy",
     "sf_probe_gemm_bf16", "sf_net_param_count", "sf_net_create", "sf_net_set_params", "sf_net_get_params",
     "sf_net_forward", "sf_net_gradients", "sf_net_train_step", "sf_net_status", "sf_net_destroy",
-    "sf_coarsest_images", "sf_warm_start", "sf_tune_pcg", "sf_pcg_schedule",
+    "sf_coarsest_images", "sf_warm_start", "sf_tune_pcg", "sf_pcg_schedule", "sf_set_pcg_schedule",
 )
 STATIC_PCG_MAX_NODES = 4096
 
@@ -162,6 +162,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sf_warm_start.argtypes = [vp, vp, fp, fp, fp, fp, vp]
     L.sf_tune_pcg.argtypes = [vp, fp, fp, fp, fp, i, vp]
     L.sf_pcg_schedule.argtypes = [vp, i, ip, ip, ip]
+    L.sf_set_pcg_schedule.argtypes = [vp, i, i, i, i]
     _lib = L
     return L
 
@@ -345,6 +346,11 @@ class Solver:
         _check(self.L.sf_pcg_schedule(self.ctx, int(level), ctypes.byref(k), ctypes.byref(b), ctypes.byref(t)),
                "sf_pcg_schedule")
         return k.value, b.value, t.value
+
+    def set_pcg_schedule(self, level: int, kind: int, blocks: int, npt: int) -> None:
+        """Sets a level's PCG schedule (as pcg_schedule reports it); SFError if the level cannot run it."""
+        _check(self.L.sf_set_pcg_schedule(self.ctx, int(level), int(kind), int(blocks), int(npt)),
+               "sf_set_pcg_schedule")
 
     def set_init(self, coarsest_delta: torch.Tensor) -> None:
         _check(self.L.sf_set_init(self.ctx, _ptr(coarsest_delta, torch.float32), _stream()), "sf_set_init")

@@ -136,6 +136,36 @@ def test_pcg_parity_grid_schedule_on_a_level_larger_than_a_cluster(mode, w, h):
     assert rel_max(x_gpu, x_ref) < 2e-4 * 20
 
 
+@pytest.mark.parametrize("kind,blocks,npt", [(3, 75, 1), (0, 75, 1), (3, 38, 2), (0, 38, 2), (3, 19, 4),
+                                             (0, 19, 4), (2, 15, 3)])
+def test_pcg_schedule_set_explicitly(kind, blocks, npt):
+    """sf_set_pcg_schedule takes any schedule the tuner would consider for a
+    level (here every one for the 4800 nodes of the 640x480 level 0: grid
+    forms of 1, 2 and 4 nodes per lane group, and one cluster of 15 CTAs with
+    the state in distributed shared memory), solves with it, and rejects the
+    rest without changing the level's schedule."""
+    solver, lv, op = _level_setup(640, 480, 8, 4, 0)
+    before = solver.pcg_schedule(0)
+    for bad in ((3, 74, 1), (5, 75, 1), (1, 75, 1)):
+        with pytest.raises(sf.SFError):
+            solver.set_pcg_schedule(0, *bad)
+        assert solver.pcg_schedule(0) == before
+    solver.set_pcg_schedule(0, kind, blocks, npt)
+    assert solver.pcg_schedule(0) == (kind, blocks, npt)
+    rng = np.random.default_rng(4)
+    base, delta = _smooth_state(lv.G, rng)
+    wf = np.ones(lv.G, dtype=np.float32)
+    blocks_, rhs, _, _ = solver.probe_assemble(0, _dev(base), _dev(delta), _dev(wf))
+    x_gpu = solver.probe_pcg(0, 20).cpu().numpy()
+    A = lib_blocks_to_oracle(blocks_.cpu().numpy().astype(np.float64), lv.nx, lv.ny)
+    x_ref, _, _ = O.pcg(lv.nx, lv.ny, A, rhs.cpu().numpy().astype(np.float64), 20)
+    assert rel_max(x_gpu, x_ref) < 2e-4 * 20
+    # a whole frame runs on the new schedule (the frame graph is captured again)
+    q = scenes.SceneVideo(640, 480, 1, seed=3).frames(1)[0]
+    solver.solve(_dev(q))
+    assert solver.stats().status == sf.OK
+
+
 def test_energy_parity_with_given_and_computed_W():
     solver, lv, op = _level_setup(160, 120, 4, 3, 0, w_epi=0.3)
     rng = np.random.default_rng(4)
