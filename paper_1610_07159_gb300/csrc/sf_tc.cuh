@@ -1,7 +1,7 @@
 // sf_tc.cuh -- Blackwell (sm_103a) tensor-core primitives written as inline
 // PTX: shared-memory matrix descriptors, the tcgen05 instruction descriptor
 // for BF16 x BF16 -> FP32, tensor-memory allocation, MMA issue and commit,
-// tensor-memory loads, and mbarrier waits with a time limit.
+// tensor-memory loads, TMA tile copies, and mbarrier waits with a time limit.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -28,6 +28,24 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
     d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Shared-memory matrix descriptor, K-major operand in the 128-byte swizzle
+// layout that a TMA tile copy with CU_TENSOR_MAP_SWIZZLE_128B writes: rows of
+// 128 bytes (64 BF16 along K), the 16-byte chunks of row r stored at chunk
+// index (chunk ^ (r & 7)), 8-row groups 1024 bytes apart (sbo). The tile must
+// start on a 1024-byte boundary; a K step inside the 128-byte row advances the
+// start address (the swizzle is applied to the address bits). The leading
+// byte offset is not used by this layout (field set to 1). Swizzle mode 2
+// (128-byte) in [61, 64), descriptor version 1 in [46, 48), base offset 0.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
     return d;
 }
 
@@ -83,6 +101,26 @@ __device__ __forceinline__ void mbar_init(uint32_t saddr, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr), "r"(count) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One arrival on the mbarrier that also expects `bytes` of asynchronous
+// copies (TMA) to complete on it before the phase can end.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t saddr, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr), "r"(bytes) : "memory");
+}
+
+// TMA: copies the box of a 2-D tensor map at coordinates (x, y) (x along the
+// contiguous dimension, in elements; x times the element size must be a
+// multiple of 16 bytes) into shared memory at dst, completing `box bytes` of
+// transactions on the mbarrier. Out-of-bound elements are filled with zeros.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t saddr, uint32_t parity)
