@@ -286,7 +286,11 @@ __device__ __forceinline__ void dsm_owner(int m, int rank, int n_lo, int npc, in
     }
 }
 
-template <int NPT>
+// ONE: the whole level in one CTA. Its own shared memory is then addressed
+// directly (no distributed-shared-memory window) and CTA barriers stand in for
+// the cluster barriers; the arithmetic and the order of every sum are those of
+// the cluster form.
+template <int NPT, bool ONE>
 __global__ void __launch_bounds__(CT, 1) k_pcg_dsm(LevelGeom g, int npc, const float* __restrict__ node,
                                                 const float* __restrict__ rhs, const float* __restrict__ minv_g,
                                                 float* __restrict__ xout, int iters, int interleaved)
@@ -297,8 +301,20 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_dsm(LevelGeom g, int npc, const f
     __shared__ float2 cpart[2][2]; // [parity][gamma, delta] of this CTA as float-float pairs
     cg::cluster_group cl = cg::this_cluster();
     const int G = g.G, nx = g.nx, ny = g.ny;
-    const int rank = (int)cl.block_rank();
-    const int C = (int)cl.num_blocks();
+    const int rank = ONE ? 0 : (int)cl.block_rank();
+    const int C = ONE ? 1 : (int)cl.num_blocks();
+    auto csync = [&]() {
+        if constexpr (ONE)
+            __syncthreads();
+        else
+            cl.sync();
+    };
+    auto peer = [&](auto* p, int r) {
+        if constexpr (ONE)
+            return p;
+        else
+            return cl.map_shared_rank(p, r);
+    };
     const int n_lo = rank * npc;
     const int n_own = min(npc, G - n_lo);
     const int q4 = threadIdx.x & 3;
@@ -337,7 +353,7 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_dsm(LevelGeom g, int npc, const f
             xr[k][h] = wr[k][h] = sr[k][h] = pr[k][h] = 0.f;
         }
     }
-    cl.sync();
+    csync();
 
     float alpha = 0.f, beta = 0.f;
     ff gam{0.f, 0.f};
@@ -389,11 +405,13 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_dsm(LevelGeom g, int npc, const f
                     if (ss == 2 && q4 != 0) continue;
                     int owner, blk, pn;
                     if (!stencil_slot(s, ii, jj, nx, ny, n, owner, blk, pn)) continue;
-                    int ro, lo, rp, lp;
-                    dsm_owner(owner, rank, n_lo, npc, ro, lo);
-                    dsm_owner(pn, rank, n_lo, npc, rp, lp);
-                    const float* ob = cl.map_shared_rank(sm, ro) + lo * NODE_F + blk * 24;
-                    const float* pb = cl.map_shared_rank(sm, rp) + lp * NODE_F;
+                    int ro = 0, lo = owner, rp = 0, lp = pn;
+                    if constexpr (!ONE) {
+                        dsm_owner(owner, rank, n_lo, npc, ro, lo);
+                        dsm_owner(pn, rank, n_lo, npc, rp, lp);
+                    }
+                    const float* ob = peer(sm, ro) + lo * NODE_F + blk * 24;
+                    const float* pb = peer(sm, rp) + lp * NODE_F;
                     float B[NB], mm[6], rv[6], wv[6], sv[6], u[6];
                     ld21(ob, B);
                     ld6(pb + NF_BLK, mm);
@@ -435,11 +453,11 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_dsm(LevelGeom g, int npc, const f
             cpart[slot][0] = make_float2(ga.hi, ga.lo);
             cpart[slot][1] = make_float2(de.hi, de.lo);
         }
-        cl.sync();
+        csync();
         // every CTA sums the CTAs' partials in rank order
         ff G2{0.f, 0.f}, D2{0.f, 0.f};
         for (int rk = 0; rk < C; ++rk) {
-            const float2* rp = &cl.map_shared_rank(&cpart[0][0], rk)[slot * 2];
+            const float2* rp = &peer(&cpart[0][0], rk)[slot * 2];
             const float2 a = rp[0], b = rp[1];
             G2 = ff_add(G2, ff{a.x, a.y});
             D2 = ff_add(D2, ff{b.x, b.y});
@@ -476,15 +494,22 @@ __global__ void __launch_bounds__(CT, 1) k_pcg_dsm(LevelGeom g, int npc, const f
                 xout[c * G + n] = xr[k][h];
         }
     }
-    cl.sync(); // no CTA leaves while others may still read its shared memory
+    csync(); // no CTA leaves while others may still read its shared memory
 }
 
 template <int NPT>
 cudaError_t launch_dsm(int ctas, int npc, const LevelGeom& g, const float* node, const float* rhs, const float* minv,
                        float* x, int iters, int interleaved, cudaStream_t st)
 {
-    auto kern = k_pcg_dsm<NPT>;
     const size_t smem = (size_t)npc * NODE_F * sizeof(float);
+    if (ctas == 1) {
+        auto one = k_pcg_dsm<NPT, true>;
+        cudaError_t e = cudaFuncSetAttribute(one, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        one<<<1, CT, smem, st>>>(g, npc, node, rhs, minv, x, iters, interleaved);
+        return cudaGetLastError();
+    }
+    auto kern = k_pcg_dsm<NPT, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (ctas > 8) {
