@@ -493,10 +493,10 @@ SF_API void sf_batch_destroy(sf_batch* b);
 
 /* ---- allocation-free PCG ------------------------------------------------
  * The paper has no counterpart to this call: it exists for callers that
- * cannot allocate device memory where they solve (inside a CUDA graph
- * capture, where cudaMalloc is not allowed; in real-time loops that must not
- * meet the allocator's implicit device synchronisation; under memory pools
- * that forbid raw allocations after start-up).
+ * cannot allocate device memory where they solve: real-time loops that must
+ * not meet the allocator's implicit device synchronisation, and host
+ * applications whose memory pool or fixed device budget forbids a library's
+ * raw allocations after start-up.
  *
  * Runs `iters` Jacobi-preconditioned CG iterations from x = 0 on a block
  * system in the layout sf_probe_assemble writes: blocks [G][5][6][6] (each

@@ -2,10 +2,9 @@
 // solve of a warp-grid block system without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they solve:
-// code running while a CUDA graph is being captured (cudaMalloc is not
-// allowed inside a capture), real-time loops that must not hit the
-// allocator's implicit device synchronisation, and hosts whose memory pool
-// forbids raw allocations after start-up. For them this entry point keeps its
+// real-time loops that must not hit the allocator's implicit device
+// synchronisation, and host applications whose memory pool or fixed device
+// budget forbids a library's raw allocations after start-up. For them this entry point keeps its
 // scratch in one file-scope __device__ array, fixed at build time:
 // SF_STATIC_PCG_MAX_NODES nodes (z and two p buffers, 18 floats per node,
 // 288 KiB, plus 32 reduction slots). Every GPU that loads the library holds

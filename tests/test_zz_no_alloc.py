@@ -1,10 +1,10 @@
 """sf_pcg_static, the PCG entry point that allocates nothing, against the
 context's PCG (sf_probe_pcg) and the FP64 oracle's PCG on the same systems.
 
-It serves callers that cannot allocate device memory where they solve: code
-inside a CUDA graph capture (cudaMalloc is not allowed there), real-time loops
-that must not meet the allocator's implicit device synchronisation, and hosts
-whose memory pool forbids raw allocations after start-up. Its scratch is a
+It serves callers that cannot allocate device memory where they solve:
+real-time loops that must not meet the allocator's implicit device
+synchronisation, and host applications whose memory pool or fixed device
+budget forbids a library's raw allocations after start-up. Its scratch is a
 fixed device array inside the library, shared by every call.
 
 This file sorts last, so a run that stops at the first failure has already
