@@ -84,16 +84,33 @@ enum { SF_TEMPORAL_PROPAGATE = 0, SF_TEMPORAL_COPY = 1, SF_TEMPORAL_ZERO = 2 };
 enum { SF_FP32 = 0, SF_MIXED_BF16 = 1, SF_MIXED_FP16 = 2 };
 /* Columns of Table 1 (Appendix A). */
 enum { SF_PRESET_FIG2 = 0, SF_PRESET_FIG568 = 1, SF_PRESET_FIG79 = 2 };
-/* Schedule of the PCG solve, per level the first that fits: SF_PCG_DSM (one
- * cluster, the whole state in distributed shared memory, one barrier per
- * iteration), then a single cluster with vectors in global memory, then a
- * cooperative launch over the GPU. SF_PCG_DSM starts at the first, the others
- * at the second; SF_PCG_GRID takes only the last. SF_PCG_CLUSTER and
- * SF_PCG_GRID run the textbook loop (two reductions and two barriers per
- * iteration); SF_PCG_AUTO and SF_PCG_ONE_REDUCTION run its Chronopoulos-Gear
- * form (the same iterates in exact arithmetic, one fused reduction and one
- * barrier per iteration). */
-enum { SF_PCG_AUTO = 0, SF_PCG_CLUSTER = 1, SF_PCG_GRID = 2, SF_PCG_DSM = 3, SF_PCG_ONE_REDUCTION = 4 };
+/* Schedule of the PCG solve, per level the first that fits: a staged grid
+ * (SF_PCG_AUTO and SF_PCG_PIPELINED only: a cooperative launch over the GPU
+ * whose coupling blocks fit in shared memory and whose neighbours' vectors
+ * are exchanged as self-tagged words, without memory fences; SF_PCG_AUTO runs
+ * the one-reduction form there, SF_PCG_PIPELINED the pipelined form of PCG of
+ * Ghysels and Vanroose 2014, which hides the grid reduction's latency behind
+ * the matrix-vector product but keeps w = A M r by recurrence, so its
+ * rounding drifts further from the textbook loop on ill-conditioned systems),
+ * SF_PCG_DSM (one cluster, the whole state in distributed shared memory, one
+ * barrier per iteration), then a single cluster with vectors in global
+ * memory, then a cooperative launch over the GPU. SF_PCG_AUTO and
+ * SF_PCG_PIPELINED start at the first and skip the second, SF_PCG_DSM starts
+ * at the second, SF_PCG_CLUSTER and SF_PCG_ONE_REDUCTION at the third;
+ * SF_PCG_GRID takes only the last. SF_PCG_CLUSTER and SF_PCG_GRID run the
+ * textbook loop (two reductions and two barriers per iteration); the other
+ * cluster and grid schedules its Chronopoulos-Gear form (one fused reduction
+ * and one barrier per iteration). All are the same iterates in exact
+ * arithmetic. sf_tune_pcg considers the pipelined form only under
+ * SF_PCG_PIPELINED. */
+enum {
+    SF_PCG_AUTO = 0,
+    SF_PCG_CLUSTER = 1,
+    SF_PCG_GRID = 2,
+    SF_PCG_DSM = 3,
+    SF_PCG_ONE_REDUCTION = 4,
+    SF_PCG_PIPELINED = 5
+};
 /* Linear solver of each Gauss-Newton step. SF_SOLVER_PCG: Jacobi-PCG on the
  * whole level (Section 5.1), pcg_iters iterations. SF_SOLVER_SCHWARZ: the
  * domain decomposition of Section 5.2, data-parallel alternating Schwarz
@@ -135,7 +152,7 @@ typedef struct sf_params {
     int max_backtracks;           /* step halvings tried before a step is rejected (4) */
     int use_graph;                /* 1: replay the frame as one captured CUDA graph */
     int profile_mask;             /* bit k set: time every launch of kernel class k with CUDA events */
-    int pcg_mode;                 /* SF_PCG_AUTO | _CLUSTER | _GRID | _DSM | _ONE_REDUCTION */
+    int pcg_mode;                 /* SF_PCG_AUTO | _CLUSTER | _GRID | _DSM | _ONE_REDUCTION | _PIPELINED */
     int video;                    /* 1: allocate the level pipeline of sf_solve_video */
     int record_cells;             /* 1: record the bilinear cell decisions at cell edges (sf_probe_cells) */
     int solver;                   /* SF_SOLVER_PCG | SF_SOLVER_SCHWARZ */
@@ -251,8 +268,11 @@ SF_API int sf_get_state(sf_ctx* ctx, int level, float* delta, float* total, void
 SF_API int sf_tune_pcg(sf_ctx* ctx, const float* L_t, const float* R_t, const float* L_t1, const float* R_t1, int reps,
                        void* stream);
 /* The PCG schedule of a level: kind 0 grid / 1 cluster (two reductions per
- * iteration), 3 grid / 4 cluster (one reduction), 2 distributed shared
- * memory; CTAs; nodes per four-lane group. */
+ * iteration), 3 grid / 4 cluster (one reduction), 5 grid (one reduction,
+ * coupling blocks staged in shared memory, published vectors as self-tagged
+ * 64-bit words: no memory fences in the exchange), 6 grid (pipelined, staged
+ * and self-tagged like 5), 2 distributed shared memory; CTAs; nodes per
+ * four-lane group. */
 SF_API int sf_pcg_schedule(const sf_ctx* ctx, int level, int* kind, int* blocks, int* npt);
 /* Sets the PCG schedule of a level (kind, CTAs, nodes per group as
  * sf_pcg_schedule reports them), for a schedule kept from an earlier tuning

@@ -31,7 +31,7 @@ struct LevelBuf {
     float *prev_delta = nullptr, *prev_total = nullptr;
     float *node = nullptr, *rhs = nullptr, *minv = nullptr;
     float *z = nullptr, *p0 = nullptr, *p1 = nullptr;
-    float* pub = nullptr; // one-reduction PCG: [2][r, w, s][6][G]
+    float* pub = nullptr; // one-reduction PCG: [2][r, w, s][6][G] floats, or as many 64-bit tagged words
     float* cell = nullptr;
     uint2* cellrec = nullptr;  // [gn][cellcap] cell decisions at cell edges (record_cells)
     unsigned* celln = nullptr; // [gn] records per step
@@ -618,7 +618,7 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
         p->max_backtracks < 0 || p->max_backtracks > 8 || p->robust_mode < 0 || p->robust_mode > 1 ||
         p->grad_mode < 0 || p->grad_mode > 1 || p->wfeat_mode < 0 || p->wfeat_mode > 1 || p->temporal_mode < 0 ||
         p->temporal_mode > 2 || p->precision < SF_FP32 || p->precision > SF_MIXED_FP16 || !(p->wfeat_tau > 0.f) ||
-        p->pcg_mode < 0 || p->pcg_mode > SF_PCG_ONE_REDUCTION || p->solver < SF_SOLVER_PCG ||
+        p->pcg_mode < 0 || p->pcg_mode > SF_PCG_PIPELINED || p->solver < SF_SOLVER_PCG ||
         p->solver > SF_SOLVER_SCHWARZ || (p->solver == SF_SOLVER_SCHWARZ && (p->schwarz_tile < 1 ||
                                                                                p->schwarz_overlap < 0)) ||
         p->occlusion < 0 || p->occlusion > 1 || !(p->occ_tau >= 0.f) || p->illumination < 0 ||
@@ -678,7 +678,7 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
     }
     for (int l = 0; l < levels; ++l) {
         c->trial_blocks[l] = trials_blocks(c->geo[l], p->precision, c->sm_count);
-        c->plan[l] = pcg_plan(c->geo[l].G, c->sm_count, p->pcg_mode);
+        c->plan[l] = pcg_plan(c->geo[l].G, c->sm_count, p->pcg_mode, c->geo[l].nx);
         // a level needs the plan of the solver it runs (the global PCG has a size limit, Schwarz does not)
         if ((p->solver == SF_SOLVER_PCG && c->plan[l].blocks < 1) ||
             (p->solver == SF_SOLVER_SCHWARZ &&
@@ -697,7 +697,7 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
              dalloc(c, &b.delta, G6) && dalloc(c, &b.x, G6) && dalloc(c, &b.wf, (size_t)g.G) &&
              dalloc(c, &b.prev_delta, G6) && dalloc(c, &b.prev_total, G6) &&
              dalloc(c, &b.node, (size_t)NODE_VALS * g.G) && dalloc(c, &b.rhs, G6) && dalloc(c, &b.minv, G6) &&
-             dalloc(c, &b.z, G6) && dalloc(c, &b.p0, G6) && dalloc(c, &b.p1, G6) && dalloc(c, &b.pub, 6 * G6) &&
+             dalloc(c, &b.z, G6) && dalloc(c, &b.p0, G6) && dalloc(c, &b.p1, G6) && dalloc(c, &b.pub, 12 * G6) &&
              dalloc(c, &b.cell, (size_t)CELL_VALS * (g.ncx * g.ncy));
         if (ok && (p->occlusion || p->illumination)) {
             const int nbuf = p->video ? 2 : 1;
@@ -1535,8 +1535,9 @@ int sf_tune_pcg(sf_ctx* c, const float* L_t, const float* R_t, const float* L_t1
         LevelBuf& b = c->lv[l];
         const int iters = c->prm.pcg_iters[l];
         if (iters < 1 || c->prm.solver == SF_SOLVER_SCHWARZ) continue;
+        const bool pipelined = c->prm.pcg_mode == SF_PCG_PIPELINED;
         const std::string key = std::to_string(g.nx) + "x" + std::to_string(g.ny) + "|" + std::to_string(iters) + "|" +
-                                std::to_string(c->sm_count);
+                                std::to_string(c->sm_count) + (pipelined ? "|p" : "");
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             auto it = g_pcg_tune.find(key);
@@ -1545,8 +1546,8 @@ int sf_tune_pcg(sf_ctx* c, const float* L_t, const float* R_t, const float* L_t1
                 continue;
             }
         }
-        PcgPlan cand[16];
-        const int nc = pcg_candidates(g.G, c->sm_count, cand, 16);
+        PcgPlan cand[24];
+        const int nc = pcg_candidates(g.G, c->sm_count, cand, 24, g.nx, pipelined);
         float best = -1.f;
         PcgPlan pick = c->plan[l];
         for (int k = 0; k < nc && !rc; ++k) {
@@ -1592,8 +1593,8 @@ int sf_tune_pcg(sf_ctx* c, const float* L_t, const float* R_t, const float* L_t1
 int sf_set_pcg_schedule(sf_ctx* c, int level, int kind, int blocks, int npt)
 {
     if (!c || level < 0 || level >= c->L) return fail(SF_ERR_ARG);
-    PcgPlan cand[16];
-    const int nc = pcg_candidates(c->geo[level].G, c->sm_count, cand, 16);
+    PcgPlan cand[24];
+    const int nc = pcg_candidates(c->geo[level].G, c->sm_count, cand, 24, c->geo[level].nx, true);
     int k = 0;
     while (k < nc && !(cand[k].cluster == kind && cand[k].blocks == blocks && cand[k].npt == npt)) ++k;
     if (k == nc) return fail(SF_ERR_ARG);

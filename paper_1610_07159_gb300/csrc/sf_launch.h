@@ -69,12 +69,16 @@ struct PcgPlan {
     int npt;     // nodes per four-lane group
     int cluster; // 2: one cluster, state in distributed shared memory;
                  // 1: one cluster, vectors in global memory; 0: cooperative grid;
-                 // 3 / 4: grid / one cluster with one reduction per iteration
+                 // 3 / 4: grid / one cluster with one reduction per iteration;
+                 // 5: grid, one reduction, self-tagged published vectors;
+                 // 6: grid, pipelined (reduction behind the product)
     int npc;     // nodes per CTA (cluster == 2)
 };
-PcgPlan pcg_plan(int G, int sm_count, int mode);
+PcgPlan pcg_plan(int G, int sm_count, int mode, int nx);
 // every schedule that can run a level of G nodes (for the autotuner)
-int pcg_candidates(int G, int sm_count, PcgPlan* out, int max);
+// (nx > 0: also the kind-5 plans, and with `pipelined` the kind-6 plans,
+// whose shared memory fits the level's rows of nx nodes)
+int pcg_candidates(int G, int sm_count, PcgPlan* out, int max, int nx, bool pipelined);
 cudaError_t launch_pcg(const LevelGeom& g, const PcgPlan& plan, const float* node, const float* rhs,
                        const float* minv, float* x, float* z, float* p0, float* p1, float* pub, float2* part,
                        unsigned long long* bar, int* status, int iters, int interleaved_out, cudaStream_t st);

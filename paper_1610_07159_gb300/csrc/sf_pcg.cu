@@ -660,19 +660,89 @@ __device__ __forceinline__ void tagged_clear(unsigned long long* slots)
     }
 }
 
+// Warp 0's half of a tagged reduction: polls the four words of every block
+// in slot sl until each carries `tag` (lane l takes blocks l, l + 32, ...),
+// then folds them in the order of ff_fixed_sum, so that every block forms the
+// same bit-identical sums. Gives up like grid_barrier (status word every 64
+// polls, ~1 s); returns 0 then. ok = 0 on entry skips the poll.
+template <bool kFence>
+__device__ __forceinline__ int warp_poll_fold(const unsigned long long* sl, int nb, unsigned tag, int* status,
+                                              int lane, int ok, ff& va, ff& vb)
+{
+    unsigned long long v[TAG_MAXB / 32][4];
+    const long long t0 = clock64();
+    for (unsigned k = 0; ok; ++k) {
+        bool ready = true;
+#pragma unroll
+        for (int j = 0; j < TAG_MAXB / 32; ++j) {
+            const int blk = lane + 32 * j;
+            if (blk < nb) {
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    v[j][w] = ld_relaxed_u64(sl + (size_t)blk * 4 + w);
+                    ready = ready && (unsigned)(v[j][w] >> 32) == tag;
+                }
+            }
+        }
+        if (__all_sync(0xffffffffu, ready)) break;
+        if (((k + 1) & 63u) == 0u) {
+            bool fail = false;
+            if (lane == 0) {
+                if (ld_acquire_s32(status) != 0) {
+                    fail = true;
+                } else if (clock64() - t0 > 2000000000LL) {
+                    atomicOr(status, DEV_TIMEOUT);
+                    fail = true;
+                }
+            }
+            if (__any_sync(0xffffffffu, fail)) {
+                ok = 0;
+                break;
+            }
+        }
+    }
+    if (kFence) fence_acquire_gpu(); // every block's published vectors after its tag
+    va = ff{0.f, 0.f};
+    vb = ff{0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < TAG_MAXB / 32; ++j) {
+        if (ok && lane + 32 * j < nb) {
+            va = ff_add(va, ff{__uint_as_float((unsigned)v[j][0]), __uint_as_float((unsigned)v[j][1])});
+            vb = ff_add(vb, ff{__uint_as_float((unsigned)v[j][2]), __uint_as_float((unsigned)v[j][3])});
+        }
+    }
+    va = ff_warp_sum(va);
+    vb = ff_warp_sum(vb);
+    return ok;
+}
+
+struct NoSide {
+    __device__ __forceinline__ bool operator()() const { return true; }
+};
+
+// kFence = false serves kernels whose published vectors carry their own tags
+// (k_pcg1h): the partial words then order nothing but themselves. A thread
+// passes fail = true when it gave up on a wait of its own; the block then
+// publishes its partials and returns false without polling. While warp 0
+// polls, warps 1.. run side() (k_pcg1h fetches its next halo there); a false
+// from it makes the reduction return false too.
+template <bool kFence = true, class Side = NoSide>
 __device__ __forceinline__ bool allreduce2_tagged(float a, float b, ff* sh, unsigned long long* slots, unsigned tag,
-                                                  int* status, ff& ra, ff& rb)
+                                                  int* status, ff& ra, ff& rb, bool fail = false,
+                                                  Side side = Side{})
 {
     __shared__ ff bc[2];
-    __shared__ int ok_sh;
+    __shared__ int ok_sh, fail_sh, side_fail_sh;
     const int nb = gridDim.x;
     unsigned long long* sl = slots + (size_t)(tag & 1u) * 4 * nb;
     const float wa = warp_sum(a), wb = warp_sum(b);
+    if (!kFence && threadIdx.x == 0) fail_sh = side_fail_sh = 0;
     __syncthreads();
     if ((threadIdx.x & 31) == 0) {
         sh[2 * (threadIdx.x >> 5)] = ff_from(wa);
         sh[2 * (threadIdx.x >> 5) + 1] = ff_from(wb);
     }
+    if (!kFence && fail) fail_sh = 1;
     __syncthreads();
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
@@ -682,67 +752,28 @@ __device__ __forceinline__ bool allreduce2_tagged(float a, float b, ff* sh, unsi
                 ta = ff_add(ta, sh[2 * w]);
                 tb = ff_add(tb, sh[2 * w + 1]);
             }
-            fence_release_gpu(); // the block's published vectors before its tag
+            if (kFence) fence_release_gpu(); // the block's published vectors before its tag
             unsigned long long* my = sl + (size_t)blockIdx.x * 4;
             st_relaxed_u64(my + 0, tag_word(tag, ta.hi));
             st_relaxed_u64(my + 1, tag_word(tag, ta.lo));
             st_relaxed_u64(my + 2, tag_word(tag, tb.hi));
             st_relaxed_u64(my + 3, tag_word(tag, tb.lo));
         }
-        unsigned long long v[TAG_MAXB / 32][4];
-        int ok = 1;
-        const long long t0 = clock64();
-        for (unsigned k = 0;; ++k) {
-            bool ready = true;
-#pragma unroll
-            for (int j = 0; j < TAG_MAXB / 32; ++j) {
-                const int blk = lane + 32 * j;
-                if (blk < nb) {
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) {
-                        v[j][w] = ld_relaxed_u64(sl + (size_t)blk * 4 + w);
-                        ready = ready && (unsigned)(v[j][w] >> 32) == tag;
-                    }
-                }
-            }
-            if (__all_sync(0xffffffffu, ready)) break;
-            if (((k + 1) & 63u) == 0u) {
-                bool fail = false;
-                if (lane == 0) {
-                    if (ld_acquire_s32(status) != 0) {
-                        fail = true;
-                    } else if (clock64() - t0 > 2000000000LL) {
-                        atomicOr(status, DEV_TIMEOUT);
-                        fail = true;
-                    }
-                }
-                if (__any_sync(0xffffffffu, fail)) {
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        fence_acquire_gpu(); // every block's published vectors after its tag
-        ff va{0.f, 0.f}, vb{0.f, 0.f};
-#pragma unroll
-        for (int j = 0; j < TAG_MAXB / 32; ++j) {
-            if (lane + 32 * j < nb) {
-                va = ff_add(va, ff{__uint_as_float((unsigned)v[j][0]), __uint_as_float((unsigned)v[j][1])});
-                vb = ff_add(vb, ff{__uint_as_float((unsigned)v[j][2]), __uint_as_float((unsigned)v[j][3])});
-            }
-        }
-        va = ff_warp_sum(va);
-        vb = ff_warp_sum(vb);
+        ff va, vb;
+        int ok = (kFence || !fail_sh) ? 1 : 0;
+        ok = warp_poll_fold<kFence>(sl, nb, tag, status, lane, ok, va, vb);
         if (lane == 0) {
             bc[0] = va;
             bc[1] = vb;
             ok_sh = ok;
         }
+    } else if (!kFence && !fail_sh) {
+        if (!side()) side_fail_sh = 1;
     }
     __syncthreads();
     ra = bc[0];
     rb = bc[1];
-    return ok_sh != 0;
+    return ok_sh != 0 && (kFence || side_fail_sh == 0);
 }
 
 template <int NPT, class Sync>
@@ -944,6 +975,771 @@ cudaError_t launch_cluster1(int blocks, const LevelGeom& g, const float* node, c
                               ClusterSync{});
 }
 
+// ---------------------------------------------------------------------------
+// The one-reduction grid PCG with self-validating published vectors and its
+// operands in shared memory (plan kind 5). The same iterates as k_pcg1, bit
+// for bit: the arithmetic is the same, only where the operands come from and
+// how the blocks exchange them differ.
+//
+// Self-tagged words. Every published value of r, w and s is one 64-bit word,
+// (tag << 32) | value bits, written with a single relaxed store, so each value
+// carries its own proof of freshness: a reader checks the tag of every word
+// and reads again while a word is stale. Nothing has to order the vectors
+// before the partial sums, so the exchange needs no memory fence.
+//
+// Shared memory. A block owns NPT segments of NPB consecutive nodes (segment
+// k starts at n0_k); the stencil of its nodes reaches hw = nx + 1 nodes to
+// either side. At the start the block copies the coupling blocks of its nodes
+// and of the hw nodes before each segment (they do not change during the
+// solve) into shared memory, coalesced, so the matrix-vector product reads no
+// global memory. Per iteration it forms u = M (r - alpha (w + beta s)) once
+// per node of [n0_k - hw, n0_k + NPB + hw) in shared memory: owned nodes from
+// the owners' registers (the same rounding), the 2 hw nodes on either side
+// from their published words, read coalesced. While warp 0 polls the other
+// blocks' partial sums, warps 1.. fetch the next iteration's halo words and
+// wait until they carry the expected tag, so the halo's L2 round trip and the
+// wait for late neighbours overlap the poll; entries beyond their share are
+// read by the whole block after the poll.
+//
+// Tags: r_0 and s_{-1} (written before the launch's one full barrier) and
+// the set-up pass's w_0 carry tag 1 in buffer 0; iteration i >= 0 reads
+// buffer i & 1 expecting tag i + 1 and publishes r_{i+1}, s_i and w_{i+1}
+// into buffer (i + 1) & 1 with tag i + 2. Before the barrier each node clears
+// (tag 0) the words that a reader checks before this launch rewrites them:
+// buffer 0's w and all of buffer 1. So no word left by an earlier launch, or
+// by another kernel sharing the buffer, can pass a check. A word of tag i + 1
+// is overwritten (with tag i + 3) only by an owner that has seen every
+// block's partial sums of iteration i, which each block forms after reading
+// the values of iteration i: a reader never loses a value it still needs.
+// pubw holds [2 parities][r, w, s][6][G] words; the dynamic shared memory
+// [NPT][NODE_VALS][ls] floats of blocks (ls >= NPB + hw, padded so that the
+// four block rows a warp reads at once fall in different banks), then
+// [NPT][6][NPB + 2 hw] floats of u.
+// ---------------------------------------------------------------------------
+constexpr int HPF = 5;       // halo entries per thread and round
+constexpr int HFT = PT - 32; // threads that fetch the halo during the poll (warps 1..)
+
+__device__ __forceinline__ unsigned word_tag(unsigned long long w) { return (unsigned)(w >> 32); }
+
+__device__ __forceinline__ float word_val(unsigned long long w) { return __uint_as_float((unsigned)w); }
+
+__device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long* p) { return __ldcg(p); }
+
+struct Halo {
+    int G, hw, hn, items; // nodes, nodes on each side (nx + 1), u span (NPB + 2 hw), entries NPT * 12 hw
+};
+
+// Entry f of the halo (segment, component, side, offset): the word offset
+// c * G + m of node m, component c, and its index in the u array; -1 if f
+// lies outside the halo or the level.
+template <int NPT>
+__device__ __forceinline__ int halo_entry(const Halo& h, int f, int stride, int& si)
+{
+    if (f >= h.items) return -1;
+    const int per_k = 12 * h.hw;
+    const int k = f / per_k;
+    const int rem = f - k * per_k;
+    const int c = rem / (2 * h.hw);
+    const int r2 = rem - c * 2 * h.hw;
+    const int off = r2 < h.hw ? r2 : r2 + NPB; // left side, or right of the owned segment
+    const int m = blockIdx.x * NPB + k * stride - h.hw + off;
+    if (m < 0 || m >= h.G) return -1;
+    si = (k * 6 + c) * h.hn + off;
+    return c * h.G + m;
+}
+
+// Entries f0 + j * step of the halo (indices only).
+template <int NPT>
+__device__ __forceinline__ void halo_index(const Halo& h, int f0, int step, int stride, int (&gi)[HPF],
+                                           int (&si)[HPF])
+{
+#pragma unroll
+    for (int j = 0; j < HPF; ++j) gi[j] = halo_entry<NPT>(h, f0 + j * step, stride, si[j]);
+}
+
+// Issues the loads of a round's entries (plain L2 loads, which the compiler
+// may batch); SETUP reads one word per entry (r, or w in k_pcg1p), else r, w, s.
+template <bool SETUP>
+__device__ __forceinline__ void halo_load(const unsigned long long* R, size_t G6, const int (&gi)[HPF],
+                                          unsigned long long (&v)[HPF][3])
+{
+#pragma unroll
+    for (int j = 0; j < HPF; ++j) {
+        if (gi[j] >= 0) {
+            v[j][0] = ld_cg_u64(R + gi[j]);
+            if (!SETUP) {
+                v[j][1] = ld_cg_u64(R + G6 + gi[j]);
+                v[j][2] = ld_cg_u64(R + 2 * G6 + gi[j]);
+            }
+        }
+    }
+}
+
+template <int NPT, bool SETUP>
+__device__ __forceinline__ void halo_issue(const Halo& h, const unsigned long long* R, size_t G6, int f0, int step,
+                                           int stride, int (&gi)[HPF], int (&si)[HPF],
+                                           unsigned long long (&v)[HPF][3])
+{
+    halo_index<NPT>(h, f0, step, stride, gi, si);
+    halo_load<SETUP>(R, G6, gi, v);
+}
+
+// Reads the stale words of a round again, all together (relaxed loads),
+// until every word carries `tag`; gives up like the tagged poll (status word
+// every 64 passes, ~1 s). False on giving up.
+template <bool SETUP>
+__device__ __forceinline__ bool halo_wait(const unsigned long long* R, size_t G6, unsigned tag, int* status,
+                                          const int (&gi)[HPF], unsigned long long (&v)[HPF][3])
+{
+    auto fresh = [&](int j) {
+        return word_tag(v[j][0]) == tag && (SETUP || (word_tag(v[j][1]) == tag && word_tag(v[j][2]) == tag));
+    };
+    unsigned stale = 0;
+#pragma unroll
+    for (int j = 0; j < HPF; ++j)
+        if (gi[j] >= 0 && !fresh(j)) stale |= 1u << j;
+    long long t0 = 0;
+    for (unsigned k = 0; stale != 0u; ++k) {
+        if (k == 0) t0 = clock64();
+#pragma unroll
+        for (int j = 0; j < HPF; ++j)
+            if ((stale >> j) & 1u) {
+                v[j][0] = ld_relaxed_u64(R + gi[j]);
+                if (!SETUP) {
+                    v[j][1] = ld_relaxed_u64(R + G6 + gi[j]);
+                    v[j][2] = ld_relaxed_u64(R + 2 * G6 + gi[j]);
+                }
+            }
+        unsigned left = 0;
+#pragma unroll
+        for (int j = 0; j < HPF; ++j)
+            if (((stale >> j) & 1u) && !fresh(j)) left |= 1u << j;
+        stale = left;
+        if (stale != 0u && ((k + 1) & 63u) == 0u) {
+            if (ld_acquire_s32(status) != 0) return false;
+            if (clock64() - t0 > 2000000000LL) {
+                atomicOr(status, DEV_TIMEOUT);
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+// u of every entry of a round, into the u array.
+template <bool SETUP>
+__device__ __forceinline__ void halo_u(const float* __restrict__ minv, float alpha, float beta, float* uh,
+                                       const int (&gi)[HPF], const int (&si)[HPF],
+                                       const unsigned long long (&v)[HPF][3])
+{
+#pragma unroll
+    for (int j = 0; j < HPF; ++j) {
+        if (gi[j] < 0) continue;
+        const float mm = __ldg(minv + gi[j]);
+        uh[si[j]] = SETUP ? mm * word_val(v[j][0])
+                          : mm * fmaf(-alpha, fmaf(beta, word_val(v[j][2]), word_val(v[j][1])), word_val(v[j][0]));
+    }
+}
+
+template <int NPT>
+__global__ void __launch_bounds__(PT, 1) k_pcg1h(LevelGeom g, const float* __restrict__ node,
+                                                 const float* __restrict__ rhs, const float* __restrict__ minv,
+                                                 float* __restrict__ xout, unsigned long long* pubw, float2* part,
+                                                 unsigned long long* bar, int* status, int iters, int interleaved,
+                                                 int ls)
+{
+    extern __shared__ float smem_h[];
+    __shared__ ff sred[2 * (PT / 32)];
+    GridSync sy{0ull};
+    sy.start(bar);
+    const int G = g.G, nx = g.nx, ny = g.ny;
+    const size_t G6 = (size_t)6 * G;
+    const int q4 = threadIdx.x & 3;
+    const int c0 = q4, c1 = q4 + 4;
+    const bool has1 = c1 < 6;
+    const int stride = gridDim.x * NPB;
+    const int slot0 = blockIdx.x * NPB + (threadIdx.x >> 2);
+    Halo hl;
+    hl.G = G;
+    hl.hw = nx + 1;
+    hl.hn = NPB + 2 * hl.hw;
+    hl.items = NPT * 12 * hl.hw;
+    float* sB = smem_h;                             // [NPT][NODE_VALS][ls]
+    float* uh = smem_h + (size_t)NPT * NODE_VALS * ls; // [NPT][6][hn]
+    float xr[NPT][2], rr[NPT][2], ur[NPT][2], wr[NPT][2], sr[NPT][2], pr[NPT][2], mr[NPT][2];
+    int ni[NPT], nj[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int n = slot0 + k * stride;
+        nj[k] = n / nx;
+        ni[k] = n - nj[k] * nx;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = h ? c1 : c0;
+            const bool live = n < G && (h == 0 || has1);
+            const float r0 = live ? rhs[c * G + n] : 0.f;
+            mr[k][h] = live ? minv[c * G + n] : 0.f;
+            rr[k][h] = r0;
+            ur[k][h] = mr[k][h] * r0;
+            xr[k][h] = wr[k][h] = sr[k][h] = pr[k][h] = 0.f;
+            if (live) {
+                const size_t o = (size_t)c * G + n;
+                pubw[0 * G6 + o] = tag_word(1u, r0);  // r_0, buffer 0
+                pubw[1 * G6 + o] = 0ull;              // buffer 0's w: cleared
+                pubw[2 * G6 + o] = tag_word(1u, 0.f); // s_{-1} = 0
+                pubw[3 * G6 + o] = 0ull;              // buffer 1: cleared
+                pubw[4 * G6 + o] = 0ull;
+                pubw[5 * G6 + o] = 0ull;
+            }
+        }
+    }
+    // the coupling blocks of the segments' nodes and of the hw nodes before them
+    {
+        const int span = hl.hw + NPB;
+#pragma unroll 1
+        for (int k = 0; k < NPT; ++k) {
+            const int mlo = blockIdx.x * NPB + k * stride - hl.hw;
+            float* dst = sB + (size_t)k * NODE_VALS * ls;
+#pragma unroll 4
+            for (int idx = threadIdx.x; idx < NODE_VALS * span; idx += PT) {
+                const int row = idx / span;
+                const int l = idx - row * span;
+                const int m = mlo + l;
+                dst[row * ls + l] = (m >= 0 && m < G) ? __ldg(node + (size_t)row * G + m) : 0.f;
+            }
+        }
+    }
+    unsigned long long* slots = reinterpret_cast<unsigned long long*>(part);
+    tagged_clear(slots);
+    bool ok = sy.sync(bar, status); // the launch's one full barrier: clears, r_0 and the staged blocks
+    float alpha = 0.f, beta = 0.f;
+    ff gam{0.f, 0.f};
+    int nred = 0;
+    int gi[HPF], si[HPF], gf[HPF], sf[HPF];
+    unsigned long long hv[HPF][3];
+    const int fetcher = (int)threadIdx.x - 32; // warps 1.. fetch the first HFT * HPF entries
+    if (fetcher >= 0) {
+        halo_index<NPT>(hl, fetcher, HFT, stride, gf, sf); // the same entries every iteration
+        halo_load<true>(pubw, G6, gf, hv);
+        ok = halo_wait<true>(pubw, G6, 1u, status, gf, hv) && ok; // r_0 is there since the barrier
+    }
+    ok = __syncthreads_and(ok);
+    for (int i = -1; i < iters && ok; ++i) {
+        const int par = i < 0 ? 0 : (i & 1);
+        const int npar = i < 0 ? 0 : (par ^ 1);
+        const unsigned rtag = i < 0 ? 1u : (unsigned)i + 1u;
+        const unsigned wtag = i < 0 ? 1u : (unsigned)i + 2u;
+        const unsigned long long* R = pubw + (size_t)par * 3 * G6;
+        unsigned long long* Rn = pubw + (size_t)npar * 3 * G6;
+        if (i >= 0) {
+#pragma unroll
+            for (int k = 0; k < NPT; ++k)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    pr[k][h] = fmaf(beta, pr[k][h], ur[k][h]);
+                    sr[k][h] = fmaf(beta, sr[k][h], wr[k][h]);
+                    xr[k][h] = fmaf(alpha, pr[k][h], xr[k][h]);
+                    rr[k][h] = fmaf(-alpha, sr[k][h], rr[k][h]);
+                    ur[k][h] = mr[k][h] * rr[k][h];
+                }
+            if (i == iters - 1) break;
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int n = slot0 + k * stride;
+                if (n >= G) continue;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (!(h == 0 || has1)) continue;
+                    const size_t o = (size_t)(h ? c1 : c0) * G + n;
+                    st_relaxed_u64(Rn + o, tag_word(wtag, rr[k][h]));
+                    st_relaxed_u64(Rn + 2 * G6 + o, tag_word(wtag, sr[k][h]));
+                }
+            }
+        }
+        // u of the owned nodes from registers, of the halo from the fetched words
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            const int n = slot0 + k * stride;
+            if (n >= G) continue;
+            const int own = (k * 6) * hl.hn + hl.hw + (n - (blockIdx.x * NPB + k * stride));
+            uh[own + c0 * hl.hn] = ur[k][0];
+            if (has1) uh[own + c1 * hl.hn] = ur[k][1];
+        }
+        bool fail = false;
+        if (fetcher >= 0) {
+            if (i < 0)
+                halo_u<true>(minv, alpha, beta, uh, gf, sf, hv);
+            else
+                halo_u<false>(minv, alpha, beta, uh, gf, sf, hv);
+        }
+        for (int base = HFT * HPF; base < hl.items; base += PT * HPF) {
+            if (i < 0) {
+                halo_issue<NPT, true>(hl, R, G6, base + (int)threadIdx.x, PT, stride, gi, si, hv);
+                fail = !halo_wait<true>(R, G6, rtag, status, gi, hv) || fail;
+                halo_u<true>(minv, alpha, beta, uh, gi, si, hv);
+            } else {
+                halo_issue<NPT, false>(hl, R, G6, base + (int)threadIdx.x, PT, stride, gi, si, hv);
+                fail = !halo_wait<false>(R, G6, rtag, status, gi, hv) || fail;
+                halo_u<false>(minv, alpha, beta, uh, gi, si, hv);
+            }
+        }
+        __syncthreads();
+        float gp = 0.f, dp = 0.f;
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            const int n = slot0 + k * stride;
+            const bool live = n < G;
+            const int n0 = blockIdx.x * NPB + k * stride;
+            const int ubase = (k * 6) * hl.hn + hl.hw - n0;
+            float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (live) {
+                const int ii = ni[k], jj = nj[k];
+#pragma unroll
+                for (int ss = 0; ss < 3; ++ss) {
+                    const int s = ss == 2 ? 8 : q4 + 4 * ss;
+                    if (ss == 2 && q4 != 0) continue;
+                    int owner, blk, pn;
+                    if (!stencil_slot(s, ii, jj, nx, ny, n, owner, blk, pn)) continue;
+                    const float* Bs = sB + (size_t)(k * NODE_VALS + blk * NB) * ls + (owner - n0 + hl.hw);
+                    float B[NB], u[6];
+#pragma unroll
+                    for (int e = 0; e < NB; ++e) B[e] = Bs[e * ls];
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) u[c] = uh[ubase + c * hl.hn + pn];
+                    sym_matvec_acc(B, u, q);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                q[c] += __shfl_xor_sync(0xffffffffu, q[c], 1);
+                q[c] += __shfl_xor_sync(0xffffffffu, q[c], 2);
+            }
+            if (live) {
+                wr[k][0] = sel6(q, c0);
+                wr[k][1] = has1 ? sel6(q, c1) : 0.f;
+                st_relaxed_u64(Rn + G6 + (size_t)c0 * G + n, tag_word(wtag, wr[k][0]));
+                if (has1) st_relaxed_u64(Rn + G6 + (size_t)c1 * G + n, tag_word(wtag, wr[k][1]));
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    gp = fmaf(rr[k][h], ur[k][h], gp);
+                    dp = fmaf(wr[k][h], ur[k][h], dp);
+                }
+            }
+        }
+        // while warp 0 polls, warps 1.. fetch the next iteration's halo (which
+        // iteration i + 1 forms only if it is not the last)
+        const bool next = i + 2 < iters;
+        auto fetch = [&]() -> bool {
+            if (!next) return true;
+            halo_load<false>(Rn, G6, gf, hv);
+            return halo_wait<false>(Rn, G6, wtag, status, gf, hv);
+        };
+        ff G2, D2;
+        ok = allreduce2_tagged<false>(gp, dp, sred, slots, (unsigned)nred + 1u, status, G2, D2, fail, fetch) && ok;
+        ++nred;
+        if (!ok) break;
+        if (i < 0) {
+            if (!(G2.hi > 1e-30f) || !(D2.hi > 1e-30f)) break; // x stays 0
+            alpha = G2.hi / D2.hi;
+            beta = 0.f;
+        } else {
+            const float bnew = G2.hi / gam.hi;
+            const float pap = D2.hi - bnew * G2.hi / alpha;
+            if (!(G2.hi > 1e-30f) || !(pap > 1e-30f)) break;
+            beta = bnew;
+            alpha = G2.hi / pap;
+        }
+        gam = G2;
+    }
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int n = slot0 + k * stride;
+        if (n >= G) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!(h == 0 || has1)) continue;
+            const int c = h ? c1 : c0;
+            if (interleaved)
+                xout[n * 6 + c] = xr[k][h];
+            else
+                xout[c * G + n] = xr[k][h];
+        }
+    }
+}
+
+// Row stride of the staged blocks: at least NPB + hw, and = 8 (mod 32), so
+// that block rows b * NB apart start 8 banks apart.
+int halo_ls(int nx)
+{
+    const int span = NPB + nx + 1;
+    return span + ((8 - span % 32) + 32) % 32;
+}
+
+size_t halo_smem(int npt, int nx)
+{
+    return ((size_t)npt * NODE_VALS * halo_ls(nx) + (size_t)npt * 6 * (NPB + 2 * (nx + 1))) * sizeof(float);
+}
+
+template <int NPT>
+cudaError_t launch_grid1h(int blocks, const LevelGeom& g, const float* node, const float* rhs, const float* minv,
+                          float* x, float* pub, float2* part, unsigned long long* bar, int* status, int iters,
+                          int interleaved, cudaStream_t st)
+{
+    if (blocks < 1 || blocks > TAG_MAXB) return cudaErrorInvalidValue; // the tagged reduction polls TAG_MAXB slots
+    if ((uintptr_t)pub & 7) return cudaErrorInvalidValue;               // 64-bit words
+    const size_t smem = halo_smem(NPT, g.nx);
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_pcg1h<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    LevelGeom gg = g;
+    int ls = halo_ls(g.nx);
+    unsigned long long* pubw = reinterpret_cast<unsigned long long*>(pub);
+    void* args[] = {(void*)&gg,  (void*)&node,   (void*)&rhs,   (void*)&minv,        (void*)&x,  (void*)&pubw,
+                    (void*)&part, (void*)&bar,   (void*)&status, (void*)&iters, (void*)&interleaved, (void*)&ls};
+    return cudaLaunchCooperativeKernel((const void*)k_pcg1h<NPT>, dim3(blocks), dim3(PT), args, smem, st);
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined PCG over the grid (plan kind 6): the reduction's latency hidden
+// behind the matrix-vector product. This is the pipelined form of PCG of
+// Ghysels and Vanroose ("Hiding global synchronization latency in the
+// preconditioned Conjugate Gradient algorithm", Parallel Computing 40, 2014):
+// with u = M r, w = A u, m = M w and n = A m, one iteration takes
+//   gamma = r.u, delta = w.u            (one fused reduction, started)
+//   m = M w, n = A m                    (while the reduction completes)
+//   beta = gamma / gamma_prev, alpha = gamma / (delta - beta gamma / alpha_prev)
+//   z = n + beta z, q = m + beta q, s = w + beta s, p = u + beta p
+//   x += alpha p, r -= alpha s, u -= alpha q, w -= alpha z
+// and keeps s = A p, q = M s, z = A q by recurrence: the iterates of the
+// textbook loop in exact arithmetic, rounded differently. The product needs
+// only the neighbours' w, published once per iteration as self-tagged words
+// (as in k_pcg1h); the coupling blocks are staged in shared memory as there.
+// A block publishes its partial sums, forms m over its nodes and halo
+// (waiting for late neighbours' w), runs the product, and only then polls the
+// other blocks' partials, which have had the product's duration to arrive.
+//
+// Words: w_i in buffer i & 1 with tag i + 1 (w_0 from the set-up product
+// A M r_0), r_0 with tag 1 in a third buffer for the set-up; both w buffers
+// are cleared before the launch's one full barrier. w_{i+2} overwrites w_i
+// only after its owner has seen every block's partial sums of iteration
+// i + 1, which each block forms from values computed with the w_i it read.
+// pubw holds [w buffer 0][w buffer 1][r_0], each [6][G] words.
+// ---------------------------------------------------------------------------
+
+// A block's partial sums of a and b (float-float, warps in order, as
+// allreduce2_tagged), published by thread 0 as four tagged words.
+__device__ __forceinline__ void tagged_publish(float a, float b, ff* sh, unsigned long long* slots, unsigned tag)
+{
+    const int nb = gridDim.x;
+    unsigned long long* sl = slots + (size_t)(tag & 1u) * 4 * nb;
+    const float wa = warp_sum(a), wb = warp_sum(b);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        sh[2 * (threadIdx.x >> 5)] = ff_from(wa);
+        sh[2 * (threadIdx.x >> 5) + 1] = ff_from(wb);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ff ta{0.f, 0.f}, tb{0.f, 0.f};
+        for (int w = 0; w < PT / 32; ++w) {
+            ta = ff_add(ta, sh[2 * w]);
+            tb = ff_add(tb, sh[2 * w + 1]);
+        }
+        unsigned long long* my = sl + (size_t)blockIdx.x * 4;
+        st_relaxed_u64(my + 0, tag_word(tag, ta.hi));
+        st_relaxed_u64(my + 1, tag_word(tag, ta.lo));
+        st_relaxed_u64(my + 2, tag_word(tag, tb.hi));
+        st_relaxed_u64(my + 3, tag_word(tag, tb.lo));
+    }
+}
+
+// The other half: warp 0 polls and folds every block's words of `tag`; the
+// sums reach every thread through shared memory (one CTA barrier).
+__device__ __forceinline__ bool tagged_collect(const unsigned long long* slots, unsigned tag, int* status, ff& ra,
+                                               ff& rb)
+{
+    __shared__ ff bcc[2];
+    __shared__ int okc;
+    if (threadIdx.x < 32) {
+        const int nb = gridDim.x;
+        ff va, vb;
+        const int ok = warp_poll_fold<false>(slots + (size_t)(tag & 1u) * 4 * nb, nb, tag, status, threadIdx.x, 1,
+                                             va, vb);
+        if (threadIdx.x == 0) {
+            bcc[0] = va;
+            bcc[1] = vb;
+            okc = ok;
+        }
+    }
+    __syncthreads();
+    ra = bcc[0];
+    rb = bcc[1];
+    return okc != 0;
+}
+
+// out = A v over the block's nodes, v from the u array (owned nodes and
+// halo), the coupling blocks from the staged copy.
+template <int NPT>
+__device__ __forceinline__ void smem_apply(const float* sB, const float* uh, int ls, const Halo& hl, int nx, int ny,
+                                           int slot0, int stride, int q4, const int (&ni)[NPT], const int (&nj)[NPT],
+                                           float (&out)[NPT][2])
+{
+    const int c0 = q4, c1 = q4 + 4;
+    const bool has1 = c1 < 6;
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int n = slot0 + k * stride;
+        const bool live = n < hl.G;
+        const int n0 = blockIdx.x * NPB + k * stride;
+        const int ubase = (k * 6) * hl.hn + hl.hw - n0;
+        float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (live) {
+#pragma unroll
+            for (int ss = 0; ss < 3; ++ss) {
+                const int s = ss == 2 ? 8 : q4 + 4 * ss;
+                if (ss == 2 && q4 != 0) continue;
+                int owner, blk, pn;
+                if (!stencil_slot(s, ni[k], nj[k], nx, ny, n, owner, blk, pn)) continue;
+                const float* Bs = sB + (size_t)(k * NODE_VALS + blk * NB) * ls + (owner - n0 + hl.hw);
+                float B[NB], u[6];
+#pragma unroll
+                for (int e = 0; e < NB; ++e) B[e] = Bs[e * ls];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) u[c] = uh[ubase + c * hl.hn + pn];
+                sym_matvec_acc(B, u, q);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            q[c] += __shfl_xor_sync(0xffffffffu, q[c], 1);
+            q[c] += __shfl_xor_sync(0xffffffffu, q[c], 2);
+        }
+        out[k][0] = live ? sel6(q, c0) : 0.f;
+        out[k][1] = (live && has1) ? sel6(q, c1) : 0.f;
+    }
+}
+
+// Fills the u array with M v: owned nodes from own[][] (already M v), the
+// halo from the words of V carrying `tag`; entries of the first round use
+// the fixed indices g0/s0 (loads already issued into hv when `issued`).
+template <int NPT>
+__device__ __forceinline__ bool smem_fill(const Halo& hl, const unsigned long long* V, size_t G6,
+                                          const float* __restrict__ minv, unsigned tag, int* status, float* uh,
+                                          int slot0, int stride, int q4, const float (&own)[NPT][2],
+                                          const int (&g0)[HPF], const int (&s0)[HPF], bool issued,
+                                          unsigned long long (&hv)[HPF][3])
+{
+    const int c0 = q4, c1 = q4 + 4;
+    const bool has1 = c1 < 6;
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int n = slot0 + k * stride;
+        if (n >= hl.G) continue;
+        const int o = (k * 6) * hl.hn + hl.hw + (n - (blockIdx.x * NPB + k * stride));
+        uh[o + c0 * hl.hn] = own[k][0];
+        if (has1) uh[o + c1 * hl.hn] = own[k][1];
+    }
+    if (!issued) halo_load<true>(V, G6, g0, hv);
+    bool ok = halo_wait<true>(V, G6, tag, status, g0, hv);
+    halo_u<true>(minv, 0.f, 0.f, uh, g0, s0, hv);
+    for (int base = PT * HPF; base < hl.items; base += PT * HPF) {
+        int gi[HPF], si[HPF];
+        halo_issue<NPT, true>(hl, V, G6, base + (int)threadIdx.x, PT, stride, gi, si, hv);
+        ok = halo_wait<true>(V, G6, tag, status, gi, hv) && ok;
+        halo_u<true>(minv, 0.f, 0.f, uh, gi, si, hv);
+    }
+    return ok;
+}
+
+template <int NPT>
+__global__ void __launch_bounds__(PT, 1) k_pcg1p(LevelGeom g, const float* __restrict__ node,
+                                                 const float* __restrict__ rhs, const float* __restrict__ minv,
+                                                 float* __restrict__ xout, unsigned long long* pubw, float2* part,
+                                                 unsigned long long* bar, int* status, int iters, int interleaved,
+                                                 int ls)
+{
+    extern __shared__ float smem_h[];
+    __shared__ ff sred[2 * (PT / 32)];
+    GridSync sy{0ull};
+    sy.start(bar);
+    const int G = g.G, nx = g.nx, ny = g.ny;
+    const size_t G6 = (size_t)6 * G;
+    const int q4 = threadIdx.x & 3;
+    const int c0 = q4, c1 = q4 + 4;
+    const bool has1 = c1 < 6;
+    const int stride = gridDim.x * NPB;
+    const int slot0 = blockIdx.x * NPB + (threadIdx.x >> 2);
+    Halo hl;
+    hl.G = G;
+    hl.hw = nx + 1;
+    hl.hn = NPB + 2 * hl.hw;
+    hl.items = NPT * 12 * hl.hw;
+    float* sB = smem_h;
+    float* uh = smem_h + (size_t)NPT * NODE_VALS * ls;
+    const unsigned long long* R0 = pubw + 2 * G6; // w buffer b at pubw + b * G6
+    float xr[NPT][2], rr[NPT][2], ur[NPT][2], wr[NPT][2], zr[NPT][2], qr[NPT][2], sr[NPT][2], pr[NPT][2],
+        mr[NPT][2], nr[NPT][2], mw[NPT][2];
+    int ni[NPT], nj[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int n = slot0 + k * stride;
+        nj[k] = n / nx;
+        ni[k] = n - nj[k] * nx;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = h ? c1 : c0;
+            const bool live = n < G && (h == 0 || has1);
+            const float r0 = live ? rhs[c * G + n] : 0.f;
+            mr[k][h] = live ? minv[c * G + n] : 0.f;
+            rr[k][h] = r0;
+            ur[k][h] = mr[k][h] * r0;
+            xr[k][h] = wr[k][h] = zr[k][h] = qr[k][h] = sr[k][h] = pr[k][h] = nr[k][h] = mw[k][h] = 0.f;
+            if (live) {
+                const size_t o = (size_t)c * G + n;
+                pubw[o] = 0ull;                          // w buffers: cleared
+                pubw[G6 + o] = 0ull;
+                pubw[2 * G6 + o] = tag_word(1u, r0);     // r_0
+            }
+        }
+    }
+    {
+        const int span = hl.hw + NPB;
+#pragma unroll 1
+        for (int k = 0; k < NPT; ++k) {
+            const int mlo = blockIdx.x * NPB + k * stride - hl.hw;
+            float* dst = sB + (size_t)k * NODE_VALS * ls;
+#pragma unroll 4
+            for (int idx = threadIdx.x; idx < NODE_VALS * span; idx += PT) {
+                const int row = idx / span;
+                const int l = idx - row * span;
+                const int m = mlo + l;
+                dst[row * ls + l] = (m >= 0 && m < G) ? __ldg(node + (size_t)row * G + m) : 0.f;
+            }
+        }
+    }
+    unsigned long long* slots = reinterpret_cast<unsigned long long*>(part);
+    tagged_clear(slots);
+    bool ok = sy.sync(bar, status); // the launch's one full barrier: clears, r_0 and the staged blocks
+    int g0[HPF], s0[HPF];
+    unsigned long long hv[HPF][3];
+    halo_index<NPT>(hl, (int)threadIdx.x, PT, stride, g0, s0); // the first round's entries, fixed
+    // set-up: w_0 = A M r_0
+    if (ok) {
+        const bool fail = !smem_fill<NPT>(hl, R0, G6, minv, 1u, status, uh, slot0, stride, q4, ur, g0, s0, false, hv);
+        ok = !__syncthreads_or(fail);
+    }
+    if (ok) {
+        smem_apply<NPT>(sB, uh, ls, hl, nx, ny, slot0, stride, q4, ni, nj, wr);
+        if (iters > 1) {
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int n = slot0 + k * stride;
+                if (n >= G) continue;
+                st_relaxed_u64(pubw + (size_t)c0 * G + n, tag_word(1u, wr[k][0]));
+                if (has1) st_relaxed_u64(pubw + (size_t)c1 * G + n, tag_word(1u, wr[k][1]));
+            }
+        }
+    }
+    float alpha = 0.f, beta = 0.f;
+    ff gam{0.f, 0.f};
+    for (int i = 0; i < iters && ok; ++i) {
+        const bool last = i == iters - 1;
+        const unsigned tag = (unsigned)i + 1u;
+        const unsigned long long* W = pubw + (size_t)(i & 1) * G6;
+        float gp = 0.f, dp = 0.f;
+#pragma unroll
+        for (int k = 0; k < NPT; ++k)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                gp = fmaf(rr[k][h], ur[k][h], gp);
+                dp = fmaf(wr[k][h], ur[k][h], dp);
+                mw[k][h] = mr[k][h] * wr[k][h];
+            }
+        if (!last) halo_load<true>(W, G6, g0, hv); // in flight during the block sums
+        tagged_publish(gp, dp, sred, slots, tag);
+        if (!last) {
+            // m = M w and n = A m while the other blocks' partials arrive
+            const bool fail = !smem_fill<NPT>(hl, W, G6, minv, tag, status, uh, slot0, stride, q4, mw, g0, s0, true, hv);
+            if (__syncthreads_or(fail)) {
+                ok = false;
+                break;
+            }
+            smem_apply<NPT>(sB, uh, ls, hl, nx, ny, slot0, stride, q4, ni, nj, nr);
+        }
+        ff G2, D2;
+        ok = tagged_collect(slots, tag, status, G2, D2);
+        if (!ok) break;
+        if (i == 0) {
+            if (!(G2.hi > 1e-30f) || !(D2.hi > 1e-30f)) break; // x stays 0
+            alpha = G2.hi / D2.hi;
+            beta = 0.f;
+        } else {
+            const float bnew = G2.hi / gam.hi;
+            const float pap = D2.hi - bnew * G2.hi / alpha;
+            if (!(G2.hi > 1e-30f) || !(pap > 1e-30f)) break;
+            beta = bnew;
+            alpha = G2.hi / pap;
+        }
+        gam = G2;
+#pragma unroll
+        for (int k = 0; k < NPT; ++k)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                zr[k][h] = fmaf(beta, zr[k][h], nr[k][h]);
+                qr[k][h] = fmaf(beta, qr[k][h], mw[k][h]);
+                sr[k][h] = fmaf(beta, sr[k][h], wr[k][h]);
+                pr[k][h] = fmaf(beta, pr[k][h], ur[k][h]);
+                xr[k][h] = fmaf(alpha, pr[k][h], xr[k][h]);
+                rr[k][h] = fmaf(-alpha, sr[k][h], rr[k][h]);
+                ur[k][h] = fmaf(-alpha, qr[k][h], ur[k][h]);
+                wr[k][h] = fmaf(-alpha, zr[k][h], wr[k][h]);
+            }
+        if (i + 2 < iters) { // w_{i+1}, read by iteration i + 1's product
+            unsigned long long* Wn = pubw + (size_t)((i + 1) & 1) * G6;
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int n = slot0 + k * stride;
+                if (n >= G) continue;
+                st_relaxed_u64(Wn + (size_t)c0 * G + n, tag_word(tag + 1u, wr[k][0]));
+                if (has1) st_relaxed_u64(Wn + (size_t)c1 * G + n, tag_word(tag + 1u, wr[k][1]));
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int n = slot0 + k * stride;
+        if (n >= G) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!(h == 0 || has1)) continue;
+            const int c = h ? c1 : c0;
+            if (interleaved)
+                xout[n * 6 + c] = xr[k][h];
+            else
+                xout[c * G + n] = xr[k][h];
+        }
+    }
+}
+
+template <int NPT>
+cudaError_t launch_grid1p(int blocks, const LevelGeom& g, const float* node, const float* rhs, const float* minv,
+                          float* x, float* pub, float2* part, unsigned long long* bar, int* status, int iters,
+                          int interleaved, cudaStream_t st)
+{
+    if (blocks < 1 || blocks > TAG_MAXB) return cudaErrorInvalidValue; // the tagged reduction polls TAG_MAXB slots
+    if ((uintptr_t)pub & 7) return cudaErrorInvalidValue;               // 64-bit words
+    const size_t smem = halo_smem(NPT, g.nx);
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_pcg1p<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    LevelGeom gg = g;
+    int ls = halo_ls(g.nx);
+    unsigned long long* pubw = reinterpret_cast<unsigned long long*>(pub);
+    void* args[] = {(void*)&gg,  (void*)&node,   (void*)&rhs,   (void*)&minv,        (void*)&x,  (void*)&pubw,
+                    (void*)&part, (void*)&bar,   (void*)&status, (void*)&iters, (void*)&interleaved, (void*)&ls};
+    return cudaLaunchCooperativeKernel((const void*)k_pcg1p<NPT>, dim3(blocks), dim3(PT), args, smem, st);
+}
+
 // blocks of a cooperative launch that the GPU holds at once: the smallest
 // per-SM occupancy over the grid kernels, times the SMs
 int max_coop_blocks(int sm_count)
@@ -961,6 +1757,12 @@ int max_coop_blocks(int sm_count)
     take((const void*)k_pcg1<1, GridSync>);
     take((const void*)k_pcg1<2, GridSync>);
     take((const void*)k_pcg1<4, GridSync>);
+    take((const void*)k_pcg1h<1>);
+    take((const void*)k_pcg1h<2>);
+    take((const void*)k_pcg1h<4>);
+    take((const void*)k_pcg1p<1>);
+    take((const void*)k_pcg1p<2>);
+    take((const void*)k_pcg1p<4>);
     return per_sm * sm_count;
 }
 
@@ -989,7 +1791,7 @@ int max_cluster_blocks()
     return cached;
 }
 
-int dsm_max_npc()
+size_t smem_optin()
 {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
@@ -997,18 +1799,38 @@ int dsm_max_npc()
         cudaGetLastError();
         optin = 227 * 1024;
     }
+    return (size_t)optin;
+}
+
+int dsm_max_npc()
+{
     // static shared memory of the kernel is small (< 1 KB); keep 2 KB spare
-    return (optin - 2048) / (int)(NODE_F * sizeof(float));
+    return ((int)smem_optin() - 2048) / (int)(NODE_F * sizeof(float));
 }
 
 } // namespace
 
-PcgPlan pcg_plan(int G, int sm_count, int mode)
+PcgPlan pcg_plan(int G, int sm_count, int mode, int nx)
 {
-    // preference: DSM (DSM only) -> cluster with global vectors (AUTO, DSM,
-    // CLUSTER) -> cooperative grid (all)
+    // preference: the staged, self-tagged grid (AUTO: the one-reduction form,
+    // kind 5, measured faster than kinds 1-4 at every 640x480 level;
+    // PIPELINED: kind 6) -> DSM (DSM only) -> cluster with global vectors
+    // (AUTO, DSM, CLUSTER, ONE_REDUCTION, PIPELINED) -> cooperative grid (all)
     PcgPlan p{1, 1, 0, 0};
     const int maxc = max_cluster_blocks();
+    if ((mode == SF_PCG_AUTO || mode == SF_PCG_PIPELINED) && nx > 0) {
+        int cap = max_coop_blocks(sm_count);
+        if (cap > TAG_MAXB) cap = TAG_MAXB;
+        for (int npt : {1, 2, 4}) {
+            const int need = std::max(1, (G + NPB * npt - 1) / (NPB * npt));
+            if (need <= cap && halo_smem(npt, nx) + 2048 <= smem_optin()) {
+                p.blocks = need;
+                p.npt = npt;
+                p.cluster = mode == SF_PCG_PIPELINED ? 6 : 5;
+                return p;
+            }
+        }
+    }
     if (mode == SF_PCG_DSM) {
         const int cap = dsm_max_npc();
         for (int npt = 1; npt <= 3; ++npt) {
@@ -1024,8 +1846,8 @@ PcgPlan pcg_plan(int G, int sm_count, int mode)
             }
         }
     }
-    // AUTO takes the one-reduction form (measured faster at every level size)
-    const bool one = mode == SF_PCG_ONE_REDUCTION || mode == SF_PCG_AUTO;
+    // otherwise the one-reduction form (measured faster than the textbook loop at every level size)
+    const bool one = mode == SF_PCG_ONE_REDUCTION || mode == SF_PCG_AUTO || mode == SF_PCG_PIPELINED;
     if (mode != SF_PCG_GRID) {
         for (int npt : {1, 2, 4}) {
             const int need = (G + NPB * npt - 1) / (NPB * npt);
@@ -1053,7 +1875,7 @@ PcgPlan pcg_plan(int G, int sm_count, int mode)
     return p;
 }
 
-int pcg_candidates(int G, int sm_count, PcgPlan* out, int max)
+int pcg_candidates(int G, int sm_count, PcgPlan* out, int max, int nx, bool pipelined)
 {
     int n = 0;
     auto push = [&](PcgPlan p) {
@@ -1068,7 +1890,13 @@ int pcg_candidates(int G, int sm_count, PcgPlan* out, int max)
             push(PcgPlan{need, npt, 4, 0});
             push(PcgPlan{need, npt, 1, 0});
         }
-        if (need <= cap && need <= TAG_MAXB) push(PcgPlan{need, npt, 3, 0});
+        if (need <= cap && need <= TAG_MAXB) {
+            if (nx > 0 && halo_smem(npt, nx) + 2048 <= smem_optin()) {
+                if (pipelined) push(PcgPlan{need, npt, 6, 0});
+                push(PcgPlan{need, npt, 5, 0});
+            }
+            push(PcgPlan{need, npt, 3, 0});
+        }
         if (need <= cap) push(PcgPlan{need, npt, 0, 0});
     }
     const int dcap = dsm_max_npc();
@@ -1088,6 +1916,20 @@ cudaError_t launch_pcg(const LevelGeom& g, const PcgPlan& plan, const float* nod
                        float* x, float* z, float* p0, float* p1, float* pub, float2* part, unsigned long long* bar,
                        int* status, int iters, int interleaved_out, cudaStream_t st)
 {
+    if (plan.cluster == 6) {
+        switch (plan.npt) {
+        case 1: return launch_grid1p<1>(plan.blocks, g, node, rhs, minv, x, pub, part, bar, status, iters, interleaved_out, st);
+        case 2: return launch_grid1p<2>(plan.blocks, g, node, rhs, minv, x, pub, part, bar, status, iters, interleaved_out, st);
+        default: return launch_grid1p<4>(plan.blocks, g, node, rhs, minv, x, pub, part, bar, status, iters, interleaved_out, st);
+        }
+    }
+    if (plan.cluster == 5) {
+        switch (plan.npt) {
+        case 1: return launch_grid1h<1>(plan.blocks, g, node, rhs, minv, x, pub, part, bar, status, iters, interleaved_out, st);
+        case 2: return launch_grid1h<2>(plan.blocks, g, node, rhs, minv, x, pub, part, bar, status, iters, interleaved_out, st);
+        default: return launch_grid1h<4>(plan.blocks, g, node, rhs, minv, x, pub, part, bar, status, iters, interleaved_out, st);
+        }
+    }
     if (plan.cluster == 3 || plan.cluster == 4) {
         const bool grid = plan.cluster == 3;
         switch (plan.npt) {

@@ -26,7 +26,7 @@ WFEAT_EIG, WFEAT_OFF = 0, 1
 TEMPORAL_PROPAGATE, TEMPORAL_COPY, TEMPORAL_ZERO = 0, 1, 2
 FP32, MIXED_BF16, MIXED_FP16 = 0, 1, 2
 K_PYRAMID, K_LEVEL, K_ASSEMBLE, K_GATHER, K_PCG, K_ENERGY = range(6)
-PCG_AUTO, PCG_CLUSTER, PCG_GRID, PCG_DSM, PCG_ONE_REDUCTION = 0, 1, 2, 3, 4
+PCG_AUTO, PCG_CLUSTER, PCG_GRID, PCG_DSM, PCG_ONE_REDUCTION, PCG_PIPELINED = 0, 1, 2, 3, 4, 5
 SOLVER_PCG, SOLVER_SCHWARZ = 0, 1
 PRESET_FIG2, PRESET_FIG568, PRESET_FIG79 = 0, 1, 2
 

@@ -103,7 +103,8 @@ def test_assemble_parity(w, h, s_, level, kw):
 
 
 @pytest.mark.parametrize("iters,mode", [(1, 0), (5, 0), (20, 0), (20, sf.PCG_CLUSTER), (20, sf.PCG_GRID),
-                                        (1, sf.PCG_DSM), (20, sf.PCG_DSM), (1, sf.PCG_ONE_REDUCTION), (20, sf.PCG_ONE_REDUCTION)])
+                                        (1, sf.PCG_DSM), (20, sf.PCG_DSM), (1, sf.PCG_ONE_REDUCTION), (20, sf.PCG_ONE_REDUCTION),
+                                        (2, sf.PCG_PIPELINED), (20, sf.PCG_PIPELINED)])
 def test_pcg_parity_on_the_same_system(iters, mode):
     solver, lv, op = _level_setup(160, 120, 4, 3, 0, pcg_mode=mode)
     rng = np.random.default_rng(3)
@@ -117,7 +118,7 @@ def test_pcg_parity_on_the_same_system(iters, mode):
     assert rel_max(x_gpu, x_ref) < 2e-4 * iters
 
 
-@pytest.mark.parametrize("mode", [sf.PCG_GRID, sf.PCG_ONE_REDUCTION])
+@pytest.mark.parametrize("mode", [sf.PCG_GRID, sf.PCG_ONE_REDUCTION, sf.PCG_PIPELINED])
 @pytest.mark.parametrize("w,h", [(640, 480), (800, 720), (1280, 720)])
 def test_pcg_parity_grid_schedule_on_a_level_larger_than_a_cluster(mode, w, h):
     """Level 0 takes the cooperative-grid schedule: 640x480 (4800 nodes, 75
@@ -136,17 +137,71 @@ def test_pcg_parity_grid_schedule_on_a_level_larger_than_a_cluster(mode, w, h):
     assert rel_max(x_gpu, x_ref) < 2e-4 * 20
 
 
-@pytest.mark.parametrize("kind,blocks,npt", [(3, 75, 1), (0, 75, 1), (3, 38, 2), (0, 38, 2), (3, 19, 4),
-                                             (0, 19, 4), (2, 15, 3)])
+@pytest.mark.parametrize("kind", [5, 6])
+@pytest.mark.parametrize("w,h", [(640, 480), (800, 720), (1280, 720)])
+def test_self_tagged_grid_pcg(kind, w, h):
+    """Kinds 5 and 6 exchange the published vectors as self-tagged words,
+    without memory fences, with the coupling blocks staged in shared memory.
+    Kind 5 runs the one-reduction grid's arithmetic in the same order, so its
+    x equals kind 3's bit for bit; kind 6 is the pipelined form (the
+    reduction behind the product), the same iterates in exact arithmetic.
+    Both match the oracle after 1, 7 and 20 iterations, and repeat bit for
+    bit; solves in a row check that words left by one cannot pass the next
+    one's tag checks."""
+    solver, lv, op = _level_setup(w, h, 8, 4, 0, pcg_mode=sf.PCG_ONE_REDUCTION)
+    k3, blocks, npt = solver.pcg_schedule(0)
+    assert k3 == 3
+    rng = np.random.default_rng(5)
+    base, delta = _smooth_state(lv.G, rng)
+    wf = np.ones(lv.G, dtype=np.float32)
+    blocks_, rhs, _, _ = solver.probe_assemble(0, _dev(base), _dev(delta), _dev(wf))
+    x3 = solver.probe_pcg(0, 20).cpu().numpy()
+    solver.set_pcg_schedule(0, kind, blocks, npt)
+    A = lib_blocks_to_oracle(blocks_.cpu().numpy().astype(np.float64), lv.nx, lv.ny)
+    b64 = rhs.cpu().numpy().astype(np.float64)
+    xs = {}
+    for iters in (20, 1, 7, 20):
+        x = solver.probe_pcg(0, iters).cpu().numpy()
+        assert solver.stats().status == sf.OK
+        x_ref, _, _ = O.pcg(lv.nx, lv.ny, A, b64, iters)
+        assert rel_max(x, x_ref) < 2e-4 * iters, iters
+        if iters in xs:
+            assert np.array_equal(x, xs[iters])
+        xs[iters] = x
+    if kind == 5:
+        assert np.array_equal(x3, xs[20])
+
+
+def test_pipelined_grid_pcg_frame_parity():
+    """A 640x480 frame (stride 8, 4 levels, 3 GN x 20 PCG) with every level on
+    the pipelined grid PCG (kind 6) matches the oracle like the default."""
+    q = scenes.SceneVideo(640, 480, 1, seed=100).frames(1)[0]
+    sp, op = make_params([3], [20])
+    solver = sf.Solver(640, 480, 8, 4, sp)
+    for l in range(4):
+        _, _, nx, ny = solver.dims(l)
+        solver.set_pcg_schedule(l, 6, -(-nx * ny // 64), 1)
+    fields = solver.solve(_dev(q)).cpu().numpy()
+    st = solver.stats()
+    assert st.status == sf.OK
+    qf = q.astype(np.float64)
+    ref = O.solve_frame(qf, 8, 4, op, W_given=solver.wmasks())
+    own = O.solve_frame(qf, 8, 4, op)
+    _assert_frame_parity(fields, st, ref, own, op, 4)
+
+
+@pytest.mark.parametrize("kind,blocks,npt", [(3, 75, 1), (5, 75, 1), (6, 75, 1), (0, 75, 1), (3, 38, 2), (5, 38, 2),
+                                             (6, 38, 2), (0, 38, 2), (3, 19, 4), (0, 19, 4), (2, 15, 3)])
 def test_pcg_schedule_set_explicitly(kind, blocks, npt):
     """sf_set_pcg_schedule takes any schedule the tuner would consider for a
     level (here every one for the 4800 nodes of the 640x480 level 0: grid
     forms of 1, 2 and 4 nodes per lane group, and one cluster of 15 CTAs with
     the state in distributed shared memory), solves with it, and rejects the
-    rest without changing the level's schedule."""
+    rest without changing the level's schedule: among them kinds 5 and 6 at 4
+    nodes per group, whose staged blocks would not fit in shared memory."""
     solver, lv, op = _level_setup(640, 480, 8, 4, 0)
     before = solver.pcg_schedule(0)
-    for bad in ((3, 74, 1), (5, 75, 1), (1, 75, 1)):
+    for bad in ((3, 74, 1), (7, 75, 1), (1, 75, 1), (5, 19, 4), (6, 19, 4)):
         with pytest.raises(sf.SFError):
             solver.set_pcg_schedule(0, *bad)
         assert solver.pcg_schedule(0) == before
@@ -249,7 +304,7 @@ def test_config1_frame_parity():
 @pytest.mark.parametrize("kw", [{"robust_mode": O.SQRT_PAPER}, {"grad_mode": O.GRAD_LITERAL},
                                 {"wfeat_mode": O.WFEAT_OFF, "eps_p": 0.0}, {"use_graph": 0},
                                 {"pcg_mode": sf.PCG_GRID}, {"pcg_mode": sf.PCG_CLUSTER}, {"pcg_mode": sf.PCG_DSM},
-                                {"pcg_mode": sf.PCG_ONE_REDUCTION}])
+                                {"pcg_mode": sf.PCG_ONE_REDUCTION}, {"pcg_mode": sf.PCG_PIPELINED}])
 def test_config1_frame_parity_modes(kw):
     q = scenes.plane_quadruple(seed=2)
     for r in _solve_both(q, 4, 3, [5], [10], **kw):
@@ -263,7 +318,7 @@ def test_pcg_autotuner_keeps_parity():
     sp, op = make_params([5], [10])
     solver = sf.Solver(160, 120, 4, 3, sp)
     sched = solver.tune_pcg(_dev(q), reps=2)
-    assert all(k in (0, 1, 2, 3, 4) and b >= 1 and t in (1, 2, 3, 4) for k, b, t in sched)
+    assert all(k in (0, 1, 2, 3, 4, 5, 6) and b >= 1 and t in (1, 2, 3, 4) for k, b, t in sched)
     fields = solver.solve(_dev(q)).cpu().numpy()
     st = solver.stats()
     assert st.status == sf.OK and st.frames == 1
