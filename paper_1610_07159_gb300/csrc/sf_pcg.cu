@@ -1141,6 +1141,40 @@ __device__ __forceinline__ void halo_u(const float* __restrict__ minv, float alp
     }
 }
 
+// With one node per four-lane group the coupling blocks of a lane's stencil
+// slots stay in registers for the whole solve (loaded once from global
+// memory) instead of being staged in shared memory: lane q holds slots q and
+// q + 4, lane 0 also slot 8. A slot outside the level holds zeros and points
+// at the node itself, so the product runs without branches.
+struct SlotRegs {
+    float B[3][NB];
+    int pn[3]; // neighbour node of each slot
+    __device__ __forceinline__ void load(const float* __restrict__ node, int G, int nx, int ny, int n, int i, int j,
+                                         int q4)
+    {
+#pragma unroll
+        for (int ss = 0; ss < 3; ++ss) {
+            const int s = ss == 2 ? 8 : q4 + 4 * ss;
+            int owner = n, blk = 0, p = n;
+            const bool on = n < G && !(ss == 2 && q4 != 0) && stencil_slot(s, i, j, nx, ny, n, owner, blk, p);
+            pn[ss] = on ? p : n; // an absent slot (zero block) reads the node itself
+#pragma unroll
+            for (int e = 0; e < NB; ++e) B[ss][e] = on ? __ldg(node + (size_t)(blk * NB + e) * G + owner) : 0.f;
+        }
+    }
+    // q += A_slots u, u read from the u array at ubase + c * hn + pn
+    __device__ __forceinline__ void apply(const float* uh, int ubase, int hn, float* q) const
+    {
+#pragma unroll
+        for (int ss = 0; ss < 3; ++ss) {
+            float u[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) u[c] = uh[ubase + c * hn + pn[ss]];
+            sym_matvec_acc(B[ss], u, q);
+        }
+    }
+};
+
 template <int NPT>
 __global__ void __launch_bounds__(PT, 1) k_pcg1h(LevelGeom g, const float* __restrict__ node,
                                                  const float* __restrict__ rhs, const float* __restrict__ minv,
@@ -1164,8 +1198,8 @@ __global__ void __launch_bounds__(PT, 1) k_pcg1h(LevelGeom g, const float* __res
     hl.hw = nx + 1;
     hl.hn = NPB + 2 * hl.hw;
     hl.items = NPT * 12 * hl.hw;
-    float* sB = smem_h;                             // [NPT][NODE_VALS][ls]
-    float* uh = smem_h + (size_t)NPT * NODE_VALS * ls; // [NPT][6][hn]
+    float* sB = smem_h; // [NPT][NODE_VALS][ls] (NPT > 1)
+    float* uh = smem_h + (NPT == 1 ? 0 : (size_t)NPT * NODE_VALS * ls); // [NPT][6][hn]
     float xr[NPT][2], rr[NPT][2], ur[NPT][2], wr[NPT][2], sr[NPT][2], pr[NPT][2], mr[NPT][2];
     int ni[NPT], nj[NPT];
 #pragma unroll
@@ -1193,8 +1227,12 @@ __global__ void __launch_bounds__(PT, 1) k_pcg1h(LevelGeom g, const float* __res
             }
         }
     }
-    // the coupling blocks of the segments' nodes and of the hw nodes before them
-    {
+    // the coupling blocks: in registers with one node per group, else those of
+    // the segments' nodes and of the hw nodes before them in shared memory
+    SlotRegs sr1;
+    if constexpr (NPT == 1) {
+        sr1.load(node, G, nx, ny, slot0, ni[0], nj[0], q4);
+    } else {
         const int span = hl.hw + NPB;
 #pragma unroll 1
         for (int k = 0; k < NPT; ++k) {
@@ -1292,7 +1330,9 @@ __global__ void __launch_bounds__(PT, 1) k_pcg1h(LevelGeom g, const float* __res
             const int n0 = blockIdx.x * NPB + k * stride;
             const int ubase = (k * 6) * hl.hn + hl.hw - n0;
             float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (live) {
+            if constexpr (NPT == 1) {
+                sr1.apply(uh, ubase, hl.hn, q);
+            } else if (live) {
                 const int ii = ni[k], jj = nj[k];
 #pragma unroll
                 for (int ss = 0; ss < 3; ++ss) {
@@ -1375,9 +1415,12 @@ int halo_ls(int nx)
     return span + ((8 - span % 32) + 32) % 32;
 }
 
+// Dynamic shared memory of k_pcg1h / k_pcg1p: the u array, and with more
+// than one node per group the staged blocks before it.
 size_t halo_smem(int npt, int nx)
 {
-    return ((size_t)npt * NODE_VALS * halo_ls(nx) + (size_t)npt * 6 * (NPB + 2 * (nx + 1))) * sizeof(float);
+    const size_t staged = npt == 1 ? 0 : (size_t)npt * NODE_VALS * halo_ls(nx);
+    return (staged + (size_t)npt * 6 * (NPB + 2 * (nx + 1))) * sizeof(float);
 }
 
 template <int NPT>
@@ -1480,9 +1523,9 @@ __device__ __forceinline__ bool tagged_collect(const unsigned long long* slots, 
 // out = A v over the block's nodes, v from the u array (owned nodes and
 // halo), the coupling blocks from the staged copy.
 template <int NPT>
-__device__ __forceinline__ void smem_apply(const float* sB, const float* uh, int ls, const Halo& hl, int nx, int ny,
-                                           int slot0, int stride, int q4, const int (&ni)[NPT], const int (&nj)[NPT],
-                                           float (&out)[NPT][2])
+__device__ __forceinline__ void smem_apply(const float* sB, const SlotRegs& sr1, const float* uh, int ls,
+                                           const Halo& hl, int nx, int ny, int slot0, int stride, int q4,
+                                           const int (&ni)[NPT], const int (&nj)[NPT], float (&out)[NPT][2])
 {
     const int c0 = q4, c1 = q4 + 4;
     const bool has1 = c1 < 6;
@@ -1493,7 +1536,9 @@ __device__ __forceinline__ void smem_apply(const float* sB, const float* uh, int
         const int n0 = blockIdx.x * NPB + k * stride;
         const int ubase = (k * 6) * hl.hn + hl.hw - n0;
         float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (live) {
+        if constexpr (NPT == 1) {
+            sr1.apply(uh, ubase, hl.hn, q);
+        } else if (live) {
 #pragma unroll
             for (int ss = 0; ss < 3; ++ss) {
                 const int s = ss == 2 ? 8 : q4 + 4 * ss;
@@ -1574,8 +1619,8 @@ __global__ void __launch_bounds__(PT, 1) k_pcg1p(LevelGeom g, const float* __res
     hl.hw = nx + 1;
     hl.hn = NPB + 2 * hl.hw;
     hl.items = NPT * 12 * hl.hw;
-    float* sB = smem_h;
-    float* uh = smem_h + (size_t)NPT * NODE_VALS * ls;
+    float* sB = smem_h; // [NPT][NODE_VALS][ls] (NPT > 1)
+    float* uh = smem_h + (NPT == 1 ? 0 : (size_t)NPT * NODE_VALS * ls);
     const unsigned long long* R0 = pubw + 2 * G6; // w buffer b at pubw + b * G6
     float xr[NPT][2], rr[NPT][2], ur[NPT][2], wr[NPT][2], zr[NPT][2], qr[NPT][2], sr[NPT][2], pr[NPT][2],
         mr[NPT][2], nr[NPT][2], mw[NPT][2];
@@ -1602,7 +1647,10 @@ __global__ void __launch_bounds__(PT, 1) k_pcg1p(LevelGeom g, const float* __res
             }
         }
     }
-    {
+    SlotRegs sr1;
+    if constexpr (NPT == 1) {
+        sr1.load(node, G, nx, ny, slot0, ni[0], nj[0], q4);
+    } else {
         const int span = hl.hw + NPB;
 #pragma unroll 1
         for (int k = 0; k < NPT; ++k) {
@@ -1629,7 +1677,7 @@ __global__ void __launch_bounds__(PT, 1) k_pcg1p(LevelGeom g, const float* __res
         ok = !__syncthreads_or(fail);
     }
     if (ok) {
-        smem_apply<NPT>(sB, uh, ls, hl, nx, ny, slot0, stride, q4, ni, nj, wr);
+        smem_apply<NPT>(sB, sr1, uh, ls, hl, nx, ny, slot0, stride, q4, ni, nj, wr);
         if (iters > 1) {
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
@@ -1664,7 +1712,7 @@ __global__ void __launch_bounds__(PT, 1) k_pcg1p(LevelGeom g, const float* __res
                 ok = false;
                 break;
             }
-            smem_apply<NPT>(sB, uh, ls, hl, nx, ny, slot0, stride, q4, ni, nj, nr);
+            smem_apply<NPT>(sB, sr1, uh, ls, hl, nx, ny, slot0, stride, q4, ni, nj, nr);
         }
         ff G2, D2;
         ok = tagged_collect(slots, tag, status, G2, D2);
