@@ -217,7 +217,9 @@ __global__ void __launch_bounds__(ETHREADS) k_gather_rhs(LevelGeom g, const floa
             cr.t = 0.f;
             cr.accepted = 0;
             cr.n_excluded = (int)sx;
-            cr.pad = 0;
+            cr.t1_ok = 0;
+            cr.E_t1 = cr.E_cur;
+            for (int q = 0; q < 5; ++q) cr.terms_t1[q] = cr.terms_cur[q];
             *ctrl = cr;
             if (!isfinite(cr.E_cur)) atomicOr(status, DEV_NUMERIC);
             __threadfence();
@@ -228,14 +230,18 @@ __global__ void __launch_bounds__(ETHREADS) k_gather_rhs(LevelGeom g, const floa
 
 // Energy at base + delta (+ t x): pixel blocks first, then node blocks;
 // the last block to finish sums the partials in a fixed order and writes the
-// record (energy, the five weighted terms, excluded pixels).
-template <class TT>
+// record (energy, the five weighted terms, excluded pixels). TRIAL: the first
+// trial of a Gauss-Newton step (t = 1, W of the step): the last block writes
+// the energy and terms into the step's control record instead and whether
+// the step passes (E <= E_cur); a non-finite energy fails the trial, as in
+// k_trials, without raising an error.
+template <class TT, bool TRIAL = false>
 __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, const typename TT::T* __restrict__ tex,
                                                      const float* __restrict__ base, const float* __restrict__ delta,
                                                      const float* __restrict__ x, float t, const float* __restrict__ wf,
                                                      DevParams P, LevelMaps M, uint8_t* __restrict__ Wmask, int wmode,
                                                      float2* __restrict__ part, unsigned* counter,
-                                                     double* __restrict__ rec, int* status)
+                                                     double* __restrict__ rec, int* status, StepCtrl* ctrl = nullptr)
 {
     __shared__ ff sred[6 * (ETHREADS / 32)];
     __shared__ bool last_sh;
@@ -295,23 +301,32 @@ __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, c
             terms[3] = (double)P.w_reg * P.w_epi * s[3];
             terms[4] = (double)P.w_reg * P.w_mag * s[4];
             const double E = terms[0] + terms[1] + terms[2] + terms[3] + terms[4];
-            rec[0] = E;
-            for (int q = 0; q < 5; ++q) rec[1 + q] = terms[q];
-            rec[6] = s[5];
-            if (!isfinite(E)) atomicOr(status, DEV_NUMERIC);
+            if (TRIAL) {
+                ctrl->E_t1 = E;
+                for (int q = 0; q < 5; ++q) ctrl->terms_t1[q] = terms[q];
+                ctrl->t1_ok = E <= ctrl->E_cur ? 1 : 0;
+            } else {
+                rec[0] = E;
+                for (int q = 0; q < 5; ++q) rec[1 + q] = terms[q];
+                rec[6] = s[5];
+                if (!isfinite(E)) atomicOr(status, DEV_NUMERIC);
+            }
             __threadfence();
             *counter = 0u;
         }
     }
 }
 
-// All backtracking trials of one Gauss-Newton step and the update in one
-// cooperative launch: for t = 1, 1/2, ... every block sums its share of the
-// pixel and node energies at delta + t x (W of the step), a bounded grid
-// barrier, then warp 0 of every block forms the fixed-order totals, so all
-// blocks take the same decision; the first t whose energy does not exceed E_cur is taken
-// and applied (delta += t x). Replaces max_backtracks + 1 trial launches, most
-// of which found the step already taken, and the update launch.
+// The backtracking trials of one Gauss-Newton step and the update in one
+// cooperative launch. The full step (t = 1) was tried by k_energy in trial
+// mode just before (one pixel per thread over the whole GPU, its verdict in
+// the control record); when it passed, every block applies it (delta += x)
+// with no barrier. Otherwise, for t = 1/2, 1/4, ... every block sums its
+// share of the pixel and node energies at delta + t x (W of the step), a
+// bounded grid barrier, then warp 0 of every block forms the fixed-order
+// totals, so all blocks take the same decision; the first t whose energy does
+// not exceed E_cur is taken and applied. Replaces max_backtracks + 1 trial
+// launches, most of which found the step already taken, and the update launch.
 template <class TT>
 __global__ void __launch_bounds__(ETHREADS) k_trials(LevelGeom g, const typename TT::T* __restrict__ tex,
                                                      const float* base, float* delta, const float* x,
@@ -326,11 +341,17 @@ __global__ void __launch_bounds__(ETHREADS) k_trials(LevelGeom g, const typename
     const int tid = blockIdx.x * ETHREADS + threadIdx.x, stride = nb * ETHREADS;
     const double E_cur = ctrl->E_cur;
     const int N = g.w * g.h;
-    float t = 1.f, t_acc = 0.f;
+    float t = 0.5f, t_acc = 0.f;
     double E_acc = E_cur, terms_acc[5];
     for (int q = 0; q < 5; ++q) terms_acc[q] = ctrl->terms_cur[q];
     bool ok = true;
-    for (int j = 0; j <= max_bt && ok; ++j, t *= 0.5f) {
+    if (ctrl->t1_ok) {
+        t_acc = 1.f;
+        E_acc = ctrl->E_t1;
+        for (int q = 0; q < 5; ++q) terms_acc[q] = ctrl->terms_t1[q];
+        max_bt = 0; // no backtracking
+    }
+    for (int j = 1; j <= max_bt && ok; ++j, t *= 0.5f) {
         float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
         for (int p = tid; p < N; p += stride) {
             const int y = p / g.w, xx = p - y * g.w;
@@ -525,6 +546,18 @@ cudaError_t launch_trials(const LevelGeom& g, const void* tex, int prec, const f
                           unsigned long long* bar, StepCtrl* ctrl, int max_bt, int blocks, cudaStream_t st,
                           const LevelMaps& M)
 {
+    // the full step first: one pixel per thread, the verdict into the control record
+    {
+        int npix = (g.w * g.h + ETHREADS - 1) / ETHREADS;
+        if (npix > 152 * 8) npix = 152 * 8; // larger levels loop (the partial slots and the last block's fold)
+        const int nnode = (g.G + ETHREADS - 1) / ETHREADS;
+        SF_TEX_DISPATCH(prec, TT, (k_energy<TT, true><<<npix + nnode, ETHREADS, 0, st>>>(
+                                      g, npix, static_cast<const typename TT::T*>(tex), base, delta, x, 1.f, wf, P, M,
+                                      const_cast<uint8_t*>(Wmask), 0, sc.en_part, sc.counters + 2, nullptr,
+                                      sc.status, ctrl)));
+        const cudaError_t e0 = cudaGetLastError();
+        if (e0 != cudaSuccess) return e0;
+    }
     LevelGeom gg = g;
     DevParams pp = P;
     LevelMaps mm = M;

@@ -395,7 +395,9 @@ __global__ void __launch_bounds__(BT, 2) k_batch_frame(const BSeq* __restrict__ 
                 c.t = t_acc;
                 c.accepted = t_acc > 0.f;
                 c.n_excluded = n_excl;
-                c.pad = 0;
+                c.t1_ok = t_acc == 1.f;
+                c.E_t1 = c.t1_ok ? E_acc : E_cur;
+                for (int q = 0; q < 5; ++q) c.terms_t1[q] = c.t1_ok ? terms_acc[q] : terms_cur[q];
                 B.ctrl[gi] = c;
             }
             if (t_acc > 0.f)

@@ -303,7 +303,7 @@ int enqueue_level(sf_ctx* c, int l, const LevelIO& io, cudaStream_t st, int& nl)
         e = launch_trials(g, io.tex, P.precision, b.base, b.delta, b.x, b.wf, c->dp[l], Wst, sc,
                           c->bar + SF_MAX_LEVELS + l, ctrl, P.max_backtracks, c->trial_blocks[l], st, M);
         if (e != cudaSuccess) return check_cuda(e);
-        ++nl;
+        nl += 2; // the full step's trial, then the backtracking trials and the update
         prof_mark(c, SF_K_ENERGY, false, st);
     }
     prof_mark(c, SF_K_LEVEL, true, st);

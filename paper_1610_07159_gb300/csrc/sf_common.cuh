@@ -77,7 +77,9 @@ struct StepCtrl {
     float t;             // accepted step length, 0 = rejected
     int accepted;
     int n_excluded;
-    int pad;
+    int t1_ok;           // the full step (t = 1) passed its trial (k_energy, trial mode)
+    double E_t1;         // energy and weighted terms at the full step (W of the step)
+    double terms_t1[5];
 };
 
 // Per-frame arguments read by the kernels of a captured graph.

@@ -52,8 +52,10 @@ void launch_gather(const LevelGeom& g, const float* cell, const float* base, con
 void launch_energy(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta, const float* x,
                    float t, const float* wf, const DevParams& P, uint8_t* Wmask, int wmode, const Scratch& sc,
                    double* rec, cudaStream_t st, const LevelMaps& M = LevelMaps{nullptr, nullptr});
-// all backtracking trials of a step and its update in one cooperative launch
-// of `blocks` CTAs (trials_blocks: all co-resident), on its own barrier counter
+// the trials of a step and its update: the full step's trial over the whole
+// GPU (k_energy in trial mode), then the backtracking trials and the update
+// in one cooperative launch of `blocks` CTAs (trials_blocks: all
+// co-resident), on its own barrier counter
 int trials_blocks(const LevelGeom& g, int prec, int sm_count);
 cudaError_t launch_trials(const LevelGeom& g, const void* tex, int prec, const float* base, float* delta, const float* x,
                           const float* wf, const DevParams& P, const uint8_t* Wmask, const Scratch& sc,
