@@ -485,6 +485,7 @@ __device__ __forceinline__ void ff_block_fixed_sum_n(const float2* const (&part)
         out[k] = ff{0.f, 0.f};
         nmax = n[k] > nmax ? n[k] : nmax;
     }
+#pragma unroll 4
     for (int i = threadIdx.x; i < nmax; i += NT) {
         float2 t[K];
 #pragma unroll
