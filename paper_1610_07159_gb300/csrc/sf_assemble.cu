@@ -187,13 +187,11 @@ __global__ void __launch_bounds__(ETHREADS) k_gather_rhs(LevelGeom g, const floa
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) gpart[q * MAX_PART + blockIdx.x] = make_float2(tb[q].hi, tb[q].lo);
-        __threadfence();
-        const unsigned done = atomicAdd(counter, 1u);
-        last_sh = done == gridDim.x - 1;
+        last_sh = atom_add_release_gpu(counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last_sh) return;
-    __threadfence();
+    fence_acquire_gpu_fold();
     {
         const float2* const parts[6] = {apart, apart + MAX_PART, apart + 2 * MAX_PART,
                                         gpart, gpart + MAX_PART, gpart + 2 * MAX_PART};
@@ -222,8 +220,7 @@ __global__ void __launch_bounds__(ETHREADS) k_gather_rhs(LevelGeom g, const floa
             for (int q = 0; q < 5; ++q) cr.terms_t1[q] = cr.terms_cur[q];
             *ctrl = cr;
             if (!isfinite(cr.E_cur)) atomicOr(status, DEV_NUMERIC);
-            __threadfence();
-            *counter = 0u;
+            *counter = 0u; // the next launch (a later kernel) sees it
         }
     }
 }
@@ -276,14 +273,10 @@ __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, c
             for (int q = 0; q < 6; ++q) part[q * MAX_PART + blockIdx.x] = make_float2(sq[q].hi, sq[q].lo);
         }
     }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned done = atomicAdd(counter, 1u);
-        last_sh = done == gridDim.x - 1;
-    }
+    if (threadIdx.x == 0) last_sh = atom_add_release_gpu(counter, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!last_sh) return;
-    __threadfence();
+    fence_acquire_gpu_fold();
     {
         const float2* const parts[6] = {part, part + MAX_PART, part + 2 * MAX_PART,
                                         part + 3 * MAX_PART, part + 4 * MAX_PART, part + 5 * MAX_PART};
@@ -311,8 +304,7 @@ __global__ void __launch_bounds__(ETHREADS) k_energy(LevelGeom g, int npixblk, c
                 rec[6] = s[5];
                 if (!isfinite(E)) atomicOr(status, DEV_NUMERIC);
             }
-            __threadfence();
-            *counter = 0u;
+            *counter = 0u; // the next launch (a later kernel) sees it
         }
     }
 }

@@ -497,6 +497,20 @@ __device__ __forceinline__ void ff_block_fixed_sum_n(const float2* const (&part)
     ff_block_sum_n<NT, K>(out, sh);
 }
 
+// The last-block pattern of the fixed-order folds: thread 0 counts its block
+// in with a release atomic (its partial-sum stores before the count), and
+// the last block's threads read the partials after an acquire fence. Only
+// the counting thread's own stores are ordered, so no block waits for the
+// rest of its writes (a full __threadfence would).
+__device__ __forceinline__ unsigned atom_add_release_gpu(unsigned* p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void fence_acquire_gpu_fold() { asm volatile("fence.acquire.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ void cluster_sync_all()
 {
     asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
