@@ -377,7 +377,7 @@ SF_API int sf_probe_fma_rate(int reps, double* flops_per_s, void* stream);
  * The device-wide waits of this library (the grid barriers of the PCG,
  * Schwarz and trial kernels, the mbarrier waits of the tensor-core GEMM) are
  * bounded: a wait that runs out latches a status bit and returns, so a lost
- * block never hangs the GPU. These two calls run the same wait code with a
+ * block never hangs the GPU. These calls run the same wait code with a
  * short limit on a condition that a test controls; they have no counterpart
  * in the paper.
  *
@@ -393,6 +393,18 @@ SF_API int sf_probe_barrier_timeout(int skip_block, long long limit_cycles, int*
  * one thread arrives first, with arrive = 0 nothing does. *completed: 1 if
  * the wait saw the phase complete, 0 if it ran out. */
 SF_API int sf_probe_mbarrier_timeout(int arrive, long long limit_cycles, int* completed);
+/* sf_probe_tagged_timeout: the waits of the self-tagged PCG exchange
+ * (schedule kinds 5 and 6), limit `limit_cycles` SM clocks, in a cooperative
+ * launch of min(SMs, 160) blocks. mode 0: every block but `skip_block`
+ * publishes its tagged partial-sum words and every block polls all blocks'
+ * words; mode 1: every block but `skip_block` publishes one tagged word and
+ * every block waits for the next block's word, as a halo reader does.
+ * skip_block = -1: every block publishes. Waits for the launch and writes the
+ * latched status (*status: SF_OK, or SF_ERR_TIMEOUT when a wait ran out) and
+ * the number of blocks that came back (*returned). SF_ERR_ARG for a mode
+ * other than 0 or 1, a limit outside [1, 4e9] or skip_block past the grid.
+ * Allocates its own small device buffers. */
+SF_API int sf_probe_tagged_timeout(int mode, int skip_block, long long limit_cycles, int* status, int* returned);
 
 /* C[s][M][N] = A[M, K] * B[N, K]^T over split s of K (K split into `splits`
  * contiguous ranges of 64-wide chunks; the splits' partial products are

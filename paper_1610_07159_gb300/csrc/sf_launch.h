@@ -81,6 +81,8 @@ PcgPlan pcg_plan(int G, int sm_count, int mode, int nx);
 // (nx > 0: also the kind-5 plans, and with `pipelined` the kind-6 plans,
 // whose shared memory fits the level's rows of nx nodes)
 int pcg_candidates(int G, int sm_count, PcgPlan* out, int max, int nx, bool pipelined);
+// the self-tagged exchange's waits with a short limit (sf_probe_tagged_timeout)
+int tag_timeout_probe(int mode, int skip_block, long long limit_cycles, int* status, int* returned);
 cudaError_t launch_pcg(const LevelGeom& g, const PcgPlan& plan, const float* node, const float* rhs,
                        const float* minv, float* x, float* z, float* p0, float* p1, float* pub, float2* part,
                        unsigned long long* bar, int* status, int iters, int interleaved_out, cudaStream_t st);

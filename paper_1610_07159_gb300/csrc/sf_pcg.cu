@@ -667,7 +667,7 @@ __device__ __forceinline__ void tagged_clear(unsigned long long* slots)
 // polls, ~1 s); returns 0 then. ok = 0 on entry skips the poll.
 template <bool kFence>
 __device__ __forceinline__ int warp_poll_fold(const unsigned long long* sl, int nb, unsigned tag, int* status,
-                                              int lane, int ok, ff& va, ff& vb)
+                                              int lane, int ok, ff& va, ff& vb, long long limit = 2000000000LL)
 {
     unsigned long long v[TAG_MAXB / 32][4];
     const long long t0 = clock64();
@@ -690,7 +690,7 @@ __device__ __forceinline__ int warp_poll_fold(const unsigned long long* sl, int 
             if (lane == 0) {
                 if (ld_acquire_s32(status) != 0) {
                     fail = true;
-                } else if (clock64() - t0 > 2000000000LL) {
+                } else if (clock64() - t0 > limit) {
                     atomicOr(status, DEV_TIMEOUT);
                     fail = true;
                 }
@@ -1089,7 +1089,8 @@ __device__ __forceinline__ void halo_issue(const Halo& h, const unsigned long lo
 // every 64 passes, ~1 s). False on giving up.
 template <bool SETUP>
 __device__ __forceinline__ bool halo_wait(const unsigned long long* R, size_t G6, unsigned tag, int* status,
-                                          const int (&gi)[HPF], unsigned long long (&v)[HPF][3])
+                                          const int (&gi)[HPF], unsigned long long (&v)[HPF][3],
+                                          long long limit = 2000000000LL)
 {
     auto fresh = [&](int j) {
         return word_tag(v[j][0]) == tag && (SETUP || (word_tag(v[j][1]) == tag && word_tag(v[j][2]) == tag));
@@ -1117,7 +1118,7 @@ __device__ __forceinline__ bool halo_wait(const unsigned long long* R, size_t G6
         stale = left;
         if (stale != 0u && ((k + 1) & 63u) == 0u) {
             if (ld_acquire_s32(status) != 0) return false;
-            if (clock64() - t0 > 2000000000LL) {
+            if (clock64() - t0 > limit) {
                 atomicOr(status, DEV_TIMEOUT);
                 return false;
             }
@@ -1788,6 +1789,40 @@ cudaError_t launch_grid1p(int blocks, const LevelGeom& g, const float* node, con
     return cudaLaunchCooperativeKernel((const void*)k_pcg1p<NPT>, dim3(blocks), dim3(PT), args, smem, st);
 }
 
+// Failure-detection probe of the self-tagged exchange (the waits of
+// k_pcg1h and k_pcg1p, with a short limit). mode 0: every block but
+// skip_block publishes its tagged partial words and warp 0 of every block
+// polls all blocks' words (warp_poll_fold); mode 1: every block but
+// skip_block publishes one tagged word and thread 0 of every block waits for
+// the next block's word as a halo reader does (halo_wait). With a block that
+// never publishes, every wait runs out, latches DEV_TIMEOUT and returns.
+__global__ void __launch_bounds__(PT) k_tag_probe(unsigned long long* slots, unsigned long long* words, int* status,
+                                                  int skip_block, long long limit, int mode, int* returned)
+{
+    const int nb = gridDim.x;
+    const bool publish = (int)blockIdx.x != skip_block;
+    if (mode == 0) {
+        unsigned long long* sl = slots + (size_t)4 * nb; // the slot of tag 1
+        if (threadIdx.x < 32) {
+            if (threadIdx.x == 0 && publish)
+                for (int w = 0; w < 4; ++w) st_relaxed_u64(sl + (size_t)blockIdx.x * 4 + w, tag_word(1u, 1.f));
+            ff va, vb;
+            warp_poll_fold<false>(sl, nb, 1u, status, threadIdx.x, 1, va, vb, limit);
+        }
+    } else if (threadIdx.x == 0) {
+        if (publish) st_relaxed_u64(words + blockIdx.x, tag_word(1u, 1.f));
+        int gi[HPF];
+        unsigned long long v[HPF][3];
+#pragma unroll
+        for (int j = 0; j < HPF; ++j) gi[j] = -1;
+        gi[0] = (int)((blockIdx.x + 1) % nb);
+        v[0][0] = ld_cg_u64(words + gi[0]);
+        halo_wait<true>(words, 0, 1u, status, gi, v, limit);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(returned, 1);
+}
+
 // blocks of a cooperative launch that the GPU holds at once: the smallest
 // per-SM occupancy over the grid kernels, times the SMs
 int max_coop_blocks(int sm_count)
@@ -2008,6 +2043,47 @@ cudaError_t launch_pcg(const LevelGeom& g, const PcgPlan& plan, const float* nod
     case 2: return launch_grid<2>(plan.blocks, g, node, rhs, minv, x, z, p0, p1, part, bar, status, iters, interleaved_out, st);
     default: return launch_grid<4>(plan.blocks, g, node, rhs, minv, x, z, p0, p1, part, bar, status, iters, interleaved_out, st);
     }
+}
+
+int tag_timeout_probe(int mode, int skip_block, long long limit_cycles, int* status, int* returned)
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return SF_ERR_CUDA;
+    }
+    const int nb = std::min(sms, TAG_MAXB);
+    if (skip_block >= nb) return SF_ERR_ARG;
+    unsigned long long* buf = nullptr; // slots [2][nb][4], then nb words
+    int* w = nullptr;                  // [0] status, [1] blocks returned
+    const size_t nw = (size_t)8 * nb + nb;
+    if (cudaMalloc(&buf, nw * sizeof(*buf)) != cudaSuccess || cudaMalloc(&w, 2 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(buf);
+        return SF_ERR_OOM;
+    }
+    cudaMemset(buf, 0, nw * sizeof(*buf));
+    cudaMemset(w, 0, 2 * sizeof(int));
+    unsigned long long* slots = buf;
+    unsigned long long* words = buf + (size_t)8 * nb;
+    int* st = w;
+    int* ret = w + 1;
+    void* args[] = {(void*)&slots, (void*)&words, (void*)&st, (void*)&skip_block, (void*)&limit_cycles,
+                    (void*)&mode,  (void*)&ret};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_tag_probe, dim3(nb), dim3(PT), args, 0, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(h, w, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    cudaFree(w);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SF_ERR_CUDA;
+    }
+    *status = (h[0] & DEV_TIMEOUT) ? SF_ERR_TIMEOUT : (h[0] ? SF_ERR_STATE : SF_OK);
+    *returned = h[1];
+    return SF_OK;
 }
 
 } // namespace sfk

@@ -99,3 +99,11 @@ extern "C" SF_API int sf_probe_mbarrier_timeout(int arrive, long long limit_cycl
     *completed = h;
     return SF_OK;
 }
+
+extern "C" SF_API int sf_probe_tagged_timeout(int mode, int skip_block, long long limit_cycles, int* status,
+                                              int* returned)
+{
+    if (!status || !returned || (mode != 0 && mode != 1) || limit_cycles < 1 || limit_cycles > 4000000000LL)
+        return SF_ERR_ARG;
+    return sfk::tag_timeout_probe(mode, skip_block, limit_cycles, status, returned);
+}

@@ -36,7 +36,7 @@ EXPORTED = (
     "sf_get_stats", "sf_get_state", "sf_kernel_times", "sf_destroy", "sf_status_string", "sf_last_error", "sf_probe_pyramid",
     "sf_probe_feature_weights", "sf_probe_assemble", "sf_probe_pcg", "sf_probe_wmask", "sf_probe_energy",
     "sf_probe_cells", "sf_probe_fma_rate", "sf_probe_schwarz", "sf_probe_vmask", "sf_probe_occlusion",
-    "sf_probe_illum", "sf_probe_barrier_timeout", "sf_probe_mbarrier_timeout",
+    "sf_probe_illum", "sf_probe_barrier_timeout", "sf_probe_mbarrier_timeout", "sf_probe_tagged_timeout",
     "sf_pcg_static", "sf_batch_create", "sf_batch_layout", "sf_batch_solve", "sf_batch_set_schedule",
     "sf_batch_get_schedule", "sf_batch_tune", "sf_batch_sequence", "sf_batch_reset", "sf_batch_destroy",
     "sf_probe_gemm_bf16", "sf_net_param_count", "sf_net_create", "sf_net_set_params", "sf_net_get_params",
@@ -128,6 +128,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.sf_probe_vmask.argtypes = [vp, i, fp, vp]
     L.sf_probe_barrier_timeout.argtypes = [i, ctypes.c_longlong, ip, ip]
     L.sf_probe_mbarrier_timeout.argtypes = [i, ctypes.c_longlong, ip]
+    L.sf_probe_tagged_timeout.argtypes = [i, i, ctypes.c_longlong, ip, ip]
     L.sf_probe_occlusion.argtypes = [vp, i, fp, fp, vp]
     L.sf_probe_illum.argtypes = [vp, i, fp, fp, vp]
     L.sf_probe_wmask.argtypes = [vp, i, i, fp, vp]
@@ -210,6 +211,16 @@ def barrier_timeout_probe(skip_block: int, limit_cycles: int) -> tuple[int, int]
     st, ret = ctypes.c_int(), ctypes.c_int()
     _check(load().sf_probe_barrier_timeout(int(skip_block), int(limit_cycles), ctypes.byref(st), ctypes.byref(ret)),
            "sf_probe_barrier_timeout")
+    return st.value, ret.value
+
+
+def tagged_timeout_probe(mode: int, skip_block: int, limit_cycles: int) -> tuple[int, int]:
+    """(latched status, blocks back) of the self-tagged exchange's waits: mode 0
+    the partial-sum poll, mode 1 a halo word; block skip_block never publishes
+    (-1: all do)."""
+    st, ret = ctypes.c_int(), ctypes.c_int()
+    _check(load().sf_probe_tagged_timeout(int(mode), int(skip_block), int(limit_cycles), ctypes.byref(st),
+                                          ctypes.byref(ret)), "sf_probe_tagged_timeout")
     return st.value, ret.value
 
 

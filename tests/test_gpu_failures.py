@@ -2,9 +2,10 @@
 
 The device-wide waits of the library are bounded: a wait that runs out latches
 a status bit and returns, so a lost block never hangs the GPU. The tests run
-the library's own grid barrier and mbarrier wait with a limit of about a
-millisecond on a condition they control (a block that never arrives, an
-mbarrier that nothing completes), and feed non-finite images, which the
+the library's own grid barrier, the waits of the self-tagged PCG exchange and
+the mbarrier wait with a limit of about a millisecond on a condition they
+control (a block that never arrives or publishes, an mbarrier that nothing
+completes), and feed non-finite images, which the
 solve must report as SF_ERR_NUMERIC and then recover from after sf_reset.
 Nothing here traps, faults or waits without a bound."""
 
@@ -43,6 +44,21 @@ def test_grid_barrier_times_out_when_a_block_never_arrives():
         assert returned == sms - 1  # every waiting block came back
     # the GPU stays usable: the next barrier passes
     assert sf.barrier_timeout_probe(-1, LIMIT) == (sf.OK, sms)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_self_tagged_waits_time_out_when_a_block_never_publishes(mode):
+    """The waits of the self-tagged PCG exchange (kinds 5 and 6): the poll of
+    the partial-sum words (mode 0) and a halo reader's wait for a word (mode
+    1) pass when every block publishes, and run out, latch SF_ERR_TIMEOUT and
+    return in every block when one block never does."""
+    nb = min(torch.cuda.get_device_properties(0).multi_processor_count, 160)
+    assert sf.tagged_timeout_probe(mode, -1, LIMIT) == (sf.OK, nb)
+    for skip in (0, nb - 1):
+        status, returned = sf.tagged_timeout_probe(mode, skip, LIMIT)
+        assert status == sf.ERR_TIMEOUT, status
+        assert returned == nb  # every block came back
+    assert sf.tagged_timeout_probe(mode, -1, LIMIT) == (sf.OK, nb)
 
 
 def test_mbarrier_wait_completes_or_times_out():
