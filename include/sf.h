@@ -86,12 +86,14 @@ enum { SF_FP32 = 0, SF_MIXED_BF16 = 1, SF_MIXED_FP16 = 2 };
 enum { SF_PRESET_FIG2 = 0, SF_PRESET_FIG568 = 1, SF_PRESET_FIG79 = 2 };
 /* Schedule of the PCG solve, per level the first that fits: a staged grid
  * (SF_PCG_AUTO and SF_PCG_PIPELINED only: a cooperative launch over the GPU
- * whose coupling blocks fit in shared memory and whose neighbours' vectors
- * are exchanged as self-tagged words, without memory fences; SF_PCG_AUTO runs
- * the one-reduction form there, SF_PCG_PIPELINED the pipelined form of PCG of
- * Ghysels and Vanroose 2014, which hides the grid reduction's latency behind
- * the matrix-vector product but keeps w = A M r by recurrence, so its
- * rounding drifts further from the textbook loop on ill-conditioned systems),
+ * whose coupling blocks fit in registers or shared memory and whose
+ * neighbours' vectors are exchanged as self-tagged words, without memory
+ * fences; SF_PCG_AUTO runs the one-reduction form there, SF_PCG_PIPELINED
+ * the pipelined form of PCG of Ghysels and Vanroose 2014, which hides the
+ * grid reduction's latency behind the matrix-vector product but keeps
+ * w = A u, s, q and z by recurrence (u = M r is formed), so its rounding
+ * drifts further from the textbook loop: on some frames its fields end a few
+ * 1e-3 px from the FP64 oracle's, where the default stays within 1e-3),
  * SF_PCG_DSM (one cluster, the whole state in distributed shared memory, one
  * barrier per iteration), then a single cluster with vectors in global
  * memory, then a cooperative launch over the GPU. SF_PCG_AUTO and

@@ -1453,9 +1453,17 @@ cudaError_t launch_grid1h(int blocks, const LevelGeom& g, const float* node, con
 //   m = M w, n = A m                    (while the reduction completes)
 //   beta = gamma / gamma_prev, alpha = gamma / (delta - beta gamma / alpha_prev)
 //   z = n + beta z, q = m + beta q, s = w + beta s, p = u + beta p
-//   x += alpha p, r -= alpha s, u -= alpha q, w -= alpha z
-// and keeps s = A p, q = M s, z = A q by recurrence: the iterates of the
-// textbook loop in exact arithmetic, rounded differently. The product needs
+//   x += alpha p, r -= alpha s, u = M r, w -= alpha z
+// and keeps s = A p, q = M s, z = A q and w = A u by recurrence: the
+// iterates of the textbook loop in exact arithmetic, rounded differently.
+// The paper of Ghysels and Vanroose also recurs u -= alpha q; forming
+// u = M r from the recurred r instead (M is diagonal, so it costs nothing)
+// keeps gamma = r.u consistent with r, and measured it halves the drift from
+// the textbook loop on an ill-conditioned system (final energy 4.7e-5 from
+// the FP64 oracle's against 1.1e-4 with the recurrence, 5.9e-5 for k_pcg1h).
+// Its fields still drift further: on a 640x480 frame with the occlusion and
+// illumination maps they end 1.8e-3 px from the oracle's (k_pcg1h: 7e-4), so
+// it is the opt-in SF_PCG_PIPELINED, not the default. The product needs
 // only the neighbours' w, published once per iteration as self-tagged words
 // (as in k_pcg1h); the coupling blocks are staged in shared memory as there.
 // A block publishes its partial sums, forms m over its nodes and halo
@@ -1740,7 +1748,7 @@ __global__ void __launch_bounds__(PT, 1) k_pcg1p(LevelGeom g, const float* __res
                 pr[k][h] = fmaf(beta, pr[k][h], ur[k][h]);
                 xr[k][h] = fmaf(alpha, pr[k][h], xr[k][h]);
                 rr[k][h] = fmaf(-alpha, sr[k][h], rr[k][h]);
-                ur[k][h] = fmaf(-alpha, qr[k][h], ur[k][h]);
+                ur[k][h] = mr[k][h] * rr[k][h]; // u = M r formed, not recurred
                 wr[k][h] = fmaf(-alpha, zr[k][h], wr[k][h]);
             }
         if (i + 2 < iters) { // w_{i+1}, read by iteration i + 1's product
@@ -1898,7 +1906,7 @@ PcgPlan pcg_plan(int G, int sm_count, int mode, int nx)
     // preference: the staged, self-tagged grid (AUTO: the one-reduction form,
     // kind 5, measured faster than kinds 1-4 at every 640x480 level;
     // PIPELINED: kind 6) -> DSM (DSM only) -> cluster with global vectors
-    // (AUTO, DSM, CLUSTER, ONE_REDUCTION, PIPELINED) -> cooperative grid (all)
+    // (all but GRID) -> cooperative grid (all)
     PcgPlan p{1, 1, 0, 0};
     const int maxc = max_cluster_blocks();
     if ((mode == SF_PCG_AUTO || mode == SF_PCG_PIPELINED) && nx > 0) {
@@ -1930,7 +1938,7 @@ PcgPlan pcg_plan(int G, int sm_count, int mode, int nx)
         }
     }
     // otherwise the one-reduction form (measured faster than the textbook loop at every level size)
-    const bool one = mode == SF_PCG_ONE_REDUCTION || mode == SF_PCG_AUTO || mode == SF_PCG_PIPELINED;
+    const bool one = mode != SF_PCG_CLUSTER && mode != SF_PCG_GRID && mode != SF_PCG_DSM;
     if (mode != SF_PCG_GRID) {
         for (int npt : {1, 2, 4}) {
             const int need = (G + NPB * npt - 1) / (NPB * npt);
