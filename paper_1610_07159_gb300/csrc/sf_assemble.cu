@@ -540,7 +540,12 @@ cudaError_t launch_trials(const LevelGeom& g, const void* tex, int prec, const f
 {
     // the full step first: one pixel per thread, the verdict into the control record
     {
+        // one pixel per thread while that is at most four blocks per SM of a
+        // GB300; two beyond (half the partials for the last block to fold:
+        // measured at 640x480 level 0 23 -> 19 us, while the small levels
+        // lose at two)
         int npix = (g.w * g.h + ETHREADS - 1) / ETHREADS;
+        if (npix > 152 * 4) npix = (g.w * g.h + 2 * ETHREADS - 1) / (2 * ETHREADS);
         if (npix > 152 * 8) npix = 152 * 8; // larger levels loop (the partial slots and the last block's fold)
         const int nnode = (g.G + ETHREADS - 1) / ETHREADS;
         SF_TEX_DISPATCH(prec, TT, (k_energy<TT, true><<<npix + nnode, ETHREADS, 0, st>>>(
