@@ -948,7 +948,7 @@ def run_ours(args):
                      "frac_of_measured_fp32_fma": asm_flops / asm_s / fma_flops if asm_ms else None},
         "gather": {"launches": ser[sf.K_GATHER][1], "ms_total": ser[sf.K_GATHER][0],
                    "us_per_launch": 1e3 * ser[sf.K_GATHER][0] / max(ser[sf.K_GATHER][1], 1),
-                   "note": "k_gather_blocks and k_gather_rhs, one event pair around both"},
+                   "note": "k_gather (node blocks, right-hand side, preconditioner and energy in one launch)"},
         "trials": {"launches": ser[sf.K_ENERGY][1], "ms_total": ser[sf.K_ENERGY][0],
                    "us_per_launch": 1e3 * ser[sf.K_ENERGY][0] / max(ser[sf.K_ENERGY][1], 1)},
         "pipelined_pass": {"note": "the same classes inside the level pipeline, where launches of different "

@@ -56,23 +56,18 @@ __device__ __forceinline__ float cell_entry(const float* __restrict__ cell, int 
     return __ldg(cell + (size_t)v * ncx * ncy + cj * ncx + ci);
 }
 
-// The node blocks of the Gauss-Newton system, one thread per (entry, node):
-// entry v = b * 21 + e of node n is the sum of its cells' pair blocks (the
+// Entry v = b * 21 + e of node n of the Gauss-Newton system (k_gather runs
+// one thread per (entry, node)): the sum of its cells' pair blocks (the
 // chain rule of Eq. 7), plus for the node's own block the smoothness
 // (Eq. 14), epipolar (Eqs. 15-17) and magnitude (Eq. 18) rows and for the E
 // and S blocks the smoothness coupling, added in the order gather_node4
 // adds them, so the values are the same bit for bit. Entry-parallel: every
 // thread has a few independent loads, where a node-parallel gather waits on
 // long chains of them.
-__global__ void __launch_bounds__(ETHREADS) k_gather_blocks(LevelGeom g, const float* __restrict__ cell,
-                                                            const float* __restrict__ base,
-                                                            const float* __restrict__ delta,
-                                                            const float* __restrict__ wf, DevParams P,
-                                                            float* __restrict__ node)
+__device__ __forceinline__ float node_value(const LevelGeom& g, const float* __restrict__ cell,
+                                            const float* __restrict__ base, const float* __restrict__ delta,
+                                            const float* __restrict__ wf, const DevParams& P, int v, int n)
 {
-    const int t = blockIdx.x * ETHREADS + threadIdx.x;
-    if (t >= NODE_VALS * g.G) return;
-    const int v = t / g.G, n = t - v * g.G;
     const int b = v / NB, e = v - b * NB;
     const int i = n % g.nx, j = n / g.nx;
     const int ncx = g.ncx, ncy = g.ncy;
@@ -122,27 +117,36 @@ __global__ void __launch_bounds__(ETHREADS) k_gather_blocks(LevelGeom g, const f
     } else {
         acc += cell_entry(cell, ncx, ncy, i - 1, j, pair_idx(1, 2) * NB + e);
     }
-    node[t] = acc;
+    return acc;
 }
 
-// The right-hand side and Jacobi preconditioner, one thread per (component,
-// node) (the cells' part of b plus the prior rows, in gather_node4's order),
-// and the prior energies at the linearisation point (the thread of component
-// 0); the last block to finish forms the step's record from the assembly's
-// and these partials in a fixed order.
-__global__ void __launch_bounds__(ETHREADS) k_gather_rhs(LevelGeom g, const float* __restrict__ cell,
-                                                         const float* __restrict__ base,
-                                                         const float* __restrict__ delta,
-                                                         const float* __restrict__ wf, DevParams P,
-                                                         const float* __restrict__ node, float* __restrict__ rhs,
-                                                         float* __restrict__ minv, float2* __restrict__ gpart,
-                                                         const float2* __restrict__ apart, int n_asm,
-                                                         unsigned* counter, StepCtrl* __restrict__ ctrl, int* status)
+// The node system in one launch of two kinds of blocks. The first nrhs
+// blocks: the right-hand side and Jacobi preconditioner, one thread per
+// (component, node) (the cells' part of b plus the prior rows, in
+// gather_node4's order; the diagonal entry for the preconditioner formed by
+// node_value, as the block threads form it), and the prior energies at the
+// linearisation point (the thread of component 0); the last of them to
+// finish forms the step's record from the assembly's and these partials in a
+// fixed order. The rest: the node blocks, one thread per (entry, node).
+__global__ void __launch_bounds__(ETHREADS) k_gather(LevelGeom g, int nrhs, const float* __restrict__ cell,
+                                                     const float* __restrict__ base, const float* __restrict__ delta,
+                                                     const float* __restrict__ wf, DevParams P,
+                                                     float* __restrict__ node, float* __restrict__ rhs,
+                                                     float* __restrict__ minv, float2* __restrict__ gpart,
+                                                     const float2* __restrict__ apart, int n_asm, unsigned* counter,
+                                                     StepCtrl* __restrict__ ctrl, int* status)
 {
     __shared__ ff sred[6 * (ETHREADS / 32)];
     __shared__ bool last_sh;
-    const int t = blockIdx.x * ETHREADS + threadIdx.x;
     const int G = g.G;
+    if ((int)blockIdx.x >= nrhs) {
+        const int tb = ((int)blockIdx.x - nrhs) * ETHREADS + threadIdx.x;
+        if (tb >= NODE_VALS * G) return;
+        const int v = tb / G, n = tb - v * G;
+        node[tb] = node_value(g, cell, base, delta, wf, P, v, n);
+        return;
+    }
+    const int t = blockIdx.x * ETHREADS + threadIdx.x;
     float es = 0.f, ee = 0.f, em = 0.f;
     if (t < 6 * G) {
         const int u = t / G, n = t - u * G;
@@ -176,7 +180,7 @@ __global__ void __launch_bounds__(ETHREADS) k_gather_rhs(LevelGeom g, const floa
         }
         bb -= P.w_reg * P.w_mag * P.mfl[u >> 1] * du;
         rhs[u * G + n] = bb;
-        const float dg = node[(size_t)sym_idx(u, u) * G + n];
+        const float dg = node_value(g, cell, base, delta, wf, P, sym_idx(u, u), n);
         minv[u * G + n] = dg > 0.f ? 1.f / dg : 1.f;
         if (u == 0) node_prior_energy(g, P, base, delta, nullptr, 0.f, wf, n, es, ee, em);
     }
@@ -187,7 +191,7 @@ __global__ void __launch_bounds__(ETHREADS) k_gather_rhs(LevelGeom g, const floa
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) gpart[q * MAX_PART + blockIdx.x] = make_float2(tb[q].hi, tb[q].lo);
-        last_sh = atom_add_release_gpu(counter, 1u) == gridDim.x - 1;
+        last_sh = atom_add_release_gpu(counter, 1u) == (unsigned)nrhs - 1;
     }
     __syncthreads();
     if (!last_sh) return;
@@ -195,7 +199,7 @@ __global__ void __launch_bounds__(ETHREADS) k_gather_rhs(LevelGeom g, const floa
     {
         const float2* const parts[6] = {apart, apart + MAX_PART, apart + 2 * MAX_PART,
                                         gpart, gpart + MAX_PART, gpart + 2 * MAX_PART};
-        const int nb = (int)gridDim.x;
+        const int nb = nrhs;
         const int cnt[6] = {n_asm, n_asm, n_asm, nb, nb, nb};
         ff f[6];
         ff_block_fixed_sum_n<ETHREADS, 6>(parts, cnt, sred, f);
@@ -490,12 +494,13 @@ void launch_gather(const LevelGeom& g, const float* cell, const float* base, con
                    const DevParams& P, float* node, float* rhs, float* minv, const Scratch& sc, StepCtrl* ctrl,
                    int n_asm_blocks, cudaStream_t st)
 {
-    // the node blocks entry by entry, then the right-hand side, preconditioner and energy component by component
-    const int bblocks = (NODE_VALS * g.G + ETHREADS - 1) / ETHREADS;
-    k_gather_blocks<<<bblocks, ETHREADS, 0, st>>>(g, cell, base, delta, wf, P, node);
+    // one launch: the right-hand side, preconditioner and energy component by component, beside the node blocks
+    // entry by entry
     const int rblocks = (6 * g.G + ETHREADS - 1) / ETHREADS;
-    k_gather_rhs<<<rblocks, ETHREADS, 0, st>>>(g, cell, base, delta, wf, P, node, rhs, minv, sc.gat_part,
-                                               sc.asm_part, n_asm_blocks, sc.counters + 0, ctrl, sc.status);
+    const int bblocks = (NODE_VALS * g.G + ETHREADS - 1) / ETHREADS;
+    k_gather<<<rblocks + bblocks, ETHREADS, 0, st>>>(g, rblocks, cell, base, delta, wf, P, node, rhs, minv,
+                                                     sc.gat_part, sc.asm_part, n_asm_blocks, sc.counters + 0, ctrl,
+                                                     sc.status);
 }
 
 void launch_energy(const LevelGeom& g, const void* tex, int prec, const float* base, const float* delta, const float* x,
