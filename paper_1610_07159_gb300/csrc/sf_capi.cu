@@ -298,7 +298,7 @@ int enqueue_level(sf_ctx* c, int l, const LevelIO& io, cudaStream_t st, int& nl)
                                          c->pcg_part[l], c->bar + l, c->status, P.pcg_iters[l], 0, st);
         prof_mark(c, SF_K_PCG, false, st);
         if (e != cudaSuccess) return check_cuda(e);
-        nl += 4; // assembly, the two gather passes, the linear solve
+        nl += 3; // assembly, gather, the linear solve
         prof_mark(c, SF_K_ENERGY, true, st);
         e = launch_trials(g, io.tex, P.precision, b.base, b.delta, b.x, b.wf, c->dp[l], Wst, sc,
                           c->bar + SF_MAX_LEVELS + l, ctrl, P.max_backtracks, c->trial_blocks[l], st, M);
