@@ -987,12 +987,14 @@ cudaError_t launch_cluster1(int blocks, const LevelGeom& g, const float* node, c
 // and reads again while a word is stale. Nothing has to order the vectors
 // before the partial sums, so the exchange needs no memory fence.
 //
-// Shared memory. A block owns NPT segments of NPB consecutive nodes (segment
-// k starts at n0_k); the stencil of its nodes reaches hw = nx + 1 nodes to
-// either side. At the start the block copies the coupling blocks of its nodes
-// and of the hw nodes before each segment (they do not change during the
-// solve) into shared memory, coalesced, so the matrix-vector product reads no
-// global memory. Per iteration it forms u = M (r - alpha (w + beta s)) once
+// Registers and shared memory. A block owns NPT segments of NPB consecutive
+// nodes (segment k starts at n0_k); the stencil of its nodes reaches
+// hw = nx + 1 nodes to either side. The coupling blocks do not change during
+// the solve: with one node per four-lane group (NPT = 1) each lane loads its
+// slots' blocks into registers once (SlotRegs); with more, the block copies
+// the blocks of its nodes and of the hw nodes before each segment into shared
+// memory at the start, coalesced. Either way the matrix-vector product reads
+// no global memory. Per iteration it forms u = M (r - alpha (w + beta s)) once
 // per node of [n0_k - hw, n0_k + NPB + hw) in shared memory: owned nodes from
 // the owners' registers (the same rounding), the 2 hw nodes on either side
 // from their published words, read coalesced. While warp 0 polls the other
@@ -1012,9 +1014,9 @@ cudaError_t launch_cluster1(int blocks, const LevelGeom& g, const float* node, c
 // block's partial sums of iteration i, which each block forms after reading
 // the values of iteration i: a reader never loses a value it still needs.
 // pubw holds [2 parities][r, w, s][6][G] words; the dynamic shared memory
-// [NPT][NODE_VALS][ls] floats of blocks (ls >= NPB + hw, padded so that the
-// four block rows a warp reads at once fall in different banks), then
-// [NPT][6][NPB + 2 hw] floats of u.
+// (NPT > 1) [NPT][NODE_VALS][ls] floats of blocks (ls >= NPB + hw, padded so
+// that the four block rows a warp reads at once start in different banks),
+// then [NPT][6][NPB + 2 hw] floats of u (NPT = 1: the u array alone).
 // ---------------------------------------------------------------------------
 constexpr int HPF = 5;       // halo entries per thread and round
 constexpr int HFT = PT - 32; // threads that fetch the halo during the poll (warps 1..)
@@ -1465,7 +1467,7 @@ cudaError_t launch_grid1h(int blocks, const LevelGeom& g, const float* node, con
 // illumination maps they end 1.8e-3 px from the oracle's (k_pcg1h: 7e-4), so
 // it is the opt-in SF_PCG_PIPELINED, not the default. The product needs
 // only the neighbours' w, published once per iteration as self-tagged words
-// (as in k_pcg1h); the coupling blocks are staged in shared memory as there.
+// (as in k_pcg1h); the coupling blocks sit in registers or shared memory as there.
 // A block publishes its partial sums, forms m over its nodes and halo
 // (waiting for late neighbours' w), runs the product, and only then polls the
 // other blocks' partials, which have had the product's duration to arrive.
