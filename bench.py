@@ -78,11 +78,11 @@ def level_sizes():
     return out
 
 
-def pcg_bytes_per_frame(model="survey"):
+def pcg_bytes_per_frame(model="per_node_860"):
     """Algorithmic PCG bytes of one frame: the 860 B/node/iteration model
-    ("survey"), or the own count of the one-reduction kernel ("one_reduction"),
+    ("per_node_860"), or the own count of the one-reduction kernel ("one_reduction"),
     of the staged one ("staged") or of the pipelined one ("pipelined")."""
-    if model == "survey":
+    if model == "per_node_860":
         return sum(GN * nx * ny * PCG * PCG_MODEL_ITER_B for _, _, nx, ny in level_sizes())
     if model in ("staged", "pipelined"):
         words = 144 if model == "staged" else 48
@@ -929,7 +929,7 @@ def run_ours(args):
     pcg_ms, pcg_n = ser[sf.K_PCG]
     asm_ms, asm_n = ser[sf.K_ASSEMBLE]
     pcg_s, asm_s = pcg_ms / 1e3, asm_ms / 1e3
-    pcg_model_bytes = pcg_bytes_per_frame("survey") * NFRAMES
+    pcg_model_bytes = pcg_bytes_per_frame("per_node_860") * NFRAMES
     pcg_kern = PCG_KERNEL.get(pcg_schedules[0][0], "k_pcg1")
     own_model = {"k_pcg1p": "pipelined", "k_pcg1h": "staged"}.get(pcg_kern, "one_reduction")
     pcg_kernel_bytes = pcg_bytes_per_frame(own_model) * NFRAMES
