@@ -106,6 +106,11 @@ struct sf_ctx {
     cudaStream_t vstream[SF_MAX_LEVELS]{};
     cudaEvent_t vev[SF_MAX_LEVELS]{};
     cudaEvent_t vfork = nullptr;
+    // host outputs: level 0's fields leave through their own stream, so the
+    // device-to-host copy of frame f overlaps the next frames' levels
+    cudaStream_t vcopy = nullptr;
+    cudaEvent_t vdone0 = nullptr;                        // level 0 of a frame done (reused per frame)
+    cudaEvent_t vcopied[SF_MAX_LEVELS]{};                // [ring slot] its staged output copied out
 };
 
 namespace {
@@ -140,6 +145,10 @@ void free_ctx(sf_ctx* c)
         if (c->vev[l]) cudaEventDestroy(c->vev[l]);
     }
     if (c->vfork) cudaEventDestroy(c->vfork);
+    if (c->vcopy) cudaStreamDestroy(c->vcopy);
+    if (c->vdone0) cudaEventDestroy(c->vdone0);
+    for (cudaEvent_t e : c->vcopied)
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_begin) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_end) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
@@ -356,7 +365,9 @@ int enqueue_frame(sf_ctx* c, cudaStream_t st)
 // s - (L - 1 - l), levels on their own streams, with a join between steps.
 // Level l of frame f needs level l + 1 of frame f (previous step) and level l
 // of frame f - 1 (previous step), so the result equals the sequential order.
-// host_in / host_out: stage frames from and to host memory through the ring.
+// host_in / host_out: stage frames from and to host memory through the ring;
+// a frame's fields are copied out on the copy stream after its level 0, and
+// level 0 writes a ring slot again only after that slot's copy has finished.
 int enqueue_video(sf_ctx* c, const float* frames, const float* host_in, int n, float* outs, float* host_out,
                   cudaStream_t st)
 {
@@ -367,6 +378,7 @@ int enqueue_video(sf_ctx* c, const float* frames, const float* host_in, int n, f
     c->nprof = 0;
     if (cudaEventRecord(c->vfork, st) != cudaSuccess) return check_cuda(cudaGetLastError());
     for (int l = 0; l < L; ++l) cudaStreamWaitEvent(c->vstream[l], c->vfork, 0);
+    if (host_out) cudaStreamWaitEvent(c->vcopy, c->vfork, 0);
     if (f0 > 0)
         for (int l = 0; l < L; ++l) {
             const size_t bytes = (size_t)6 * c->geo[l].G * sizeof(float);
@@ -400,6 +412,8 @@ int enqueue_video(sf_ctx* c, const float* frames, const float* host_in, int n, f
             const bool has_c = l < L - 1;
             float* out = nullptr;
             if (l == 0) out = host_out ? c->vout[slot] : outs + (size_t)fl * G6;
+            // the slot's previous frame has left it (a no-op for an event not recorded yet)
+            if (l == 0 && host_out) cudaStreamWaitEvent(bs, c->vcopied[slot], 0);
             // the maps of frame fg pass from level l + 1 to level l in the pipeline's previous step; the
             // next frame's are written meanwhile into the buffer of the other parity
             LevelIO io{c->ring_tex[slot][l], c->lv[l].vis[fg & 1], c->lv[l].illum[fg & 1],
@@ -410,13 +424,22 @@ int enqueue_video(sf_ctx* c, const float* frames, const float* host_in, int n, f
                        (l == L - 1 && fl == 0) ? c->pending_init : 0};
             int rc = enqueue_level(c, l, io, bs, nl);
             if (rc) return rc;
-            if (l == 0 && host_out)
-                cudaMemcpyAsync(host_out + (size_t)fl * G6, out, G6 * sizeof(float), cudaMemcpyDeviceToHost, bs);
+            if (l == 0 && host_out) {
+                cudaEventRecord(c->vdone0, bs);
+                cudaStreamWaitEvent(c->vcopy, c->vdone0, 0);
+                cudaMemcpyAsync(host_out + (size_t)fl * G6, out, G6 * sizeof(float), cudaMemcpyDeviceToHost,
+                                c->vcopy);
+                cudaEventRecord(c->vcopied[slot], c->vcopy);
+            }
         }
     }
     for (int l = 0; l < L; ++l) {
         cudaEventRecord(c->vev[l], c->vstream[l]);
         cudaStreamWaitEvent(st, c->vev[l], 0);
+    }
+    if (host_out) {
+        cudaEventRecord(c->vdone0, c->vcopy);
+        cudaStreamWaitEvent(st, c->vdone0, 0);
     }
     // hand the last frame's state back to the single-frame path
     const int fz = f0 + n - 1;
@@ -761,6 +784,10 @@ sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_p
         for (int l = 0; l < levels && sok; ++l)
             sok = cudaStreamCreateWithFlags(&c->vstream[l], cudaStreamNonBlocking) == cudaSuccess &&
                   cudaEventCreateWithFlags(&c->vev[l], cudaEventDisableTiming) == cudaSuccess;
+        sok = sok && cudaStreamCreateWithFlags(&c->vcopy, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&c->vdone0, cudaEventDisableTiming) == cudaSuccess;
+        for (int r = 0; r < c->ring && sok; ++r)
+            sok = cudaEventCreateWithFlags(&c->vcopied[r], cudaEventDisableTiming) == cudaSuccess;
     }
     if (!sok || cudaDeviceSynchronize() != cudaSuccess) {
         cudaGetLastError();

@@ -360,6 +360,13 @@ def test_video_pipeline_equals_frame_by_frame():
     host_out = torch.empty((n, 6, 30, 40), dtype=torch.float32).pin_memory()
     vid2.solve_video_host(torch.from_numpy(v).pin_memory(), host_out)
     assert np.array_equal(host_out.numpy(), ref)
+    # in two calls: ring slots reused within a call (6 frames, 3 slots) and across calls
+    vid3 = sf.Solver(320, 240, 8, 3, sp_v)
+    host_a = torch.empty((4, 6, 30, 40), dtype=torch.float32).pin_memory()
+    host_b = torch.empty((2, 6, 30, 40), dtype=torch.float32).pin_memory()
+    vid3.solve_video_host(torch.from_numpy(v[:4]).pin_memory(), host_a)
+    vid3.solve_video_host(torch.from_numpy(v[4:]).pin_memory(), host_b)
+    assert np.array_equal(np.concatenate([host_a.numpy(), host_b.numpy()]), ref)
     plain = sf.Solver(320, 240, 8, 3, sp)
     assert plain.L.sf_solve_video(plain.ctx, 1, 1, 1, None) == sf.ERR_STATE
 
