@@ -23,6 +23,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "sf_launch.h"
 #include "sf_stages.cuh"
@@ -1859,10 +1860,16 @@ int max_coop_blocks(int sm_count)
     return per_sm * sm_count;
 }
 
+// per device, cached under a lock (the query sets a function attribute)
 int max_cluster_blocks()
 {
-    static int cached = -1;
-    if (cached > 0) return cached;
+    static std::mutex mu;
+    static int cached[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cached[dev] > 0) return cached[dev];
     auto kern = k_pcg<1, ClusterSync>;
     int n = 8;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
@@ -1880,8 +1887,8 @@ int max_cluster_blocks()
         if (cudaOccupancyMaxPotentialClusterSize(&m, kern, &cfg) == cudaSuccess && m > 0) n = m;
     }
     cudaGetLastError();
-    cached = n > 16 ? 16 : n;
-    return cached;
+    cached[dev] = n > 16 ? 16 : n;
+    return cached[dev];
 }
 
 size_t smem_optin()
