@@ -53,6 +53,13 @@ MUTANTS = {
         "*dpx = clx ? 0.0 : (1 - fy) * (p10 - p00) + fy * (p11 - p01);",
         "*dpx = clx ? 0.0 : fy * (p10 - p00) + (1 - fy) * (p11 - p01);"),
     "Jacobi preconditioner dropped": ("Minv[n * 6 + u] = d > 0.0 ? 1.0 / d : 1.0;", "Minv[n * 6 + u] = 1.0;"),
+    "Jacobi preconditioner as diag(A) instead of its inverse": ("Minv[n * 6 + u] = d > 0.0 ? 1.0 / d : 1.0;",
+                                                                 "Minv[n * 6 + u] = d > 0.0 ? d : 1.0;"),
+    "PCG beta inverted": ("double beta = rz_new / rz;", "double beta = rz / rz_new;"),
+    "PCG direction from the unpreconditioned residual": (
+        "for (int a = 0; a < N; ++a) pv[a] = z[a] + beta * pv[a];",
+        "for (int a = 0; a < N; ++a) pv[a] = r[a] + beta * pv[a];"),
+    "PCG step length over p.p": ("double alpha = rz / pq;", "double alpha = rz / dot(N, pv, pv);"),
     "Schwarz residual sign": ("for (int a = 0; a < N; ++a) r[a] = b[a] - r[a];",
                               "for (int a = 0; a < N; ++a) r[a] = b[a] + r[a];"),
     "Schwarz update not restricted to the tile": (

@@ -422,6 +422,34 @@ def test_pcg_matches_dense_cholesky_and_decreases_model():
     assert model10[-1] >= m_star - 1e-9 * abs(m_star)
 
 
+def test_pcg_iterate_is_the_preconditioned_krylov_minimiser():
+    """Section 5.1 solves each step by Jacobi-preconditioned CG from x = 0. In
+    exact arithmetic its k-th iterate is the point of the Krylov space
+    span{M b, (M A) M b, ..., (M A)^(k-1) M b}, M = diag(A)^-1, closest to the
+    solution in the A-norm. That optimality property fixes every iterate
+    without any of CG's own recurrences: here it is formed with a dense
+    orthonormal basis of the space and the projected system, and the oracle's
+    iterates must match it for k = 1 .. 8 (a wrong preconditioner, step length
+    or direction update gives other points of other spaces)."""
+    lv = _tiny_level()
+    rng = np.random.default_rng(21)
+    base, delta = _smooth_state(lv, rng)
+    A, b, _, _ = O.assemble(lv, base, delta, 1.0 + rng.random(lv.G), O.Params(eps_p=0.3))
+    Ad = _dense(A, lv.nx, lv.ny)
+    bv = b.reshape(-1)
+    d = np.diag(Ad).copy()
+    Minv = np.where(d > 0, 1.0 / np.where(d > 0, d, 1.0), 1.0)
+    K = [Minv * bv]
+    for k in range(1, 9):
+        V, _ = np.linalg.qr(np.stack(K, axis=1))
+        y = np.linalg.solve(V.T @ Ad @ V, V.T @ bv)
+        x_star = V @ y
+        x, _, its = O.pcg(lv.nx, lv.ny, A, b, k)
+        assert its == k
+        np.testing.assert_allclose(x.reshape(-1), x_star, rtol=0, atol=1e-9 * np.max(np.abs(x_star)))
+        K.append(Minv * (Ad @ K[-1]))
+
+
 # --------------------------------------------------------------------------- #
 # hierarchy and temporal transfer
 # --------------------------------------------------------------------------- #
