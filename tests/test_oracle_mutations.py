@@ -60,6 +60,21 @@ MUTANTS = {
         "for (int a = 0; a < N; ++a) pv[a] = z[a] + beta * pv[a];",
         "for (int a = 0; a < N; ++a) pv[a] = r[a] + beta * pv[a];"),
     "PCG step length over p.p": ("double alpha = rz / pq;", "double alpha = rz / dot(N, pv, pv);"),
+    "backtracking by quarters": ("++bt, t *= 0.5) {", "++bt, t *= 0.25) {"),
+    "temporal transfer along the stereo field": ("double X = (double)(i * s) - 2.0 * T_prev[2 * G + n];",
+                                                 "double X = (double)(i * s) - 2.0 * T_prev[0 * G + n];"),
+    "level F without the Frobenius rescale": ("for (int a = 0; a < 9; ++a) Fl[a] *= sqrt(n0 / n1);",
+                                              "for (int a = 0; a < 9; ++a) Fl[a] *= 1.0;"),
+    "smoothness system weight from one node": (
+        "double c = p->w_reg * p->w_smooth * (wf[n] + wf[m]) * wfl[fld];",
+        "double c = p->w_reg * p->w_smooth * 2.0 * wf[n] * wfl[fld];"),
+    "magnitude system weight from the smoothness weights": ("double cm = p->w_reg * p->w_mag * mfl[fld];",
+                                                            "double cm = p->w_reg * p->w_mag * wfl[fld];"),
+    "epipolar pair of time 1 with the wrong left image": ("int il = tt == 0 ? 0 : 2, ir = tt == 0 ? 1 : 3;",
+                                                          "int il = tt == 0 ? 0 : 1, ir = tt == 0 ? 1 : 3;"),
+    "F transposed in the epipolar product": (
+        "Fr[a] = Fl[a * 3 + 0] * rr[0] + Fl[a * 3 + 1] * rr[1] + Fl[a * 3 + 2] * rr[2];",
+        "Fr[a] = Fl[0 * 3 + a] * rr[0] + Fl[1 * 3 + a] * rr[1] + Fl[2 * 3 + a] * rr[2];"),
     "Schwarz residual sign": ("for (int a = 0; a < N; ++a) r[a] = b[a] - r[a];",
                               "for (int a = 0; a < N; ++a) r[a] = b[a] + r[a];"),
     "Schwarz update not restricted to the tile": (

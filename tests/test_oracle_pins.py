@@ -756,3 +756,38 @@ def test_backtracking_safeguard_is_exercised_and_keeps_energy_monotone():
     for st in steps:
         assert st[1] <= st[0]
         assert st[2] in (0.0, 1.0, 0.5, 0.25, 0.125, 0.0625)
+
+
+def test_backtracking_takes_the_first_halving_that_does_not_raise_the_energy():
+    """C18: a step takes the first t of 1, 1/2, 1/4, 1/8, 1/16 with E(delta + t x; W) <= E(delta; W), with
+    W taken at the step's linearisation point. On the overshooting scene above, each step is rebuilt from the state
+    the solve reached before it (a solve with fewer steps), its energies at those t are evaluated, and the t (and
+    accepted energy) the solve recorded must be the first that passes."""
+    q = scenes.random_quadruple(48, 40, 1, sigma=0.01)
+    kw = dict(pcg_iters=(30,) * 8, m_s=1e-4, m_m=1e-4, m_d=1e-4, w_s=0.1, w_m=0.1, w_d=0.1,
+              robust_mode=O.SQRT_PAPER)
+    lv = O.Level(O.level_planes(O.pyramid(q, 1)[0]), 4, 0)
+    p = O.Params(gn_iters=(6,) * 8, **kw)
+    base = np.zeros(6 * lv.G)
+    wf = O.feature_weights(lv, base, p)
+    full = O.solve_frame(q, 4, 1, p)
+    checked = 0
+    for g in range(6):
+        st = full.step(0, g)
+        if not 0.0 < st[2] < 1.0:
+            continue
+        delta = (O.solve_frame(q, 4, 1, O.Params(gn_iters=(g,) * 8, **kw)).deltas(0).reshape(-1) if g else
+                 np.zeros(6 * lv.G))
+        A, b, E0, W = O.assemble(lv, base, delta, wf, p)
+        assert abs(E0 - st[0]) <= 1e-12 * abs(E0)
+        x, _, _ = O.pcg(lv.nx, lv.ny, A, b, 30)
+        x = x.T.reshape(-1)  # [G, 6] -> component-major like delta
+        t_first, e_first = 0.0, E0
+        for t in (1.0, 0.5, 0.25, 0.125, 0.0625):
+            Et, _, _ = O.energy(lv, base, delta + t * x, wf, p, W)
+            if Et <= E0:
+                t_first, e_first = t, Et
+                break
+        assert st[2] == t_first and abs(st[1] - e_first) <= 1e-12 * abs(e_first), (g, st[:3], t_first)
+        checked += 1
+    assert checked > 0
