@@ -72,6 +72,18 @@ MUTANTS = {
                                                             "double cm = p->w_reg * p->w_mag * wfl[fld];"),
     "epipolar pair of time 1 with the wrong left image": ("int il = tt == 0 ? 0 : 2, ir = tt == 0 ? 1 : 3;",
                                                           "int il = tt == 0 ? 0 : 1, ir = tt == 0 ? 1 : 3;"),
+    "halfway image as half the sum": ("    return 0.25 * acc;\n}\n\n/* ----", "    return 0.5 * acc;\n}\n\n/* ----"),
+    "structure tensor one pixel off the node": ("int qx = i * s + dx, qy = j * s + dy;",
+                                                "int qx = i * s + dx + 1, qy = j * s + dy;"),
+    "gradient IRLS weight without the 1/2": ("double og = 0.5 * p->w_grad * psi_grad_coef(",
+                                             "double og = 1.0 * p->w_grad * psi_grad_coef("),
+    "prolongation reads row i/2 for j": ("2.0 * grid_sample(nxc, nyc, Tc + c * Gc, 0.5 * i, 0.5 * j);",
+                                         "2.0 * grid_sample(nxc, nyc, Tc + c * Gc, 0.5 * i, 0.5 * i);"),
+    "temporal transfer sampled at half the y scale": (
+        "grid_sample(nx, ny, delta_prev + c * G, X / s, Y / s);",
+        "grid_sample(nx, ny, delta_prev + c * G, X / s, Y / (2 * s));"),
+    "gradient term weighted by w_photo in E": ("return p->w_photo * Ep + p->w_grad * Eg + p->w_reg",
+                                               "return p->w_photo * Ep + p->w_photo * Eg + p->w_reg"),
     "F transposed in the epipolar product": (
         "Fr[a] = Fl[a * 3 + 0] * rr[0] + Fl[a * 3 + 1] * rr[1] + Fl[a * 3 + 2] * rr[2];",
         "Fr[a] = Fl[0 * 3 + a] * rr[0] + Fl[1 * 3 + a] * rr[1] + Fl[2 * 3 + a] * rr[2];"),
