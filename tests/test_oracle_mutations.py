@@ -9,6 +9,7 @@ mistakes live only in temporary copies; the oracle itself is not touched.
 
 import concurrent.futures as cf
 import os
+import shutil
 import subprocess
 import sys
 
@@ -114,6 +115,42 @@ MUTANTS = {
 }
 
 
+# planted mistakes in oracle/net.py (the warm-start network), run against tests/test_oracle_net.py
+NET_MUTANTS = {
+    "input not centred": ("a = np.asarray(imgs, dtype=np.float64) - 0.5", "a = np.asarray(imgs, dtype=np.float64) - 0.0"),
+    "output size rounded down": ("return (n + stride - 1) // stride", "return n // stride"),
+    "loss gradient without the factor 2": ("g = 2.0 * r / r.size", "g = r / r.size"),
+    "input gradient through the flipped kernel": (
+        'dxp[sl] += np.einsum("bohw,oc->bchw", dy, w[:, :, u, v])',
+        'dxp[sl] += np.einsum("bohw,oc->bchw", dy, w[:, :, 2 - u, 2 - v])'),
+    "ReLU gate on the layer's input instead of its output": ("g = g * (pre[k] > 0.0)", "g = g * (acts[k].sum() > 0.0)"),
+    "Adam without bias correction": ("mh = mm / (1.0 - beta1 ** t)", "mh = mm"),
+    "Adam eps inside the square root": ("x - lr * mh / (np.sqrt(vh) + eps)", "x - lr * mh / np.sqrt(vh + eps)"),
+}
+NET_SRC = os.path.join(ROOT, "oracle", "net.py")
+
+
+def _run_net_mutant(name, tmpdir):
+    """A copy of the oracle package with the mistake planted in net.py, and the
+    network pins run against it from a tree of their own."""
+    text, planted = NET_MUTANTS[name]
+    src = open(NET_SRC).read()
+    assert src.count(text) == 1, f"{name}: anchor text not unique in net.py"
+    tag = "".join(ch if ch.isalnum() else "_" for ch in name)
+    top = os.path.join(tmpdir, "net_" + tag)
+    os.makedirs(os.path.join(top, "oracle"))
+    os.makedirs(os.path.join(top, "tests"))
+    with open(os.path.join(top, "oracle", "net.py"), "w") as f:
+        f.write(src.replace(text, planted))
+    shutil.copy(os.path.join(ROOT, "oracle", "__init__.py"), os.path.join(top, "oracle", "__init__.py"))
+    for fn in ("conftest.py", "test_oracle_net.py"):
+        shutil.copy(os.path.join(ROOT, "tests", fn), os.path.join(top, "tests", fn))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(top, "tests", "test_oracle_net.py"), "-x", "-q",
+                        "-p", "no:cacheprovider"], capture_output=True, text=True, env=env, cwd=top)
+    return r.returncode, r.stdout[-400:]
+
+
 def _run_mutant(name, tmpdir):
     text, planted = MUTANTS[name]
     src = open(SRC).read()
@@ -140,6 +177,26 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
     # a mutant must fail a test, not break the test run itself
     broken = [n for n, (rc, out) in results.items() if rc not in (1,)]
     assert not broken, {n: results[n][1] for n in broken}
+
+
+def test_every_planted_network_mistake_fails_a_pin(tmp_path):
+    names = sorted(NET_MUTANTS)
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        results = dict(zip(names, ex.map(lambda n: _run_net_mutant(n, str(tmp_path)), names)))
+    missed = [n for n, (rc, _) in results.items() if rc == 0]
+    assert not missed, f"network mutants that pass every pin: {missed}"
+    broken = [n for n, (rc, out) in results.items() if rc not in (1,)]
+    assert not broken, {n: results[n][1] for n in broken}
+
+
+def test_the_unmutated_network_copy_passes(tmp_path):
+    """The network harness itself: an unchanged copy passes every network pin."""
+    NET_MUTANTS["(unchanged)"] = ("import numpy as np", "import numpy as np")
+    try:
+        rc, out = _run_net_mutant("(unchanged)", str(tmp_path))
+    finally:
+        del NET_MUTANTS["(unchanged)"]
+    assert rc == 0, out
 
 
 def test_the_unmutated_copy_passes(tmp_path):

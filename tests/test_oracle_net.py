@@ -58,6 +58,18 @@ def test_network_shapes():
     assert y.shape == (3,) + N.OUT_SHAPE
 
 
+def test_mid_grey_input_gives_zero_through_a_network_without_biases():
+    """The input is centred (I - 1/2): a network whose biases are all zero maps
+    a uniform mid-grey quadruple to exactly zero whatever its weights (every
+    layer is linear in its input up to ReLU, which keeps zero), and any other
+    grey level to something non-zero."""
+    p = [(w, np.zeros_like(b)) for w, b in N.init_params(7)]
+    y, _ = N.forward(p, np.full((2,) + N.IN_SHAPE, 0.5))
+    assert np.all(y == 0.0)
+    y1, _ = N.forward(p, np.full((1,) + N.IN_SHAPE, 0.8))
+    assert np.max(np.abs(y1)) > 0.0
+
+
 def test_loss_gradient_by_finite_differences():
     rng = np.random.default_rng(3)
     p = N.init_params(4)
