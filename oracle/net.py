@@ -28,7 +28,8 @@ with xp the input padded by one zero on every side, output size ceil(n / s).
 
 Parity status: pinned (tests/test_oracle_net.py): the convolution against
 scipy.signal.correlate2d, the backward pass and the whole loss gradient by
-central finite differences, Adam by its closed form on constant gradients.
+central finite differences, Adam by its closed form on constant gradients,
+the input centring by a zero-bias network mapping mid-grey to zero.
 """
 
 from __future__ import annotations
