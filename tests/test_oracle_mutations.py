@@ -2,9 +2,12 @@
 
 Each case plants one mistake in a copy of oracle/sfo.c (a wrong sign, index,
 pairing, weight, dropped term, misplaced block, ...), builds the copy on the
-CPU, and runs the pin tests of tests/test_oracle_pins.py and
-tests/test_oracle_maps.py against it through the SFO_LIB override: every mutant must fail at least one pin. The planted
+CPU, and runs the pin tests of tests/test_oracle_pins.py,
+tests/test_oracle_maps.py and tests/test_oracle_replay.py against it through
+the SFO_LIB override: every mutant must fail at least one pin. The planted
 mistakes live only in temporary copies; the oracle itself is not touched.
+Mistakes planted in oracle/net.py run against tests/test_oracle_net.py from a
+copied tree of their own.
 """
 
 import concurrent.futures as cf
@@ -17,7 +20,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "sfo.c")
-PIN_FILES = [os.path.join(ROOT, "tests", f) for f in ("test_oracle_pins.py", "test_oracle_maps.py")]
+PIN_FILES = [os.path.join(ROOT, "tests", f) for f in ("test_oracle_pins.py", "test_oracle_maps.py", "test_oracle_replay.py")]
 
 # name -> (text in sfo.c, planted replacement); each text occurs exactly once
 MUTANTS = {
@@ -85,6 +88,11 @@ MUTANTS = {
         "grid_sample(nx, ny, delta_prev + c * G, X / s, Y / (2 * s));"),
     "gradient term weighted by w_photo in E": ("return p->w_photo * Ep + p->w_grad * Eg + p->w_reg",
                                                "return p->w_photo * Ep + p->w_photo * Eg + p->w_reg"),
+    "given W ignored": ("int Wi = Win ? Win[y * w + x] : outlier_weight(e, p->eps_p);",
+                        "int Wi = outlier_weight(e, p->eps_p);"),
+    "W disagreement margin not measured from eps_p": (
+        "if (fabs(mx - p->eps_p) > *margin) *margin = fabs(mx - p->eps_p);", "if (mx > *margin) *margin = mx;"),
+    "given cell decision ignored": ("    if (gx >= 0) {", "    if (gx >= 0 && 0) {"),
     "F transposed in the epipolar product": (
         "Fr[a] = Fl[a * 3 + 0] * rr[0] + Fl[a * 3 + 1] * rr[1] + Fl[a * 3 + 2] * rr[2];",
         "Fr[a] = Fl[0 * 3 + a] * rr[0] + Fl[1 * 3 + a] * rr[1] + Fl[2 * 3 + a] * rr[2];"),
