@@ -20,7 +20,10 @@ no fences), except that the barrier lands all of a block's stores first. Per
 iteration a block reads its two neighbours' words, forms its next value from
 them, its own value and the previous iteration's total, publishes it, and
 takes part in the tagged partial-sum reduction of the new values. Launches
-of different lengths run back to back on the same buffers. The test checks every
+of different lengths run back to back on the same buffers. As k_pcg1h's warps
+1.. do while warp 0 polls, a block may fetch the next iteration's neighbour
+words between publishing its partial sum and reading the total (chosen at
+random per iteration). The test checks every
 block's values against a sequential evaluation and that nothing deadlocks,
 and that three planted mistakes are caught: one vector buffer instead of
 two, buffer 1 not cleared, and no barrier between the clear and the
@@ -46,10 +49,13 @@ def _reference(v0, K):
     return out
 
 
-def _block(b, nb, K, v0, words, nbuf, slots, results, barrier, clear):
+def _block(b, nb, K, v0, words, nbuf, slots, results, barrier, clear, early=None):
     """One block over one launch: initial words, clear, barrier, K iterations.
     A store is yielded as ("st", array, index, word) and lands when the
-    scheduler commits it; loads read what has landed."""
+    scheduler commits it; loads read what has landed. early: a random.Random
+    that decides per iteration whether the block fetches the next iteration's
+    neighbour words (tag i + 2) before its poll of the partial sums, as
+    k_pcg1h's warps 1.. do while warp 0 polls, or after it (None: after)."""
     yield ("st", words[0], b, (1, v0[b]))
     if clear:
         for s in range(1, nbuf):
@@ -61,21 +67,32 @@ def _block(b, nb, K, v0, words, nbuf, slots, results, barrier, clear):
         while barrier["arrived"] < barrier["target"]:
             yield ("wait",)
     own, total = v0[b], sum(v0) % 1000003
-    for i in range(K):
-        buf = i % nbuf
-        vals = {}
+    fetched = None
+
+    def fetch(vals, buf, want):
         for c in ((b - 1) % nb, (b + 1) % nb):
             while True:  # a stale word is read again
                 tag, val = words[buf][c]
                 yield ("ld",)
-                if tag == i + 1:
+                if tag == want:
                     vals[c] = val
                     break
+
+    for i in range(K):
+        buf = i % nbuf
+        if fetched is None:
+            vals = {}
+            yield from fetch(vals, buf, i + 1)
+        else:
+            vals, fetched = fetched, None
         own = _next_value(vals[(b - 1) % nb], own, vals[(b + 1) % nb], total)
         yield ("st", words[(i + 1) % nbuf], b, (i + 2, own))
         # the tagged partial sums (two slots by tag parity, as allreduce2_tagged)
         k = i + 1
         yield ("st", slots[k % 2], b, (k, own))
+        if early is not None and i + 1 < K and early.random() < 0.5:
+            fetched = {}
+            yield from fetch(fetched, (i + 1) % nbuf, i + 2)
         while True:
             seen, ready = [], True
             for c in range(nb):
@@ -89,7 +106,7 @@ def _block(b, nb, K, v0, words, nbuf, slots, results, barrier, clear):
         results[b].append(own)
 
 
-def _run(nb, Ks, seed, nbuf=2, clear=True, barrier=True, max_steps=400000, land=0.35):
+def _run(nb, Ks, seed, nbuf=2, clear=True, barrier=True, max_steps=400000, land=0.35, early=False):
     """Launches of Ks[0], Ks[1], ... iterations back to back on the same buffers
     (a solve that stops early leaves low tags for the next one to meet).
     Stores of one block land in any order, as relaxed stores to different
@@ -102,7 +119,8 @@ def _run(nb, Ks, seed, nbuf=2, clear=True, barrier=True, max_steps=400000, land=
         v0 = [rng.randint(0, 1000) for _ in range(nb)]
         results = [[] for _ in range(nb)]
         bar = {"arrived": 0, "target": nb} if barrier else None
-        gens = [_block(b, nb, K, v0, words, nbuf, slots, results, bar, clear) for b in range(nb)]
+        gens = [_block(b, nb, K, v0, words, nbuf, slots, results, bar, clear,
+                       random.Random(rng.random()) if early else None) for b in range(nb)]
         pending = [[] for _ in range(nb)]
         live, steps = list(range(nb)), 0
         while live or any(pending):
@@ -134,11 +152,12 @@ def _run(nb, Ks, seed, nbuf=2, clear=True, barrier=True, max_steps=400000, land=
     return outs, wants
 
 
+@pytest.mark.parametrize("early", [False, True])
 @pytest.mark.parametrize("land", [0.05, 0.35])
 @pytest.mark.parametrize("nb,Ks", [(2, (5, 5)), (3, (9, 2)), (5, (2, 8)), (7, (1, 6, 3))])
-def test_self_tagged_exchange_gives_every_block_the_sequential_values(nb, Ks, land):
+def test_self_tagged_exchange_gives_every_block_the_sequential_values(nb, Ks, land, early):
     for seed in range(30):
-        outs, wants = _run(nb, Ks, seed, land=land)
+        outs, wants = _run(nb, Ks, seed, land=land, early=early)
         assert outs is not None, f"no progress (seed {seed})"
         assert outs == wants, seed
 
@@ -149,7 +168,7 @@ def test_one_vector_buffer_is_caught():
     never comes back."""
     failures = 0
     for seed in range(30):
-        outs, wants = _run(4, (6, 6), seed, nbuf=1, max_steps=40000)
+        outs, wants = _run(4, (6, 6), seed, nbuf=1, max_steps=40000, early=seed % 2 == 1)
         if outs is None or outs != wants:
             failures += 1
     assert failures > 0
@@ -161,7 +180,7 @@ def test_uncleared_buffer_is_caught():
     launch's check at iteration 1."""
     failures = 0
     for seed in range(200):
-        outs, wants = _run(4, (2, 6), seed, clear=False, max_steps=40000, land=0.05)
+        outs, wants = _run(4, (2, 6), seed, clear=False, max_steps=40000, land=0.05, early=seed % 2 == 1)
         if outs is None or outs != wants:
             failures += 1
     assert failures > 0
@@ -172,7 +191,7 @@ def test_missing_barrier_after_the_clear_is_caught():
     buffer-1 word of the earlier launch before the neighbour cleared it."""
     failures = 0
     for seed in range(60):
-        outs, wants = _run(4, (2, 6), seed, barrier=False, max_steps=40000)
+        outs, wants = _run(4, (2, 6), seed, barrier=False, max_steps=40000, early=seed % 2 == 1)
         if outs is None or outs != wants:
             failures += 1
     assert failures > 0
