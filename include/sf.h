@@ -30,10 +30,12 @@
  *   ownership   the context owns all of its device memory, allocated in
  *               sf_create; sf_solve allocates nothing. Caller buffers stay
  *               the caller's.
- *   errors      every call returns an sf_status. Errors raised inside
- *               kernels (a PCG barrier that gave up waiting, a non-finite
- *               energy) are latched in a device status word and reported by
- *               sf_get_stats and by the next sf_solve.
+ *   errors      every call returns an sf_status: SF_ERR_ARG for a null or
+ *               invalid argument (nothing is enqueued then), SF_ERR_CUDA for
+ *               a failed runtime call. Errors raised inside kernels (a PCG
+ *               barrier that gave up waiting, a non-finite energy) are
+ *               latched in a device status word, reported by sf_get_stats
+ *               (which waits for the work) and cleared by sf_reset.
  *   threads     one context per host thread at a time.
  */
 #ifndef SF_H
@@ -213,16 +215,18 @@ SF_API int sf_params_preset(sf_params* p, int preset);
  * error; sf_last_error() then tells why. */
 SF_API sf_ctx* sf_create(int width, int height, int grid_stride, int levels, const sf_params* p);
 
-/* Enqueues one frame on `stream`: pyramid, coarse-to-fine Gauss-Newton/PCG
- * solve from the previous frame's state (zero for the first frame after
- * create/reset), and writes the finest total fields to out_fields
- * (device, float32 [6][ny][nx]). The four inputs are device pointers. */
+/* Enqueues one frame of Algorithm 1 on `stream`: pyramid, coarse-to-fine
+ * Gauss-Newton/PCG solve (Sections 4-5) from the previous frame's state
+ * (temporal transfer, Section 5.3; zero for the first frame after
+ * create/reset), and writes the finest total fields to out_fields (device,
+ * float32 [6][ny][nx]). The four inputs are device pointers. SF_ERR_ARG for
+ * a null pointer; returns before the work ends. */
 SF_API int sf_solve(sf_ctx* ctx, const float* L_t, const float* R_t, const float* L_t1, const float* R_t1,
              float* out_fields, void* stream);
 
-/* The same from host memory: copies the four images in (host to device),
- * solves, copies the fields out (device to host) and waits for the stream.
- * Host buffers should be pinned for full copy speed. */
+/* The same (Algorithm 1) from host memory: copies the four images in (host
+ * to device), solves, copies the fields out (device to host) and waits for
+ * the stream. Host buffers should be pinned for full copy speed. */
 SF_API int sf_solve_host(sf_ctx* ctx, const float* L_t, const float* R_t, const float* L_t1, const float* R_t1,
                   float* out_fields, void* stream);
 
@@ -237,29 +241,42 @@ SF_API int sf_solve_host(sf_ctx* ctx, const float* L_t, const float* R_t, const 
  * otherwise). Enqueued on `stream` (the call returns before the work ends). */
 SF_API int sf_solve_video(sf_ctx* ctx, const float* frames, int n, float* outs, void* stream);
 
-/* The same from host memory (pinned for full copy speed): frames are copied
- * in and fields out through a ring of device slots, overlapped with the
- * solve; waits for the stream before returning. */
+/* The same (Algorithm 1, pipelined as above) from host memory (pinned for
+ * full copy speed): frames are copied in and fields out through a ring of
+ * device slots, overlapped with the solve; waits for the stream before
+ * returning. frames: host float32 [n][4][h][w]; outs: host float32
+ * [n][6][ny][nx]. SF_ERR_STATE without params.video. */
 SF_API int sf_solve_video_host(sf_ctx* ctx, const float* frames, int n, float* outs, void* stream);
 
-/* Level geometry: image size and grid size of `level` (0 = finest). */
+/* Level geometry: image size and warp-grid size of `level` (0 = finest;
+ * Section 3.3, Eq. 7: node (i, j) at level pixel (i s, j s)). SF_ERR_ARG for
+ * a level outside [0, levels); any output pointer may be NULL. */
 SF_API int sf_grid_dims(const sf_ctx* ctx, int level, int* w, int* h, int* nx, int* ny);
 
 /* Sets the coarsest level's initial delta for the next sf_solve (6 x G device
- * floats, the fields layout), replacing the temporal rule there once. */
+ * floats, the fields layout), replacing the temporal rule there once: the
+ * place where Section 5.3 transfers the previous frame's flows, used by a
+ * warm start of the first frame (smarter initialisation is future work in
+ * Section 7). The copy is enqueued on `stream`. */
 SF_API int sf_set_init(sf_ctx* ctx, const float* coarsest_delta, void* stream);
 
-/* Forgets the temporal state: the next frame starts from zero. */
+/* Forgets the temporal state (Section 5.3): the next frame starts from zero
+ * flows, as the first frame does. Waits for the device and clears the
+ * latched device status. */
 SF_API int sf_reset(sf_ctx* ctx);
 
-/* Waits for the context's work and copies its statistics. */
+/* Waits for the context's work and copies its statistics: the energy of
+ * Eq. 8 and its terms, per-step energies, step lengths and outlier counts;
+ * out->status carries the latched device status (SF_ERR_TIMEOUT,
+ * SF_ERR_NUMERIC), which is also returned. */
 SF_API int sf_get_stats(sf_ctx* ctx, sf_stats* out);
 
-/* Copies the final delta and total fields of `level` of the last frame into
- * device buffers (6 x G floats each; either may be NULL). */
+/* Copies the final delta and total fields of `level` of the last frame (the
+ * deltas and totals the hierarchy stores, Section 5.3) into device buffers
+ * (6 x G floats each; either may be NULL). */
 SF_API int sf_get_state(sf_ctx* ctx, int level, float* delta, float* total, void* stream);
 
-/* PCG schedule autotuner: solves one frame of the given quadruple (device
+/* PCG schedule autotuner (the linear solver of Section 5.1): solves one frame of the given quadruple (device
  * pointers), then times every PCG schedule that can run each level (one
  * cluster or the whole GPU, one or two reductions per iteration, 1-4 nodes
  * per four-lane group, distributed shared memory) on that level's last
@@ -289,16 +306,22 @@ SF_API int sf_set_pcg_schedule(sf_ctx* ctx, int level, int kind, int blocks, int
  * the context's work. */
 SF_API int sf_kernel_times(sf_ctx* ctx, int klass, double* total_ms, int* launches);
 
+/* Waits for the device, then frees the context and all of its device
+ * memory. NULL is ignored. */
 SF_API void sf_destroy(sf_ctx* ctx);
+/* A static, human-readable name of a status code. */
 SF_API const char* sf_status_string(int status);
+/* The status of the calling thread's last failed call (sf_create returns
+ * NULL, so its reason is read here). */
 SF_API int sf_last_error(void);
 
 /* ---- step-level entry points (parity tests and profiling) --------------
  * Each runs one stage of the solve on the context's buffers for `level`,
  * with caller-given state, on `stream`. All pointers are device pointers. */
 
-/* Builds the pyramid from four device images and copies level `level`'s
- * planes out as float32 [4][3][h][w] (I, dI/dx, dI/dy per image). */
+/* Builds the pyramid (the mip-map of Section 5.3, with the image gradients
+ * that Eqs. 1-6 and 13 sample) from four device images and copies level
+ * `level`'s planes out as float32 [4][3][h][w] (I, dI/dx, dI/dy per image). */
 SF_API int sf_probe_pyramid(sf_ctx* ctx, const float* L_t, const float* R_t, const float* L_t1, const float* R_t1,
                      int level, float* planes, void* stream);
 
@@ -306,7 +329,7 @@ SF_API int sf_probe_pyramid(sf_ctx* ctx, const float* L_t, const float* R_t, con
  * pyramid: writes G floats. */
 SF_API int sf_probe_feature_weights(sf_ctx* ctx, int level, const float* T, float* wfeat, void* stream);
 
-/* Assembles the Gauss-Newton system at base + delta (6 x G each) with
+/* Assembles the Gauss-Newton system (Section 5.1, Eqs. 19-24) at base + delta (6 x G each) with
  * feature weights wfeat (G) on the current pyramid, W taken at that state.
  * Outputs: blocks (G x 5 x 36: the node's own 6x6 block and those coupling
  * it to its E, S, SE and SW neighbours, row-major), rhs (G x 6), energy
@@ -314,8 +337,9 @@ SF_API int sf_probe_feature_weights(sf_ctx* ctx, int level, const float* T, floa
 SF_API int sf_probe_assemble(sf_ctx* ctx, int level, const float* base, const float* delta, const float* wfeat,
                       float* blocks, float* rhs, double* energy, unsigned char* W, void* stream);
 
-/* Runs `iters` PCG iterations on the system last assembled for `level`
- * (by sf_probe_assemble) and writes the solution (G x 6). */
+/* Runs `iters` Jacobi-preconditioned CG iterations (Section 5.1) from zero on
+ * the system last assembled for `level` (by sf_probe_assemble) and writes
+ * the solution (G x 6), in the level's current PCG schedule. */
 SF_API int sf_probe_pcg(sf_ctx* ctx, int level, int iters, float* x, void* stream);
 
 /* Runs `sweeps` alternating Schwarz sweeps of `patch` local PCG iterations
