@@ -556,8 +556,8 @@ SF_API void sf_batch_destroy(sf_batch* b);
  * applications whose memory pool or fixed device budget forbids a library's
  * raw allocations after start-up.
  *
- * Runs `iters` Jacobi-preconditioned CG iterations from x = 0 on a block
- * system in the layout sf_probe_assemble writes: blocks [G][5][6][6] (each
+ * Runs `iters` Jacobi-preconditioned CG iterations (Section 5.1) from x = 0
+ * on a block system in the layout sf_probe_assemble writes: blocks [G][5][6][6] (each
  * node's own block and those coupling it to its E, S, SE and SW neighbours,
  * row-major), rhs [G][6]; writes x [G][6]; G = nx * ny, all device memory,
  * enqueued on `stream`. Allocates nothing: its scratch is one file-scope
