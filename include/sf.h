@@ -121,8 +121,8 @@ enum {
  * sweeps over square subdomains of schwarz_tile x schwarz_tile grid nodes
  * plus schwarz_overlap nodes of overlap on each side; every sweep solves each
  * subdomain's system by patch_iters Jacobi-PCG iterations in shared memory
- * (the paper's "PCG iterations with patch iterations each": pcg_iters is the
- * number of sweeps), and the subdomains exchange the iterate through global
+ * (the paper counts outer PCG iterations of several patch iterations each:
+ * pcg_iters is the number of sweeps), and the subdomains exchange the iterate through global
  * memory. Restricted additive Schwarz: each node takes the correction of the
  * subdomain whose tile holds it. */
 enum { SF_SOLVER_PCG = 0, SF_SOLVER_SCHWARZ = 1 };
